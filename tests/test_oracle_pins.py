@@ -1,0 +1,388 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix (CPU only).
+
+Each test checks the oracle against something other than itself: a closed form
+(layered stack, depolarization field of the Results section, Landau equilibrium,
+tanh domain wall, integrator amplification factors, Debye screening), a brute-force
+dense solve, or the convergence rates of Table 2.  Each is chosen so that a
+plausible slip in the oracle (a dropped term, a flipped sign, a wrong weight or
+index) fails at least one of them.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import poisson, tdgl, carriers, diagnostics
+from oracle.stack import EPS0, Q_E, K_B
+from paper_2210_15668_gb300 import inputs as I
+
+
+def layered(nx, ny, n_de, n_fe, eps_de=3.9, pbc=I.PBC_FREE, h=0.5e-9, **fe):
+    return I.make_geometry(nx, ny, [I.de_layer(n_de, eps_de), I.fe_layer(n_fe, **fe)], h=h, pbc=pbc)
+
+
+def uniform_P(geom, value, ncomp=1):
+    nz = I.nz_of(geom)
+    P = np.zeros((ncomp, nz, geom["ny"], geom["nx"]))
+    P[-1, I.fe_plane_mask(geom)] = value
+    return P
+
+
+# ---------------------------------------------------------------- Poisson operator ----
+
+@pytest.mark.parametrize("V,Pval", [(0.5, 0.2), (0.0, 0.2), (-1.3, -0.05), (2.0, 0.0)])
+def test_layered_stack_closed_form(V, Pval):
+    """Metal/DE/FE/metal with x-y uniform P: Phi is piecewise linear with
+    D = (-V + P t_fe/eps_fe)/(t_fe/eps_fe + t_de/eps_de); the scheme must hit it at
+    every cell centre, and dPhi/dz in the FE must equal -E_fe."""
+    h = 0.5e-9
+    n_de, n_fe = 6, 10
+    g = layered(4, 3, n_de, n_fe)
+    pl = oracle.planes(g)
+    P = uniform_P(g, Pval)
+    phi = poisson.solve_linear(P, pl, h, 0.0, V)
+    e_de, e_fe = EPS0 * 3.9, EPS0 * 24.0
+    t_de, t_fe = n_de * h, n_fe * h
+    D = (-V + Pval * t_fe / e_fe) / (t_fe / e_fe + t_de / e_de)
+    z = (np.arange(n_de + n_fe) + 0.5) * h
+    exact = np.where(z < t_de, -D / e_de * z,
+                     -D / e_de * t_de - (D - Pval) / e_fe * (z - t_de))
+    err = np.abs(phi - exact[:, None, None]).max()
+    assert err <= 1e-13 * max(1.0, np.abs(exact).max())
+    E_fe = (D - Pval) / e_fe
+    dz = tdgl.dphi_dz(phi, P, pl, h, 0.0, V)
+    fe = pl["fe"]
+    assert np.abs(dz[fe] + E_fe).max() <= 1e-12 * max(abs(E_fe), 1.0)
+    if V == 0.0:
+        # depolarization field of the FE/DE series stack at zero bias (Results, MFIM):
+        E_dep = -Pval / (EPS0 * (24.0 + 3.9 * t_fe / t_de))
+        assert abs(E_fe - E_dep) <= 1e-12 * abs(E_dep)
+    d = diagnostics.charges(phi, P, pl, g, 0.0, V)
+    assert abs(d["Q_int"] + D) <= 1e-12 * max(abs(D), 1e-3)
+    assert abs(d["sigma_top"] + D) <= 1e-12 * max(abs(D), 1e-3)
+    assert abs(d["sigma_bot"] - D) <= 1e-12 * max(abs(D), 1e-3)
+    phi_int = -D / e_de * t_de
+    assert abs(d["V_fe"] - (V - phi_int)) <= 1e-12 * max(1.0, abs(V))
+
+
+def test_linear_capacitor_charge():
+    """All-dielectric stack: sigma_top = eps V / L exactly, and Phi is linear."""
+    h = 0.5e-9
+    g = I.make_geometry(5, 4, [I.de_layer(12, 10.0)], h=h)
+    pl = oracle.planes(g)
+    P = np.zeros((1, 12, 4, 5))
+    V = 0.7
+    phi = poisson.solve_linear(P, pl, h, 0.0, V)
+    L = 12 * h
+    z = (np.arange(12) + 0.5) * h
+    assert np.abs(phi - (V * z / L)[:, None, None]).max() < 1e-14
+    d = diagnostics.charges(phi, P, pl, g, 0.0, V)
+    assert abs(d["sigma_top"] - EPS0 * 10.0 * V / L) <= 1e-12 * EPS0 * 10.0 * V / L
+
+
+def _dense_operator(pl, h, nx, ny, shift):
+    """Assemble A + diag(shift) cell by cell from the face conductances (brute force)."""
+    eps = pl["eps"]
+    nz = eps.size
+    n = nx * ny * nz
+    M = np.zeros((n, n))
+    idx = lambda i, j, k: (k * ny + j) * nx + i  # noqa: E731
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                c = idx(i, j, k)
+                M[c, c] += shift[k]
+                for di, dj in ((1, 0), (-1, 0), (0, 1), (0, -1)):
+                    nb = idx((i + di) % nx, (j + dj) % ny, k)
+                    M[c, c] += eps[k] / h ** 2
+                    M[c, nb] -= eps[k] / h ** 2
+                for dk in (1, -1):
+                    kk = k + dk
+                    if 0 <= kk < nz:
+                        cond = 2 * eps[k] * eps[kk] / (eps[k] + eps[kk]) / h ** 2
+                        M[c, c] += cond
+                        M[c, idx(i, j, kk)] -= cond
+                    else:
+                        M[c, c] += 2 * eps[k] / h ** 2      # electrode at half a cell
+    return M
+
+
+@pytest.mark.parametrize("nx,ny,nz", [(4, 3, 6), (3, 5, 4), (1, 1, 7)])
+def test_separable_solver_vs_dense(nx, ny, nz):
+    rng = np.random.default_rng(7)
+    g = I.make_geometry(nx, ny, [I.de_layer(1, float(e)) for e in rng.uniform(2, 30, nz)])
+    pl = oracle.planes(g)
+    h = 0.5e-9
+    shift = rng.uniform(0, 1e9, nz) * EPS0
+    b = rng.standard_normal((nz, ny, nx)) * 1e8
+    M = _dense_operator(pl, h, nx, ny, shift)
+    x_dense = np.linalg.solve(M, b.ravel()).reshape(b.shape)
+    x = poisson.solve_separable(b, pl, h, shift)
+    assert np.abs(x - x_dense).max() <= 1e-12 * np.abs(x_dense).max()
+    # apply_A agrees with the dense matrix
+    y = rng.standard_normal(b.shape)
+    assert np.allclose(poisson.apply_A(y, pl, h) + shift[:, None, None] * y,
+                       (M @ y.ravel()).reshape(b.shape), rtol=1e-13, atol=1e-13 * np.abs(M).max())
+
+
+def test_manufactured_solution_second_order():
+    """Smooth eps(z) and Phi = sin(2 pi x/L) sin(2 pi y/L) sin(pi z/Lz) + V z/Lz:
+    the discrete error falls 4x per halving of h."""
+    L, Lz, V = 8e-9, 8e-9, 0.3
+    errs = []
+    for n in (8, 16, 32):
+        h = L / n
+        z = (np.arange(n) + 0.5) * h
+        x = (np.arange(n) + 0.5) * h
+        er = 10.0 + 5.0 * np.sin(np.pi * z / Lz)
+        g = I.make_geometry(n, n, [I.de_layer(1, float(e)) for e in er], h=h)
+        pl = oracle.planes(g)
+        X, Y, Z = np.meshgrid(x, x, z, indexing="ij")
+        X, Y, Z = (np.transpose(a, (2, 1, 0)) for a in (X, Y, Z))
+        kx, kz = 2 * np.pi / L, np.pi / Lz
+        S = np.sin(kx * X) * np.sin(kx * Y)
+        phi_ex = S * np.sin(kz * Z) + V * Z / Lz
+        eps = EPS0 * (10.0 + 5.0 * np.sin(kz * Z))
+        deps = EPS0 * 5.0 * kz * np.cos(kz * Z)
+        dphidz = S * kz * np.cos(kz * Z) + V / Lz
+        lap = -(2 * kx ** 2 + kz ** 2) * S * np.sin(kz * Z)
+        f = -(eps * lap + deps * dphidz)          # f = -div(eps grad phi)
+        b = f.copy()
+        b[-1] += 2 * pl["eps"][-1] * V / h ** 2
+        phi = poisson.solve_separable(b, pl, h)
+        errs.append(np.sqrt(np.mean((phi - phi_ex) ** 2)))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(1.85 < r < 2.2 for r in rates), (errs, rates)
+
+
+# ---------------------------------------------------------------- TDGL ----------------
+
+def landau_root(alpha, beta, gamma, E, lo, hi):
+    """Root of alpha P + beta P^3 + gamma P^5 = E on [lo, hi] by bisection."""
+    g = lambda P: alpha * P + beta * P ** 3 + gamma * P ** 5 - E  # noqa: E731
+    glo = g(lo)
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if (g(mid) > 0) == (glo > 0):
+            lo, glo = mid, g(mid)
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+def test_homogeneous_landau_equilibrium():
+    """Shorted metal/FE/metal, free P BC, uniform P: Phi stays 0 and P relaxes to
+    P0^2 = (-beta + sqrt(beta^2 - 4 alpha gamma)) / (2 gamma)."""
+    g = I.make_geometry(4, 4, [I.fe_layer(6)], pbc=I.PBC_FREE)
+    pl = oracle.planes(g)
+    P = uniform_P(g, 0.1)
+    phi = np.zeros(P.shape[1:])
+    for _ in range(400):
+        P, phi = tdgl.step(P, phi, pl, g, 4e-13, 0.0, 0.0)
+    a, b, c = I.HZO["alpha"], I.HZO["beta"], I.HZO["gamma"]
+    P0 = math.sqrt((-b + math.sqrt(b * b - 4 * a * c)) / (2 * c))
+    assert abs(P0 - 0.1950580) < 1e-6
+    assert np.abs(phi).max() < 1e-15
+    assert np.abs(P - P0).max() < 1e-12
+
+
+def test_landau_in_uniform_field():
+    """Metal/FE/metal at bias V, uniform P: E = -V/L inside and the steady state
+    solves alpha P + beta P^3 + gamma P^5 = E (the sign of the coupling, Eq. TDGL2)."""
+    V, n = 0.5, 10
+    g = I.make_geometry(3, 3, [I.fe_layer(n)], pbc=I.PBC_FREE)
+    pl = oracle.planes(g)
+    P = uniform_P(g, 0.19)
+    phi = tdgl.solve_poisson(P, np.zeros(P.shape[1:]), pl, g, 0.0, V)
+    for _ in range(600):
+        P, phi = tdgl.step(P, phi, pl, g, 4e-13, 0.0, V)
+    E = -V / (n * g["h"])
+    root = landau_root(I.HZO["alpha"], I.HZO["beta"], I.HZO["gamma"], E, 0.13, 0.3)
+    assert np.abs(P[0][pl["fe"]] - root).max() < 1e-12
+    # the wrong sign of the coupling would give the root for +|E|
+    wrong = landau_root(I.HZO["alpha"], I.HZO["beta"], I.HZO["gamma"], -E, 0.13, 0.3)
+    assert abs(root - wrong) > 1e-2
+
+
+def _wall_profile(n, L, P0, w):
+    h = L / n
+    x = (np.arange(n) + 0.5) * h
+    return np.tanh((x - L / 4) / w) * np.tanh((3 * L / 4 - x) / w) * P0, x, h
+
+
+def test_tanh_domain_wall_truncation_second_order():
+    """gamma = 0: P = P0 tanh(x/w), P0 = sqrt(-alpha/beta), w = sqrt(-2 g/alpha) solves
+    alpha P + beta P^3 - g P'' = 0; the discrete force on it is O(h^2)."""
+    a, b, gg = -2.5e9, 6.0e10, 1e-9
+    P0 = math.sqrt(-a / b)
+    w = math.sqrt(-2 * gg / a)
+    L = 48 * w
+    errs = []
+    for n in (192, 384, 768):
+        h = L / n
+        g = I.make_geometry(n, 1, [I.fe_layer(2, g=gg, gamma=0.0)], h=h, pbc=I.PBC_FREE)
+        pl = oracle.planes(g)
+        prof, x, _ = _wall_profile(n, L, P0, w)
+        P = np.zeros((1, 2, 1, n))
+        P[0, :, 0, :] = prof
+        f = tdgl.force(P, np.zeros(P.shape[1:]), pl, g, 0.0, 0.0)
+        # the two-wall product differs from a solution by ~e^-24; measure near walls
+        errs.append(np.abs(f).max() / (I.HZO["Gamma"] * abs(a) * P0))
+    r1, r2 = math.log2(errs[0] / errs[1]), math.log2(errs[1] / errs[2])
+    assert 1.9 < r1 < 2.1 and 1.9 < r2 < 2.1, errs
+    # a flipped gradient sign would leave an O(1) force
+    assert errs[-1] < 1e-3
+
+
+def test_tanh_domain_wall_relaxed_equilibrium():
+    """Relax the two-wall profile: it stays within O(h^2) of the tanh solution."""
+    a, b, gg = -2.5e9, 6.0e10, 1e-9
+    P0 = math.sqrt(-a / b)
+    w = math.sqrt(-2 * gg / a)
+    L, n = 48 * w, 192
+    g = I.make_geometry(n, 1, [I.fe_layer(2, g=gg, gamma=0.0)], h=L / n, pbc=I.PBC_FREE)
+    pl = oracle.planes(g)
+    prof, x, h = _wall_profile(n, L, P0, w)
+    P = np.zeros((1, 2, 1, n))
+    P[0, :, 0, :] = prof
+    phi = np.zeros(P.shape[1:])
+    dt = 0.2 * h ** 2 / (I.HZO["Gamma"] * gg)
+    for _ in range(3000):
+        P, phi = tdgl.step(P, phi, pl, g, dt, 0.0, 0.0)
+    err = np.abs(P[0, 0, 0] - prof).max() / P0
+    assert err < 5e-3 * (48 / n * 4) ** 2
+    assert np.abs(phi).max() < 1e-14
+
+
+def test_polarization_bc_limits_and_quadratic_exactness():
+    h, lam = 0.5e-9, 3e-9
+    rng = np.random.default_rng(3)
+    P0, P1 = rng.standard_normal(5), rng.standard_normal(5)
+    free = tdgl.boundary_face_value(P0, P1, tdgl.PBC_FREE, lam, h)
+    assert np.allclose(tdgl.boundary_face_value(P0, P1, tdgl.PBC_LAMBDA, 1e30, h), free, rtol=1e-12)
+    assert np.all(tdgl.boundary_face_value(P0, P1, tdgl.PBC_LAMBDA, 0.0, h) == 0.0)
+    # quadratic profiles that satisfy each BC exactly: the one-sided stencil is exact
+    g = I.make_geometry(1, 1, [I.fe_layer(6)], h=h)
+    fe = np.ones(6, dtype=bool)
+    s = (np.arange(6) + 0.5) * h          # distance from the bottom face
+    c, aa = 0.07, 3e15
+    cases = {tdgl.PBC_FREE: c + aa * s ** 2,                      # P'(0) = 0
+             tdgl.PBC_ZERO: aa * s * (s - 1e-9),                  # P(0) = 0
+             tdgl.PBC_LAMBDA: c + (c / lam) * s + aa * s ** 2}     # lam P'(0) = P(0)
+    for pbc, prof in cases.items():
+        Pc = prof[:, None, None]
+        d2 = tdgl.d2z(Pc, fe, pbc, lam, h)
+        assert abs(d2[0, 0, 0] - 2 * aa) <= 1e-9 * 2 * aa, pbc
+        assert abs(d2[2, 0, 0] - 2 * aa) <= 1e-9 * 2 * aa
+    del g
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_integrator_amplification_factor(order):
+    """beta = gamma = 0 in a shorted uniform MFM: Phi = 0, dP/dt = -Gamma alpha P, so one
+    step multiplies P by 1 - z (order 1) or 1 - z + z^2/2 (Heun, order 2), z = Gamma alpha dt."""
+    g = I.make_geometry(2, 2, [I.fe_layer(4, beta=0.0, gamma=0.0)], pbc=I.PBC_FREE)
+    pl = oracle.planes(g)
+    P = uniform_P(g, 1e-3)
+    phi = np.zeros(P.shape[1:])
+    dt = 4e-13
+    z = I.HZO["Gamma"] * I.HZO["alpha"] * dt
+    amp = (1 - z) if order == 1 else (1 - z + 0.5 * z * z)
+    for _ in range(5):
+        P, phi = tdgl.step(P, phi, pl, g, dt, 0.0, 0.0, order=order)
+    assert np.abs(P[0][pl["fe"]] - 1e-3 * amp ** 5).max() <= 1e-14 * 1e-3 * amp ** 5
+
+
+def _bump_problem(n=16, h=2e-9):
+    """Convergence-study set-up of the Numerical Validation section: 32 nm cube,
+    bottom 25% undoped Si, 25% dielectric, top 50% FE, lambda = 3 nm, Phi = 0 on both
+    faces, Gaussian bump P = 0.002 exp(-(x^2+y^2)/(2 s1^2) - (z - z0)^2/(2 s2^2))."""
+    q = n // 4
+    layers = [I.sc_layer(q, N_A=0.0, n_i=1e16), I.de_layer(q, I.EPS_SIO2), I.fe_layer(2 * q, g=1e-9)]
+    g = I.make_geometry(n, n, layers, h=h, pbc=I.PBC_LAMBDA, lam=3e-9)
+    c = (np.arange(n) + 0.5) * h - n * h / 2
+    z = (np.arange(n) + 0.5) * h
+    Z, Y, X = np.meshgrid(z, c, c, indexing="ij")
+    P = 0.002 * np.exp(-(X ** 2 + Y ** 2) / (2 * (5e-9) ** 2) - (Z - 24e-9) ** 2 / (2 * (2e-9) ** 2))
+    P[~I.fe_plane_mask(g)] = 0.0
+    return g, P[None]
+
+
+@pytest.mark.parametrize("order,target", [(1, 1.0), (2, 2.0)])
+def test_temporal_convergence_rates(order, target):
+    """Table 2, Tests 1 and 2: temporal self-convergence rates 1 and 2 (t = 400 fs,
+    dt = 50 / 25 / 12.5 fs)."""
+    g, P0 = _bump_problem()
+    pl = oracle.planes(g)
+    sols = []
+    for dt in (50e-15, 25e-15, 12.5e-15):
+        steps = int(round(400e-15 / dt))
+        sols.append(tdgl.run(P0, pl, g, dt, 0.0, 0.0, steps, order=order))
+    for which in (0, 1):
+        e1 = np.sqrt(np.mean((sols[1][which] - sols[0][which]) ** 2))
+        e2 = np.sqrt(np.mean((sols[2][which] - sols[1][which]) ** 2))
+        rate = math.log2(e1 / e2)
+        assert abs(rate - target) < 0.12, (which, rate)
+
+
+# ---------------------------------------------------------------- carriers -----------
+
+def test_neutral_bulk_at_zero_potential():
+    g = I.make_geometry(2, 2, I.mfism_stack(16))
+    pl = oracle.planes(g)
+    rho, s = carriers.charge(np.zeros((16, 2, 2)), pl)
+    assert np.abs(rho).max() <= 1e-15 * Q_E * 1e24
+    vt = K_B * 300.0 / Q_E
+    assert abs(vt - 0.025852) < 1e-6
+    sc = pl["sc"]
+    assert np.allclose(s[sc], Q_E * (1e24 + 1e8) / vt, rtol=1e-12)
+
+
+def test_debye_screening_small_signal():
+    """1-D MIS under a tiny bias: in the Si bulk the potential decays by the discrete
+    screening factor exp(kappa h), 2 cosh(kappa h) - 2 = h^2 q p0 / (eps V_T), and
+    kappa ~ 1/L_D with L_D = sqrt(eps V_T / (q N_A)) = 4.09 nm."""
+    h = 0.5e-9
+    g = I.make_geometry(1, 1, [I.sc_layer(120), I.de_layer(2, I.EPS_SIO2)], h=h)
+    pl = oracle.planes(g)
+    P = np.zeros((1, 122, 1, 1))
+    b = poisson.rhs(P, pl, h, 0.0, 1e-5)
+    phi, _ = carriers.newton_solve(b, np.zeros((122, 1, 1)), pl, h, tol=1e-10)
+    col = phi[:, 0, 0]
+    vt = K_B * 300.0 / Q_E
+    eps = EPS0 * I.EPS_SI
+    kappa = math.acosh(1 + h * h * Q_E * 1e24 / (eps * vt) / 2) / h
+    ratios = col[100:110] / col[99:109]
+    assert np.allclose(ratios, math.exp(kappa * h), rtol=1e-4)
+    L_D = math.sqrt(eps * vt / (Q_E * 1e24))
+    assert abs(L_D - 4.09e-9) < 0.01e-9
+    assert abs(kappa * L_D - 1) < 2e-3
+
+
+def test_newton_matches_lagged_fixed_point_undoped():
+    """Undoped Si (the paper's MFISM): the lagged fixed point of the paper and the
+    damped Newton reach the same potential (the nonlinear problem has one solution)."""
+    g = I.make_geometry(8, 8, [I.sc_layer(12, N_A=0.0, n_i=1e16), I.de_layer(2), I.fe_layer(8)])
+    pl = oracle.planes(g)
+    P = I.random_polarization(g, seed=11, amp=0.05)
+    b = poisson.rhs(P, pl, g["h"], 0.0, 0.4)
+    phi_n, it_n = carriers.newton_solve(b, np.zeros((22, 8, 8)), pl, g["h"])
+    phi_f, it_f = carriers.fixed_point_solve(b, np.zeros((22, 8, 8)), pl, g["h"])
+    assert np.abs(phi_n - phi_f).max() <= 1e-11 * np.abs(phi_n).max()
+    # and Newton from a different start lands on the same point
+    phi_n2, _ = carriers.newton_solve(b, np.full((22, 8, 8), 0.3), pl, g["h"])
+    assert np.abs(phi_n - phi_n2).max() <= 1e-11 * np.abs(phi_n).max()
+
+
+def test_newton_doped_residual_and_uniqueness():
+    g = I.make_geometry(8, 8, I.mfism_stack(24, n_fe=6, n_ox=2))
+    pl = oracle.planes(g)
+    P = I.random_polarization(g, seed=12, amp=0.1)
+    b = poisson.rhs(P, pl, g["h"], 0.0, 0.8)
+    phi_a, _ = carriers.newton_solve(b, np.zeros((24, 8, 8)), pl, g["h"])
+    phi_b, _ = carriers.newton_solve(b, np.full((24, 8, 8), -0.2), pl, g["h"])
+    assert np.abs(phi_a - phi_b).max() <= 1e-10 * np.abs(phi_a).max()
+    rho, _ = carriers.charge(phi_a, pl)
+    r = poisson.residual(phi_a, b, pl, g["h"], rho)
+    assert np.linalg.norm(r) <= 1e-12 * max(np.linalg.norm(b), np.linalg.norm(rho))
