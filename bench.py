@@ -1,0 +1,387 @@
+#!/usr/bin/env python
+"""Throughput of the FerroX time step (TDGL update + Poisson solve to a 1e-10
+relative residual) on the 256x256x32 MFIM Q-V sweep workload, one JSON line.
+
+A step is one time step of the whole hot path: the fused TDGL update (Eq. TDGL2)
+and the variable-permittivity Poisson solve it is coupled to, converged on the
+device.  The timed steps are the first steps of the Q-V sweep (-2 V first),
+after Step 0 and W warm-up steps.  Inputs are resident in HBM; L2 (129 MB) is
+flushed between timed steps by writing a 256 MB buffer, because the working set
+of this workload (~100 MB) would otherwise stay in L2 from one step to the next.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--precision fp64|mixed]
+
+Multi-GPU: the workload is one device stack whose domain is not split, so
+N > 1 runs N independent replicas (one per rank, seed + rank); value is the
+cells x steps of all ranks over the max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mcell-steps/s incl. Poisson to 1e-10 residual; HBM % of peak; vs plain FP64"
+UNIT = "Mcell-steps/s"
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x DFMA/clk/SM x flop/FMA x max clock
+HBM_FALLBACK_GBS = 6800.0
+
+
+# ---------------------------------------------------------------------- helpers -------
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def reduce_max(x: float, ws: int) -> float:
+    """Max over ranks (identity for one rank)."""
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": HBM_FALLBACK_GBS}, "fallback"
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2210_15668_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, fn), "rb") as f:
+            h.update(fn.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.2)
+        self.proc.terminate()
+        self.proc.wait()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[q] for r in rows for q in range(4) if r[5 + q].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------- algorithmic work -------
+
+def kernel_work(kind, cells, fe_cells, dyn_cells, tsz):
+    """Algorithmic (bytes, flops) of ONE launch of a kernel class on the fine level.
+
+    Minimum traffic the method needs per launch (each array element read or
+    written once), and arithmetic with an FMA counted as two flops."""
+    if kind == "smooth_fine":      # one colour: read the other colour's e, own r; write own e
+        return 0.5 * cells * 3 * tsz, 0.5 * cells * 11
+    if kind == "resid":            # read phi, b (dynamic planes), write r (T)
+        return cells * (8 + tsz) + dyn_cells * 8, cells * 19
+    if kind == "tdgl":             # read P, phi; write new P; write b on dynamic planes
+        return fe_cells * 24 + dyn_cells * 8, fe_cells * 45
+    if kind == "restrict":         # read e, r of the fine level, write r of the coarse level
+        return cells * 2 * tsz + cells / 8 * tsz, cells * 15
+    if kind == "prolong":          # read coarse e, read+write fine e
+        return cells * 2 * tsz + cells / 8 * tsz, cells * 16
+    if kind == "update":           # read e, read+write phi
+        return cells * (tsz + 16), cells * 1
+    if kind == "copy":
+        return fe_cells * 16, 0.0
+    return None, None
+
+
+# ------------------------------------------------------------------------ ours -------
+
+def run_ours(args, ws, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_2210_15668_gb300 import ferrox, inputs as I
+
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    cfg = I.mfim_sweep()
+    geom = cfg["geom"]
+    nz = I.nz_of(geom)
+    cells = geom["nx"] * geom["ny"] * nz
+    fe_mask = I.fe_plane_mask(geom)
+    fe_cells = int(fe_mask.sum()) * geom["nx"] * geom["ny"]
+    dyn = fe_mask | np.roll(fe_mask, 1) | np.roll(fe_mask, -1)
+    dyn_cells = int(dyn.sum()) * geom["nx"] * geom["ny"]
+    P0 = I.random_polarization(geom, cfg["seed"] + rank)
+    sweep, per_point = cfg["sweep"], cfg["steps_per_point"]
+
+    def make(precision):
+        num = ferrox.make_numerics(cfg["dt"], order=1, tol=1e-10, precision=precision, max_cycles=200)
+        d = ferrox.Device(geom, P0, numerics=num)
+        d.set_bias(0.0, sweep[0])
+        d.solve_poisson()                                  # Step 0 (untimed)
+        return d
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def timed_run(d, K, W, clocks=None):
+        stream = d.stream
+        point = 0
+        for s in range(W):
+            flush.zero_()
+            d.step(1)
+        torch.cuda.synchronize()
+        st0 = d.stats()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        barrier(ws)
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+        for s in range(K):
+            p = (W + s) // per_point
+            if p != point and p < len(sweep):
+                point = p
+                d.set_bias(0.0, sweep[p])
+            flush.zero_()
+            ev[s][0].record(stream)
+            d.step(1)
+            ev[s][1].record(stream)
+        torch.cuda.synchronize()
+        barrier(ws)
+        ck = clocks.stop() if clocks else None
+        t_ms = sum(a.elapsed_time(b) for a, b in ev)
+        st1 = d.stats()
+        return t_ms, st0, st1, ck
+
+    prec_main = ferrox.MIXED if args.precision == "mixed" else ferrox.FP64
+    dev = make(prec_main)
+    clocks = ClockSampler(local) if rank == 0 else None
+    t_ms, st0, st1, ck = timed_run(dev, args.steps, args.warmup, clocks)
+    t_max = reduce_max(t_ms, ws)
+    K = args.steps
+    value = ws * cells * K / (t_max / 1e3) / 1e6
+    cycles_per_step = (st1["cycles"] - st0["cycles"]) / K
+    launches = st1["launches"] - st0["launches"]
+
+    # per-kernel breakdown of one step (eager, event-timed) -> roofline of the dominant kernel
+    prof = dev.profile_step()
+    tsz = 4 if prec_main == ferrox.MIXED else 8
+    dom = max(prof, key=lambda k: prof[k][0])
+    dom_ms, dom_n = prof[dom]
+    peaks, peak_src = measured_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
+    by, fl = kernel_work(dom, cells, fe_cells, dyn_cells, tsz)
+    avg_s = dom_ms / max(dom_n, 1) / 1e3
+    gbs = by / avg_s / 1e9 if by else None
+    tfl = fl / avg_s / 1e12 if fl else None
+    fp64_kernel = prec_main == ferrox.FP64 or dom in ("resid", "tdgl", "update")
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if os.path.exists(tpath):
+        tj = json.load(open(tpath))
+        if tj.get("source_hash") == source_hash():
+            traffic = tj.get("per_launch_bytes", {}).get(f"{args.precision}:{dom}")
+    if fp64_kernel:
+        roof = {"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": tfl / FP64_PEAK_TFLOPS if tfl else None, "traffic": traffic,
+                "kernel": dom, "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
+                "hbm_view": {"achieved_gbs": gbs, "peak_gbs": hbm_peak,
+                             "frac": gbs / hbm_peak if gbs else None, "peak_source": peak_src}}
+    else:
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                "frac": gbs / hbm_peak if gbs else None, "traffic": traffic, "kernel": dom,
+                "peak_source": peak_src}
+    breakdown = {k: {"ms": round(v[0], 4), "launches": v[1]} for k, v in prof.items() if v[1]}
+    dev.close()
+
+    # the other precision on the same workload ("vs plain FP64")
+    other = None
+    if not args.no_compare:
+        prec_o = ferrox.FP64 if prec_main == ferrox.MIXED else ferrox.MIXED
+        d2 = make(prec_o)
+        t2, s20, s21, _ = timed_run(d2, K, args.warmup)
+        t2 = reduce_max(t2, ws)
+        v2 = ws * cells * K / (t2 / 1e3) / 1e6
+        other = {"precision": "fp64" if prec_o == ferrox.FP64 else "mixed", "value": v2,
+                 "ms_per_step": t2 / K, "vcycles_per_step": (s21["cycles"] - s20["cycles"]) / K}
+        d2.close()
+    mixed_v = value if prec_main == ferrox.MIXED else (other or {}).get("value")
+    fp64_v = value if prec_main == ferrox.FP64 else (other or {}).get("value")
+
+    # end to end through the public API with host buffers (pinned), copies inside the region
+    e2e = None
+    if not args.no_e2e:
+        d3 = make(prec_main)
+        Ph = torch.empty((1,) + (nz, geom["ny"], geom["nx"]), dtype=torch.float64).pin_memory().numpy()
+        fh = torch.empty((nz, geom["ny"], geom["nx"]), dtype=torch.float64).pin_memory().numpy()
+        d3.get_state(Ph, fh)
+        Ke = max(1, min(K, args.e2e_steps))
+        torch.cuda.synchronize()
+        barrier(ws)
+        t0 = time.perf_counter()
+        for s in range(Ke):
+            d3.set_state(Ph, fh)
+            d3.step(1)
+            d3.get_state(Ph, fh)
+        te = reduce_max(time.perf_counter() - t0, ws)
+        e2e = {"value": ws * cells * Ke / te / 1e6, "unit": UNIT, "steps": Ke,
+               "h2d_bytes_per_step": int(Ph.nbytes + fh.nbytes),
+               "d2h_bytes_per_step": int(Ph.nbytes + fh.nbytes)}
+        d3.close()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.cpu_seconds)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K,
+            "warmup": args.warmup, "ms_per_step": t_max / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec_main == ferrox.FP64 else "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": "mfim_256x256x32 Q-V sweep (first steps at -2 V), seed 1",
+                       "cells": cells, "tol": 1e-10, "order": 1,
+                       "precision": args.precision, "l2": "flushed between timed steps (256 MB write)",
+                       "parallelism": f"replicas x{ws}"},
+            "vcycles_per_step": cycles_per_step, "gpu_launches": launches,
+            "roofline": roof, "kernel_breakdown_ms_one_step": breakdown,
+            "vs_plain_fp64": (mixed_v / fp64_v) if (mixed_v and fp64_v) else None,
+            "other_precision": other, "e2e": e2e, "cpu_baseline": cpu, "clocks": ck}
+    if rank == 0:
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# --------------------------------------------------------------- oracle on CPU -------
+
+def _oracle_steps(budget_s, max_steps=None):
+    import numpy as np
+
+    import oracle
+    from oracle import tdgl
+    from paper_2210_15668_gb300 import inputs as I
+    cfg = I.mfim_sweep()
+    geom = cfg["geom"]
+    pl = oracle.planes(geom)
+    P = I.random_polarization(geom, cfg["seed"])
+    v = cfg["sweep"][0]
+    phi = tdgl.solve_poisson(P, np.zeros(P.shape[1:]), pl, geom, 0.0, v)   # Step 0
+    cells = P[0].size
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        P, phi = tdgl.step(P, phi, pl, geom, cfg["dt"], 0.0, v)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or (max_steps and n >= max_steps):
+            break
+    return cells, n, el
+
+
+def cpu_baseline(budget_s):
+    cells, n, el = _oracle_steps(budget_s)
+    return {"value": cells * n / el / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} oracle steps of mfim_256x256x32 at -2 V from Step 0 ({el:.1f} s; "
+                      "numpy FP64, exact FFT/tridiagonal Poisson solve, single thread)"}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    # warm-up steps, then the timed sample (bounded to keep the run within minutes)
+    _oracle_steps(1e9, max_steps=max(1, min(args.warmup, 3)))
+    budget = args.cpu_seconds
+    cells, n, el = _oracle_steps(budget, max_steps=args.steps)
+    value = cells * n / el / 1e6
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": n,
+            "warmup": args.warmup, "ms_per_step": el / n * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": "mfim_256x256x32 Q-V sweep (first steps at -2 V), seed 1",
+                       "cells": cells, "tol": "exact solve", "order": 1, "precision": "fp64"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{n} oracle steps in {el:.1f} s (bounded sample of the workload)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

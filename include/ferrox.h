@@ -1,0 +1,203 @@
+/*
+ * ferrox.h -- C ABI of the GB300 (sm_103a) TDGL + Poisson time-step library.
+ *
+ * The library advances the self-consistent ferroelectric device model of
+ * FerroX (arXiv 2210.15668): the time-dependent Ginzburg-Landau equation for
+ * the polarization (Eq. TDGL2) coupled to the variable-permittivity Poisson
+ * equation div(eps grad Phi) = div P - rho (Eq. Poisson), with Boltzmann carrier
+ * charge in semiconductor layers (Eq. rho, Eq. MaxBolt_ne_np), periodic x/y
+ * boundaries and Dirichlet electrodes (Methods, "Electrical boundary
+ * conditions").  One context holds one device stack on one GPU.
+ *
+ * Conventions for every entry point:
+ *   - Units are SI: metres, volts, C/m^2, F/m (eps = eps_r * eps0), seconds.
+ *   - Arrays are C-contiguous float64 with x fastest:
+ *       P   : [ncomp][Nz][Ny][Nx]  (ncomp = 1: P_z only; ncomp = 3: P_x, P_y, P_z)
+ *       phi : [Nz][Ny][Nx]
+ *     Nz is the sum of the layers' ncells; layers are listed bottom to top.
+ *   - Pointers named *_dev are device pointers owned by the caller; they are
+ *     registered at init and must stay valid until ferrox_destroy.  Pointers
+ *     named *_host are host pointers (pinned memory gives asynchronous copies).
+ *   - All work is enqueued on the CUDA stream given at init (NULL = legacy
+ *     default stream) and returns without waiting, unless stated otherwise.
+ *   - Every call returns a ferrox_status and never aborts.  Argument errors
+ *     are reported at once.  Device-side conditions (multigrid or Newton not
+ *     converged, a non-finite residual, a device wait that ran out of time)
+ *     are recorded in a sticky device status word and reported by the next
+ *     synchronising call (ferrox_sync_stats, ferrox_charge, ferrox_get_state).
+ *     ferrox_last_error() describes the last failure in words.
+ *   - Scratch memory (the multigrid hierarchy, right-hand side, CUDA graphs) is
+ *     allocated by the library at init and freed by ferrox_destroy.
+ *   - A context is not thread-safe: one host thread at a time per context.
+ */
+#ifndef FERROX_H
+#define FERROX_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ferrox_ctx ferrox_ctx; /* opaque */
+
+typedef enum {
+  FERROX_OK = 0,
+  FERROX_EINVAL = 1,     /* invalid argument (reported synchronously) */
+  FERROX_ENOMEM = 2,     /* device or host allocation failed */
+  FERROX_ECUDA = 3,      /* a CUDA runtime call failed */
+  FERROX_ENOCONV = 4,    /* multigrid / Newton reached max_cycles above tolerance */
+  FERROX_ENONFINITE = 5, /* NaN or Inf in a residual norm */
+  FERROX_ETIMEOUT = 6,   /* a bounded device wait ran out (batched persistent kernel) */
+  FERROX_ESTATE = 7      /* call not valid in the context's current state */
+} ferrox_status;
+
+/* Material kinds of a layer (Fig. 1a: ferroelectric, dielectric, semiconductor). */
+enum { FERROX_FE = 0, FERROX_DE = 1, FERROX_SC = 2 };
+
+/* Polarization boundary condition at ferroelectric faces (Methods, Eqs. Pbc,
+ * PbcFree, PbcDir): lambda dP/dn_in = P, its lambda -> infinity limit dP/dn = 0,
+ * and its lambda = 0 limit P = 0.  Each is imposed through a second-order
+ * one-sided three-point stencil. */
+enum { FERROX_PBC_FREE = 0, FERROX_PBC_ZERO = 1, FERROX_PBC_LAMBDA = 2 };
+
+/* Arithmetic of the Poisson solve: FP64 multigrid, or FP32 multigrid cycles
+ * inside an FP64 defect-correction loop (FP64 residual, potential, norms and
+ * carrier exponentials).  Both stop on the same FP64 residual test. */
+enum { FERROX_FP64 = 0, FERROX_MIXED = 1 };
+
+/* One planar layer (Table 1 lists the parameters).  Only the fields of its
+ * kind are read: Landau/gradient/kinetic data for FE, carrier data for SC. */
+typedef struct {
+  int kind;                           /* FERROX_FE / _DE / _SC */
+  int ncells;                         /* thickness in cells (>= 1; FE >= 2) */
+  double eps_r;                       /* relative permittivity (> 0) */
+  double alpha, beta, gamma;          /* Landau coefficients of P_z (Eq. free), SI */
+  double alpha_xy, beta_xy, gamma_xy; /* Landau coefficients of P_x, P_y (ncomp = 3 only) */
+  double g11, g44;                    /* gradient coefficients (Eq. grad): z, and x/y */
+  double Gamma;                       /* kinetic coefficient (Eq. TDGL1) */
+  double N_A, N_D;                    /* acceptor / donor density, m^-3 (SC) */
+  double n_i;                         /* intrinsic carrier density, m^-3 (SC) */
+  double T;                           /* temperature, K (SC) */
+} ferrox_layer;
+
+typedef struct {
+  int nx, ny;                  /* lateral cells; each even or 1 (periodic) */
+  double h;                    /* cell size (uniform, m) */
+  int nlayers;
+  const ferrox_layer* layers;  /* bottom to top; copied at init */
+  int pbc;                     /* FERROX_PBC_* */
+  double lambda;               /* extrapolation length (m) for FERROX_PBC_LAMBDA */
+  int ncomp;                   /* 1 (uniaxial, the paper's model) or 3 */
+} ferrox_geometry;
+
+typedef struct {
+  double dt;        /* time step (s) */
+  int order;        /* 1: predictor only (Steps 1a/1b); 2: with corrector (Steps 2a/2b) */
+  double tol;       /* stop when ||r||_2 <= tol * max(||b||_2, ||rho||_2); e.g. 1e-10 */
+  int nu1, nu2;     /* pre/post red-black Gauss-Seidel sweeps per V-cycle level */
+  int max_cycles;   /* V-cycles (outer iterations) allowed per solve */
+  int precision;    /* FERROX_FP64 or FERROX_MIXED */
+  int bottom_sweeps;/* sweeps on the coarsest level (0: default) */
+} ferrox_numerics;
+
+typedef struct {
+  double Q_int;        /* -<D_z> on the bottom face of the lowest FE plane (C/m^2) */
+  double phi_int_avg;  /* mean potential on that face (V) */
+  double V_fe;         /* v_top - phi_int_avg (V) */
+  double sigma_top;    /* charge on the top electrode, -<D_z(top)> (C/m^2) */
+  double sigma_bot;    /* charge on the bottom electrode, +<D_z(bottom)> (C/m^2) */
+} ferrox_charge_t;
+
+typedef struct {
+  long long steps;         /* time steps taken */
+  long long launches;      /* library kernels launched by steps and solves (device count) */
+  long long solves;        /* Poisson solves run */
+  long long cycles;        /* V-cycles (outer iterations) run, all solves */
+  int last_cycles;         /* V-cycles of the most recent solve */
+  double last_rel_res;     /* ||r|| / max(||b||, ||rho||) at the end of that solve */
+  int status;              /* sticky device status (ferrox_status) */
+} ferrox_stats;
+
+/* Create a context (a1: per-plane material tables, multigrid hierarchy, CUDA
+ * graphs).  P_dev and phi_dev are the caller's state arrays (layout above);
+ * their contents are not read until the first call that needs them.
+ * Errors: EINVAL for a malformed geometry (Nz < 2, no FE layer, an FE layer
+ * thinner than 2 cells, odd lateral size other than 1, h <= 0, eps_r <= 0,
+ * ncomp not 1 or 3, misaligned pointers), ENOMEM, ECUDA. */
+ferrox_status ferrox_init_geometry(ferrox_ctx** out, const ferrox_geometry* geom,
+                                   const ferrox_numerics* num, double* P_dev,
+                                   double* phi_dev, void* cuda_stream);
+
+/* Electrode potentials Phi(z_min) = v_bottom, Phi(z_max) = v_top; V_app = v_top -
+ * v_bottom (Methods, "Electrical boundary conditions").  Asynchronous. */
+ferrox_status ferrox_set_bias(ferrox_ctx* ctx, double v_bottom, double v_top);
+
+/* Step 0 of the Methods: solve the Poisson problem for the current P, starting
+ * from the current phi (the paper starts from phi = 0), to the tolerance.
+ * With semiconductor layers the carrier charge makes the problem nonlinear; it
+ * is solved by damped Newton, each update from one multigrid cycle on the
+ * Jacobian (diagonal shift q^2 (n + p)/kT in semiconductor cells). */
+ferrox_status ferrox_solve_poisson(ferrox_ctx* ctx);
+
+/* Step 1a alone: P <- P + dt f(P, phi) (Eq. TDGL2) on ferroelectric cells, and
+ * the Poisson right-hand side for the new P.  No solve. */
+ferrox_status ferrox_tdgl_update(ferrox_ctx* ctx);
+
+/* Advance nsteps time steps: Steps 1a/1b (order 1) or 1a/1b/2a/2b (order 2),
+ * each solve converged on the device (no host synchronisation). */
+ferrox_status ferrox_step(ferrox_ctx* ctx, int nsteps);
+
+/* Interface and electrode charges of the current state (Results, MFIM: Q and
+ * V_fe).  Synchronises the stream; returns the sticky device status. */
+ferrox_status ferrox_charge(ferrox_ctx* ctx, ferrox_charge_t* out);
+
+/* Counters and the sticky status.  Synchronises the stream. */
+ferrox_status ferrox_sync_stats(ferrox_ctx* ctx, ferrox_stats* out);
+
+/* Clear the sticky device status (after the caller has handled it). */
+ferrox_status ferrox_clear_status(ferrox_ctx* ctx);
+
+/* Copy the state between the registered device arrays and host arrays of the
+ * same layout (checkpoint / restart, and the host-buffer path of the API).
+ * ferrox_get_state synchronises; ferrox_set_state is asynchronous, so the host
+ * arrays must stay unchanged until the stream reaches the copy. Either host
+ * pointer may be NULL to skip that array. */
+ferrox_status ferrox_get_state(ferrox_ctx* ctx, double* P_host, double* phi_host);
+ferrox_status ferrox_set_state(ferrox_ctx* ctx, const double* P_host, const double* phi_host);
+
+/* Kernel classes reported by ferrox_profile_step. */
+enum {
+  FERROX_K_TDGL = 0,      /* fused TDGL update + right-hand side */
+  FERROX_K_RESID = 1,     /* FP64 outer residual, carrier charge, norms, convergence test */
+  FERROX_K_SMOOTH0 = 2,   /* red-black Gauss-Seidel colour sweep on the fine level */
+  FERROX_K_SMOOTHC = 3,   /* colour sweeps on coarser multi-block levels */
+  FERROX_K_RESTRICT = 4,  /* residual + restriction */
+  FERROX_K_PROLONG = 5,   /* prolongation + correction */
+  FERROX_K_TAIL = 6,      /* single-CTA V-cycle over the smallest levels */
+  FERROX_K_UPDATE = 7,    /* phi += correction */
+  FERROX_K_COPY = 8,      /* copy of the new polarization into the caller's array */
+  FERROX_K_COUNT = 9
+};
+
+/* One time step run eagerly (no CUDA graph) with a CUDA event pair around every
+ * launch, for a per-kernel time breakdown: on return ms[k] is the summed device
+ * time and count[k] the number of launches of class k (arrays of FERROX_K_COUNT).
+ * The result of the step is the same as ferrox_step(ctx, 1).  Synchronises. */
+ferrox_status ferrox_profile_step(ferrox_ctx* ctx, double* ms, int* count);
+
+/* Release everything the context allocated (the caller's arrays are untouched).
+ * Synchronises the stream.  NULL is accepted. */
+ferrox_status ferrox_destroy(ferrox_ctx* ctx);
+
+/* Text of the last error of this context (or of the last failed init when ctx
+ * is NULL).  The pointer stays valid until the next call on the context. */
+const char* ferrox_last_error(const ferrox_ctx* ctx);
+
+/* Multigrid hierarchy actually built: number of levels and, for level l < n,
+ * its cell counts.  Returns EINVAL if l is out of range. */
+ferrox_status ferrox_level_shape(const ferrox_ctx* ctx, int l, int* nx, int* ny, int* nz,
+                                 int* nlevels);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FERROX_H */

@@ -57,12 +57,13 @@ def rhs(P, pl, h, v_bottom, v_top):
     components the in-plane faces carry the arithmetic mean of P_x (P_y).
     """
     eps = pl["eps"]
-    Pz = P[-1]
+    fe = pl["fe"][:, None, None]          # polarization exists in ferroelectric layers only
+    Pz = P[-1] * fe
     Pf = face_polarization(Pz, eps)
     b = -(Pf[1:] - Pf[:-1]) / h
     if P.shape[0] == 3:
         for comp, axis in ((0, 2), (1, 1)):
-            Pc = P[comp]
+            Pc = P[comp] * fe
             # face average on the +side face minus the -side face
             f_plus = 0.5 * (Pc + np.roll(Pc, -1, axis=axis))
             f_minus = 0.5 * (Pc + np.roll(Pc, 1, axis=axis))

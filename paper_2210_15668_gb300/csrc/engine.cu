@@ -1,0 +1,776 @@
+// Host engine and C ABI of libferrox (see include/ferrox.h).
+//
+// A context owns, for one device stack on one GPU:
+//   * the per-plane material table of the fine grid (Fig. 1a stack, Table 1),
+//     with the TDGL z-stencil weights that encode the P boundary conditions,
+//     the flux-continuous face weights, the Dirichlet lift and the carrier data;
+//   * the multigrid hierarchy: level shapes (full coarsening, or semi-coarsening
+//     once a direction can no longer halve to an even size), per-plane couplings
+//     of every level from the fine permittivity profile (series resistance
+//     through z, parallel average across x/y), and the level arenas;
+//   * CUDA graphs of the TDGL update, the Poisson solve and the whole time step.
+//     The solve is a graph WHILE node whose condition the FP64 residual kernel
+//     sets on the device, so a step runs to the tolerance with no host round trip.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstddef>
+#include <cstdio>
+#include <cstring>
+#include <functional>
+#include <string>
+#include <vector>
+
+#include "ferrox_internal.cuh"
+
+using namespace fx;
+
+namespace {
+
+constexpr double kEps0 = 8.8541878128e-12;
+constexpr double kQ = 1.602176634e-19;
+constexpr double kKB = 1.380649e-23;
+
+std::string g_init_error;
+
+}  // namespace
+
+struct ferrox_ctx {
+  // geometry and numerics
+  int nx = 0, ny = 0, nz = 0, ncomp = 1, pbc = 0;
+  double h = 0.0, lambda = 0.0;
+  std::vector<ferrox_layer> layers;
+  ferrox_numerics num{};
+  bool has_sc = false;
+  int kd_lo = 0, kd_hi = 0, fe_lo = 0, fe_hi = 0, k_int = 0;
+  std::vector<double> epsr;  // per fine plane
+  std::vector<PlaneTDGL> planes;
+  // multigrid
+  std::vector<LevelDesc> lv;
+  int tail_first = 0;
+  long long arena = 0;
+  // device memory
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap1 = nullptr, cap2 = nullptr;
+  double* P = nullptr;
+  double* phi = nullptr;
+  double* b = nullptr;
+  double* Pbuf = nullptr;
+  double* Fbuf = nullptr;
+  void* e_arena = nullptr;
+  void* r_arena = nullptr;
+  void* s_arena = nullptr;
+  void* coef = nullptr;               // PlaneCoef<T> of all levels
+  PlaneCoef<double>* coef0 = nullptr; // level 0 in FP64 (outer residual)
+  PlaneTDGL* planes_d = nullptr;
+  LevelDesc* lv_d = nullptr;
+  DevParams* params_d = nullptr;
+  DevStats* stats_d = nullptr;
+  double* partials_d = nullptr;
+  double* charge_d = nullptr;
+  double* charge_part_d = nullptr;
+  double* host_pinned = nullptr;      // small pinned staging for charge/stats reads
+  // graphs
+  cudaGraph_t gr_step = nullptr, gr_solve = nullptr, gr_tdgl = nullptr;
+  cudaGraphExec_t ge_step = nullptr, ge_solve = nullptr, ge_tdgl = nullptr;
+  double v_bot = 0.0, v_top = 0.0;
+  std::string err;
+};
+
+namespace {
+
+ferrox_status fail(ferrox_ctx* c, ferrox_status s, const std::string& msg) {
+  if (c) c->err = msg; else g_init_error = msg;
+  return s;
+}
+
+#define FX_CK(call)                                                                          \
+  do {                                                                                       \
+    cudaError_t _e = (call);                                                                 \
+    if (_e != cudaSuccess)                                                                   \
+      return fail(ctx, FERROX_ECUDA, std::string(#call) + ": " + cudaGetErrorString(_e));    \
+  } while (0)
+
+bool lateral_can_halve(int n) { return n % 2 == 0 && (n / 2 == 1 || (n / 2) % 2 == 0); }
+
+// series resistance  int dz / eps_r(z)  between fine-grid coordinates z1 < z2 (units of h0)
+double resistance(const std::vector<double>& epsr, double z1, double z2) {
+  double R = 0.0;
+  const int n = (int)epsr.size();
+  for (int i = std::max(0, (int)std::floor(z1)); i < n && i < (int)std::ceil(z2); ++i) {
+    const double lo = std::max(z1, (double)i), hi = std::min(z2, (double)i + 1.0);
+    if (hi > lo) R += (hi - lo) / epsr[i];
+  }
+  return R;
+}
+
+void build_levels(ferrox_ctx* c) {
+  c->lv.clear();
+  LevelDesc L{};
+  L.nx = c->nx; L.ny = c->ny; L.nz = c->nz;
+  L.ncell = (long long)L.nx * L.ny * L.nz;
+  c->lv.push_back(L);
+  while ((int)c->lv.size() < kMaxLevels) {
+    LevelDesc& F = c->lv.back();
+    if (F.ncell <= 1) break;
+    F.crx = lateral_can_halve(F.nx);
+    F.cry = lateral_can_halve(F.ny);
+    F.crz = (F.nz % 2 == 0);
+    if (!F.crx && !F.cry && !F.crz) break;
+    LevelDesc C{};
+    C.nx = F.crx ? F.nx / 2 : F.nx;
+    C.ny = F.cry ? F.ny / 2 : F.ny;
+    C.nz = F.crz ? F.nz / 2 : F.nz;
+    C.ncell = (long long)C.nx * C.ny * C.nz;
+    c->lv.push_back(C);
+  }
+  c->lv.back().crx = c->lv.back().cry = c->lv.back().crz = 0;
+  long long off = 0;
+  int coff = 0;
+  for (auto& l : c->lv) {
+    l.off = off;
+    l.coef_off = coff;
+    off += (l.ncell + 31) / 32 * 32;   // keep every level 256-byte aligned
+    coff += l.nz;
+  }
+  c->arena = off;
+  c->tail_first = (int)c->lv.size() - 1;
+  for (int l = 0; l < (int)c->lv.size(); ++l)
+    if (c->lv[l].ncell <= kTailMaxCells) { c->tail_first = l; break; }
+}
+
+template <typename T>
+std::vector<PlaneCoef<T>> level_coefficients(const ferrox_ctx* c) {
+  std::vector<PlaneCoef<T>> out;
+  int fx = 1, fy = 1, fz = 1;
+  for (size_t l = 0; l < c->lv.size(); ++l) {
+    const LevelDesc& L = c->lv[l];
+    for (int K = 0; K < L.nz; ++K) {
+      double lat = 0.0;
+      int has_s = 0;
+      for (int i = K * fz; i < (K + 1) * fz; ++i) {
+        lat += c->epsr[i];
+        if (c->planes[i].sc) has_s = 1;
+      }
+      lat /= fz;
+      const double cx = L.nx > 1 ? lat / (double(fx) * fx) : 0.0;
+      const double cy = L.ny > 1 ? lat / (double(fy) * fy) : 0.0;
+      const double zlo = (K == 0) ? 0.0 : (K - 0.5) * fz;
+      const double zlo_end = (K == 0) ? 0.5 * fz : (K + 0.5) * fz;
+      const double czlo = 1.0 / (resistance(c->epsr, zlo, zlo_end) * fz);
+      const double zhi = (K + 0.5) * fz;
+      const double zhi_end = (K == L.nz - 1) ? (double)L.nz * fz : (K + 1.5) * fz;
+      const double czhi = 1.0 / (resistance(c->epsr, zhi, zhi_end) * fz);
+      PlaneCoef<T> pc{};
+      const double diag = 2.0 * cx + 2.0 * cy + czlo + czhi;
+      pc.cx = (T)cx; pc.cy = (T)cy; pc.czlo = (T)czlo; pc.czhi = (T)czhi;
+      pc.diag = (T)diag; pc.invdiag = (T)(1.0 / diag); pc.has_s = has_s;
+      out.push_back(pc);
+    }
+    if (L.crx) fx *= 2;
+    if (L.cry) fy *= 2;
+    if (L.crz) fz *= 2;
+  }
+  return out;
+}
+
+ferrox_status build_planes(ferrox_ctx* c) {
+  const int nz = c->nz;
+  c->planes.assign(nz, PlaneTDGL{});
+  c->epsr.assign(nz, 0.0);
+  std::vector<const ferrox_layer*> of(nz);
+  int k = 0;
+  for (const auto& L : c->layers)
+    for (int q = 0; q < L.ncells; ++q) of[k++] = &L;
+  const double h = c->h;
+  double kappa;  // P_b = kappa (9 P0 - P1)
+  if (c->pbc == FERROX_PBC_FREE) kappa = 1.0 / 8.0;
+  else if (c->pbc == FERROX_PBC_ZERO) kappa = 0.0;
+  else kappa = c->lambda / (3.0 * h + 8.0 * c->lambda);
+  c->fe_lo = nz; c->fe_hi = -1;
+  for (int z = 0; z < nz; ++z) {
+    const ferrox_layer& L = *of[z];
+    PlaneTDGL& p = c->planes[z];
+    c->epsr[z] = L.eps_r;
+    p.eps_r = L.eps_r;
+    p.fe = L.kind == FERROX_FE;
+    p.sc = L.kind == FERROX_SC;
+    if (p.fe) {
+      p.alpha = L.alpha; p.beta = L.beta; p.gamma = L.gamma;
+      p.alpha_xy = L.alpha_xy; p.beta_xy = L.beta_xy; p.gamma_xy = L.gamma_xy;
+      p.g11 = L.g11; p.g44 = L.g44; p.Gamma = L.Gamma;
+      c->fe_lo = std::min(c->fe_lo, z);
+      c->fe_hi = std::max(c->fe_hi, z);
+    }
+    if (p.sc) {
+      const double N = L.N_D - L.N_A;
+      const double root = std::sqrt(0.25 * N * N + L.n_i * L.n_i);
+      double n0, p0;
+      if (N <= 0) { p0 = -0.5 * N + root; n0 = p0 > 0 ? L.n_i * L.n_i / p0 : 0.0; }
+      else { n0 = 0.5 * N + root; p0 = L.n_i * L.n_i / n0; }
+      p.n0 = n0; p.p0 = p0; p.Nnet = N;
+      p.kq = kQ * h * h / kEps0;
+      p.inv_vt = kQ / (kKB * L.T);
+      c->has_sc = true;
+    }
+  }
+  for (int z = 0; z < nz; ++z) {
+    PlaneTDGL& p = c->planes[z];
+    const bool dn = z > 0 && c->planes[z - 1].fe, up = z < nz - 1 && c->planes[z + 1].fe;
+    p.b_dyn = p.fe || dn || up;
+    if (p.fe) {
+      const double ih2 = 1.0 / (h * h);
+      if (dn && up) {
+        p.wz_dn = ih2; p.wz_c = -2.0 * ih2; p.wz_up = ih2;
+      } else if (up || dn) {
+        const double wn = 4.0 * (1.0 - 2.0 * kappa) / 3.0 * ih2;
+        const double wc = 4.0 * (18.0 * kappa - 3.0) / 3.0 * ih2;
+        p.wz_c = wc;
+        p.wz_up = up ? wn : 0.0;
+        p.wz_dn = dn ? wn : 0.0;
+      } else {
+        return fail(nullptr, FERROX_EINVAL, "a ferroelectric layer must be at least 2 cells thick");
+      }
+    }
+    if (z > 0) {
+      const double eL = c->epsr[z - 1], eR = c->epsr[z];
+      p.fw_L = eL / (eL + eR);
+      p.fw_R = eR / (eL + eR);
+      p.fpc = h / (2.0 * kEps0 * (eL + eR));
+    }
+    p.lift = (z == 0 || z == nz - 1) ? 2.0 * c->epsr[z] : 0.0;
+  }
+  c->kd_lo = std::max(0, c->fe_lo - 1);
+  c->kd_hi = std::min(nz - 1, c->fe_hi + 1);
+  c->k_int = c->fe_lo;
+  return FERROX_OK;
+}
+
+// ---- enqueue helpers (used while capturing) ---------------------------------------------
+
+template <typename T>
+MGArgs<T> mg_args(ferrox_ctx* c) {
+  MGArgs<T> a;
+  a.e = static_cast<T*>(c->e_arena);
+  a.r = static_cast<T*>(c->r_arena);
+  a.s = static_cast<T*>(c->s_arena);
+  a.coef = static_cast<const PlaneCoef<T>*>(c->coef);
+  a.lv = c->lv_d;
+  return a;
+}
+
+struct NoWrap {
+  template <typename F>
+  void operator()(int, F&& f) const { f(); }
+};
+
+// One V-cycle on the correction equation; `wrap(kind, launch)` lets the profiler
+// bracket each launch with events (identity when capturing graphs).
+template <typename T, typename W = NoWrap>
+void enqueue_vcycle(ferrox_ctx* c, cudaStream_t s, W wrap = W()) {
+  MGArgs<T> a = mg_args<T>(c);
+  const int nu1 = c->num.nu1, nu2 = c->num.nu2;
+  const int constant = 0;
+  const int lt = c->tail_first, L = (int)c->lv.size() - 1;
+  for (int l = 0; l < lt; ++l) {
+    const int ks = l == 0 ? FERROX_K_SMOOTH0 : FERROX_K_SMOOTHC;
+    for (int sw = 0; sw < nu1; ++sw) {
+      wrap(ks, [&] { launch_smooth<T>(a, c->lv[l], 0, sw == 0, s); });
+      wrap(ks, [&] { launch_smooth<T>(a, c->lv[l], 1, 0, s); });
+    }
+    wrap(FERROX_K_RESTRICT, [&] { launch_restrict<T>(a, c->lv[l], c->lv[l + 1], s); });
+  }
+  wrap(FERROX_K_TAIL, [&] { launch_tail<T>(a, lt, L, nu1, nu2, c->num.bottom_sweeps, constant, s); });
+  for (int l = lt - 1; l >= 0; --l) {
+    const int ks = l == 0 ? FERROX_K_SMOOTH0 : FERROX_K_SMOOTHC;
+    wrap(FERROX_K_PROLONG, [&] { launch_prolong<T>(a, c->lv[l], c->lv[l + 1], constant, s); });
+    for (int sw = 0; sw < nu2; ++sw) {
+      wrap(ks, [&] { launch_smooth<T>(a, c->lv[l], 0, 0, s); });
+      wrap(ks, [&] { launch_smooth<T>(a, c->lv[l], 1, 0, s); });
+    }
+  }
+}
+
+// kernels launched by one outer iteration: V-cycle, update, residual
+int launches_per_cycle(const ferrox_ctx* c) {
+  const int lt = c->tail_first;
+  return lt * (2 * c->num.nu1 + 1 + 1 + 2 * c->num.nu2) + 1 + 1 + 1;
+}
+
+int tdgl_launches(const ferrox_ctx* c) { return c->ncomp == 3 ? 2 : 1; }
+
+template <typename T>
+void enqueue_resid(ferrox_ctx* c, cudaStream_t s, int first, int set_cond,
+                   unsigned long long handle) {
+  ResidArgs a{};
+  a.phi = c->phi; a.b = c->b; a.planes = c->planes_d; a.coef0 = c->coef0; a.params = c->params_d;
+  a.nx = c->nx; a.ny = c->ny; a.nz = c->nz;
+  a.r_out = c->r_arena;
+  a.s_out = c->has_sc ? c->s_arena : nullptr;
+  a.partials = c->partials_d;
+  a.stats = c->stats_d;
+  a.tol = c->num.tol;
+  a.max_cycles = c->num.max_cycles;
+  a.first = first;
+  a.set_cond = set_cond;
+  a.cond_handle = handle;
+  a.launches_per_cycle = launches_per_cycle(c);
+  launch_resid<T>(a, s);
+}
+
+template <typename T>
+void enqueue_update(ferrox_ctx* c, cudaStream_t s) {
+  double clamp = INFINITY;
+  if (c->has_sc) {
+    double tmax = 0.0;
+    for (const auto& L : c->layers) if (L.kind == FERROX_SC) tmax = std::max(tmax, L.T);
+    clamp = 10.0 * kKB * tmax / kQ;   // damped Newton: at most 10 V_T per update
+  }
+  launch_update<T>(c->phi, static_cast<const T*>(c->e_arena), (long long)c->nx * c->ny * c->nz,
+                   c->stats_d, clamp, s);
+}
+
+TDGLArgs tdgl_args(ferrox_ctx* c, int mode) {
+  TDGLArgs a{};
+  a.phi = c->phi; a.b = c->b; a.planes = c->planes_d; a.params = c->params_d;
+  a.nx = c->nx; a.ny = c->ny; a.nz = c->nz; a.ncomp = c->ncomp;
+  a.kd_lo = c->kd_lo; a.kd_hi = c->kd_hi;
+  a.dt = c->num.dt; a.inv_h = 1.0 / c->h; a.inv_h2 = 1.0 / (c->h * c->h);
+  a.b_scale = c->h / kEps0;
+  a.mode = mode;
+  a.F_store = c->Fbuf;
+  if (mode == 0 || mode == 1 || mode == 3) { a.P_in = c->P; a.P_out = c->Pbuf; a.P_base = nullptr; }
+  else { a.P_in = c->Pbuf; a.P_out = c->P; a.P_base = c->P; }
+  return a;
+}
+
+// copy the new polarization (FE planes of every component) back to the caller's array
+cudaError_t enqueue_copy_back(ferrox_ctx* c, cudaStream_t s) {
+  const long long plane = (long long)c->nx * c->ny, N = plane * c->nz;
+  const size_t off = (size_t)c->fe_lo * plane;
+  const size_t cnt = (size_t)(c->fe_hi - c->fe_lo + 1) * plane;
+  for (int q = 0; q < c->ncomp; ++q) {
+    cudaError_t e = cudaMemcpyAsync(c->P + q * N + off, c->Pbuf + q * N + off, cnt * sizeof(double),
+                                    cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// resid (sets the condition) -> WHILE { V-cycle; update; resid } on the capturing stream s
+template <typename T>
+ferrox_status capture_solve(ferrox_ctx* ctx, cudaStream_t s) {
+  cudaStreamCaptureStatus st;
+  cudaGraph_t g;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  FX_CK(cudaStreamGetCaptureInfo(s, &st, nullptr, &g, nullptr, nullptr, nullptr));
+  cudaGraphConditionalHandle h;
+  FX_CK(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+  enqueue_resid<T>(ctx, s, 1, 1, (unsigned long long)h);
+  FX_CK(cudaGetLastError());
+  FX_CK(cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, nullptr, &nd));
+  cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cn;
+  FX_CK(cudaGraphAddNode(&cn, g, deps, nullptr, nd, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  FX_CK(cudaStreamBeginCaptureToGraph(ctx->cap2, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeRelaxed));
+  enqueue_vcycle<T>(ctx, ctx->cap2);
+  enqueue_update<T>(ctx, ctx->cap2);
+  enqueue_resid<T>(ctx, ctx->cap2, 0, 1, (unsigned long long)h);
+  FX_CK(cudaGetLastError());
+  cudaGraph_t body_out;
+  FX_CK(cudaStreamEndCapture(ctx->cap2, &body_out));
+  FX_CK(cudaStreamUpdateCaptureDependencies(s, &cn, nullptr, 1, cudaStreamSetCaptureDependencies));
+  return FERROX_OK;
+}
+
+template <typename T>
+ferrox_status build_graphs_t(ferrox_ctx* ctx) {
+  cudaStream_t s = ctx->cap1;
+  ferrox_status rc;
+  // solve only
+  FX_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+  if ((rc = capture_solve<T>(ctx, s)) != FERROX_OK) return rc;
+  FX_CK(cudaStreamEndCapture(s, &ctx->gr_solve));
+  FX_CK(cudaGraphInstantiate(&ctx->ge_solve, ctx->gr_solve, 0));
+  // TDGL update only (Step 1a)
+  FX_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+  launch_tdgl(tdgl_args(ctx, 0), s);
+  FX_CK(enqueue_copy_back(ctx, s));
+  FX_CK(cudaStreamEndCapture(s, &ctx->gr_tdgl));
+  FX_CK(cudaGraphInstantiate(&ctx->ge_tdgl, ctx->gr_tdgl, 0));
+  // full time step
+  FX_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+  if (ctx->num.order == 1) {
+    launch_tdgl(tdgl_args(ctx, 0), s);                 // Step 1a
+    FX_CK(enqueue_copy_back(ctx, s));
+    if ((rc = capture_solve<T>(ctx, s)) != FERROX_OK) return rc;   // Step 1b
+  } else {
+    launch_tdgl(tdgl_args(ctx, 1), s);                 // Step 1a (P* to scratch, f(P^n) kept)
+    if ((rc = capture_solve<T>(ctx, s)) != FERROX_OK) return rc;   // Step 1b: Phi*
+    launch_tdgl(tdgl_args(ctx, 2), s);                 // Step 2a: P^{n+1} into the caller's P
+    if ((rc = capture_solve<T>(ctx, s)) != FERROX_OK) return rc;   // Step 2b
+  }
+  launch_stats_step(ctx->stats_d, 1, tdgl_launches(ctx) * ctx->num.order + 1, s);
+  FX_CK(cudaGetLastError());
+  FX_CK(cudaStreamEndCapture(s, &ctx->gr_step));
+  FX_CK(cudaGraphInstantiate(&ctx->ge_step, ctx->gr_step, 0));
+  return FERROX_OK;
+}
+
+// ---- eager, event-timed step (per-kernel breakdown) -------------------------------------
+struct EventTimer {
+  cudaStream_t s;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> rec;
+  template <typename F>
+  void operator()(int kind, F&& f) {
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, s);
+    f();
+    cudaEventRecord(b, s);
+    rec.push_back({kind, {a, b}});
+  }
+};
+
+template <typename T>
+ferrox_status profile_step_t(ferrox_ctx* ctx, double* ms, int* count) {
+  cudaStream_t s = ctx->stream;
+  EventTimer tm{s, {}};
+  auto solve = [&]() -> ferrox_status {
+    tm(FERROX_K_RESID, [&] { enqueue_resid<T>(ctx, s, 1, 0, 0ULL); });
+    for (int guard = 0; guard <= ctx->num.max_cycles + 1; ++guard) {
+      FX_CK(cudaMemcpyAsync(ctx->host_pinned, reinterpret_cast<char*>(ctx->stats_d) +
+                                                  offsetof(DevStats, last_cond),
+                            sizeof(int), cudaMemcpyDeviceToHost, s));
+      FX_CK(cudaStreamSynchronize(s));
+      int cond;
+      std::memcpy(&cond, ctx->host_pinned, sizeof(int));
+      if (!cond) break;
+      enqueue_vcycle<T>(ctx, s, std::ref(tm));
+      tm(FERROX_K_UPDATE, [&] { enqueue_update<T>(ctx, s); });
+      tm(FERROX_K_RESID, [&] { enqueue_resid<T>(ctx, s, 0, 0, 0ULL); });
+    }
+    return FERROX_OK;
+  };
+  ferrox_status rc;
+  if (ctx->num.order == 1) {
+    tm(FERROX_K_TDGL, [&] { launch_tdgl(tdgl_args(ctx, 0), s); });
+    tm(FERROX_K_COPY, [&] { enqueue_copy_back(ctx, s); });
+    if ((rc = solve()) != FERROX_OK) return rc;
+  } else {
+    tm(FERROX_K_TDGL, [&] { launch_tdgl(tdgl_args(ctx, 1), s); });
+    if ((rc = solve()) != FERROX_OK) return rc;
+    tm(FERROX_K_TDGL, [&] { launch_tdgl(tdgl_args(ctx, 2), s); });
+    if ((rc = solve()) != FERROX_OK) return rc;
+  }
+  launch_stats_step(ctx->stats_d, 1, tdgl_launches(ctx) * ctx->num.order + 1, s);
+  FX_CK(cudaGetLastError());
+  FX_CK(cudaStreamSynchronize(s));
+  for (int k = 0; k < FERROX_K_COUNT; ++k) { ms[k] = 0.0; count[k] = 0; }
+  for (auto& r : tm.rec) {
+    float t = 0.f;
+    cudaEventElapsedTime(&t, r.second.first, r.second.second);
+    ms[r.first] += t;
+    count[r.first] += 1;
+    cudaEventDestroy(r.second.first);
+    cudaEventDestroy(r.second.second);
+  }
+  return FERROX_OK;
+}
+
+void release(ferrox_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  cudaGraphExec_t ge[3] = {c->ge_step, c->ge_solve, c->ge_tdgl};
+  cudaGraph_t gr[3] = {c->gr_step, c->gr_solve, c->gr_tdgl};
+  for (auto g : ge) if (g) cudaGraphExecDestroy(g);
+  for (auto g : gr) if (g) cudaGraphDestroy(g);
+  void* ptrs[] = {c->b, c->Pbuf, c->Fbuf, c->e_arena, c->r_arena, c->s_arena, c->coef, c->coef0,
+                  c->planes_d, c->lv_d, c->params_d, c->stats_d, c->partials_d, c->charge_d,
+                  c->charge_part_d};
+  for (void* p : ptrs) if (p) cudaFree(p);
+  if (c->host_pinned) cudaFreeHost(c->host_pinned);
+  if (c->cap1) cudaStreamDestroy(c->cap1);
+  if (c->cap2) cudaStreamDestroy(c->cap2);
+  delete c;
+}
+
+ferrox_status validate(const ferrox_geometry* g, const ferrox_numerics* n, const double* P,
+                       const double* phi) {
+  auto bad = [](const char* m) { return fail(nullptr, FERROX_EINVAL, m); };
+  if (!g || !n || !P || !phi) return bad("null argument");
+  if ((reinterpret_cast<uintptr_t>(P) | reinterpret_cast<uintptr_t>(phi)) % 8)
+    return bad("state arrays must be 8-byte aligned");
+  if (g->nx < 1 || g->ny < 1) return bad("nx, ny must be >= 1");
+  if ((g->nx != 1 && g->nx % 2) || (g->ny != 1 && g->ny % 2))
+    return bad("lateral sizes must be even or 1 (periodic red-black colouring)");
+  if (!(g->h > 0.0)) return bad("h must be > 0");
+  if (g->nlayers < 1 || !g->layers) return bad("no layers");
+  if (g->ncomp != 1 && g->ncomp != 3) return bad("ncomp must be 1 or 3");
+  if (g->pbc < 0 || g->pbc > 2) return bad("unknown P boundary condition");
+  if (g->pbc == FERROX_PBC_LAMBDA && !(g->lambda >= 0.0)) return bad("lambda must be >= 0");
+  int nz = 0, nfe = 0;
+  for (int q = 0; q < g->nlayers; ++q) {
+    const ferrox_layer& L = g->layers[q];
+    if (L.ncells < 1) return bad("layer with ncells < 1");
+    if (!(L.eps_r > 0.0)) return bad("eps_r must be > 0");
+    if (L.kind < 0 || L.kind > 2) return bad("unknown layer kind");
+    if (L.kind == FERROX_FE) nfe++;
+    if (L.kind == FERROX_SC && !(L.T > 0.0)) return bad("semiconductor temperature must be > 0");
+    if (L.kind == FERROX_SC && (L.N_A < 0 || L.N_D < 0 || L.n_i < 0)) return bad("negative density");
+    nz += L.ncells;
+  }
+  if (nz < 2) return bad("Nz must be >= 2");
+  if (nfe == 0) return bad("the stack needs a ferroelectric layer");
+  if (!(n->dt > 0.0)) return bad("dt must be > 0");
+  if (n->order != 1 && n->order != 2) return bad("order must be 1 or 2");
+  if (!(n->tol > 0.0)) return bad("tol must be > 0");
+  if (n->nu1 < 1 || n->nu2 < 0) return bad("need nu1 >= 1 and nu2 >= 0");
+  if (n->max_cycles < 1) return bad("max_cycles must be >= 1");
+  if (n->precision != FERROX_FP64 && n->precision != FERROX_MIXED) return bad("unknown precision");
+  if (n->bottom_sweeps < 0) return bad("bottom_sweeps must be >= 0");
+  return FERROX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ferrox_status ferrox_init_geometry(ferrox_ctx** out, const ferrox_geometry* geom,
+                                   const ferrox_numerics* num, double* P_dev, double* phi_dev,
+                                   void* cuda_stream) {
+  if (!out) return fail(nullptr, FERROX_EINVAL, "null output pointer");
+  *out = nullptr;
+  ferrox_status rc = validate(geom, num, P_dev, phi_dev);
+  if (rc != FERROX_OK) return rc;
+  ferrox_ctx* ctx = new ferrox_ctx();
+  ctx->nx = geom->nx; ctx->ny = geom->ny; ctx->h = geom->h; ctx->pbc = geom->pbc;
+  ctx->lambda = geom->lambda; ctx->ncomp = geom->ncomp;
+  ctx->layers.assign(geom->layers, geom->layers + geom->nlayers);
+  ctx->nz = 0;
+  for (auto& L : ctx->layers) ctx->nz += L.ncells;
+  ctx->num = *num;
+  if (ctx->num.bottom_sweeps == 0) ctx->num.bottom_sweeps = 64;
+  ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  ctx->P = P_dev;
+  ctx->phi = phi_dev;
+  if ((rc = build_planes(ctx)) != FERROX_OK) { ctx->err = g_init_error; release(ctx); return rc; }
+  build_levels(ctx);
+
+  const bool mixed = ctx->num.precision == FERROX_MIXED;
+  const size_t tsz = mixed ? sizeof(float) : sizeof(double);
+  const long long N = (long long)ctx->nx * ctx->ny * ctx->nz;
+  auto cleanup = [&](ferrox_status s) { g_init_error = ctx->err; release(ctx); return s; };
+#define FX_INIT_CK(call)                                                                     \
+  do {                                                                                       \
+    cudaError_t _e = (call);                                                                 \
+    if (_e != cudaSuccess) {                                                                 \
+      ctx->err = std::string(#call) + ": " + cudaGetErrorString(_e);                        \
+      return cleanup(_e == cudaErrorMemoryAllocation ? FERROX_ENOMEM : FERROX_ECUDA);        \
+    }                                                                                        \
+  } while (0)
+  FX_INIT_CK(cudaStreamCreateWithFlags(&ctx->cap1, cudaStreamNonBlocking));
+  FX_INIT_CK(cudaStreamCreateWithFlags(&ctx->cap2, cudaStreamNonBlocking));
+  FX_INIT_CK(cudaMalloc(&ctx->b, N * sizeof(double)));
+  FX_INIT_CK(cudaMalloc(&ctx->Pbuf, ctx->ncomp * N * sizeof(double)));
+  if (ctx->num.order == 2) FX_INIT_CK(cudaMalloc(&ctx->Fbuf, ctx->ncomp * N * sizeof(double)));
+  FX_INIT_CK(cudaMalloc(&ctx->e_arena, ctx->arena * tsz));
+  FX_INIT_CK(cudaMalloc(&ctx->r_arena, ctx->arena * tsz));
+  if (ctx->has_sc) FX_INIT_CK(cudaMalloc(&ctx->s_arena, ctx->arena * tsz));
+  FX_INIT_CK(cudaMalloc(&ctx->planes_d, ctx->nz * sizeof(PlaneTDGL)));
+  FX_INIT_CK(cudaMalloc(&ctx->lv_d, ctx->lv.size() * sizeof(LevelDesc)));
+  FX_INIT_CK(cudaMalloc(&ctx->params_d, sizeof(DevParams)));
+  FX_INIT_CK(cudaMalloc(&ctx->stats_d, sizeof(DevStats)));
+  FX_INIT_CK(cudaMalloc(&ctx->partials_d, 3 * kResidBlocks * sizeof(double)));
+  FX_INIT_CK(cudaMalloc(&ctx->charge_d, 8 * sizeof(double)));
+  FX_INIT_CK(cudaMalloc(&ctx->charge_part_d, 4 * 64 * sizeof(double)));
+  FX_INIT_CK(cudaMallocHost(&ctx->host_pinned, 64 * sizeof(double)));
+  auto c64 = level_coefficients<double>(ctx);
+  FX_INIT_CK(cudaMalloc(&ctx->coef0, ctx->nz * sizeof(PlaneCoef<double>)));
+  FX_INIT_CK(cudaMemcpy(ctx->coef0, c64.data(), ctx->nz * sizeof(PlaneCoef<double>),
+                        cudaMemcpyHostToDevice));
+  if (mixed) {
+    auto c32 = level_coefficients<float>(ctx);
+    FX_INIT_CK(cudaMalloc(&ctx->coef, c32.size() * sizeof(PlaneCoef<float>)));
+    FX_INIT_CK(cudaMemcpy(ctx->coef, c32.data(), c32.size() * sizeof(PlaneCoef<float>),
+                          cudaMemcpyHostToDevice));
+  } else {
+    FX_INIT_CK(cudaMalloc(&ctx->coef, c64.size() * sizeof(PlaneCoef<double>)));
+    FX_INIT_CK(cudaMemcpy(ctx->coef, c64.data(), c64.size() * sizeof(PlaneCoef<double>),
+                          cudaMemcpyHostToDevice));
+  }
+  FX_INIT_CK(cudaMemcpy(ctx->planes_d, ctx->planes.data(), ctx->nz * sizeof(PlaneTDGL),
+                        cudaMemcpyHostToDevice));
+  FX_INIT_CK(cudaMemcpy(ctx->lv_d, ctx->lv.data(), ctx->lv.size() * sizeof(LevelDesc),
+                        cudaMemcpyHostToDevice));
+  FX_INIT_CK(cudaMemset(ctx->b, 0, N * sizeof(double)));
+  FX_INIT_CK(cudaMemset(ctx->Pbuf, 0, ctx->ncomp * N * sizeof(double)));
+  FX_INIT_CK(cudaMemset(ctx->e_arena, 0, ctx->arena * tsz));
+  FX_INIT_CK(cudaMemset(ctx->r_arena, 0, ctx->arena * tsz));
+  if (ctx->s_arena) FX_INIT_CK(cudaMemset(ctx->s_arena, 0, ctx->arena * tsz));
+  FX_INIT_CK(cudaMemset(ctx->stats_d, 0, sizeof(DevStats)));
+  DevParams p0{0.0, 0.0};
+  FX_INIT_CK(cudaMemcpy(ctx->params_d, &p0, sizeof(p0), cudaMemcpyHostToDevice));
+  FX_INIT_CK(cudaDeviceSynchronize());
+  rc = mixed ? build_graphs_t<float>(ctx) : build_graphs_t<double>(ctx);
+  if (rc != FERROX_OK) return cleanup(rc);
+#undef FX_INIT_CK
+  *out = ctx;
+  return FERROX_OK;
+}
+
+ferrox_status ferrox_set_bias(ferrox_ctx* ctx, double v_bottom, double v_top) {
+  if (!ctx) return fail(nullptr, FERROX_EINVAL, "null context");
+  if (!std::isfinite(v_bottom) || !std::isfinite(v_top)) return fail(ctx, FERROX_EINVAL, "bias not finite");
+  ctx->v_bot = v_bottom;
+  ctx->v_top = v_top;
+  launch_set_params(ctx->params_d, v_bottom, v_top, ctx->stream);
+  FX_CK(cudaGetLastError());
+  return FERROX_OK;
+}
+
+ferrox_status ferrox_solve_poisson(ferrox_ctx* ctx) {
+  if (!ctx) return fail(nullptr, FERROX_EINVAL, "null context");
+  // b of the dynamic planes from the current P, then the converged solve (Step 0)
+  launch_tdgl(tdgl_args(ctx, 3), ctx->stream);
+  FX_CK(cudaGetLastError());
+  FX_CK(cudaGraphLaunch(ctx->ge_solve, ctx->stream));
+  return FERROX_OK;
+}
+
+ferrox_status ferrox_tdgl_update(ferrox_ctx* ctx) {
+  if (!ctx) return fail(nullptr, FERROX_EINVAL, "null context");
+  FX_CK(cudaGraphLaunch(ctx->ge_tdgl, ctx->stream));
+  return FERROX_OK;
+}
+
+ferrox_status ferrox_step(ferrox_ctx* ctx, int nsteps) {
+  if (!ctx) return fail(nullptr, FERROX_EINVAL, "null context");
+  if (nsteps < 0) return fail(ctx, FERROX_EINVAL, "nsteps < 0");
+  for (int q = 0; q < nsteps; ++q) FX_CK(cudaGraphLaunch(ctx->ge_step, ctx->stream));
+  return FERROX_OK;
+}
+
+ferrox_status ferrox_profile_step(ferrox_ctx* ctx, double* ms, int* count) {
+  if (!ctx || !ms || !count) return fail(ctx, FERROX_EINVAL, "null argument");
+  return ctx->num.precision == FERROX_MIXED ? profile_step_t<float>(ctx, ms, count)
+                                            : profile_step_t<double>(ctx, ms, count);
+}
+
+ferrox_status ferrox_sync_stats(ferrox_ctx* ctx, ferrox_stats* out) {
+  if (!ctx || !out) return fail(ctx, FERROX_EINVAL, "null argument");
+  DevStats st{};
+  FX_CK(cudaMemcpyAsync(ctx->host_pinned, ctx->stats_d, sizeof(DevStats), cudaMemcpyDeviceToHost,
+                        ctx->stream));
+  FX_CK(cudaStreamSynchronize(ctx->stream));
+  std::memcpy(&st, ctx->host_pinned, sizeof(DevStats));
+  out->steps = st.steps;
+  out->launches = st.launches;
+  out->solves = st.solves;
+  out->cycles = st.cycles;
+  out->last_cycles = st.last_cycles;
+  out->last_rel_res = st.last_rel;
+  out->status = st.status;
+  if (st.status != FERROX_OK) {
+    ctx->err = st.status == FERROX_ENOCONV ? "Poisson solve reached max_cycles above tolerance"
+               : st.status == FERROX_ENONFINITE ? "non-finite residual norm"
+                                                : "device status set";
+    return (ferrox_status)st.status;
+  }
+  return FERROX_OK;
+}
+
+ferrox_status ferrox_clear_status(ferrox_ctx* ctx) {
+  if (!ctx) return fail(nullptr, FERROX_EINVAL, "null context");
+  // status is the 5th field group; clear it with a small async copy of zero
+  static const int zero = 0;
+  FX_CK(cudaMemcpyAsync(reinterpret_cast<char*>(ctx->stats_d) + offsetof(DevStats, status), &zero,
+                        sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+  FX_CK(cudaStreamSynchronize(ctx->stream));
+  return FERROX_OK;
+}
+
+ferrox_status ferrox_charge(ferrox_ctx* ctx, ferrox_charge_t* out) {
+  if (!ctx || !out) return fail(ctx, FERROX_EINVAL, "null argument");
+  ChargeArgs a{};
+  const long long N = (long long)ctx->nx * ctx->ny * ctx->nz;
+  a.phi = ctx->phi;
+  a.P = ctx->P + (long long)(ctx->ncomp - 1) * N;
+  a.planes = ctx->planes_d;
+  a.params = ctx->params_d;
+  a.nx = ctx->nx; a.ny = ctx->ny; a.nz = ctx->nz; a.k_int = ctx->k_int;
+  a.h = ctx->h; a.eps0 = kEps0;
+  a.eps_top = kEps0 * ctx->epsr[ctx->nz - 1];
+  a.eps_bot = kEps0 * ctx->epsr[0];
+  a.eps_L = ctx->k_int > 0 ? kEps0 * ctx->epsr[ctx->k_int - 1] : 0.0;
+  a.eps_R = kEps0 * ctx->epsr[ctx->k_int];
+  a.out = ctx->charge_d;
+  a.partials = ctx->charge_part_d;
+  launch_charge(a, ctx->stream);
+  FX_CK(cudaGetLastError());
+  FX_CK(cudaMemcpyAsync(ctx->host_pinned, ctx->charge_d, 4 * sizeof(double), cudaMemcpyDeviceToHost,
+                        ctx->stream));
+  FX_CK(cudaStreamSynchronize(ctx->stream));
+  const double inv = 1.0 / ((double)ctx->nx * ctx->ny);
+  const double* s = ctx->host_pinned;
+  out->Q_int = -s[0] * inv;
+  out->phi_int_avg = s[1] * inv;
+  out->V_fe = ctx->v_top - out->phi_int_avg;
+  out->sigma_top = -s[2] * inv;
+  out->sigma_bot = s[3] * inv;
+  ferrox_stats st;
+  return ferrox_sync_stats(ctx, &st);
+}
+
+ferrox_status ferrox_get_state(ferrox_ctx* ctx, double* P_host, double* phi_host) {
+  if (!ctx) return fail(nullptr, FERROX_EINVAL, "null context");
+  const long long N = (long long)ctx->nx * ctx->ny * ctx->nz;
+  if (P_host)
+    FX_CK(cudaMemcpyAsync(P_host, ctx->P, ctx->ncomp * N * sizeof(double), cudaMemcpyDeviceToHost,
+                          ctx->stream));
+  if (phi_host)
+    FX_CK(cudaMemcpyAsync(phi_host, ctx->phi, N * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  ferrox_stats st;
+  return ferrox_sync_stats(ctx, &st);
+}
+
+ferrox_status ferrox_set_state(ferrox_ctx* ctx, const double* P_host, const double* phi_host) {
+  if (!ctx) return fail(nullptr, FERROX_EINVAL, "null context");
+  const long long N = (long long)ctx->nx * ctx->ny * ctx->nz;
+  if (P_host)
+    FX_CK(cudaMemcpyAsync(ctx->P, P_host, ctx->ncomp * N * sizeof(double), cudaMemcpyHostToDevice,
+                          ctx->stream));
+  if (phi_host)
+    FX_CK(cudaMemcpyAsync(ctx->phi, phi_host, N * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  return FERROX_OK;
+}
+
+ferrox_status ferrox_destroy(ferrox_ctx* ctx) {
+  release(ctx);
+  return FERROX_OK;
+}
+
+const char* ferrox_last_error(const ferrox_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_init_error.c_str();
+}
+
+ferrox_status ferrox_level_shape(const ferrox_ctx* ctx, int l, int* nx, int* ny, int* nz,
+                                 int* nlevels) {
+  if (!ctx) return FERROX_EINVAL;
+  if (nlevels) *nlevels = (int)ctx->lv.size();
+  if (l < 0 || l >= (int)ctx->lv.size()) return FERROX_EINVAL;
+  if (nx) *nx = ctx->lv[l].nx;
+  if (ny) *ny = ctx->lv[l].ny;
+  if (nz) *nz = ctx->lv[l].nz;
+  return FERROX_OK;
+}
+
+}  // extern "C"

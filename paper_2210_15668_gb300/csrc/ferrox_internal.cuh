@@ -1,0 +1,156 @@
+// Internal declarations shared by the kernels and the host engine of libferrox.
+//
+// Scaled form of the Poisson problem used on the device: lengths in units of the
+// fine cell size h0, permittivity in units of eps0, and every cell equation
+// multiplied by h0^2/eps0.  The operator coefficients are then the relative
+// permittivities (level 0), the right-hand side is b' = b h0^2/eps0, and the
+// potential stays in volts.  The solution is unchanged by the scaling.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "../../include/ferrox.h"
+
+namespace fx {
+
+constexpr int kMaxLevels = 24;
+constexpr int kTailMaxCells = 4096;     // levels at or below this size run in one CTA
+constexpr int kTailThreads = 1024;
+constexpr int kResidBlocks = 608;       // 4 x 152 SMs; fixed so the norm sums in a fixed order
+constexpr int kResidThreads = 256;
+
+// ---- per-plane data of the fine level (device, read-only during a step) -------------
+struct PlaneTDGL {
+  int fe;          // ferroelectric plane
+  int b_dyn;       // b may be nonzero from P on this plane (FE or FE-adjacent)
+  int sc;          // semiconductor plane
+  int pad;
+  double alpha, beta, gamma;          // z component
+  double alpha_xy, beta_xy, gamma_xy; // in-plane components
+  double g11, g44, Gamma;
+  double wz_dn, wz_c, wz_up;          // d2/dz2 weights incl. 1/h^2 and the P-BC stencil
+  // lower face (k-1/2) of the plane: face potential and face polarization weights
+  double fw_L, fw_R, fpc;             // Phi_f = fw_L Phi_{k-1} + fw_R Phi_k - fpc (P_k - P_{k-1})
+  double lift;                        // scaled Dirichlet lift (multiplies V of the adjacent electrode)
+  double eps_r;
+  // carriers (scaled): rho' = kq (p0 e^{-phi/VT} - n0 e^{phi/VT} + Nnet), s' = kq (n + p)/VT
+  double kq, n0, p0, Nnet, inv_vt;
+};
+
+// ---- per-plane multigrid coefficients of one level ----------------------------------
+template <typename T>
+struct PlaneCoef {
+  T cx, cy;      // lateral couplings (0 when that lateral size is 1)
+  T czlo, czhi;  // couplings through the lower / upper z face (electrode faces included)
+  T diag;        // 2 cx + 2 cy + czlo + czhi
+  T invdiag;
+  int has_s;     // semiconductor shift present on this plane
+  int pad;
+};
+
+struct LevelDesc {
+  int nx, ny, nz;
+  int crx, cry, crz;  // this level is coarsened in x / y / z to form the next one
+  long long ncell;
+  long long off;      // element offset of the level inside the level arenas
+  int coef_off;       // offset of the level's planes in the coefficient tables
+  int pad;
+};
+
+// ---- small device-side state ---------------------------------------------------------
+struct DevParams {
+  double v_bot, v_top;
+};
+
+struct DevStats {
+  long long steps, solves, cycles, launches;
+  int last_cond, pad2;
+  int last_cycles, status;
+  double last_rel;
+  double last_rnorm, last_scale;
+  unsigned int done_ctr;
+  int cycles_this_solve;
+  int zero_phi;
+  int pad;
+};
+
+// Arguments of the outer (FP64) residual kernel.
+struct ResidArgs {
+  const double* phi;
+  const double* b;
+  const PlaneTDGL* planes;
+  const PlaneCoef<double>* coef0;
+  const DevParams* params;
+  int nx, ny, nz;
+  void* r_out;         // float or double (level-0 residual)
+  void* s_out;         // float or double (level-0 Newton shift), may be null
+  double* partials;    // [3][kResidBlocks]
+  DevStats* stats;
+  double tol;
+  int max_cycles;
+  int first;           // first residual of a solve
+  int set_cond;        // call cudaGraphSetConditional
+  unsigned long long cond_handle;
+  int launches_per_cycle;  // kernels of one outer iteration (V-cycle + update + resid)
+  int pad;
+};
+
+// ---- launchers (kernels.cu / tdgl.cu) ------------------------------------------------
+template <typename T>
+struct MGArgs {
+  T* e;                     // level arena of corrections
+  T* r;                     // level arena of right-hand sides
+  T* s;                     // level arena of Newton shifts (null when no SC)
+  const PlaneCoef<T>* coef; // all levels
+  const LevelDesc* lv;      // device copy of the level table
+};
+
+template <typename T>
+void launch_smooth(const MGArgs<T>& a, const LevelDesc& L, int color, int zero_init, cudaStream_t s);
+template <typename T>
+void launch_restrict(const MGArgs<T>& a, const LevelDesc& F, const LevelDesc& C, cudaStream_t s);
+template <typename T>
+void launch_prolong(const MGArgs<T>& a, const LevelDesc& F, const LevelDesc& C, int constant,
+                    cudaStream_t s);
+template <typename T>
+void launch_tail(const MGArgs<T>& a, int l_first, int l_last, int nu1, int nu2, int bottom_sweeps,
+                 int constant, cudaStream_t s);
+template <typename T>
+void launch_resid(const ResidArgs& a, cudaStream_t s);
+template <typename T>
+void launch_update(double* phi, const T* e0, long long n, const DevStats* stats, double clamp,
+                   cudaStream_t s);
+
+struct TDGLArgs {
+  const double* P_in;     // [ncomp][nz][ny][nx]
+  double* P_out;          // new P (FE planes written)
+  const double* P_base;   // order-2 corrector: P^n (null for the predictor)
+  double* F_store;        // predictor of order 2: f(P^n) written here; corrector: read
+  const double* phi;
+  double* b;              // scaled RHS, dynamic planes written
+  const PlaneTDGL* planes;
+  const DevParams* params;
+  int nx, ny, nz, ncomp;
+  int kd_lo, kd_hi;       // dynamic plane range
+  double dt, inv_h, inv_h2, b_scale;  // b_scale = h0/eps0
+  int mode;               // 0: order-1 update, 1: order-2 predictor, 2: order-2 corrector,
+                          // 3: right-hand side of the current P only
+};
+void launch_tdgl(const TDGLArgs& a, cudaStream_t s);
+
+struct ChargeArgs {
+  const double* phi;
+  const double* P;        // z component plane data (P + (ncomp-1) N)
+  const PlaneTDGL* planes;
+  const DevParams* params;
+  int nx, ny, nz, k_int;  // k_int: lowest FE plane (interface = its lower face)
+  double h, eps0;
+  double eps_top, eps_bot, eps_L, eps_R;
+  double* out;            // 5 doubles: sum F_int, sum Phi_f_int, sum F_top, sum F_bot
+  double* partials;
+};
+void launch_charge(const ChargeArgs& a, cudaStream_t s);
+void launch_set_params(DevParams* p, double v_bot, double v_top, cudaStream_t s);
+void launch_stats_step(DevStats* st, int nsteps, int launches, cudaStream_t s);
+
+}  // namespace fx

@@ -1,0 +1,227 @@
+"""Thin ctypes binding of libferrox (include/ferrox.h): argument marshalling only.
+
+Every step of the time step runs in the CUDA library; this module converts
+Python dicts to the C structs, passes device pointers of torch tensors and the
+current CUDA stream, and turns status codes into exceptions.  There is no CPU
+fallback: if the compiled library is missing, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libferrox.so")
+
+FERROX_OK, FERROX_EINVAL, FERROX_ENOMEM, FERROX_ECUDA = 0, 1, 2, 3
+FERROX_ENOCONV, FERROX_ENONFINITE, FERROX_ETIMEOUT, FERROX_ESTATE = 4, 5, 6, 7
+FP64, MIXED = 0, 1
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "ENONFINITE",
+                6: "ETIMEOUT", 7: "ESTATE"}
+
+
+class Layer(C.Structure):
+    _fields_ = [("kind", C.c_int), ("ncells", C.c_int), ("eps_r", C.c_double),
+                ("alpha", C.c_double), ("beta", C.c_double), ("gamma", C.c_double),
+                ("alpha_xy", C.c_double), ("beta_xy", C.c_double), ("gamma_xy", C.c_double),
+                ("g11", C.c_double), ("g44", C.c_double), ("Gamma", C.c_double),
+                ("N_A", C.c_double), ("N_D", C.c_double), ("n_i", C.c_double), ("T", C.c_double)]
+
+
+class Geometry(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("h", C.c_double), ("nlayers", C.c_int),
+                ("layers", C.POINTER(Layer)), ("pbc", C.c_int), ("lambda_", C.c_double),
+                ("ncomp", C.c_int)]
+
+
+class Numerics(C.Structure):
+    _fields_ = [("dt", C.c_double), ("order", C.c_int), ("tol", C.c_double), ("nu1", C.c_int),
+                ("nu2", C.c_int), ("max_cycles", C.c_int), ("precision", C.c_int),
+                ("bottom_sweeps", C.c_int)]
+
+
+class Charge(C.Structure):
+    _fields_ = [("Q_int", C.c_double), ("phi_int_avg", C.c_double), ("V_fe", C.c_double),
+                ("sigma_top", C.c_double), ("sigma_bot", C.c_double)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("steps", C.c_longlong), ("launches", C.c_longlong), ("solves", C.c_longlong),
+                ("cycles", C.c_longlong),
+                ("last_cycles", C.c_int), ("last_rel_res", C.c_double), ("status", C.c_int)]
+
+
+EXPORTS = ["ferrox_init_geometry", "ferrox_set_bias", "ferrox_solve_poisson", "ferrox_tdgl_update",
+           "ferrox_step", "ferrox_charge", "ferrox_sync_stats", "ferrox_clear_status",
+           "ferrox_get_state", "ferrox_set_state", "ferrox_destroy", "ferrox_last_error",
+           "ferrox_level_shape", "ferrox_profile_step"]
+
+KERNEL_CLASSES = ["tdgl", "resid", "smooth_fine", "smooth_coarse", "restrict", "prolong", "tail",
+                  "update", "copy"]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libferrox.so and declare its signatures (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libferrox not built ({path} missing): run __graft_entry__.build()")
+    lib = C.CDLL(path)
+    vp, st = C.c_void_p, C.c_int
+    lib.ferrox_init_geometry.argtypes = [C.POINTER(vp), C.POINTER(Geometry), C.POINTER(Numerics),
+                                         vp, vp, vp]
+    lib.ferrox_set_bias.argtypes = [vp, C.c_double, C.c_double]
+    for name in ("ferrox_solve_poisson", "ferrox_tdgl_update", "ferrox_destroy", "ferrox_clear_status"):
+        getattr(lib, name).argtypes = [vp]
+    lib.ferrox_step.argtypes = [vp, C.c_int]
+    lib.ferrox_charge.argtypes = [vp, C.POINTER(Charge)]
+    lib.ferrox_sync_stats.argtypes = [vp, C.POINTER(Stats)]
+    lib.ferrox_get_state.argtypes = [vp, vp, vp]
+    lib.ferrox_set_state.argtypes = [vp, vp, vp]
+    lib.ferrox_last_error.argtypes = [vp]
+    lib.ferrox_last_error.restype = C.c_char_p
+    lib.ferrox_level_shape.argtypes = [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                       C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    lib.ferrox_profile_step.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int)]
+    for name in EXPORTS:
+        if name != "ferrox_last_error":
+            getattr(lib, name).restype = st
+    _lib = lib
+    return lib
+
+
+class FerroxError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def make_layers(layers):
+    arr = (Layer * len(layers))()
+    for q, l in enumerate(layers):
+        L = arr[q]
+        L.kind, L.ncells, L.eps_r = int(l["kind"]), int(l["ncells"]), float(l["eps_r"])
+        for k in ("alpha", "beta", "gamma", "g11", "g44", "Gamma", "N_A", "N_D", "n_i", "T"):
+            setattr(L, k, float(l.get(k, 0.0)))
+        for k in ("alpha", "beta", "gamma"):
+            setattr(L, k + "_xy", float(l.get(k + "_xy", l.get(k, 0.0))))
+    return arr
+
+
+def make_numerics(dt, order=1, tol=1e-10, nu1=2, nu2=2, max_cycles=200, precision=FP64,
+                  bottom_sweeps=0):
+    return Numerics(float(dt), int(order), float(tol), int(nu1), int(nu2), int(max_cycles),
+                    int(precision), int(bottom_sweeps))
+
+
+class Device:
+    """One device stack on the current GPU: caller-owned torch state + a libferrox context.
+
+    geom: dict from paper_2210_15668_gb300.inputs.make_geometry; P0: (ncomp, Nz, Ny, Nx) array.
+    """
+
+    def __init__(self, geom, P0, numerics=None, phi0=None, stream=None, device="cuda:0"):
+        import torch
+        self.lib = load()
+        self.torch = torch
+        self.geom = geom
+        nz = sum(l["ncells"] for l in geom["layers"])
+        self.shape = (nz, geom["ny"], geom["nx"])
+        self.ncomp = geom.get("ncomp", 1)
+        self.P = torch.as_tensor(np.asarray(P0, dtype=np.float64), device=device).contiguous().clone()
+        if phi0 is None:
+            self.phi = torch.zeros(self.shape, dtype=torch.float64, device=device)
+        else:
+            self.phi = torch.as_tensor(np.asarray(phi0, dtype=np.float64), device=device).contiguous().clone()
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.P.device)
+        self._layers = make_layers(geom["layers"])
+        g = Geometry(geom["nx"], geom["ny"], geom["h"], len(geom["layers"]), self._layers,
+                     geom["pbc"], geom["lam"], self.ncomp)
+        self.numerics = numerics if numerics is not None else make_numerics(4e-13)
+        self.ctx = C.c_void_p()
+        rc = self.lib.ferrox_init_geometry(C.byref(self.ctx), C.byref(g), C.byref(self.numerics),
+                                           C.c_void_p(self.P.data_ptr()),
+                                           C.c_void_p(self.phi.data_ptr()),
+                                           C.c_void_p(self.stream.cuda_stream))
+        if rc != FERROX_OK:
+            raise FerroxError(rc, self.lib.ferrox_last_error(None).decode())
+
+    def _ck(self, rc):
+        if rc != FERROX_OK:
+            raise FerroxError(rc, self.lib.ferrox_last_error(self.ctx).decode())
+
+    def set_bias(self, v_bottom, v_top):
+        self._ck(self.lib.ferrox_set_bias(self.ctx, float(v_bottom), float(v_top)))
+
+    def solve_poisson(self):
+        self._ck(self.lib.ferrox_solve_poisson(self.ctx))
+
+    def tdgl_update(self):
+        self._ck(self.lib.ferrox_tdgl_update(self.ctx))
+
+    def step(self, n=1):
+        self._ck(self.lib.ferrox_step(self.ctx, int(n)))
+
+    def charge(self):
+        out = Charge()
+        self._ck(self.lib.ferrox_charge(self.ctx, C.byref(out)))
+        return {k: getattr(out, k) for k, _ in Charge._fields_}
+
+    def stats(self, check=True):
+        out = Stats()
+        rc = self.lib.ferrox_sync_stats(self.ctx, C.byref(out))
+        if check:
+            self._ck(rc)
+        return {k: getattr(out, k) for k, _ in Stats._fields_}
+
+    def clear_status(self):
+        self._ck(self.lib.ferrox_clear_status(self.ctx))
+
+    def get_state(self, P_host=None, phi_host=None):
+        """Copy the state into host numpy arrays (allocated if not given); synchronises."""
+        P_host = np.empty((self.ncomp,) + self.shape) if P_host is None else P_host
+        phi_host = np.empty(self.shape) if phi_host is None else phi_host
+        self._ck(self.lib.ferrox_get_state(self.ctx, C.c_void_p(P_host.ctypes.data),
+                                           C.c_void_p(phi_host.ctypes.data)))
+        return P_host, phi_host
+
+    def set_state(self, P_host=None, phi_host=None):
+        """Asynchronous copy from host arrays (keep them alive until the stream syncs)."""
+        self._keep = (P_host, phi_host)
+        pp = C.c_void_p(P_host.ctypes.data) if P_host is not None else None
+        fp = C.c_void_p(phi_host.ctypes.data) if phi_host is not None else None
+        self._ck(self.lib.ferrox_set_state(self.ctx, pp, fp))
+
+    def profile_step(self):
+        """One event-timed eager step: {kernel class: (total ms, launches)}."""
+        n = len(KERNEL_CLASSES)
+        ms = (C.c_double * n)()
+        cnt = (C.c_int * n)()
+        self._ck(self.lib.ferrox_profile_step(self.ctx, ms, cnt))
+        return {KERNEL_CLASSES[k]: (ms[k], cnt[k]) for k in range(n)}
+
+    def levels(self):
+        n = C.c_int()
+        nx, ny, nz = C.c_int(), C.c_int(), C.c_int()
+        self.lib.ferrox_level_shape(self.ctx, 0, C.byref(nx), C.byref(ny), C.byref(nz), C.byref(n))
+        out = []
+        for l in range(n.value):
+            self.lib.ferrox_level_shape(self.ctx, l, C.byref(nx), C.byref(ny), C.byref(nz), None)
+            out.append((nx.value, ny.value, nz.value))
+        return out
+
+    def close(self):
+        if self.ctx:
+            self.lib.ferrox_destroy(self.ctx)
+            self.ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
