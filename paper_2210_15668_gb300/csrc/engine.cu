@@ -50,6 +50,10 @@ struct ferrox_ctx {
   std::vector<LevelDesc> lv;
   int tail_first = 0;
   long long arena = 0;
+  std::vector<LevelDesc> lv_tail;   // tail levels with shared-memory offsets
+  long long tail_elems = 0;
+  size_t tail_smem = 0;
+  int resid_blocks = 0;
   // device memory
   cudaStream_t stream = nullptr;
   cudaStream_t cap1 = nullptr, cap2 = nullptr;
@@ -65,6 +69,7 @@ struct ferrox_ctx {
   PlaneCoef<double>* coef0 = nullptr; // level 0 in FP64 (outer residual)
   PlaneTDGL* planes_d = nullptr;
   LevelDesc* lv_d = nullptr;
+  LevelDesc* lvt_d = nullptr;
   DevParams* params_d = nullptr;
   DevStats* stats_d = nullptr;
   double* partials_d = nullptr;
@@ -135,9 +140,29 @@ void build_levels(ferrox_ctx* c) {
     coff += l.nz;
   }
   c->arena = off;
-  c->tail_first = (int)c->lv.size() - 1;
-  for (int l = 0; l < (int)c->lv.size(); ++l)
-    if (c->lv[l].ncell <= kTailMaxCells) { c->tail_first = l; break; }
+}
+
+// first level of the single-CTA tail: small enough in cells and in shared memory
+void plan_tail(ferrox_ctx* c, size_t elem_size) {
+  const int L = (int)c->lv.size() - 1;
+  const int narr = c->has_sc ? 3 : 2;
+  c->tail_first = L;
+  for (int l = 0; l <= L; ++l) {
+    const long long elems = c->arena - c->lv[l].off;
+    if (c->lv[l].ncell <= kTailMaxCells && (size_t)elems * elem_size * narr <= (size_t)kTailMaxSmem) {
+      c->tail_first = l;
+      break;
+    }
+  }
+  const long long base = c->lv[c->tail_first].off;
+  c->lv_tail.assign(c->lv.begin() + c->tail_first, c->lv.end());
+  for (auto& t : c->lv_tail) t.off -= base;
+  c->tail_elems = c->arena - base;
+  c->tail_smem = (size_t)c->tail_elems * elem_size * narr;
+  if (c->num.bottom_sweeps == 0) {     // enough sweeps to solve the coarsest level
+    const LevelDesc& B = c->lv.back();
+    c->num.bottom_sweeps = std::min(64, 2 * (B.nx + B.ny + B.nz));
+  }
 }
 
 template <typename T>
@@ -260,6 +285,14 @@ MGArgs<T> mg_args(ferrox_ctx* c) {
   return a;
 }
 
+// damped Newton in semiconductor stacks: at most 10 V_T per update
+double update_clamp(const ferrox_ctx* c) {
+  if (!c->has_sc) return INFINITY;
+  double tmax = 0.0;
+  for (const auto& L : c->layers) if (L.kind == FERROX_SC) tmax = std::max(tmax, L.T);
+  return 10.0 * kKB * tmax / kQ;
+}
+
 struct NoWrap {
   template <typename F>
   void operator()(int, F&& f) const { f(); }
@@ -276,26 +309,33 @@ void enqueue_vcycle(ferrox_ctx* c, cudaStream_t s, W wrap = W()) {
   for (int l = 0; l < lt; ++l) {
     const int ks = l == 0 ? FERROX_K_SMOOTH0 : FERROX_K_SMOOTHC;
     for (int sw = 0; sw < nu1; ++sw) {
-      wrap(ks, [&] { launch_smooth<T>(a, c->lv[l], 0, sw == 0, s); });
-      wrap(ks, [&] { launch_smooth<T>(a, c->lv[l], 1, 0, s); });
+      wrap(ks, [&] { launch_smooth<T>(a, c->lv[l], 0, sw == 0, nullptr, s); });
+      wrap(ks, [&] { launch_smooth<T>(a, c->lv[l], 1, 0, nullptr, s); });
     }
     wrap(FERROX_K_RESTRICT, [&] { launch_restrict<T>(a, c->lv[l], c->lv[l + 1], s); });
   }
-  wrap(FERROX_K_TAIL, [&] { launch_tail<T>(a, lt, L, nu1, nu2, c->num.bottom_sweeps, constant, s); });
+  TailArgs ta{c->lvt_d, L - lt + 1, c->tail_elems, c->lv[lt].off, nu1, nu2, c->num.bottom_sweeps,
+              constant};
+  wrap(FERROX_K_TAIL, [&] { launch_tail<T>(a, ta, c->tail_smem, s); });
+  const UpdateArgs upd{c->phi, c->stats_d, update_clamp(c)};
   for (int l = lt - 1; l >= 0; --l) {
     const int ks = l == 0 ? FERROX_K_SMOOTH0 : FERROX_K_SMOOTHC;
     wrap(FERROX_K_PROLONG, [&] { launch_prolong<T>(a, c->lv[l], c->lv[l + 1], constant, s); });
     for (int sw = 0; sw < nu2; ++sw) {
-      wrap(ks, [&] { launch_smooth<T>(a, c->lv[l], 0, 0, s); });
-      wrap(ks, [&] { launch_smooth<T>(a, c->lv[l], 1, 0, s); });
+      const bool fuse = (l == 0 && sw == nu2 - 1);   // phi += e folded into the last sweep
+      wrap(ks, [&] { launch_smooth<T>(a, c->lv[l], 0, 0, nullptr, s); });
+      wrap(ks, [&] { launch_smooth<T>(a, c->lv[l], 1, 0, fuse ? &upd : nullptr, s); });
     }
   }
 }
 
-// kernels launched by one outer iteration: V-cycle, update, residual
+// the fine-level update is a separate kernel only when it cannot ride on a sweep
+bool separate_update(const ferrox_ctx* c) { return c->tail_first == 0 || c->num.nu2 == 0; }
+
+// kernels launched by one outer iteration: V-cycle, (update), residual
 int launches_per_cycle(const ferrox_ctx* c) {
   const int lt = c->tail_first;
-  return lt * (2 * c->num.nu1 + 1 + 1 + 2 * c->num.nu2) + 1 + 1 + 1;
+  return lt * (2 * c->num.nu1 + 1 + 1 + 2 * c->num.nu2) + 1 + (separate_update(c) ? 1 : 0) + 1;
 }
 
 int tdgl_launches(const ferrox_ctx* c) { return c->ncomp == 3 ? 2 : 1; }
@@ -321,14 +361,9 @@ void enqueue_resid(ferrox_ctx* c, cudaStream_t s, int first, int set_cond,
 
 template <typename T>
 void enqueue_update(ferrox_ctx* c, cudaStream_t s) {
-  double clamp = INFINITY;
-  if (c->has_sc) {
-    double tmax = 0.0;
-    for (const auto& L : c->layers) if (L.kind == FERROX_SC) tmax = std::max(tmax, L.T);
-    clamp = 10.0 * kKB * tmax / kQ;   // damped Newton: at most 10 V_T per update
-  }
+  if (!separate_update(c)) return;
   launch_update<T>(c->phi, static_cast<const T*>(c->e_arena), (long long)c->nx * c->ny * c->nz,
-                   c->stats_d, clamp, s);
+                   c->stats_d, update_clamp(c), s);
 }
 
 TDGLArgs tdgl_args(ferrox_ctx* c, int mode) {
@@ -455,7 +490,7 @@ ferrox_status profile_step_t(ferrox_ctx* ctx, double* ms, int* count) {
       std::memcpy(&cond, ctx->host_pinned, sizeof(int));
       if (!cond) break;
       enqueue_vcycle<T>(ctx, s, std::ref(tm));
-      tm(FERROX_K_UPDATE, [&] { enqueue_update<T>(ctx, s); });
+      if (separate_update(ctx)) tm(FERROX_K_UPDATE, [&] { enqueue_update<T>(ctx, s); });
       tm(FERROX_K_RESID, [&] { enqueue_resid<T>(ctx, s, 0, 0, 0ULL); });
     }
     return FERROX_OK;
@@ -494,7 +529,7 @@ void release(ferrox_ctx* c) {
   for (auto g : ge) if (g) cudaGraphExecDestroy(g);
   for (auto g : gr) if (g) cudaGraphDestroy(g);
   void* ptrs[] = {c->b, c->Pbuf, c->Fbuf, c->e_arena, c->r_arena, c->s_arena, c->coef, c->coef0,
-                  c->planes_d, c->lv_d, c->params_d, c->stats_d, c->partials_d, c->charge_d,
+                  c->planes_d, c->lv_d, c->lvt_d, c->params_d, c->stats_d, c->partials_d, c->charge_d,
                   c->charge_part_d};
   for (void* p : ptrs) if (p) cudaFree(p);
   if (c->host_pinned) cudaFreeHost(c->host_pinned);
@@ -558,7 +593,6 @@ ferrox_status ferrox_init_geometry(ferrox_ctx** out, const ferrox_geometry* geom
   ctx->nz = 0;
   for (auto& L : ctx->layers) ctx->nz += L.ncells;
   ctx->num = *num;
-  if (ctx->num.bottom_sweeps == 0) ctx->num.bottom_sweeps = 64;
   ctx->stream = static_cast<cudaStream_t>(cuda_stream);
   ctx->P = P_dev;
   ctx->phi = phi_dev;
@@ -567,6 +601,8 @@ ferrox_status ferrox_init_geometry(ferrox_ctx** out, const ferrox_geometry* geom
 
   const bool mixed = ctx->num.precision == FERROX_MIXED;
   const size_t tsz = mixed ? sizeof(float) : sizeof(double);
+  plan_tail(ctx, tsz);
+  ctx->resid_blocks = ((ctx->nx + kResidBX - 1) / kResidBX) * ((ctx->ny + kResidBY - 1) / kResidBY);
   const long long N = (long long)ctx->nx * ctx->ny * ctx->nz;
   auto cleanup = [&](ferrox_status s) { g_init_error = ctx->err; release(ctx); return s; };
 #define FX_INIT_CK(call)                                                                     \
@@ -589,7 +625,11 @@ ferrox_status ferrox_init_geometry(ferrox_ctx** out, const ferrox_geometry* geom
   FX_INIT_CK(cudaMalloc(&ctx->lv_d, ctx->lv.size() * sizeof(LevelDesc)));
   FX_INIT_CK(cudaMalloc(&ctx->params_d, sizeof(DevParams)));
   FX_INIT_CK(cudaMalloc(&ctx->stats_d, sizeof(DevStats)));
-  FX_INIT_CK(cudaMalloc(&ctx->partials_d, 3 * kResidBlocks * sizeof(double)));
+  FX_INIT_CK(cudaMalloc(&ctx->partials_d, 3 * (size_t)ctx->resid_blocks * sizeof(double)));
+  FX_INIT_CK(cudaMalloc(&ctx->lvt_d, ctx->lv_tail.size() * sizeof(LevelDesc)));
+  FX_INIT_CK(cudaMemcpy(ctx->lvt_d, ctx->lv_tail.data(), ctx->lv_tail.size() * sizeof(LevelDesc),
+                        cudaMemcpyHostToDevice));
+  FX_INIT_CK(mixed ? tail_prepare<float>(ctx->tail_smem) : tail_prepare<double>(ctx->tail_smem));
   FX_INIT_CK(cudaMalloc(&ctx->charge_d, 8 * sizeof(double)));
   FX_INIT_CK(cudaMalloc(&ctx->charge_part_d, 4 * 64 * sizeof(double)));
   FX_INIT_CK(cudaMallocHost(&ctx->host_pinned, 64 * sizeof(double)));

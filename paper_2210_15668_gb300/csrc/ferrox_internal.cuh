@@ -16,8 +16,8 @@ namespace fx {
 constexpr int kMaxLevels = 24;
 constexpr int kTailMaxCells = 4096;     // levels at or below this size run in one CTA
 constexpr int kTailThreads = 1024;
-constexpr int kResidBlocks = 608;       // 4 x 152 SMs; fixed so the norm sums in a fixed order
-constexpr int kResidThreads = 256;
+constexpr int kTailMaxSmem = 200 * 1024; // shared memory available to the tail CTA
+constexpr int kResidBX = 32, kResidBY = 8; // residual: one thread per (x, y) column
 
 // ---- per-plane data of the fine level (device, read-only during a step) -------------
 struct PlaneTDGL {
@@ -65,6 +65,7 @@ struct DevParams {
 struct DevStats {
   long long steps, solves, cycles, launches;
   int last_cond, pad2;
+  double bnorm2;          // ||b||^2 of the current solve (b is fixed within a solve)
   int last_cycles, status;
   double last_rel;
   double last_rnorm, last_scale;
@@ -84,7 +85,7 @@ struct ResidArgs {
   int nx, ny, nz;
   void* r_out;         // float or double (level-0 residual)
   void* s_out;         // float or double (level-0 Newton shift), may be null
-  double* partials;    // [3][kResidBlocks]
+  double* partials;    // [3][number of residual blocks]
   DevStats* stats;
   double tol;
   int max_cycles;
@@ -105,16 +106,36 @@ struct MGArgs {
   const LevelDesc* lv;      // device copy of the level table
 };
 
+// phi += e folded into the last fine-level black sweep
+struct UpdateArgs {
+  double* phi;
+  const DevStats* stats;
+  double clamp;
+};
+
+// levels handled by the single-CTA tail; offsets of lv are relative to the tail base
+struct TailArgs {
+  const LevelDesc* lv;  // device table of the tail levels (shared-memory offsets)
+  int nlev;
+  long long elems;      // elements per tail array in shared memory
+  long long base;       // arena offset of the first tail level
+  int nu1, nu2, bottom_sweeps, constant;
+};
+
 template <typename T>
-void launch_smooth(const MGArgs<T>& a, const LevelDesc& L, int color, int zero_init, cudaStream_t s);
+void launch_smooth(const MGArgs<T>& a, const LevelDesc& L, int color, int zero_init,
+                   const UpdateArgs* upd, cudaStream_t s);
 template <typename T>
 void launch_restrict(const MGArgs<T>& a, const LevelDesc& F, const LevelDesc& C, cudaStream_t s);
 template <typename T>
 void launch_prolong(const MGArgs<T>& a, const LevelDesc& F, const LevelDesc& C, int constant,
                     cudaStream_t s);
 template <typename T>
-void launch_tail(const MGArgs<T>& a, int l_first, int l_last, int nu1, int nu2, int bottom_sweeps,
-                 int constant, cudaStream_t s);
+size_t tail_smem_bytes(long long elems, bool has_s);
+template <typename T>
+cudaError_t tail_prepare(size_t smem);
+template <typename T>
+void launch_tail(const MGArgs<T>& a, const TailArgs& t, size_t smem, cudaStream_t s);
 template <typename T>
 void launch_resid(const ResidArgs& a, cudaStream_t s);
 template <typename T>

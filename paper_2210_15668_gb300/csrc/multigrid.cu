@@ -6,14 +6,17 @@
 // is an independent cell-centred multigrid written for one GPU:
 //   * the outer loop works in FP64: r = b + rho(phi) - A phi, the Newton shift
 //     s = -d rho/d phi in semiconductor cells, and the norms that decide
-//     convergence (||r|| <= tol max(||b||, ||rho||)), all in one kernel whose last
-//     block sums the per-block partials in a fixed order (deterministic);
+//     convergence (||r|| <= tol max(||b||, ||rho||)), all in one z-marching
+//     kernel whose last block sums the per-block partials in a fixed order
+//     (deterministic) and sets the CUDA-graph loop condition;
 //   * one V-cycle on (A + diag s) e = r in precision T (double, or float in the
-//     mixed form): red-black Gauss-Seidel smoothing, residual fused with
-//     full-weighting (8-child mean) restriction, trilinear (or constant)
-//     prolongation fused with the correction, and the levels at or below
-//     kTailMaxCells handled by one CTA in a single launch;
-//   * phi += e in FP64 (clamped in semiconductor stacks: damped Newton).
+//     mixed form): red-black Gauss-Seidel colour sweeps, residual fused with
+//     8-child-mean restriction, trilinear prolongation fused with the
+//     correction (one thread per coarse cell, separable), and every level at or
+//     below the tail size solved by one CTA in shared memory in one launch;
+//   * phi += e in FP64 fused into the last fine-level black sweep (clamped in
+//     semiconductor stacks: damped Newton).
+// Launch grids are 3-D (x chunk, row, plane), so no kernel divides indices.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -29,9 +32,8 @@ __device__ __forceinline__ long long lidx(const LevelDesc& L, int i, int j, int 
 
 // (r + sum of couplings * neighbours) of one cell; the Gauss-Seidel numerator.
 template <typename T>
-__device__ __forceinline__ T gs_numerator(const T* e, const T* r,
-                                          const PlaneCoef<T>& c, const LevelDesc& L, int i, int j,
-                                          int k, long long id) {
+__device__ __forceinline__ T gs_numerator(const T* e, const T* r, const PlaneCoef<T>& c,
+                                          const LevelDesc& L, int i, int j, int k, long long id) {
   const int im = (i == 0) ? L.nx - 1 : i - 1;
   const int ip = (i == L.nx - 1) ? 0 : i + 1;
   const int jm = (j == 0) ? L.ny - 1 : j - 1;
@@ -50,38 +52,47 @@ __device__ __forceinline__ T gs_numerator(const T* e, const T* r,
   return acc;
 }
 
+struct Upd {
+  double* phi;      // fine-level potential (null: no fused update)
+  double clamp;
+  int zero;         // set phi = 0 (degenerate zero right-hand side)
+};
+
 template <typename T>
-__device__ __forceinline__ void smooth_cell(const MGArgs<T>& a, const LevelDesc& L, int i, int j,
-                                            int k, int color, int zero_init) {
-  const PlaneCoef<T> c = a.coef[L.coef_off + k];
-  const long long id = lidx(L, i, j, k);
-  if (zero_init) {
-    // first red half-sweep from e = 0: e_red = r / diag, and black cells start at 0
-    T d = c.has_s ? T(1) / (c.diag + a.s[id]) : c.invdiag;
-    a.e[id] = a.r[id] * d;
-    (void)color;
-    return;
-  }
-  T num = gs_numerator(a.e, a.r, c, L, i, j, k, id);
-  a.e[id] = c.has_s ? num / (c.diag + a.s[id]) : num * c.invdiag;
+__device__ __forceinline__ void apply_update(const Upd& u, long long idx, T e) {
+  if (u.zero) u.phi[idx] = 0.0;
+  else u.phi[idx] += fmin(fmax((double)e, -u.clamp), u.clamp);
 }
 
-// colour sweep over a level; t enumerates (half-row position, row, plane)
+// One red/black pair position (ip) of a row: update the cell of `color`; on a
+// zero-start sweep also zero the other cell; optionally fold both cells' final
+// corrections into phi (last black sweep of the fine level).
 template <typename T>
-__device__ __forceinline__ void smooth_item(const MGArgs<T>& a, const LevelDesc& L, long long t,
-                                            int color, int zero_init) {
-  const int hx = (L.nx + 1) >> 1;
-  const int ip = (int)(t % hx);
-  const long long rest = t / hx;
-  const int j = (int)(rest % L.ny);
-  const int k = (int)(rest / L.ny);
+__device__ __forceinline__ void smooth_pair(const MGArgs<T>& a, const LevelDesc& L, int ip, int j,
+                                            int k, int color, int zero_init, const Upd& u) {
   const int par = (j + k + color) & 1;
   const int i = 2 * ip + par;
-  if (i < L.nx) smooth_cell(a, L, i, j, k, color, zero_init);
-  if (zero_init) {
-    const int i2 = 2 * ip + (par ^ 1);
-    if (i2 < L.nx) a.e[lidx(L, i2, j, k)] = T(0);
+  const int i2 = 2 * ip + (par ^ 1);
+  const PlaneCoef<T> c = a.coef[L.coef_off + k];
+  T ev = T(0);
+  long long id = -1;
+  if (i < L.nx) {
+    id = lidx(L, i, j, k);
+    if (zero_init) {
+      const T d = c.has_s ? T(1) / (c.diag + a.s[id]) : c.invdiag;
+      ev = a.r[id] * d;
+    } else {
+      const T num = gs_numerator(a.e, a.r, c, L, i, j, k, id);
+      ev = c.has_s ? num / (c.diag + a.s[id]) : num * c.invdiag;
+    }
+    a.e[id] = ev;
   }
+  if (i2 < L.nx) {
+    const long long id2 = lidx(L, i2, j, k);
+    if (zero_init) a.e[id2] = T(0);
+    if (u.phi) apply_update(u, id2 - L.off, a.e[id2]);
+  }
+  if (u.phi && id >= 0) apply_update(u, id - L.off, ev);
 }
 
 // residual of one fine cell: r - (A + s) e
@@ -96,12 +107,8 @@ __device__ __forceinline__ T cell_residual(const MGArgs<T>& a, const LevelDesc& 
 }
 
 template <typename T>
-__device__ __forceinline__ void restrict_item(const MGArgs<T>& a, const LevelDesc& F,
-                                              const LevelDesc& C, long long t) {
-  const int I = (int)(t % C.nx);
-  const long long rest = t / C.nx;
-  const int J = (int)(rest % C.ny);
-  const int K = (int)(rest / C.ny);
+__device__ __forceinline__ void restrict_cell(const MGArgs<T>& a, const LevelDesc& F,
+                                              const LevelDesc& C, int I, int J, int K) {
   const int nxc = F.crx ? 2 : 1, nyc = F.cry ? 2 : 1, nzc = F.crz ? 2 : 1;
   const int i0 = F.crx ? 2 * I : I, j0 = F.cry ? 2 * J : J, k0 = F.crz ? 2 * K : K;
   T sum = T(0), ssum = T(0);
@@ -117,105 +124,151 @@ __device__ __forceinline__ void restrict_item(const MGArgs<T>& a, const LevelDes
   if (a.s) a.s[idc] = ssum * inv;
 }
 
+// Prolongation + correction for the children of coarse cell (I, J, K).
+// Cell-centred trilinear interpolation, separable: along every coarsened
+// direction a child takes 3/4 of its own coarse value and 1/4 of the coarse
+// neighbour on its side; an electrode beyond the coarse grid acts as a ghost
+// cell holding -e (zero correction on the electrode face).
 template <typename T>
-__device__ __forceinline__ void prolong_item(const MGArgs<T>& a, const LevelDesc& F,
-                                             const LevelDesc& C, long long t, int constant) {
-  const int i = (int)(t % F.nx);
-  const long long rest = t / F.nx;
-  const int j = (int)(rest % F.ny);
-  const int k = (int)(rest / F.ny);
-  const int I = F.crx ? (i >> 1) : i, J = F.cry ? (j >> 1) : j, K = F.crz ? (k >> 1) : k;
-  const long long id = lidx(F, i, j, k);
+__device__ __forceinline__ void prolong_cell(const MGArgs<T>& a, const LevelDesc& F,
+                                             const LevelDesc& C, int I, int J, int K, int constant) {
+  const int nxc = F.crx ? 2 : 1, nyc = F.cry ? 2 : 1, nzc = F.crz ? 2 : 1;
+  T* e = a.e;
   if (constant) {
-    a.e[id] += a.e[lidx(C, I, J, K)];
+    const T E0 = e[lidx(C, I, J, K)];
+    for (int c = 0; c < nzc; ++c)
+      for (int b = 0; b < nyc; ++b)
+        for (int q = 0; q < nxc; ++q)
+          e[lidx(F, F.crx ? 2 * I + q : I, F.cry ? 2 * J + b : J, F.crz ? 2 * K + c : K)] += E0;
     return;
   }
-  // trilinear, cell-centred: weights 3/4 (own coarse cell) and 1/4 (the coarse
-  // neighbour on the side of the fine cell) per coarsened direction
-  int In = I, Jn = J, Kn = K;
-  T wxo = T(1), wyo = T(1), wzo = T(1);
-  T wxn = T(0), wyn = T(0), wzn = T(0);
-  if (F.crx) {
-    In = (i & 1) ? (I + 1 == C.nx ? 0 : I + 1) : (I == 0 ? C.nx - 1 : I - 1);
-    wxo = T(0.75); wxn = T(0.25);
-  }
-  if (F.cry) {
-    Jn = (j & 1) ? (J + 1 == C.ny ? 0 : J + 1) : (J == 0 ? C.ny - 1 : J - 1);
-    wyo = T(0.75); wyn = T(0.25);
-  }
-  if (F.crz) {
-    Kn = (k & 1) ? K + 1 : K - 1;
-    wzo = T(0.75); wzn = T(0.25);
-    if (Kn < 0 || Kn >= C.nz) {   // electrode: ghost value -e (zero correction on the face)
-      Kn = K; wzo = T(0.5); wzn = T(0);
+  const int Im = I == 0 ? C.nx - 1 : I - 1, Ip = I + 1 == C.nx ? 0 : I + 1;
+  const int Jm = J == 0 ? C.ny - 1 : J - 1, Jp = J + 1 == C.ny ? 0 : J + 1;
+  const int xs[3] = {Im, I, Ip}, ys[3] = {Jm, J, Jp};
+  T Z[2][3][3];
+#pragma unroll
+  for (int yy = 0; yy < 3; ++yy)
+#pragma unroll
+    for (int xx = 0; xx < 3; ++xx) {
+      if ((!F.cry && yy != 1) || (!F.crx && xx != 1)) continue;
+      const T Ec = e[lidx(C, xs[xx], ys[yy], K)];
+      if (F.crz) {
+        Z[0][yy][xx] = (K > 0) ? fma(T(0.75), Ec, T(0.25) * e[lidx(C, xs[xx], ys[yy], K - 1)])
+                               : T(0.5) * Ec;
+        Z[1][yy][xx] = (K + 1 < C.nz) ? fma(T(0.75), Ec, T(0.25) * e[lidx(C, xs[xx], ys[yy], K + 1)])
+                                      : T(0.5) * Ec;
+      } else {
+        Z[0][yy][xx] = Ec;
+      }
+    }
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    if (c >= nzc) break;
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      if (b >= nyc) break;
+      T Y[3];
+#pragma unroll
+      for (int xx = 0; xx < 3; ++xx) {
+        if (!F.crx && xx != 1) continue;
+        Y[xx] = F.cry ? fma(T(0.75), Z[c][1][xx], T(0.25) * Z[c][b ? 2 : 0][xx]) : Z[c][1][xx];
+      }
+      const int fj = F.cry ? 2 * J + b : J, fk = F.crz ? 2 * K + c : K;
+      if (F.crx) {
+        const long long f0 = lidx(F, 2 * I, fj, fk);
+        e[f0] += fma(T(0.75), Y[1], T(0.25) * Y[0]);
+        e[f0 + 1] += fma(T(0.75), Y[1], T(0.25) * Y[2]);
+      } else {
+        e[lidx(F, I, fj, fk)] += Y[1];
+      }
     }
   }
-  const T* E = a.e;
-  T v0 = wxo * E[lidx(C, I, J, K)] + wxn * E[lidx(C, In, J, K)];
-  T v1 = wxo * E[lidx(C, I, Jn, K)] + wxn * E[lidx(C, In, Jn, K)];
-  T lo = wyo * v0 + wyn * v1;
-  T v2 = wxo * E[lidx(C, I, J, Kn)] + wxn * E[lidx(C, In, J, Kn)];
-  T v3 = wxo * E[lidx(C, I, Jn, Kn)] + wxn * E[lidx(C, In, Jn, Kn)];
-  T hi = wyo * v2 + wyn * v3;
-  a.e[id] += wzo * lo + wzn * hi;
 }
+
+// ---- multi-block kernels (3-D grids: x chunk, row chunk, plane) ----------------------
 
 template <typename T>
 __global__ void __launch_bounds__(256) smooth_kernel(MGArgs<T> a, LevelDesc L, int color,
-                                                     int zero_init) {
-  const long long total = (long long)((L.nx + 1) >> 1) * L.ny * L.nz;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x)
-    smooth_item(a, L, t, color, zero_init);
+                                                     int zero_init, Upd u, const DevStats* st) {
+  const int ip = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (ip >= ((L.nx + 1) >> 1) || j >= L.ny) return;
+  if (u.phi) u.zero = st->zero_phi;
+  smooth_pair(a, L, ip, j, k, color, zero_init, u);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256) restrict_kernel(MGArgs<T> a, LevelDesc F, LevelDesc C) {
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < C.ncell;
-       t += (long long)gridDim.x * blockDim.x)
-    restrict_item(a, F, C, t);
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+  if (I >= C.nx || J >= C.ny) return;
+  restrict_cell(a, F, C, I, J, (int)blockIdx.z);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256) prolong_kernel(MGArgs<T> a, LevelDesc F, LevelDesc C,
                                                       int constant) {
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < F.ncell;
-       t += (long long)gridDim.x * blockDim.x)
-    prolong_item(a, F, C, t, constant);
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+  if (I >= C.nx || J >= C.ny) return;
+  prolong_cell(a, F, C, I, J, (int)blockIdx.z, constant);
 }
 
-// All levels l_first..l_last in one CTA: a complete V-cycle below l_first
-// (pre-smoothing, restriction, bottom sweeps, prolongation, post-smoothing),
-// with block barriers between the phases.
+// ---- single-CTA tail: the smallest levels in shared memory ---------------------------
+
 template <typename T>
 __device__ void tail_smooth(const MGArgs<T>& a, const LevelDesc& L, int sweeps, int zero_first) {
-  const long long half = (long long)((L.nx + 1) >> 1) * L.ny * L.nz;
+  const int hx = (L.nx + 1) >> 1;
+  const int items = hx * L.ny * L.nz;
+  const Upd none{nullptr, 0.0, 0};
   for (int sw = 0; sw < sweeps; ++sw)
     for (int color = 0; color < 2; ++color) {
       const int zi = (zero_first && sw == 0 && color == 0);
-      for (long long t = threadIdx.x; t < half; t += blockDim.x) smooth_item(a, L, t, color, zi);
+      for (int t = threadIdx.x; t < items; t += blockDim.x) {
+        const int ip = t % hx, rest = t / hx;
+        smooth_pair(a, L, ip, rest % L.ny, rest / L.ny, color, zi, none);
+      }
       __syncthreads();
     }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kTailThreads) tail_kernel(MGArgs<T> a, int l_first, int l_last,
-                                                            int nu1, int nu2, int bottom_sweeps,
-                                                            int constant) {
-  for (int l = l_first; l < l_last; ++l) {
-    const LevelDesc F = a.lv[l], C = a.lv[l + 1];
-    tail_smooth(a, F, nu1, 1);
-    for (long long t = threadIdx.x; t < C.ncell; t += blockDim.x) restrict_item(a, F, C, t);
+__global__ void __launch_bounds__(kTailThreads) tail_kernel(MGArgs<T> g, TailArgs t) {
+  extern __shared__ __align__(16) unsigned char tail_smem[];
+  T* se = reinterpret_cast<T*>(tail_smem);
+  T* sr = se + t.elems;
+  T* ss = g.s ? sr + t.elems : nullptr;
+  const LevelDesc* lv = t.lv;
+  const int n0 = (int)lv[0].ncell;
+  for (int q = threadIdx.x; q < n0; q += blockDim.x) {
+    sr[q] = g.r[t.base + q];
+    if (ss) ss[q] = g.s[t.base + q];
+  }
+  __syncthreads();
+  MGArgs<T> a;
+  a.e = se; a.r = sr; a.s = ss; a.coef = g.coef; a.lv = lv;
+  for (int l = 0; l + 1 < t.nlev; ++l) {
+    const LevelDesc F = lv[l], C = lv[l + 1];
+    tail_smooth(a, F, t.nu1, 1);
+    const int nc = (int)C.ncell;
+    for (int q = threadIdx.x; q < nc; q += blockDim.x)
+      restrict_cell(a, F, C, q % C.nx, (q / C.nx) % C.ny, q / (C.nx * C.ny));
     __syncthreads();
   }
-  tail_smooth(a, a.lv[l_last], bottom_sweeps, 1);
-  for (int l = l_last - 1; l >= l_first; --l) {
-    const LevelDesc F = a.lv[l], C = a.lv[l + 1];
-    for (long long t = threadIdx.x; t < F.ncell; t += blockDim.x) prolong_item(a, F, C, t, constant);
+  tail_smooth(a, lv[t.nlev - 1], t.bottom_sweeps, 1);
+  for (int l = t.nlev - 2; l >= 0; --l) {
+    const LevelDesc F = lv[l], C = lv[l + 1];
+    const int nc = (int)C.ncell;
+    for (int q = threadIdx.x; q < nc; q += blockDim.x)
+      prolong_cell(a, F, C, q % C.nx, (q / C.nx) % C.ny, q / (C.nx * C.ny), t.constant);
     __syncthreads();
-    tail_smooth(a, F, nu2, 0);
+    tail_smooth(a, F, t.nu2, 0);
   }
+  for (int q = threadIdx.x; q < n0; q += blockDim.x) g.e[t.base + q] = se[q];
 }
+
+// ---- FP64 outer residual --------------------------------------------------------------
 
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -225,11 +278,13 @@ __device__ __forceinline__ double warp_sum(double v) {
 // Block sum of three values; result valid in thread 0.
 __device__ __forceinline__ void block_sum3(double& x, double& y, double& z) {
   __shared__ double sh[3][32];
+  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+  const int nthr = blockDim.x * blockDim.y;
   x = warp_sum(x); y = warp_sum(y); z = warp_sum(z);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int w = tid >> 5, l = tid & 31;
   if (l == 0) { sh[0][w] = x; sh[1][w] = y; sh[2][w] = z; }
   __syncthreads();
-  const int nw = (blockDim.x + 31) >> 5;
+  const int nw = (nthr + 31) >> 5;
   if (w == 0) {
     x = l < nw ? sh[0][l] : 0.0;
     y = l < nw ? sh[1][l] : 0.0;
@@ -240,79 +295,85 @@ __device__ __forceinline__ void block_sum3(double& x, double& y, double& z) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kResidThreads) resid_kernel(ResidArgs a) {
+__global__ void __launch_bounds__(kResidBX* kResidBY) resid_kernel(ResidArgs a) {
   const int nx = a.nx, ny = a.ny, nz = a.nz;
+  const int i = blockIdx.x * kResidBX + threadIdx.x;
+  const int j = blockIdx.y * kResidBY + threadIdx.y;
   const long long plane = (long long)nx * ny;
-  const long long total = plane * nz;
-  const double v_bot = a.params->v_bot, v_top = a.params->v_top;
   T* r_out = static_cast<T*>(a.r_out);
   T* s_out = static_cast<T*>(a.s_out);
   double acc_r = 0.0, acc_b = 0.0, acc_rho = 0.0;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(t % nx);
-    const int j = (int)((t / nx) % ny);
-    const int k = (int)(t / plane);
-    const PlaneCoef<double> c = a.coef0[k];
-    const PlaneTDGL& pt = a.planes[k];
+  if (i < nx && j < ny) {
+    const double v_bot = a.params->v_bot, v_top = a.params->v_top;
     const int im = (i == 0) ? nx - 1 : i - 1, ip = (i == nx - 1) ? 0 : i + 1;
-    const int jm = (j == 0) ? ny - 1 : j - 1, jp = (j == ny - 1) ? 0 : j + 1;
+    const long long dxm = im - i, dxp = ip - i;
+    const long long dym = (long long)((j == 0) ? ny - 1 : j - 1) * nx - (long long)j * nx;
+    const long long dyp = (long long)((j == ny - 1) ? 0 : j + 1) * nx - (long long)j * nx;
     const double* phi = a.phi;
-    const double pc = phi[t];
-    const double sx = phi[t - i + im] + phi[t - i + ip];
-    const double sy = phi[t + (long long)(jm - j) * nx] + phi[t + (long long)(jp - j) * nx];
-    const double pd = (k > 0) ? phi[t - plane] : 0.0;
-    const double pu = (k < nz - 1) ? phi[t + plane] : 0.0;
-    double off = c.cx * sx;
-    off = fma(c.cy, sy, off);
-    off = fma(c.czlo, pd, off);
-    off = fma(c.czhi, pu, off);
-    double bb;
-    if (pt.b_dyn) {
-      bb = a.b[t];
-    } else {
-      bb = 0.0;
-      if (k == 0) bb += pt.lift * v_bot;
-      if (k == nz - 1) bb += pt.lift * v_top;
+    const long long col = (long long)j * nx + i;
+    double pd = 0.0, pc = phi[col];
+    for (int k = 0; k < nz; ++k) {
+      const long long t = k * plane + col;
+      const double pu = (k < nz - 1) ? phi[t + plane] : 0.0;
+      const PlaneCoef<double> c = a.coef0[k];
+      const PlaneTDGL& pt = a.planes[k];
+      const double sx = phi[t + dxm] + phi[t + dxp];
+      const double sy = phi[t + dym] + phi[t + dyp];
+      double off = c.cx * sx;
+      off = fma(c.cy, sy, off);
+      off = fma(c.czlo, pd, off);
+      off = fma(c.czhi, pu, off);
+      double bb;
+      if (pt.b_dyn) {
+        bb = a.b[t];
+      } else {
+        bb = 0.0;
+        if (k == 0) bb += pt.lift * v_bot;
+        if (k == nz - 1) bb += pt.lift * v_top;
+      }
+      double rho = 0.0;
+      if (pt.sc) {
+        const double u = pc * pt.inv_vt;
+        const double n = pt.n0 * exp(u);
+        const double p = pt.p0 * exp(-u);
+        rho = pt.kq * (p - n + pt.Nnet);
+        if (s_out) s_out[t] = (T)(pt.kq * (n + p) * pt.inv_vt);
+        acc_rho = fma(rho, rho, acc_rho);
+      }
+      const double r = (bb + rho) - fma(c.diag, pc, -off);
+      r_out[t] = (T)r;
+      acc_r = fma(r, r, acc_r);
+      if (a.first) acc_b = fma(bb, bb, acc_b);
+      pd = pc;
+      pc = pu;
     }
-    double rho = 0.0, sh = 0.0;
-    if (pt.sc) {
-      const double u = pc * pt.inv_vt;
-      const double n = pt.n0 * exp(u);
-      const double p = pt.p0 * exp(-u);
-      rho = pt.kq * (p - n + pt.Nnet);
-      sh = pt.kq * (n + p) * pt.inv_vt;
-    }
-    const double r = (bb + rho) - fma(c.diag, pc, -off);
-    r_out[t] = (T)r;
-    if (s_out && pt.sc) s_out[t] = (T)sh;
-    acc_r = fma(r, r, acc_r);
-    acc_b = fma(bb, bb, acc_b);
-    acc_rho = fma(rho, rho, acc_rho);
   }
   block_sum3(acc_r, acc_b, acc_rho);
   __shared__ bool last;
-  if (threadIdx.x == 0) {
-    a.partials[blockIdx.x] = acc_r;
-    a.partials[gridDim.x + blockIdx.x] = acc_b;
-    a.partials[2 * gridDim.x + blockIdx.x] = acc_rho;
+  const int nblk = gridDim.x * gridDim.y;
+  const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  if (tid == 0) {
+    a.partials[bid] = acc_r;
+    a.partials[nblk + bid] = acc_b;
+    a.partials[2 * nblk + bid] = acc_rho;
     __threadfence();
     const unsigned int prev = atomicAdd(&a.stats->done_ctr, 1u);
-    last = (prev == gridDim.x - 1);
+    last = (prev == (unsigned)nblk - 1);
   }
   __syncthreads();
   if (!last) return;
   __threadfence();
-  // fixed-order sum of the partials: thread t takes blocks t, t+256, ..., then a tree
+  // fixed-order sum of the partials (deterministic)
   double sr = 0.0, sb = 0.0, sq = 0.0;
   const volatile double* P = a.partials;
-  for (int q = threadIdx.x; q < (int)gridDim.x; q += blockDim.x) {
+  for (int q = tid; q < nblk; q += blockDim.x * blockDim.y) {
     sr += P[q];
-    sb += P[gridDim.x + q];
-    sq += P[2 * gridDim.x + q];
+    sb += P[nblk + q];
+    sq += P[2 * nblk + q];
   }
   block_sum3(sr, sb, sq);
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     DevStats* st = a.stats;
     st->done_ctr = 0;
     if (a.first) {
@@ -320,9 +381,10 @@ __global__ void __launch_bounds__(kResidThreads) resid_kernel(ResidArgs a) {
       st->cycles_this_solve = 0;
       st->zero_phi = 0;
       st->launches += 1;
+      st->bnorm2 = sb;          // b is fixed during a solve
     }
     const double rn = sqrt(sr);
-    const double scale = fmax(sqrt(sb), sqrt(sq));
+    const double scale = fmax(sqrt(st->bnorm2), sqrt(sq));
     int cond;
     if (!isfinite(rn) || !isfinite(scale)) {
       if (st->status == 0) st->status = FERROX_ENONFINITE;
@@ -355,69 +417,90 @@ template <typename T>
 __global__ void __launch_bounds__(256) update_kernel(double* __restrict__ phi, const T* __restrict__ e0,
                                                      long long n, const DevStats* stats,
                                                      double clamp) {
-  const bool zero = stats->zero_phi != 0;
+  const Upd u{phi, clamp, stats->zero_phi};
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
-       t += (long long)gridDim.x * blockDim.x) {
-    if (zero) {
-      phi[t] = 0.0;
-    } else {
-      const double d = (double)e0[t];
-      phi[t] += fmin(fmax(d, -clamp), clamp);
-    }
-  }
+       t += (long long)gridDim.x * blockDim.x)
+    apply_update(u, t, e0[t]);
 }
 
-int grid_for(long long work, int threads) {
-  long long b = (work + threads - 1) / threads;
-  const long long cap = 152LL * 16;
-  if (b > cap) b = cap;
-  if (b < 1) b = 1;
-  return (int)b;
+// 2-D block over (x items, rows): x extent a power of two up to 128
+void block_shape(int nxi, int ny, dim3& block, dim3& grid, int nz) {
+  int bx = 1;
+  while (bx < nxi && bx < 128) bx <<= 1;
+  int by = 256 / bx;
+  if (by > ny) { by = 1; while (by < ny) by <<= 1; }
+  block = dim3(bx, by, 1);
+  grid = dim3((nxi + bx - 1) / bx, (ny + by - 1) / by, nz);
 }
 
 }  // namespace
 
 template <typename T>
-void launch_smooth(const MGArgs<T>& a, const LevelDesc& L, int color, int zero_init, cudaStream_t s) {
-  const long long half = (long long)((L.nx + 1) >> 1) * L.ny * L.nz;
-  smooth_kernel<T><<<grid_for(half, 256), 256, 0, s>>>(a, L, color, zero_init);
+void launch_smooth(const MGArgs<T>& a, const LevelDesc& L, int color, int zero_init,
+                   const UpdateArgs* upd, cudaStream_t s) {
+  dim3 block, grid;
+  block_shape((L.nx + 1) >> 1, L.ny, block, grid, L.nz);
+  Upd u{nullptr, 0.0, 0};
+  const DevStats* st = nullptr;
+  if (upd) { u.phi = upd->phi; u.clamp = upd->clamp; st = upd->stats; }
+  smooth_kernel<T><<<grid, block, 0, s>>>(a, L, color, zero_init, u, st);
 }
 
 template <typename T>
 void launch_restrict(const MGArgs<T>& a, const LevelDesc& F, const LevelDesc& C, cudaStream_t s) {
-  restrict_kernel<T><<<grid_for(C.ncell, 256), 256, 0, s>>>(a, F, C);
+  dim3 block, grid;
+  block_shape(C.nx, C.ny, block, grid, C.nz);
+  restrict_kernel<T><<<grid, block, 0, s>>>(a, F, C);
 }
 
 template <typename T>
 void launch_prolong(const MGArgs<T>& a, const LevelDesc& F, const LevelDesc& C, int constant,
                     cudaStream_t s) {
-  prolong_kernel<T><<<grid_for(F.ncell, 256), 256, 0, s>>>(a, F, C, constant);
+  dim3 block, grid;
+  block_shape(C.nx, C.ny, block, grid, C.nz);
+  prolong_kernel<T><<<grid, block, 0, s>>>(a, F, C, constant);
 }
 
 template <typename T>
-void launch_tail(const MGArgs<T>& a, int l_first, int l_last, int nu1, int nu2, int bottom_sweeps,
-                 int constant, cudaStream_t s) {
-  tail_kernel<T><<<1, kTailThreads, 0, s>>>(a, l_first, l_last, nu1, nu2, bottom_sweeps, constant);
+size_t tail_smem_bytes(long long elems, bool has_s) {
+  return (size_t)elems * sizeof(T) * (has_s ? 3 : 2);
+}
+
+template <typename T>
+cudaError_t tail_prepare(size_t smem) {
+  return cudaFuncSetAttribute(tail_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <typename T>
+void launch_tail(const MGArgs<T>& a, const TailArgs& t, size_t smem, cudaStream_t s) {
+  tail_kernel<T><<<1, kTailThreads, smem, s>>>(a, t);
 }
 
 template <typename T>
 void launch_resid(const ResidArgs& a, cudaStream_t s) {
-  resid_kernel<T><<<kResidBlocks, kResidThreads, 0, s>>>(a);
+  dim3 block(kResidBX, kResidBY);
+  dim3 grid((a.nx + kResidBX - 1) / kResidBX, (a.ny + kResidBY - 1) / kResidBY);
+  resid_kernel<T><<<grid, block, 0, s>>>(a);
 }
 
 template <typename T>
 void launch_update(double* phi, const T* e0, long long n, const DevStats* stats, double clamp,
                    cudaStream_t s) {
-  update_kernel<T><<<grid_for(n, 256), 256, 0, s>>>(phi, e0, n, stats, clamp);
+  long long b = (n + 255) / 256;
+  if (b > 152LL * 16) b = 152LL * 16;
+  update_kernel<T><<<(int)b, 256, 0, s>>>(phi, e0, n, stats, clamp);
 }
 
 #define FX_INST(T)                                                                              \
-  template void launch_smooth<T>(const MGArgs<T>&, const LevelDesc&, int, int, cudaStream_t);   \
+  template void launch_smooth<T>(const MGArgs<T>&, const LevelDesc&, int, int,                  \
+                                 const UpdateArgs*, cudaStream_t);                              \
   template void launch_restrict<T>(const MGArgs<T>&, const LevelDesc&, const LevelDesc&,        \
                                    cudaStream_t);                                               \
   template void launch_prolong<T>(const MGArgs<T>&, const LevelDesc&, const LevelDesc&, int,    \
                                   cudaStream_t);                                                \
-  template void launch_tail<T>(const MGArgs<T>&, int, int, int, int, int, int, cudaStream_t);   \
+  template size_t tail_smem_bytes<T>(long long, bool);                                          \
+  template cudaError_t tail_prepare<T>(size_t);                                                 \
+  template void launch_tail<T>(const MGArgs<T>&, const TailArgs&, size_t, cudaStream_t);        \
   template void launch_resid<T>(const ResidArgs&, cudaStream_t);                                \
   template void launch_update<T>(double*, const T*, long long, const DevStats*, double,         \
                                  cudaStream_t);
