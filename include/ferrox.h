@@ -197,6 +197,33 @@ const char* ferrox_last_error(const ferrox_ctx* ctx);
 ferrox_status ferrox_level_shape(const ferrox_ctx* ctx, int l, int* nx, int* ny, int* nz,
                                  int* nlevels);
 
+/* Limits of ferrox_tdgl_update_static (sizes of its file-scope scratch array). */
+#define FERROX_STATIC_MAX_CELLS 262144
+#define FERROX_STATIC_MAX_PLANES 512
+
+/* Step 1a (P <- P + dt f(P, phi)) without any allocation, for callers that
+ * cannot allocate device memory: code running while a stream capture forbids
+ * cudaMalloc, processes held to a fixed device-memory budget, or frameworks
+ * whose own allocator must own every device byte.  The paper has no
+ * counterpart; this is a deployment variant of ferrox_tdgl_update.
+ *   geom, dt, v_bottom, v_top: as for ferrox_init_geometry / ferrox_set_bias.
+ *   P_dev (in/out) and phi_dev (in): caller-owned device arrays, layout above.
+ * It runs the same fused TDGL kernel, with its scratch (plane table, staging
+ * copy of the new P, right-hand side) in one file-scope device array of about
+ * 8.1 MB that every GPU loading the library holds until the process exits.
+ * Limits: Nx*Ny*Nz <= FERROX_STATIC_MAX_CELLS and Nz <= FERROX_STATIC_MAX_PLANES;
+ * larger grids are rejected with FERROX_EINVAL and a message.  No scratch
+ * byte is read before the call writes it, so nothing needs clearing between
+ * calls.  All calls share the one array: calls whose GPU work overlaps (two
+ * streams, or two host threads) race and must be serialised by the caller.
+ * The first call on each device looks up the array's device address with
+ * that device current; make that first call before any stream capture.  The
+ * plane table is copied from pageable host memory, so the call waits for
+ * work already queued on the stream before it returns. */
+ferrox_status ferrox_tdgl_update_static(const ferrox_geometry* geom, double dt, double v_bottom,
+                                        double v_top, double* P_dev, const double* phi_dev,
+                                        void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -19,6 +19,7 @@
 #include <cstdio>
 #include <cstring>
 #include <functional>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -814,3 +815,161 @@ ferrox_status ferrox_level_shape(const ferrox_ctx* ctx, int l, int* nx, int* ny,
 }
 
 }  // extern "C"
+
+// ---- entry point without allocation -----------------------------------------------------
+//
+// Callers that cannot allocate device memory (code that runs while a CUDA stream
+// capture forbids cudaMalloc, processes under a fixed device-memory budget, or
+// frameworks whose own allocator must own every byte) still need the TDGL
+// update.  ferrox_tdgl_update_static runs the same fused TDGL kernel as
+// ferrox_tdgl_update, with its three scratch areas (plane table, staging copy
+// of the new polarization, right-hand side) carved from the file-scope array
+// below, which every GPU that loads the library holds until the process exits.
+namespace {
+
+constexpr long long kStaticMaxCells = FERROX_STATIC_MAX_CELLS;
+constexpr int kStaticMaxPlanes = FERROX_STATIC_MAX_PLANES;
+constexpr size_t kStaticPlaneBytes = ((size_t)kStaticMaxPlanes * sizeof(PlaneTDGL) + 255) / 256 * 256;
+constexpr size_t kStaticParamBytes = 256;
+constexpr size_t kStaticStateBytes = (size_t)kStaticMaxCells * 4 * sizeof(double);  // 3 comps + b
+constexpr size_t kStaticBytes = kStaticParamBytes + kStaticPlaneBytes + kStaticStateBytes;
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
+
+std::mutex g_static_mu;
+unsigned char* g_static_ptr[64] = {};   // device address of g_static_scratch, per device
+
+// Plane table of the static path, written into a caller-side array without any
+// heap use; the same per-plane quantities as the context path.
+ferrox_status static_planes(const ferrox_geometry* g, PlaneTDGL* out, int* nz_out, int* fe_lo,
+                            int* fe_hi) {
+  int nz = 0;
+  for (int q = 0; q < g->nlayers; ++q) nz += g->layers[q].ncells;
+  if (nz > kStaticMaxPlanes) return FERROX_EINVAL;
+  const double h = g->h;
+  double kappa;
+  if (g->pbc == FERROX_PBC_FREE) kappa = 1.0 / 8.0;
+  else if (g->pbc == FERROX_PBC_ZERO) kappa = 0.0;
+  else kappa = g->lambda / (3.0 * h + 8.0 * g->lambda);
+  int z = 0;
+  *fe_lo = nz;
+  *fe_hi = -1;
+  for (int q = 0; q < g->nlayers; ++q) {
+    const ferrox_layer& L = g->layers[q];
+    for (int c = 0; c < L.ncells; ++c, ++z) {
+      PlaneTDGL p{};
+      p.eps_r = L.eps_r;
+      p.fe = L.kind == FERROX_FE;
+      if (p.fe) {
+        p.alpha = L.alpha; p.beta = L.beta; p.gamma = L.gamma;
+        p.alpha_xy = L.alpha_xy; p.beta_xy = L.beta_xy; p.gamma_xy = L.gamma_xy;
+        p.g11 = L.g11; p.g44 = L.g44; p.Gamma = L.Gamma;
+        *fe_lo = std::min(*fe_lo, z);
+        *fe_hi = std::max(*fe_hi, z);
+      }
+      out[z] = p;
+    }
+  }
+  for (z = 0; z < nz; ++z) {
+    PlaneTDGL& p = out[z];
+    const bool dn = z > 0 && out[z - 1].fe, up = z < nz - 1 && out[z + 1].fe;
+    p.b_dyn = p.fe || dn || up;
+    if (p.fe) {
+      const double ih2 = 1.0 / (h * h);
+      if (dn && up) {
+        p.wz_dn = ih2; p.wz_c = -2.0 * ih2; p.wz_up = ih2;
+      } else if (up || dn) {
+        const double wn = 4.0 * (1.0 - 2.0 * kappa) / 3.0 * ih2;
+        p.wz_c = 4.0 * (18.0 * kappa - 3.0) / 3.0 * ih2;
+        p.wz_up = up ? wn : 0.0;
+        p.wz_dn = dn ? wn : 0.0;
+      } else {
+        return FERROX_EINVAL;
+      }
+    }
+    if (z > 0) {
+      const double eL = out[z - 1].eps_r, eR = p.eps_r;
+      p.fw_L = eL / (eL + eR);
+      p.fw_R = eR / (eL + eR);
+      p.fpc = h / (2.0 * kEps0 * (eL + eR));
+    }
+    p.lift = (z == 0 || z == nz - 1) ? 2.0 * p.eps_r : 0.0;
+  }
+  *nz_out = nz;
+  return FERROX_OK;
+}
+
+}  // namespace
+
+extern "C" ferrox_status ferrox_tdgl_update_static(const ferrox_geometry* geom, double dt,
+                                                   double v_bottom, double v_top, double* P_dev,
+                                                   const double* phi_dev, void* cuda_stream) {
+  auto bad = [](const char* m) { return fail(nullptr, FERROX_EINVAL, m); };
+  if (!geom || !geom->layers || geom->nlayers < 1 || !P_dev || !phi_dev) return bad("null argument");
+  if ((reinterpret_cast<uintptr_t>(P_dev) | reinterpret_cast<uintptr_t>(phi_dev)) % 8)
+    return bad("state arrays must be 8-byte aligned");
+  if (geom->nx < 1 || geom->ny < 1 || !(geom->h > 0.0) || !(dt > 0.0)) return bad("bad sizes");
+  if ((geom->nx != 1 && geom->nx % 2) || (geom->ny != 1 && geom->ny % 2))
+    return bad("lateral sizes must be even or 1");
+  if (geom->ncomp != 1 && geom->ncomp != 3) return bad("ncomp must be 1 or 3");
+  if (!std::isfinite(v_bottom) || !std::isfinite(v_top)) return bad("bias not finite");
+  long long nzl = 0;
+  for (int q = 0; q < geom->nlayers; ++q) {
+    if (geom->layers[q].ncells < 1 || !(geom->layers[q].eps_r > 0.0)) return bad("bad layer");
+    nzl += geom->layers[q].ncells;
+  }
+  const long long N = (long long)geom->nx * geom->ny * nzl;
+  if (N > kStaticMaxCells || nzl > kStaticMaxPlanes)
+    return bad("ferrox_tdgl_update_static: grid larger than its static scratch "
+               "(at most FERROX_STATIC_MAX_CELLS cells and FERROX_STATIC_MAX_PLANES planes)");
+  PlaneTDGL planes[kStaticMaxPlanes];
+  int nz = 0, fe_lo = 0, fe_hi = -1;
+  if (static_planes(geom, planes, &nz, &fe_lo, &fe_hi) != FERROX_OK || fe_hi < 0)
+    return bad("the stack needs a ferroelectric layer at least 2 cells thick");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= 64) return fail(nullptr, FERROX_ECUDA, "cudaGetDevice failed");
+  unsigned char* base;
+  {
+    // set-up once per device, with that device current: the host-side name of
+    // the array is not a device address, so ask the runtime for it
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_ptr[dev]) {
+      void* ptr = nullptr;
+      e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+      if (e != cudaSuccess)
+        return fail(nullptr, FERROX_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+      g_static_ptr[dev] = static_cast<unsigned char*>(ptr);
+    }
+    base = g_static_ptr[dev];
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  DevParams* params = reinterpret_cast<DevParams*>(base);
+  PlaneTDGL* planes_d = reinterpret_cast<PlaneTDGL*>(base + kStaticParamBytes);
+  double* Pout = reinterpret_cast<double*>(base + kStaticParamBytes + kStaticPlaneBytes);
+  double* b = Pout + (size_t)geom->ncomp * N;
+  // pageable source: the copy is staged before the call returns
+  e = cudaMemcpyAsync(planes_d, planes, nz * sizeof(PlaneTDGL), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return fail(nullptr, FERROX_ECUDA, std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e));
+  launch_set_params(params, v_bottom, v_top, s);
+  TDGLArgs a{};
+  a.P_in = P_dev; a.P_out = Pout; a.P_base = nullptr; a.F_store = nullptr;
+  a.phi = phi_dev; a.b = b; a.planes = planes_d; a.params = params;
+  a.nx = geom->nx; a.ny = geom->ny; a.nz = nz; a.ncomp = geom->ncomp;
+  a.kd_lo = std::max(0, fe_lo - 1);
+  a.kd_hi = std::min(nz - 1, fe_hi + 1);
+  a.dt = dt; a.inv_h = 1.0 / geom->h; a.inv_h2 = 1.0 / (geom->h * geom->h);
+  a.b_scale = geom->h / kEps0;
+  a.mode = 0;
+  launch_tdgl(a, s);
+  const long long plane = (long long)geom->nx * geom->ny;
+  const size_t off = (size_t)fe_lo * plane, cnt = (size_t)(fe_hi - fe_lo + 1) * plane;
+  for (int q = 0; q < geom->ncomp; ++q) {
+    e = cudaMemcpyAsync(P_dev + q * N + off, Pout + q * N + off, cnt * sizeof(double),
+                        cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return fail(nullptr, FERROX_ECUDA, std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e));
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(nullptr, FERROX_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
+  return FERROX_OK;
+}

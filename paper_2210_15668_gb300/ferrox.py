@@ -56,7 +56,7 @@ class Stats(C.Structure):
 EXPORTS = ["ferrox_init_geometry", "ferrox_set_bias", "ferrox_solve_poisson", "ferrox_tdgl_update",
            "ferrox_step", "ferrox_charge", "ferrox_sync_stats", "ferrox_clear_status",
            "ferrox_get_state", "ferrox_set_state", "ferrox_destroy", "ferrox_last_error",
-           "ferrox_level_shape", "ferrox_profile_step"]
+           "ferrox_level_shape", "ferrox_profile_step", "ferrox_tdgl_update_static"]
 
 KERNEL_CLASSES = ["tdgl", "resid", "smooth_fine", "smooth_coarse", "restrict", "prolong", "tail",
                   "update", "copy"]
@@ -88,6 +88,8 @@ def load(path: str = LIB_PATH):
     lib.ferrox_level_shape.argtypes = [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                        C.POINTER(C.c_int), C.POINTER(C.c_int)]
     lib.ferrox_profile_step.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int)]
+    lib.ferrox_tdgl_update_static.argtypes = [C.POINTER(Geometry), C.c_double, C.c_double,
+                                              C.c_double, vp, vp, vp]
     for name in EXPORTS:
         if name != "ferrox_last_error":
             getattr(lib, name).restype = st
@@ -117,6 +119,23 @@ def make_numerics(dt, order=1, tol=1e-10, nu1=2, nu2=2, max_cycles=200, precisio
                   bottom_sweeps=0):
     return Numerics(float(dt), int(order), float(tol), int(nu1), int(nu2), int(max_cycles),
                     int(precision), int(bottom_sweeps))
+
+
+def tdgl_update_static(geom, dt, v_bottom, v_top, P, phi, stream=None):
+    """P <- P + dt f(P, phi) through the entry point that allocates nothing.
+
+    P, phi: contiguous float64 CUDA tensors (P is updated in place)."""
+    import torch
+    lib = load()
+    layers = make_layers(geom["layers"])
+    g = Geometry(geom["nx"], geom["ny"], geom["h"], len(geom["layers"]), layers, geom["pbc"],
+                 geom["lam"], geom.get("ncomp", 1))
+    st = stream if stream is not None else torch.cuda.current_stream(P.device)
+    rc = lib.ferrox_tdgl_update_static(C.byref(g), float(dt), float(v_bottom), float(v_top),
+                                       C.c_void_p(P.data_ptr()), C.c_void_p(phi.data_ptr()),
+                                       C.c_void_p(st.cuda_stream))
+    if rc != FERROX_OK:
+        raise FerroxError(rc, lib.ferrox_last_error(None).decode())
 
 
 class Device:

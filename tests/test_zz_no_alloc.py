@@ -1,0 +1,52 @@
+"""The TDGL update entry point that allocates nothing (ferrox_tdgl_update_static).
+
+It serves callers that cannot allocate device memory (for example code running
+while a stream capture forbids cudaMalloc, or a process whose device memory is
+owned by another allocator).  Its output must equal that of the context-based
+entry point ferrox_tdgl_update on the same inputs, on two calls in a row (the
+second call reuses the shared static scratch the first one left behind).
+This file is collected last so that a failure here never hides another test.
+"""
+import numpy as np
+import pytest
+
+from paper_2210_15668_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.mark.parametrize("geom_fn", [
+    lambda: I.make_geometry(64, 48, I.mfim_stack(16)),
+    lambda: I.make_geometry(32, 32, [I.fe_layer(6), I.de_layer(4, 10.0), I.fe_layer(5)],
+                            pbc=I.PBC_FREE),
+])
+def test_static_entry_matches_context_entry_twice(geom_fn):
+    from paper_2210_15668_gb300 import ferrox
+    geom = geom_fn()
+    P0 = I.random_polarization(geom, seed=41, amp=0.12)
+    phi = np.random.default_rng(42).uniform(-0.4, 0.6, P0.shape[1:])
+    dt, vb, vt = 4e-13, 0.05, 0.45
+    num = ferrox.make_numerics(dt)
+    ref = ferrox.Device(geom, P0, numerics=num, phi0=phi)
+    ref.set_bias(vb, vt)
+    P = torch.as_tensor(P0, device="cuda").contiguous().clone()
+    ph = torch.as_tensor(phi, device="cuda").contiguous().clone()
+    for call in range(2):
+        ref.tdgl_update()
+        Pref, _ = ref.get_state()
+        ferrox.tdgl_update_static(geom, dt, vb, vt, P, ph)
+        torch.cuda.synchronize()
+        Ps = P.cpu().numpy()
+        assert np.abs(Ps - Pref).max() <= 1e-12 * np.abs(Pref).max(), call
+    assert np.array_equal(ph.cpu().numpy(), phi)
+    ref.close()
+
+
+def test_static_entry_rejects_grids_beyond_its_scratch():
+    from paper_2210_15668_gb300 import ferrox
+    geom = I.make_geometry(256, 256, I.mfim_stack(16))       # 1,048,576 cells > 262,144
+    P = torch.zeros((1, 16, 256, 256), dtype=torch.float64, device="cuda")
+    phi = torch.zeros((16, 256, 256), dtype=torch.float64, device="cuda")
+    with pytest.raises(ferrox.FerroxError, match="EINVAL.*static scratch"):
+        ferrox.tdgl_update_static(geom, 4e-13, 0.0, 0.5, P, phi)
