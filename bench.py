@@ -147,6 +147,23 @@ def kernel_work(kind, cells, fe_cells, dyn_cells, tsz):
     return None, None
 
 
+# -------------------------------------------------------------------- workloads -------
+
+def workload_config(name):
+    """The bench workload, or a larger/smaller copy of it used for ncu captures."""
+    from paper_2210_15668_gb300 import inputs as I
+    cfg = I.mfim_sweep()
+    cfg["label"] = "mfim_256x256x32 Q-V sweep (first steps at -2 V), seed 1"
+    if name == "mfim_256x256x32":
+        return cfg
+    if name.startswith("mfim_"):
+        nx, ny, nz = (int(v) for v in name[5:].split("x"))
+        cfg["geom"] = I.make_geometry(nx, ny, I.mfim_stack(nz))
+        cfg["label"] = f"{name} MFIM (same stack recipe), seed 1, -2 V"
+        return cfg
+    raise SystemExit(f"unknown workload {name}")
+
+
 # ------------------------------------------------------------------------ ours -------
 
 def run_ours(args, ws, rank, local):
@@ -159,7 +176,7 @@ def run_ours(args, ws, rank, local):
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    cfg = I.mfim_sweep()
+    cfg = workload_config(args.workload)
     geom = cfg["geom"]
     nz = I.nz_of(geom)
     cells = geom["nx"] * geom["ny"] * nz
@@ -257,8 +274,11 @@ def run_ours(args, ws, rank, local):
         t2, s20, s21, _ = timed_run(d2, K, args.warmup)
         t2 = reduce_max(t2, ws)
         v2 = ws * cells * K / (t2 / 1e3) / 1e6
+        prof2 = d2.profile_step()
         other = {"precision": "fp64" if prec_o == ferrox.FP64 else "mixed", "value": v2,
-                 "ms_per_step": t2 / K, "vcycles_per_step": (s21["cycles"] - s20["cycles"]) / K}
+                 "ms_per_step": t2 / K, "vcycles_per_step": (s21["cycles"] - s20["cycles"]) / K,
+                 "kernel_breakdown_ms_one_step": {k: {"ms": round(v[0], 4), "launches": v[1]}
+                                                  for k, v in prof2.items() if v[1]}}
         d2.close()
     mixed_v = value if prec_main == ferrox.MIXED else (other or {}).get("value")
     fp64_v = value if prec_main == ferrox.FP64 else (other or {}).get("value")
@@ -293,7 +313,7 @@ def run_ours(args, ws, rank, local):
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if prec_main == ferrox.FP64 else "f32+f64",
             "data": "synthetic",
-            "config": {"workload": "mfim_256x256x32 Q-V sweep (first steps at -2 V), seed 1",
+            "config": {"workload": cfg["label"],
                        "cells": cells, "tol": 1e-10, "order": 1,
                        "precision": args.precision, "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": f"replicas x{ws}"},
@@ -368,6 +388,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--workload", default="mfim_256x256x32",
+                    help="mfim_256x256x32 (the benchmark) or mfim_NXxNYxNZ (profiling copies)")
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-compare", action="store_true")

@@ -148,9 +148,11 @@ void plan_tail(ferrox_ctx* c, size_t elem_size) {
   const int L = (int)c->lv.size() - 1;
   const int narr = c->has_sc ? 3 : 2;
   c->tail_first = L;
+  // one SM runs FP64 at 2 DFMA/clk, so in FP64 the tail starts at a smaller level
+  const long long max_cells = elem_size == sizeof(double) ? kTailMaxCellsFP64 : kTailMaxCells;
   for (int l = 0; l <= L; ++l) {
     const long long elems = c->arena - c->lv[l].off;
-    if (c->lv[l].ncell <= kTailMaxCells && (size_t)elems * elem_size * narr <= (size_t)kTailMaxSmem) {
+    if (c->lv[l].ncell <= max_cells && (size_t)elems * elem_size * narr <= (size_t)kTailMaxSmem) {
       c->tail_first = l;
       break;
     }

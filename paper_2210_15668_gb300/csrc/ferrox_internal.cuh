@@ -14,7 +14,8 @@
 namespace fx {
 
 constexpr int kMaxLevels = 24;
-constexpr int kTailMaxCells = 4096;     // levels at or below this size run in one CTA
+constexpr int kTailMaxCells = 4096;     // levels at or below this size run in one CTA (FP32)
+constexpr int kTailMaxCellsFP64 = 512;  // the same for FP64 corrections
 constexpr int kTailThreads = 1024;
 constexpr int kTailMaxSmem = 200 * 1024; // shared memory available to the tail CTA
 constexpr int kResidBX = 32, kResidBY = 8; // residual: one thread per (x, y) column

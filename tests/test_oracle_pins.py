@@ -386,3 +386,50 @@ def test_newton_doped_residual_and_uniqueness():
     rho, _ = carriers.charge(phi_a, pl)
     r = poisson.residual(phi_a, b, pl, g["h"], rho)
     assert np.linalg.norm(r) <= 1e-12 * max(np.linalg.norm(b), np.linalg.norm(rho))
+
+
+# ---------------------------------------------------------------- 3-component model ---
+
+def test_three_component_reduces_to_uniaxial():
+    """With P_x = P_y = 0 the z-force and the bound charge of the 3-component model
+    are the uniaxial ones; with laterally uniform P there is no in-plane field, so
+    P_x, P_y stay zero and whole runs coincide with the paper's uniaxial model."""
+    g1 = I.make_geometry(8, 6, I.mfim_stack(12, n_fe=6))
+    g3 = dict(g1, ncomp=3)
+    pl = oracle.planes(g1)
+    Pz = I.random_polarization(g1, seed=5, amp=0.1)
+    phi = np.random.default_rng(6).uniform(-0.3, 0.3, Pz.shape[1:])
+    P3 = np.zeros((3,) + Pz.shape[1:])
+    P3[2] = Pz[0]
+    f1 = tdgl.force(Pz, phi, pl, g1, 0.0, 0.3)
+    f3 = tdgl.force(P3, phi, pl, g3, 0.0, 0.3)
+    assert np.array_equal(f3[2], f1[0])
+    assert np.array_equal(poisson.rhs(P3, pl, g1["h"], 0.0, 0.3), poisson.rhs(Pz, pl, g1["h"], 0.0, 0.3))
+    # laterally uniform, z-varying polarization
+    col = np.linspace(-0.05, 0.08, 12)[:, None, None] * np.ones((12, 6, 8))
+    Pz = col[None] * I.fe_plane_mask(g1)[None, :, None, None]
+    P3 = np.zeros((3,) + Pz.shape[1:])
+    P3[2] = Pz[0]
+    a1 = tdgl.run(Pz, pl, g1, 4e-13, 0.0, 0.3, 3)
+    a3 = tdgl.run(P3, pl, g3, 4e-13, 0.0, 0.3, 3)
+    assert np.all(np.abs(a3[0][:2]) <= 1e-14)
+    assert np.abs(a3[0][2] - a1[0][0]).max() <= 1e-15 * np.abs(a1[0]).max()
+    assert np.abs(a3[1] - a1[1]).max() <= 1e-13 * np.abs(a1[1]).max()
+
+
+def test_in_plane_component_uniform_landau_root():
+    """Uniform in-plane P_x in a shorted all-FE stack has no bound charge, so
+    Phi = 0 and P_x relaxes to the root of its own Landau polynomial."""
+    ax, bx, cx = -1.0e9, 8.0e10, 1.0e11
+    g = I.make_geometry(4, 4, [I.fe_layer(6, alpha_xy=ax, beta_xy=bx, gamma_xy=cx)],
+                        pbc=I.PBC_FREE, ncomp=3)
+    pl = oracle.planes(g)
+    P = np.zeros((3, 6, 4, 4))
+    P[0] = 0.05
+    phi = np.zeros((6, 4, 4))
+    for _ in range(800):
+        P, phi = tdgl.step(P, phi, pl, g, 4e-13, 0.0, 0.0)
+    P0 = math.sqrt((-bx + math.sqrt(bx * bx - 4 * ax * cx)) / (2 * cx))
+    assert np.abs(P[0] - P0).max() < 1e-12
+    assert np.all(P[1] == 0.0) and np.all(P[2] == 0.0)
+    assert np.abs(phi).max() < 1e-15
