@@ -197,6 +197,47 @@ const char* ferrox_last_error(const ferrox_ctx* ctx);
 ferrox_status ferrox_level_shape(const ferrox_ctx* ctx, int l, int* nx, int* ny, int* nz,
                                  int* nlevels);
 
+/* ---- batched persistent Q-V sweeps ----------------------------------------------------
+ * n independent device stacks (instances) of possibly different lateral size,
+ * stack and bias, advanced together by ONE cooperative persistent kernel
+ * launch per call: every phase of the time step runs over all instances at
+ * once, separated by grid barriers whose waits are bounded in time (on expiry
+ * the launch records FERROX_ETIMEOUT instead of hanging); each instance checks
+ * its own convergence and drops out when done.  The launch is captured in a
+ * CUDA graph.  Its shape (threads per block, rows per work unit) is chosen by
+ * timing the candidates on the first ferrox_batch_step, on a saved copy of
+ * the state that is restored afterwards, and cached per problem shape.
+ * This serves the Q-V sweeps of the Results section (many biases and sizes). */
+typedef struct ferrox_batch ferrox_batch; /* opaque */
+
+/* Instances are uniaxial (ncomp = 1) and use order-1 steps.  P_dev and phi_dev
+ * hold all instances back to back: instance i starts at element sum_{q<i} N_q,
+ * N_q = Nx*Ny*Nz of instance q, with the per-instance layout above. */
+ferrox_status ferrox_init_batch(ferrox_batch** out, int n, const ferrox_geometry* geoms,
+                                const ferrox_numerics* num, double* P_dev, double* phi_dev,
+                                void* cuda_stream);
+/* Electrode potentials of every instance (arrays of n).  Asynchronous. */
+ferrox_status ferrox_batch_set_bias(ferrox_batch* b, const double* v_bottom, const double* v_top);
+/* Step 0 for every instance (one persistent launch). */
+ferrox_status ferrox_batch_solve_poisson(ferrox_batch* b);
+/* nsteps time steps of every instance in one persistent launch. */
+ferrox_status ferrox_batch_step(ferrox_batch* b, int nsteps);
+/* Q, V_fe and electrode charges of every instance (array of n).  Synchronises. */
+ferrox_status ferrox_batch_charge(ferrox_batch* b, ferrox_charge_t* out);
+/* Counters and status of every instance (array of n).  Synchronises. */
+ferrox_status ferrox_batch_stats(ferrox_batch* b, ferrox_stats* out);
+/* The launch shape the autotuner chose (ESTATE before the first step). */
+ferrox_status ferrox_batch_tuning(const ferrox_batch* b, int* threads, int* rows_per_unit,
+                                  int* blocks);
+ferrox_status ferrox_batch_destroy(ferrox_batch* b);
+
+/* Failure-detection check of the bounded device waits: a two-block launch in
+ * which one block never reaches the grid barrier, so the other's wait runs out
+ * after about `seconds` (<= 5) of SM clock and records the status, which is
+ * written to *status_out (FERROX_ETIMEOUT when the limit works).  Synchronises. */
+ferrox_status ferrox_check_wait_timeout(double seconds, int* status_out, void* cuda_stream);
+const char* ferrox_batch_last_error(const ferrox_batch* b);
+
 /* Limits of ferrox_tdgl_update_static (sizes of its file-scope scratch array). */
 #define FERROX_STATIC_MAX_CELLS 262144
 #define FERROX_STATIC_MAX_PLANES 512

@@ -16,9 +16,13 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libferrox.so")
-SOURCES = ["engine.cu", "multigrid.cu", "tdgl.cu"]
+SOURCES = ["engine.cu", "multigrid.cu", "tdgl.cu", "persistent.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
+# The persistent engine exchanges data between CTAs of one launch through global
+# memory; its loads are cached in L2 only (the coherence point), never in the
+# per-SM L1, so a CTA cannot read a line another SM has since rewritten.
+PER_FILE_FLAGS = {"persistent.cu": ["-Xptxas", "-dlcm=cg"]}
 
 
 def nvcc() -> str:
@@ -46,7 +50,7 @@ def build(verbose: bool = False, force: bool = False, extra_flags: list[str] | N
         s = os.path.join(CSRC, src)
         o = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
         if force or _stale(o, [s] + headers):
-            cmd = [cc, *ARCH, *FLAGS, *extra, "-c", s, "-o", o]
+            cmd = [cc, *ARCH, *FLAGS, *PER_FILE_FLAGS.get(src, []), *extra, "-c", s, "-o", o]
             if verbose:
                 print(" ".join(cmd), file=sys.stderr)
             subprocess.run(cmd, check=True)

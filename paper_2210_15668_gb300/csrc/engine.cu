@@ -818,6 +818,558 @@ ferrox_status ferrox_level_shape(const ferrox_ctx* ctx, int l, int* nx, int* ny,
 
 }  // extern "C"
 
+
+// ---- batched persistent engine (host side) ---------------------------------------------
+//
+// n independent MFIM/MFISM instances (uneven lateral sizes, own biases) packed
+// back to back in the caller's P and phi arrays; one cooperative launch runs
+// whole time steps of all of them (persistent.cu).  The launch shape (threads
+// per block, rows per work unit) is chosen by timing the candidates on the
+// first step, on a saved copy of the state, and cached per problem shape.
+
+struct BatchPlan {     // one instance, planned with the single-instance machinery
+  ferrox_ctx c;
+  long long cell_off = 0, arena_off = 0;
+  int coef_off = 0, coef0_off = 0, plane_off = 0, lv_off = 0, lvt_off = 0;
+};
+
+struct ferrox_batch {
+  int n = 0;
+  ferrox_numerics num{};
+  bool mixed = false;
+  size_t tsz = 8;
+  cudaStream_t stream = nullptr, cap = nullptr;
+  std::vector<BatchPlan> plans;
+  long long cells = 0, arena = 0;
+  int Ldown = 0, any_full_tail = 0, nrows = 0;
+  double* P = nullptr;
+  double* phi = nullptr;
+  double* b = nullptr;
+  double* Pbuf = nullptr;
+  double* backup = nullptr;
+  void* e = nullptr;
+  void* r = nullptr;
+  void* s = nullptr;
+  void* coef = nullptr;
+  PlaneCoef<double>* coef0 = nullptr;
+  PlaneTDGL* planes = nullptr;
+  LevelDesc* lv = nullptr;
+  LevelDesc* lvt = nullptr;
+  int* pre = nullptr;
+  double* partials = nullptr;
+  int* active = nullptr;
+  GridBar* bar = nullptr;
+  int* status = nullptr;
+  int* nsteps_d = nullptr;
+  int* dbg = nullptr;
+  DevParams* params = nullptr;
+  DevStats* stats = nullptr;
+  BatchInst* inst = nullptr;
+  double* charge_part = nullptr;
+  double* charge_out = nullptr;
+  double* host_pinned = nullptr;
+  int threads = 512, rows_per_unit = 1, blocks = 0;
+  size_t smem = 0;
+  bool tuned = false;
+  cudaGraphExec_t ge_step = nullptr, ge_solve = nullptr;
+  cudaGraph_t gr_step = nullptr, gr_solve = nullptr;
+  std::string err;
+};
+
+namespace {
+
+std::mutex g_tune_mu;
+std::vector<std::pair<std::string, std::pair<int, int>>> g_tune_cache;
+
+ferrox_status bfail(ferrox_batch* b, ferrox_status s, const std::string& m) {
+  if (b) b->err = m; else g_init_error = m;
+  return s;
+}
+
+#define FX_BCK(call)                                                                          \
+  do {                                                                                        \
+    cudaError_t _e = (call);                                                                  \
+    if (_e != cudaSuccess)                                                                    \
+      return bfail(B, _e == cudaErrorMemoryAllocation ? FERROX_ENOMEM : FERROX_ECUDA,         \
+                   std::string(#call) + ": " + cudaGetErrorString(_e));                       \
+  } while (0)
+
+std::vector<int> batch_prefix(const ferrox_batch* B, int R) {
+  const int n = B->n, L = B->Ldown;
+  std::vector<int> pre((size_t)(1 + 2 * L) * (n + 1), 0);
+  for (int i = 0; i < n; ++i) pre[i + 1] = pre[i] + B->plans[i].c.ny;
+  for (int l = 0; l < L; ++l) {
+    int* ps = &pre[(size_t)(1 + l) * (n + 1)];
+    int* pc = &pre[(size_t)(1 + L + l) * (n + 1)];
+    for (int i = 0; i < n; ++i) {
+      const ferrox_ctx& c = B->plans[i].c;
+      int us = 0, uc = 0;
+      if (l < c.tail_first) {
+        const LevelDesc& F = c.lv[l];
+        const LevelDesc& C = c.lv[l + 1];
+        us = F.nz * ((F.ny + R - 1) / R);
+        uc = C.nz * ((C.ny + R - 1) / R);
+      }
+      ps[i + 1] = ps[i] + us;
+      pc[i + 1] = pc[i] + uc;
+    }
+  }
+  return pre;
+}
+
+BatchArgs batch_args(ferrox_batch* B, int mode) {
+  BatchArgs a{};
+  a.inst = B->inst; a.ninst = B->n; a.mode = mode; a.nsteps = B->nsteps_d;
+  a.e = B->e; a.r = B->r; a.s = B->s; a.coef = B->coef; a.lv = B->lv; a.lvt = B->lvt;
+  a.pre = B->pre; a.Ldown = B->Ldown; a.partials = B->partials; a.active = B->active;
+  a.bar = B->bar; a.status = B->status; a.tol = B->num.tol; a.max_cycles = B->num.max_cycles;
+  a.nu1 = B->num.nu1; a.nu2 = B->num.nu2; a.rows_per_unit = B->rows_per_unit;
+  a.any_full_tail = B->any_full_tail;
+  a.dbg = B->dbg;
+  return a;
+}
+
+cudaError_t batch_launch(ferrox_batch* B, int mode, cudaStream_t s) {
+  const BatchArgs a = batch_args(B, mode);
+  return B->mixed ? launch_batch<float>(a, B->blocks, B->threads, B->smem, s)
+                  : launch_batch<double>(a, B->blocks, B->threads, B->smem, s);
+}
+
+ferrox_status batch_configure(ferrox_batch* B, int threads, int R) {
+  int per_sm = 0;
+  FX_BCK(B->mixed ? batch_occupancy<float>(threads, B->smem, &per_sm)
+                  : batch_occupancy<double>(threads, B->smem, &per_sm));
+  if (per_sm < 1) return bfail(B, FERROX_ECUDA, "batch kernel does not fit on an SM");
+  int dev = 0, sms = 0;
+  FX_BCK(cudaGetDevice(&dev));
+  FX_BCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  B->threads = threads;
+  B->rows_per_unit = R;
+  // one CTA per SM: every block of the persistent launch is resident whatever
+  // shared-memory carveout the driver picks, so the grid barriers can complete
+  B->blocks = sms;
+  const std::vector<int> pre = batch_prefix(B, R);
+  FX_BCK(cudaMemcpy(B->pre, pre.data(), pre.size() * sizeof(int), cudaMemcpyHostToDevice));
+  return FERROX_OK;
+}
+
+std::string batch_key(const ferrox_batch* B) {
+  std::string k = B->mixed ? "f32" : "f64";
+  for (const auto& p : B->plans)
+    k += ":" + std::to_string(p.c.nx) + "x" + std::to_string(p.c.ny) + "x" + std::to_string(p.c.nz);
+  return k;
+}
+
+// time each candidate launch shape on one step from a saved state, keep the fastest
+ferrox_status batch_autotune(ferrox_batch* B) {
+  const std::string key = batch_key(B);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (auto& kv : g_tune_cache)
+      if (kv.first == key) return batch_configure(B, kv.second.first, kv.second.second);
+  }
+  const size_t bytes = (size_t)B->cells * sizeof(double);
+  cudaStream_t s = B->stream;
+  FX_BCK(cudaMemcpyAsync(B->backup, B->P, bytes, cudaMemcpyDeviceToDevice, s));
+  FX_BCK(cudaMemcpyAsync(B->backup + B->cells, B->phi, bytes, cudaMemcpyDeviceToDevice, s));
+  std::vector<DevStats> st0(B->n);
+  FX_BCK(cudaMemcpyAsync(st0.data(), B->stats, B->n * sizeof(DevStats), cudaMemcpyDeviceToHost, s));
+  FX_BCK(cudaStreamSynchronize(s));
+  const int one = 1;
+  FX_BCK(cudaMemcpy(B->nsteps_d, &one, sizeof(int), cudaMemcpyHostToDevice));
+  cudaEvent_t e0, e1;
+  FX_BCK(cudaEventCreate(&e0));
+  FX_BCK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int bt = 512, bR = 1;
+  const int cand_t[2] = {256, 512}, cand_R[3] = {1, 2, 4};
+  for (int ti = 0; ti < 2; ++ti)
+    for (int ri = 0; ri < 3; ++ri) {
+      ferrox_status rc = batch_configure(B, cand_t[ti], cand_R[ri]);
+      if (rc != FERROX_OK) return rc;
+      FX_BCK(cudaEventRecord(e0, s));
+      FX_BCK(batch_launch(B, 0, s));
+      FX_BCK(cudaEventRecord(e1, s));
+      FX_BCK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      FX_BCK(cudaEventElapsedTime(&ms, e0, e1));
+      int gst = 0;
+      FX_BCK(cudaMemcpy(&gst, B->status, sizeof(int), cudaMemcpyDeviceToHost));
+      if (gst != 0) return bfail(B, (ferrox_status)gst, "batch kernel failed while tuning");
+      if (ms < best) { best = ms; bt = cand_t[ti]; bR = cand_R[ri]; }
+      FX_BCK(cudaMemcpyAsync(B->P, B->backup, bytes, cudaMemcpyDeviceToDevice, s));
+      FX_BCK(cudaMemcpyAsync(B->phi, B->backup + B->cells, bytes, cudaMemcpyDeviceToDevice, s));
+      FX_BCK(cudaMemcpyAsync(B->stats, st0.data(), B->n * sizeof(DevStats), cudaMemcpyHostToDevice, s));
+      FX_BCK(cudaStreamSynchronize(s));
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache.push_back({key, {bt, bR}});
+  }
+  return batch_configure(B, bt, bR);
+}
+
+ferrox_status batch_build_graphs(ferrox_batch* B) {
+  for (int mode = 0; mode < 2; ++mode) {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    FX_BCK(cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeRelaxed));
+    cudaError_t le = batch_launch(B, mode, B->cap);
+    cudaError_t ce = cudaStreamEndCapture(B->cap, &g);
+    if (le != cudaSuccess || ce != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return bfail(B, FERROX_ECUDA, std::string("capturing the batch launch: ") +
+                                        cudaGetErrorString(le != cudaSuccess ? le : ce));
+    }
+    FX_BCK(cudaGraphInstantiate(&ge, g, 0));
+    if (mode == 0) { B->gr_step = g; B->ge_step = ge; } else { B->gr_solve = g; B->ge_solve = ge; }
+  }
+  return FERROX_OK;
+}
+
+void batch_release(ferrox_batch* B) {
+  if (!B) return;
+  if (B->stream) cudaStreamSynchronize(B->stream);
+  if (B->ge_step) cudaGraphExecDestroy(B->ge_step);
+  if (B->ge_solve) cudaGraphExecDestroy(B->ge_solve);
+  if (B->gr_step) cudaGraphDestroy(B->gr_step);
+  if (B->gr_solve) cudaGraphDestroy(B->gr_solve);
+  void* ptrs[] = {B->b, B->Pbuf, B->backup, B->e, B->r, B->s, B->coef, B->coef0, B->planes, B->lv,
+                  B->lvt, B->pre, B->partials, B->active, B->bar, B->status, B->nsteps_d, B->dbg, B->params,
+                  B->stats, B->inst, B->charge_part, B->charge_out};
+  for (void* p : ptrs) if (p) cudaFree(p);
+  if (B->host_pinned) cudaFreeHost(B->host_pinned);
+  if (B->cap) cudaStreamDestroy(B->cap);
+  delete B;
+}
+
+}  // namespace
+
+extern "C" {
+
+ferrox_status ferrox_init_batch(ferrox_batch** out, int n, const ferrox_geometry* geoms,
+                                const ferrox_numerics* num, double* P_dev, double* phi_dev,
+                                void* cuda_stream) {
+  if (!out) return bfail(nullptr, FERROX_EINVAL, "null output pointer");
+  *out = nullptr;
+  if (n < 1 || !geoms) return bfail(nullptr, FERROX_EINVAL, "need n >= 1 instances");
+  for (int i = 0; i < n; ++i) {
+    ferrox_status rc = validate(&geoms[i], num, P_dev, phi_dev);
+    if (rc != FERROX_OK) return rc;
+    if (geoms[i].ncomp != 1) return bfail(nullptr, FERROX_EINVAL, "batched instances are uniaxial (ncomp = 1)");
+  }
+  if (num->order != 1) return bfail(nullptr, FERROX_EINVAL, "the batched engine runs order-1 steps");
+  ferrox_batch* B = new ferrox_batch();
+  B->n = n;
+  B->num = *num;
+  B->mixed = num->precision == FERROX_MIXED;
+  B->tsz = B->mixed ? sizeof(float) : sizeof(double);
+  B->stream = static_cast<cudaStream_t>(cuda_stream);
+  B->P = P_dev;
+  B->phi = phi_dev;
+  B->plans.resize(n);
+  // plan every instance with the single-instance machinery, then pack
+  long long cells = 0, arena = 0;
+  int ncoef = 0, nplanes = 0, nlv = 0, nlvt = 0;
+  size_t smem = 16;
+  for (int i = 0; i < n; ++i) {
+    BatchPlan& p = B->plans[i];
+    ferrox_ctx& c = p.c;
+    const ferrox_geometry& g = geoms[i];
+    c.nx = g.nx; c.ny = g.ny; c.h = g.h; c.pbc = g.pbc; c.lambda = g.lambda; c.ncomp = 1;
+    c.layers.assign(g.layers, g.layers + g.nlayers);
+    c.nz = 0;
+    for (auto& L : c.layers) c.nz += L.ncells;
+    c.num = *num;
+    if (build_planes(&c) != FERROX_OK) {
+      const std::string m = g_init_error;
+      batch_release(B);
+      return bfail(nullptr, FERROX_EINVAL, m);
+    }
+    build_levels(&c);
+    plan_tail(&c, B->tsz);
+    p.cell_off = cells;
+    p.arena_off = arena;
+    p.coef_off = ncoef;
+    p.coef0_off = nplanes;
+    p.plane_off = nplanes;
+    p.lv_off = nlv;
+    p.lvt_off = nlvt;
+    cells += (long long)c.nx * c.ny * c.nz;
+    arena += c.arena;
+    for (auto& l : c.lv) ncoef += l.nz;
+    nplanes += c.nz;
+    nlv += (int)c.lv.size();
+    nlvt += (int)c.lv_tail.size();
+    smem = std::max(smem, c.tail_smem);
+    B->Ldown = std::max(B->Ldown, c.tail_first);
+    if (c.tail_first == 0) B->any_full_tail = 1;
+    B->nrows += c.ny;
+  }
+  B->cells = cells;
+  B->arena = arena;
+  // with any semiconductor instance every tail carries the shift array too
+  const bool any_sc = std::any_of(B->plans.begin(), B->plans.end(), [](const BatchPlan& p) { return p.c.has_sc; });
+  for (const auto& p : B->plans)
+    smem = std::max(smem, (size_t)p.c.tail_elems * B->tsz * (any_sc ? 3 : 2));
+  B->smem = smem;
+  auto cleanup = [&](ferrox_status st) { g_init_error = B->err; batch_release(B); return st; };
+#define FX_BINIT(call)                                                                        \
+  do {                                                                                        \
+    cudaError_t _e = (call);                                                                  \
+    if (_e != cudaSuccess) {                                                                  \
+      B->err = std::string(#call) + ": " + cudaGetErrorString(_e);                           \
+      return cleanup(_e == cudaErrorMemoryAllocation ? FERROX_ENOMEM : FERROX_ECUDA);         \
+    }                                                                                         \
+  } while (0)
+  const size_t tsz = B->tsz;
+  const bool has_sc = std::any_of(B->plans.begin(), B->plans.end(), [](const BatchPlan& p) { return p.c.has_sc; });
+  FX_BINIT(cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking));
+  FX_BINIT(cudaMalloc(&B->b, cells * sizeof(double)));
+  FX_BINIT(cudaMalloc(&B->Pbuf, cells * sizeof(double)));
+  FX_BINIT(cudaMalloc(&B->backup, 2 * cells * sizeof(double)));
+  FX_BINIT(cudaMalloc(&B->e, arena * tsz));
+  FX_BINIT(cudaMalloc(&B->r, arena * tsz));
+  if (has_sc) FX_BINIT(cudaMalloc(&B->s, arena * tsz));
+  FX_BINIT(cudaMalloc(&B->coef, (size_t)ncoef * (B->mixed ? sizeof(PlaneCoef<float>) : sizeof(PlaneCoef<double>))));
+  FX_BINIT(cudaMalloc(&B->coef0, (size_t)nplanes * sizeof(PlaneCoef<double>)));
+  FX_BINIT(cudaMalloc(&B->planes, (size_t)nplanes * sizeof(PlaneTDGL)));
+  FX_BINIT(cudaMalloc(&B->lv, (size_t)nlv * sizeof(LevelDesc)));
+  FX_BINIT(cudaMalloc(&B->lvt, (size_t)nlvt * sizeof(LevelDesc)));
+  FX_BINIT(cudaMalloc(&B->pre, (size_t)(1 + 2 * B->Ldown) * (n + 1) * sizeof(int)));
+  FX_BINIT(cudaMalloc(&B->partials, (size_t)3 * B->nrows * sizeof(double)));
+  FX_BINIT(cudaMalloc(&B->active, n * sizeof(int)));
+  FX_BINIT(cudaMalloc(&B->bar, sizeof(GridBar)));
+  FX_BINIT(cudaMalloc(&B->status, sizeof(int)));
+  FX_BINIT(cudaMalloc(&B->nsteps_d, sizeof(int)));
+  FX_BINIT(cudaMalloc(&B->dbg, (8 + 1024) * sizeof(int)));
+  FX_BINIT(cudaMemset(B->dbg, 0, (8 + 1024) * sizeof(int)));
+  FX_BINIT(cudaMalloc(&B->params, n * sizeof(DevParams)));
+  FX_BINIT(cudaMalloc(&B->stats, n * sizeof(DevStats)));
+  FX_BINIT(cudaMalloc(&B->inst, n * sizeof(BatchInst)));
+  FX_BINIT(cudaMalloc(&B->charge_part, (size_t)n * 4 * 64 * sizeof(double)));
+  FX_BINIT(cudaMalloc(&B->charge_out, (size_t)n * 8 * sizeof(double)));
+  FX_BINIT(cudaMallocHost(&B->host_pinned, (size_t)n * 8 * sizeof(double) + 64));
+  // tables
+  std::vector<unsigned char> coefT;
+  std::vector<PlaneCoef<double>> coef0;
+  std::vector<PlaneTDGL> planes;
+  std::vector<LevelDesc> lv, lvt;
+  std::vector<BatchInst> inst(n);
+  for (int i = 0; i < n; ++i) {
+    BatchPlan& p = B->plans[i];
+    ferrox_ctx& c = p.c;
+    auto c64 = level_coefficients<double>(&c);
+    for (int k = 0; k < c.nz; ++k) coef0.push_back(c64[k]);
+    if (B->mixed) {
+      auto c32 = level_coefficients<float>(&c);
+      const unsigned char* q = reinterpret_cast<const unsigned char*>(c32.data());
+      coefT.insert(coefT.end(), q, q + c32.size() * sizeof(PlaneCoef<float>));
+    } else {
+      const unsigned char* q = reinterpret_cast<const unsigned char*>(c64.data());
+      coefT.insert(coefT.end(), q, q + c64.size() * sizeof(PlaneCoef<double>));
+    }
+    planes.insert(planes.end(), c.planes.begin(), c.planes.end());
+    for (auto L : c.lv) { L.off += p.arena_off; L.coef_off += p.coef_off; lv.push_back(L); }
+    for (auto L : c.lv_tail) { L.coef_off += p.coef_off; lvt.push_back(L); }
+    BatchInst& I = inst[i];
+    I.P = B->P + p.cell_off;
+    I.Pbuf = B->Pbuf + p.cell_off;
+    I.phi = B->phi + p.cell_off;
+    I.clamp = update_clamp(&c);
+    I.fe_lo = c.fe_lo; I.fe_hi = c.fe_hi;
+    I.lv_off = p.lv_off; I.nlev = (int)c.lv.size(); I.tail_first = c.tail_first;
+    I.lvt_off = p.lvt_off; I.nlev_tail = (int)c.lv_tail.size();
+    I.bottom_sweeps = c.num.bottom_sweeps;
+    I.tail_elems = c.tail_elems;
+    I.tail_base = c.lv[c.tail_first].off + p.arena_off;
+    TDGLArgs& t = I.tdgl;
+    t.P_in = I.P; t.P_out = I.Pbuf; t.P_base = nullptr; t.F_store = nullptr;
+    t.phi = I.phi; t.b = B->b + p.cell_off; t.planes = B->planes + p.plane_off; t.params = B->params + i;
+    t.nx = c.nx; t.ny = c.ny; t.nz = c.nz; t.ncomp = 1; t.kd_lo = c.kd_lo; t.kd_hi = c.kd_hi;
+    t.dt = num->dt; t.inv_h = 1.0 / c.h; t.inv_h2 = 1.0 / (c.h * c.h); t.b_scale = c.h / kEps0; t.mode = 0;
+    ResidArgs& ra = I.resid;
+    ra.phi = I.phi; ra.b = t.b; ra.planes = t.planes; ra.coef0 = B->coef0 + p.coef0_off; ra.params = t.params;
+    ra.nx = c.nx; ra.ny = c.ny; ra.nz = c.nz;
+    ra.r_out = static_cast<char*>(B->r) + (size_t)p.arena_off * tsz;
+    ra.s_out = has_sc && c.has_sc ? static_cast<char*>(B->s) + (size_t)p.arena_off * tsz : nullptr;
+    ra.partials = nullptr;
+    ra.stats = B->stats + i;
+    ra.tol = num->tol; ra.max_cycles = num->max_cycles; ra.first = 1; ra.set_cond = 0;
+    ra.cond_handle = 0; ra.launches_per_cycle = 0;
+  }
+  FX_BINIT(cudaMemcpy(B->coef, coefT.data(), coefT.size(), cudaMemcpyHostToDevice));
+  FX_BINIT(cudaMemcpy(B->coef0, coef0.data(), coef0.size() * sizeof(PlaneCoef<double>), cudaMemcpyHostToDevice));
+  FX_BINIT(cudaMemcpy(B->planes, planes.data(), planes.size() * sizeof(PlaneTDGL), cudaMemcpyHostToDevice));
+  FX_BINIT(cudaMemcpy(B->lv, lv.data(), lv.size() * sizeof(LevelDesc), cudaMemcpyHostToDevice));
+  FX_BINIT(cudaMemcpy(B->lvt, lvt.data(), lvt.size() * sizeof(LevelDesc), cudaMemcpyHostToDevice));
+  FX_BINIT(cudaMemcpy(B->inst, inst.data(), n * sizeof(BatchInst), cudaMemcpyHostToDevice));
+  FX_BINIT(cudaMemset(B->b, 0, cells * sizeof(double)));
+  FX_BINIT(cudaMemset(B->Pbuf, 0, cells * sizeof(double)));
+  FX_BINIT(cudaMemset(B->e, 0, arena * tsz));
+  FX_BINIT(cudaMemset(B->r, 0, arena * tsz));
+  if (B->s) FX_BINIT(cudaMemset(B->s, 0, arena * tsz));
+  FX_BINIT(cudaMemset(B->bar, 0, sizeof(GridBar)));
+  FX_BINIT(cudaMemset(B->status, 0, sizeof(int)));
+  FX_BINIT(cudaMemset(B->stats, 0, n * sizeof(DevStats)));
+  FX_BINIT(cudaMemset(B->params, 0, n * sizeof(DevParams)));
+  FX_BINIT(B->mixed ? batch_prepare<float>(B->smem) : batch_prepare<double>(B->smem));
+  ferrox_status rc = batch_configure(B, 512, 1);
+  if (rc != FERROX_OK) return cleanup(rc);
+  FX_BINIT(cudaDeviceSynchronize());
+#undef FX_BINIT
+  *out = B;
+  return FERROX_OK;
+}
+
+ferrox_status ferrox_batch_set_bias(ferrox_batch* B, const double* v_bottom, const double* v_top) {
+  if (!B || !v_bottom || !v_top) return bfail(B, FERROX_EINVAL, "null argument");
+  std::vector<DevParams> p(B->n);
+  for (int i = 0; i < B->n; ++i) {
+    if (!std::isfinite(v_bottom[i]) || !std::isfinite(v_top[i])) return bfail(B, FERROX_EINVAL, "bias not finite");
+    p[i].v_bot = v_bottom[i];
+    p[i].v_top = v_top[i];
+  }
+  // pageable source: staged before the call returns
+  FX_BCK(cudaMemcpyAsync(B->params, p.data(), B->n * sizeof(DevParams), cudaMemcpyHostToDevice, B->stream));
+  return FERROX_OK;
+}
+
+ferrox_status ferrox_batch_solve_poisson(ferrox_batch* B) {
+  if (!B) return bfail(nullptr, FERROX_EINVAL, "null batch");
+  if (B->ge_solve) FX_BCK(cudaGraphLaunch(B->ge_solve, B->stream));
+  else FX_BCK(batch_launch(B, 1, B->stream));
+  return FERROX_OK;
+}
+
+ferrox_status ferrox_batch_step(ferrox_batch* B, int nsteps) {
+  if (!B) return bfail(nullptr, FERROX_EINVAL, "null batch");
+  if (nsteps < 0) return bfail(B, FERROX_EINVAL, "nsteps < 0");
+  if (nsteps == 0) return FERROX_OK;
+  if (!B->tuned) {
+    ferrox_status rc = batch_autotune(B);
+    if (rc != FERROX_OK) return rc;
+    rc = batch_build_graphs(B);
+    if (rc != FERROX_OK) return rc;
+    B->tuned = true;
+  }
+  // pageable source: staged before the call returns, so the graph reads this count
+  FX_BCK(cudaMemcpyAsync(B->nsteps_d, &nsteps, sizeof(int), cudaMemcpyHostToDevice, B->stream));
+  FX_BCK(cudaGraphLaunch(B->ge_step, B->stream));
+  return FERROX_OK;
+}
+
+ferrox_status ferrox_batch_stats(ferrox_batch* B, ferrox_stats* out) {
+  if (!B || !out) return bfail(B, FERROX_EINVAL, "null argument");
+  std::vector<DevStats> st(B->n);
+  int gst = 0;
+  FX_BCK(cudaMemcpyAsync(st.data(), B->stats, B->n * sizeof(DevStats), cudaMemcpyDeviceToHost, B->stream));
+  FX_BCK(cudaMemcpyAsync(&gst, B->status, sizeof(int), cudaMemcpyDeviceToHost, B->stream));
+  FX_BCK(cudaStreamSynchronize(B->stream));
+  ferrox_status worst = (ferrox_status)gst;
+  for (int i = 0; i < B->n; ++i) {
+    out[i].steps = st[i].steps;
+    out[i].launches = st[i].steps;
+    out[i].solves = st[i].solves;
+    out[i].cycles = st[i].cycles;
+    out[i].last_cycles = st[i].last_cycles;
+    out[i].last_rel_res = st[i].last_rel;
+    out[i].status = gst ? gst : st[i].status;
+    if (worst == FERROX_OK && st[i].status) worst = (ferrox_status)st[i].status;
+  }
+  if (worst != FERROX_OK) B->err = worst == FERROX_ETIMEOUT ? "a bounded grid barrier ran out of time"
+                                                            : "an instance reported a device error";
+  return worst;
+}
+
+ferrox_status ferrox_batch_charge(ferrox_batch* B, ferrox_charge_t* out) {
+  if (!B || !out) return bfail(B, FERROX_EINVAL, "null argument");
+  std::vector<DevParams> prm(B->n);
+  FX_BCK(cudaMemcpyAsync(prm.data(), B->params, B->n * sizeof(DevParams), cudaMemcpyDeviceToHost, B->stream));
+  for (int i = 0; i < B->n; ++i) {
+    const ferrox_ctx& c = B->plans[i].c;
+    ChargeArgs a{};
+    a.phi = B->phi + B->plans[i].cell_off;
+    a.P = B->P + B->plans[i].cell_off;
+    a.planes = B->planes + B->plans[i].plane_off;
+    a.params = B->params + i;
+    a.nx = c.nx; a.ny = c.ny; a.nz = c.nz; a.k_int = c.k_int;
+    a.h = c.h; a.eps0 = kEps0;
+    a.eps_top = kEps0 * c.epsr[c.nz - 1];
+    a.eps_bot = kEps0 * c.epsr[0];
+    a.eps_L = c.k_int > 0 ? kEps0 * c.epsr[c.k_int - 1] : 0.0;
+    a.eps_R = kEps0 * c.epsr[c.k_int];
+    a.out = B->charge_out + 8 * i;
+    a.partials = B->charge_part + (size_t)4 * 64 * i;
+    launch_charge(a, B->stream);
+  }
+  FX_BCK(cudaGetLastError());
+  FX_BCK(cudaMemcpyAsync(B->host_pinned, B->charge_out, (size_t)B->n * 8 * sizeof(double),
+                         cudaMemcpyDeviceToHost, B->stream));
+  FX_BCK(cudaStreamSynchronize(B->stream));
+  for (int i = 0; i < B->n; ++i) {
+    const ferrox_ctx& c = B->plans[i].c;
+    const double* s = B->host_pinned + 8 * i;
+    const double inv = 1.0 / ((double)c.nx * c.ny);
+    out[i].Q_int = -s[0] * inv;
+    out[i].phi_int_avg = s[1] * inv;
+    out[i].V_fe = prm[i].v_top - out[i].phi_int_avg;
+    out[i].sigma_top = -s[2] * inv;
+    out[i].sigma_bot = s[3] * inv;
+  }
+  std::vector<ferrox_stats> st(B->n);
+  return ferrox_batch_stats(B, st.data());
+}
+
+ferrox_status ferrox_batch_tuning(const ferrox_batch* B, int* threads, int* rows_per_unit, int* blocks) {
+  if (!B) return FERROX_EINVAL;
+  if (threads) *threads = B->threads;
+  if (rows_per_unit) *rows_per_unit = B->rows_per_unit;
+  if (blocks) *blocks = B->blocks;
+  return B->tuned ? FERROX_OK : FERROX_ESTATE;
+}
+
+ferrox_status ferrox_check_wait_timeout(double seconds, int* status_out, void* cuda_stream) {
+  ferrox_batch* B = nullptr;
+  if (!status_out || !(seconds > 0.0) || seconds > 5.0) return bfail(nullptr, FERROX_EINVAL, "bad argument");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  GridBar* gb = nullptr;
+  int* st = nullptr;
+  FX_BCK(cudaMalloc(&gb, sizeof(GridBar)));
+  FX_BCK(cudaMalloc(&st, sizeof(int)));
+  FX_BCK(cudaMemsetAsync(gb, 0, sizeof(GridBar), s));
+  FX_BCK(cudaMemsetAsync(st, 0, sizeof(int), s));
+  FX_BCK(launch_barrier_timeout(gb, st, (long long)(seconds * 2.0e9), s));
+  FX_BCK(cudaMemcpyAsync(status_out, st, sizeof(int), cudaMemcpyDeviceToHost, s));
+  FX_BCK(cudaStreamSynchronize(s));
+  cudaFree(gb);
+  cudaFree(st);
+  return FERROX_OK;
+}
+
+// self-check record of the last persistent launch: [0] set when a wait ran out,
+// [1] its barrier number, [2] the waiting block, [3] arrivals seen, [4] generation,
+// [8 + b] barriers block b passed (negative: it left on a failed wait)
+ferrox_status ferrox_batch_debug(ferrox_batch* B, int* out, int n) {
+  if (!B || !out || n < 8) return FERROX_EINVAL;
+  FX_BCK(cudaMemcpy(out, B->dbg, std::min(n, 8 + 1024) * sizeof(int), cudaMemcpyDeviceToHost));
+  return FERROX_OK;
+}
+
+ferrox_status ferrox_batch_destroy(ferrox_batch* B) {
+  batch_release(B);
+  return FERROX_OK;
+}
+
+const char* ferrox_batch_last_error(const ferrox_batch* B) {
+  return B ? B->err.c_str() : g_init_error.c_str();
+}
+
+}  // extern "C"
+
 // ---- entry point without allocation -----------------------------------------------------
 //
 // Callers that cannot allocate device memory (code that runs while a CUDA stream

@@ -172,6 +172,55 @@ struct ChargeArgs {
   double* partials;
 };
 void launch_charge(const ChargeArgs& a, cudaStream_t s);
+
+// ---- persistent batched engine (persistent.cu) ---------------------------------------
+constexpr long long kBarrierSpinCycles = 2000000000LL;  // ~1 s at 2 GHz: a wait never hangs
+
+struct GridBar {
+  unsigned int count, gen, abort, pad;
+};
+
+struct BatchInst {
+  TDGLArgs tdgl;        // P_in = P, P_out = Pbuf, instance arenas
+  ResidArgs resid;      // r_out/s_out: the instance's level 0; stats: the instance's
+  double* P;
+  double* Pbuf;
+  double* phi;
+  double clamp;
+  int fe_lo, fe_hi;
+  int lv_off, nlev, tail_first, lvt_off, nlev_tail, bottom_sweeps;
+  long long tail_elems, tail_base;
+};
+
+struct BatchArgs {
+  const BatchInst* inst;
+  int ninst;
+  int mode;             // 0: time steps, 1: Poisson solve only (Step 0)
+  const int* nsteps;    // device: steps per launch
+  void* e;              // correction arena (T)
+  void* r;              // right-hand-side arena (T)
+  void* s;              // Newton shift arena (T) or null
+  const void* coef;     // PlaneCoef<T> of all levels of all instances
+  const LevelDesc* lv;  // levels of all instances (arena offsets)
+  const LevelDesc* lvt; // tail levels of all instances (shared-memory offsets)
+  const int* pre;       // unit prefix tables: rows, smoothing rows per level, coarse rows per level
+  int Ldown;            // deepest multi-block level count over instances
+  double* partials;     // 3 per row unit
+  int* active;          // per instance
+  GridBar* bar;
+  int* status;          // global status (barrier time-out)
+  double tol;
+  int max_cycles, nu1, nu2, rows_per_unit, any_full_tail, pad;
+  int* dbg;             // optional self-check record (null: off)
+};
+
+cudaError_t launch_barrier_timeout(GridBar* gb, int* status, long long limit, cudaStream_t s);
+template <typename T>
+cudaError_t batch_prepare(size_t smem);
+template <typename T>
+cudaError_t batch_occupancy(int threads, size_t smem, int* blocks_per_sm);
+template <typename T>
+cudaError_t launch_batch(const BatchArgs& a, int blocks, int threads, size_t smem, cudaStream_t s);
 void launch_set_params(DevParams* p, double v_bot, double v_top, cudaStream_t s);
 void launch_stats_step(DevStats* st, int nsteps, int launches, cudaStream_t s);
 

@@ -21,169 +21,13 @@
 #include <math.h>
 
 #include "ferrox_internal.cuh"
+#include "mg_device.cuh"
 
 namespace fx {
 
 namespace {
 
-__device__ __forceinline__ long long lidx(const LevelDesc& L, int i, int j, int k) {
-  return L.off + ((long long)k * L.ny + j) * L.nx + i;
-}
-
-// (r + sum of couplings * neighbours) of one cell; the Gauss-Seidel numerator.
-template <typename T>
-__device__ __forceinline__ T gs_numerator(const T* e, const T* r, const PlaneCoef<T>& c,
-                                          const LevelDesc& L, int i, int j, int k, long long id) {
-  const int im = (i == 0) ? L.nx - 1 : i - 1;
-  const int ip = (i == L.nx - 1) ? 0 : i + 1;
-  const int jm = (j == 0) ? L.ny - 1 : j - 1;
-  const int jp = (j == L.ny - 1) ? 0 : j + 1;
-  const long long row = id - i;
-  const long long plane = (long long)L.nx * L.ny;
-  T sx = e[row + im] + e[row + ip];
-  T sy = e[id + (long long)(jm - j) * L.nx] + e[id + (long long)(jp - j) * L.nx];
-  T ed = (k > 0) ? e[id - plane] : T(0);
-  T eu = (k < L.nz - 1) ? e[id + plane] : T(0);
-  T acc = r[id];
-  acc = fma(c.cx, sx, acc);
-  acc = fma(c.cy, sy, acc);
-  acc = fma(c.czlo, ed, acc);
-  acc = fma(c.czhi, eu, acc);
-  return acc;
-}
-
-struct Upd {
-  double* phi;      // fine-level potential (null: no fused update)
-  double clamp;
-  int zero;         // set phi = 0 (degenerate zero right-hand side)
-};
-
-template <typename T>
-__device__ __forceinline__ void apply_update(const Upd& u, long long idx, T e) {
-  if (u.zero) u.phi[idx] = 0.0;
-  else u.phi[idx] += fmin(fmax((double)e, -u.clamp), u.clamp);
-}
-
-// One red/black pair position (ip) of a row: update the cell of `color`; on a
-// zero-start sweep also zero the other cell; optionally fold both cells' final
-// corrections into phi (last black sweep of the fine level).
-template <typename T>
-__device__ __forceinline__ void smooth_pair(const MGArgs<T>& a, const LevelDesc& L, int ip, int j,
-                                            int k, int color, int zero_init, const Upd& u) {
-  const int par = (j + k + color) & 1;
-  const int i = 2 * ip + par;
-  const int i2 = 2 * ip + (par ^ 1);
-  const PlaneCoef<T> c = a.coef[L.coef_off + k];
-  T ev = T(0);
-  long long id = -1;
-  if (i < L.nx) {
-    id = lidx(L, i, j, k);
-    if (zero_init) {
-      const T d = c.has_s ? T(1) / (c.diag + a.s[id]) : c.invdiag;
-      ev = a.r[id] * d;
-    } else {
-      const T num = gs_numerator(a.e, a.r, c, L, i, j, k, id);
-      ev = c.has_s ? num / (c.diag + a.s[id]) : num * c.invdiag;
-    }
-    a.e[id] = ev;
-  }
-  if (i2 < L.nx) {
-    const long long id2 = lidx(L, i2, j, k);
-    if (zero_init) a.e[id2] = T(0);
-    if (u.phi) apply_update(u, id2 - L.off, a.e[id2]);
-  }
-  if (u.phi && id >= 0) apply_update(u, id - L.off, ev);
-}
-
-// residual of one fine cell: r - (A + s) e
-template <typename T>
-__device__ __forceinline__ T cell_residual(const MGArgs<T>& a, const LevelDesc& L, int i, int j,
-                                           int k) {
-  const PlaneCoef<T> c = a.coef[L.coef_off + k];
-  const long long id = lidx(L, i, j, k);
-  T num = gs_numerator(a.e, a.r, c, L, i, j, k, id);   // r + couplings * neighbours
-  T d = c.has_s ? c.diag + a.s[id] : c.diag;
-  return fma(-d, a.e[id], num);
-}
-
-template <typename T>
-__device__ __forceinline__ void restrict_cell(const MGArgs<T>& a, const LevelDesc& F,
-                                              const LevelDesc& C, int I, int J, int K) {
-  const int nxc = F.crx ? 2 : 1, nyc = F.cry ? 2 : 1, nzc = F.crz ? 2 : 1;
-  const int i0 = F.crx ? 2 * I : I, j0 = F.cry ? 2 * J : J, k0 = F.crz ? 2 * K : K;
-  T sum = T(0), ssum = T(0);
-  for (int dk = 0; dk < nzc; ++dk)
-    for (int dj = 0; dj < nyc; ++dj)
-      for (int di = 0; di < nxc; ++di) {
-        sum += cell_residual(a, F, i0 + di, j0 + dj, k0 + dk);
-        if (a.s) ssum += a.s[lidx(F, i0 + di, j0 + dj, k0 + dk)];
-      }
-  const T inv = T(1) / T(nxc * nyc * nzc);
-  const long long idc = lidx(C, I, J, K);
-  a.r[idc] = sum * inv;
-  if (a.s) a.s[idc] = ssum * inv;
-}
-
-// Prolongation + correction for the children of coarse cell (I, J, K).
-// Cell-centred trilinear interpolation, separable: along every coarsened
-// direction a child takes 3/4 of its own coarse value and 1/4 of the coarse
-// neighbour on its side; an electrode beyond the coarse grid acts as a ghost
-// cell holding -e (zero correction on the electrode face).
-template <typename T>
-__device__ __forceinline__ void prolong_cell(const MGArgs<T>& a, const LevelDesc& F,
-                                             const LevelDesc& C, int I, int J, int K, int constant) {
-  const int nxc = F.crx ? 2 : 1, nyc = F.cry ? 2 : 1, nzc = F.crz ? 2 : 1;
-  T* e = a.e;
-  if (constant) {
-    const T E0 = e[lidx(C, I, J, K)];
-    for (int c = 0; c < nzc; ++c)
-      for (int b = 0; b < nyc; ++b)
-        for (int q = 0; q < nxc; ++q)
-          e[lidx(F, F.crx ? 2 * I + q : I, F.cry ? 2 * J + b : J, F.crz ? 2 * K + c : K)] += E0;
-    return;
-  }
-  const int Im = I == 0 ? C.nx - 1 : I - 1, Ip = I + 1 == C.nx ? 0 : I + 1;
-  const int Jm = J == 0 ? C.ny - 1 : J - 1, Jp = J + 1 == C.ny ? 0 : J + 1;
-  const int xs[3] = {Im, I, Ip}, ys[3] = {Jm, J, Jp};
-  T Z[2][3][3];
-#pragma unroll
-  for (int yy = 0; yy < 3; ++yy)
-#pragma unroll
-    for (int xx = 0; xx < 3; ++xx) {
-      if ((!F.cry && yy != 1) || (!F.crx && xx != 1)) continue;
-      const T Ec = e[lidx(C, xs[xx], ys[yy], K)];
-      if (F.crz) {
-        Z[0][yy][xx] = (K > 0) ? fma(T(0.75), Ec, T(0.25) * e[lidx(C, xs[xx], ys[yy], K - 1)])
-                               : T(0.5) * Ec;
-        Z[1][yy][xx] = (K + 1 < C.nz) ? fma(T(0.75), Ec, T(0.25) * e[lidx(C, xs[xx], ys[yy], K + 1)])
-                                      : T(0.5) * Ec;
-      } else {
-        Z[0][yy][xx] = Ec;
-      }
-    }
-#pragma unroll
-  for (int c = 0; c < 2; ++c) {
-    if (c >= nzc) break;
-#pragma unroll
-    for (int b = 0; b < 2; ++b) {
-      if (b >= nyc) break;
-      T Y[3];
-#pragma unroll
-      for (int xx = 0; xx < 3; ++xx) {
-        if (!F.crx && xx != 1) continue;
-        Y[xx] = F.cry ? fma(T(0.75), Z[c][1][xx], T(0.25) * Z[c][b ? 2 : 0][xx]) : Z[c][1][xx];
-      }
-      const int fj = F.cry ? 2 * J + b : J, fk = F.crz ? 2 * K + c : K;
-      if (F.crx) {
-        const long long f0 = lidx(F, 2 * I, fj, fk);
-        e[f0] += fma(T(0.75), Y[1], T(0.25) * Y[0]);
-        e[f0 + 1] += fma(T(0.75), Y[1], T(0.25) * Y[2]);
-      } else {
-        e[lidx(F, I, fj, fk)] += Y[1];
-      }
-    }
-  }
-}
+using namespace dev;
 
 // ---- multi-block kernels (3-D grids: x chunk, row chunk, plane) ----------------------
 
@@ -215,139 +59,18 @@ __global__ void __launch_bounds__(256) prolong_kernel(MGArgs<T> a, LevelDesc F, 
   prolong_cell(a, F, C, I, J, (int)blockIdx.z, constant);
 }
 
-// ---- single-CTA tail: the smallest levels in shared memory ---------------------------
-
-template <typename T>
-__device__ void tail_smooth(const MGArgs<T>& a, const LevelDesc& L, int sweeps, int zero_first) {
-  const int hx = (L.nx + 1) >> 1;
-  const int items = hx * L.ny * L.nz;
-  const Upd none{nullptr, 0.0, 0};
-  for (int sw = 0; sw < sweeps; ++sw)
-    for (int color = 0; color < 2; ++color) {
-      const int zi = (zero_first && sw == 0 && color == 0);
-      for (int t = threadIdx.x; t < items; t += blockDim.x) {
-        const int ip = t % hx, rest = t / hx;
-        smooth_pair(a, L, ip, rest % L.ny, rest / L.ny, color, zi, none);
-      }
-      __syncthreads();
-    }
-}
-
 template <typename T>
 __global__ void __launch_bounds__(kTailThreads) tail_kernel(MGArgs<T> g, TailArgs t) {
   extern __shared__ __align__(16) unsigned char tail_smem[];
-  T* se = reinterpret_cast<T*>(tail_smem);
-  T* sr = se + t.elems;
-  T* ss = g.s ? sr + t.elems : nullptr;
-  const LevelDesc* lv = t.lv;
-  const int n0 = (int)lv[0].ncell;
-  for (int q = threadIdx.x; q < n0; q += blockDim.x) {
-    sr[q] = g.r[t.base + q];
-    if (ss) ss[q] = g.s[t.base + q];
-  }
-  __syncthreads();
-  MGArgs<T> a;
-  a.e = se; a.r = sr; a.s = ss; a.coef = g.coef; a.lv = lv;
-  for (int l = 0; l + 1 < t.nlev; ++l) {
-    const LevelDesc F = lv[l], C = lv[l + 1];
-    tail_smooth(a, F, t.nu1, 1);
-    const int nc = (int)C.ncell;
-    for (int q = threadIdx.x; q < nc; q += blockDim.x)
-      restrict_cell(a, F, C, q % C.nx, (q / C.nx) % C.ny, q / (C.nx * C.ny));
-    __syncthreads();
-  }
-  tail_smooth(a, lv[t.nlev - 1], t.bottom_sweeps, 1);
-  for (int l = t.nlev - 2; l >= 0; --l) {
-    const LevelDesc F = lv[l], C = lv[l + 1];
-    const int nc = (int)C.ncell;
-    for (int q = threadIdx.x; q < nc; q += blockDim.x)
-      prolong_cell(a, F, C, q % C.nx, (q / C.nx) % C.ny, q / (C.nx * C.ny), t.constant);
-    __syncthreads();
-    tail_smooth(a, F, t.nu2, 0);
-  }
-  for (int q = threadIdx.x; q < n0; q += blockDim.x) g.e[t.base + q] = se[q];
-}
-
-// ---- FP64 outer residual --------------------------------------------------------------
-
-__device__ __forceinline__ double warp_sum(double v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Block sum of three values; result valid in thread 0.
-__device__ __forceinline__ void block_sum3(double& x, double& y, double& z) {
-  __shared__ double sh[3][32];
-  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-  const int nthr = blockDim.x * blockDim.y;
-  x = warp_sum(x); y = warp_sum(y); z = warp_sum(z);
-  const int w = tid >> 5, l = tid & 31;
-  if (l == 0) { sh[0][w] = x; sh[1][w] = y; sh[2][w] = z; }
-  __syncthreads();
-  const int nw = (nthr + 31) >> 5;
-  if (w == 0) {
-    x = l < nw ? sh[0][l] : 0.0;
-    y = l < nw ? sh[1][l] : 0.0;
-    z = l < nw ? sh[2][l] : 0.0;
-    x = warp_sum(x); y = warp_sum(y); z = warp_sum(z);
-  }
-  __syncthreads();
+  tail_vcycle<T>(g, t, tail_smem);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kResidBX* kResidBY) resid_kernel(ResidArgs a) {
-  const int nx = a.nx, ny = a.ny, nz = a.nz;
   const int i = blockIdx.x * kResidBX + threadIdx.x;
   const int j = blockIdx.y * kResidBY + threadIdx.y;
-  const long long plane = (long long)nx * ny;
-  T* r_out = static_cast<T*>(a.r_out);
-  T* s_out = static_cast<T*>(a.s_out);
   double acc_r = 0.0, acc_b = 0.0, acc_rho = 0.0;
-  if (i < nx && j < ny) {
-    const double v_bot = a.params->v_bot, v_top = a.params->v_top;
-    const int im = (i == 0) ? nx - 1 : i - 1, ip = (i == nx - 1) ? 0 : i + 1;
-    const long long dxm = im - i, dxp = ip - i;
-    const long long dym = (long long)((j == 0) ? ny - 1 : j - 1) * nx - (long long)j * nx;
-    const long long dyp = (long long)((j == ny - 1) ? 0 : j + 1) * nx - (long long)j * nx;
-    const double* phi = a.phi;
-    const long long col = (long long)j * nx + i;
-    double pd = 0.0, pc = phi[col];
-    for (int k = 0; k < nz; ++k) {
-      const long long t = k * plane + col;
-      const double pu = (k < nz - 1) ? phi[t + plane] : 0.0;
-      const PlaneCoef<double> c = a.coef0[k];
-      const PlaneTDGL& pt = a.planes[k];
-      const double sx = phi[t + dxm] + phi[t + dxp];
-      const double sy = phi[t + dym] + phi[t + dyp];
-      double off = c.cx * sx;
-      off = fma(c.cy, sy, off);
-      off = fma(c.czlo, pd, off);
-      off = fma(c.czhi, pu, off);
-      double bb;
-      if (pt.b_dyn) {
-        bb = a.b[t];
-      } else {
-        bb = 0.0;
-        if (k == 0) bb += pt.lift * v_bot;
-        if (k == nz - 1) bb += pt.lift * v_top;
-      }
-      double rho = 0.0;
-      if (pt.sc) {
-        const double u = pc * pt.inv_vt;
-        const double n = pt.n0 * exp(u);
-        const double p = pt.p0 * exp(-u);
-        rho = pt.kq * (p - n + pt.Nnet);
-        if (s_out) s_out[t] = (T)(pt.kq * (n + p) * pt.inv_vt);
-        acc_rho = fma(rho, rho, acc_rho);
-      }
-      const double r = (bb + rho) - fma(c.diag, pc, -off);
-      r_out[t] = (T)r;
-      acc_r = fma(r, r, acc_r);
-      if (a.first) acc_b = fma(bb, bb, acc_b);
-      pd = pc;
-      pc = pu;
-    }
-  }
+  if (i < a.nx && j < a.ny) resid_column<T>(a, i, j, acc_r, acc_b, acc_rho);
   block_sum3(acc_r, acc_b, acc_rho);
   __shared__ bool last;
   const int nblk = gridDim.x * gridDim.y;
@@ -374,41 +97,8 @@ __global__ void __launch_bounds__(kResidBX* kResidBY) resid_kernel(ResidArgs a) 
   }
   block_sum3(sr, sb, sq);
   if (tid == 0) {
-    DevStats* st = a.stats;
-    st->done_ctr = 0;
-    if (a.first) {
-      st->solves += 1;
-      st->cycles_this_solve = 0;
-      st->zero_phi = 0;
-      st->launches += 1;
-      st->bnorm2 = sb;          // b is fixed during a solve
-    }
-    const double rn = sqrt(sr);
-    const double scale = fmax(sqrt(st->bnorm2), sqrt(sq));
-    int cond;
-    if (!isfinite(rn) || !isfinite(scale)) {
-      if (st->status == 0) st->status = FERROX_ENONFINITE;
-      cond = 0;
-    } else if (rn <= a.tol * scale) {
-      cond = 0;
-    } else if (st->cycles_this_solve >= a.max_cycles) {
-      if (st->status == 0) st->status = FERROX_ENOCONV;
-      cond = 0;
-    } else {
-      // scale == 0 with r != 0: b = 0 and rho(phi) = 0, whose solution is phi = 0
-      if (scale == 0.0) st->zero_phi = 1;
-      cond = 1;
-    }
-    if (cond) {
-      st->cycles_this_solve += 1;
-      st->cycles += 1;
-      st->launches += a.launches_per_cycle;
-    }
-    st->last_cond = cond;
-    st->last_cycles = st->cycles_this_solve;
-    st->last_rnorm = rn;
-    st->last_scale = scale;
-    st->last_rel = scale > 0.0 ? rn / scale : (rn > 0.0 ? INFINITY : 0.0);
+    a.stats->done_ctr = 0;
+    const int cond = decide(a.stats, sr, sb, sq, a.first, a.tol, a.max_cycles, a.launches_per_cycle);
     if (a.set_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)a.cond_handle, cond);
   }
 }

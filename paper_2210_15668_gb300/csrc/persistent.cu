@@ -1,0 +1,379 @@
+// Persistent batched engine: many independent device stacks (a Q-V sweep of
+// instances with uneven lateral sizes and biases) advanced by ONE cooperative
+// kernel launch.
+//
+// Every phase of the time step (TDGL update, FP64 residual, per-instance
+// convergence decision, each multigrid level's sweeps and transfers, the
+// shared-memory tail) runs over the work units of all instances at once; the
+// phases are separated by a grid barrier.  Each instance decides its own
+// convergence and drops out of the remaining cycles when done.  Work units are
+// rows (or `rows_per_unit` consecutive rows) of one plane of one instance,
+// handled by one warp whose lanes run along x; the unit -> instance map is a
+// binary search in per-phase prefix tables.  Barrier waits are bounded in time:
+// on expiry the kernel records FERROX_ETIMEOUT and every block leaves after at
+// most one more bounded wait, so a fault elsewhere can never hang the GPU.
+#include <cuda_runtime.h>
+
+#include "ferrox_internal.cuh"
+#include "mg_device.cuh"
+#include "tdgl_device.cuh"
+
+namespace fx {
+
+namespace {
+
+using namespace dev;
+
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned int atom_add_acq_rel(unsigned int* p, unsigned int v) {
+  unsigned int old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
+__device__ __forceinline__ void st_release(unsigned int* p, unsigned int v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid-wide barrier with a time limit.  Returns false (and records the status)
+// when the wait ran out or another block has already aborted.
+__device__ bool grid_barrier(GridBar* gb, int* status, long long limit = kBarrierSpinCycles,
+                             int* dbg = nullptr, int nbar = 0) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    __threadfence();
+    const unsigned int gen = ld_acquire(&gb->gen);
+    if (atom_add_acq_rel(&gb->count, 1u) == gridDim.x - 1) {
+      gb->count = 0;
+      st_release(&gb->gen, gen + 1);
+    } else {
+      const long long t0 = clock64();
+      while (ld_acquire(&gb->gen) == gen) {
+        if (ld_acquire(&gb->abort)) { ok = 0; break; }
+        if (clock64() - t0 > limit) {
+          if (dbg && atomicCAS(&dbg[0], 0, 1) == 0) {   // where the first wait ran out
+            dbg[1] = nbar;
+            dbg[2] = (int)blockIdx.x;
+            dbg[3] = (int)ld_acquire(&gb->count);
+            dbg[4] = (int)gen;
+          }
+          atomicCAS(status, 0, (int)FERROX_ETIMEOUT);
+          st_release(&gb->abort, 1u);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    if (ok && ld_acquire(&gb->abort)) ok = 0;
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+__device__ __forceinline__ int find_inst(const int* pre, int n, int u) {
+  int lo = 0, hi = n;   // pre[lo] <= u < pre[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (pre[mid] <= u) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// control flags written by other CTAs of this launch: read at L2
+__device__ __forceinline__ int ld_flag(const int* p) { return __ldcg(p); }
+
+// Warp-level sum (all lanes active), result in every lane.
+__device__ __forceinline__ double wsum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T>
+struct Ctx {
+  const BatchArgs& A;
+  MGArgs<T> mg;
+  int lane, gwarp, nwarps;
+};
+
+// ---- phases -----------------------------------------------------------------------------
+
+// TDGL update (or right-hand side only) of every active column: unit = one row.
+template <typename T>
+__device__ void phase_tdgl(const Ctx<T>& c, int mode) {
+  const BatchArgs& A = c.A;
+  const int* pre = A.pre;   // space 0: rows
+  const int total = pre[A.ninst];
+  for (int u = c.gwarp; u < total; u += c.nwarps) {
+    const int i = find_inst(pre, A.ninst, u);
+    const BatchInst& I = A.inst[i];
+    TDGLArgs t = I.tdgl;
+    t.mode = mode;
+    const int j = u - pre[i];
+    for (int x = c.lane; x < t.nx; x += 32) tdgl_column(t, x, j);
+  }
+}
+
+// FP64 residual of every active instance; copies the new P back first (order 1).
+template <typename T>
+__device__ void phase_resid(const Ctx<T>& c, int first, int copy_back) {
+  const BatchArgs& A = c.A;
+  const int* pre = A.pre;
+  const int total = pre[A.ninst];
+  for (int u = c.gwarp; u < total; u += c.nwarps) {
+    const int i = find_inst(pre, A.ninst, u);
+    if (!ld_flag(A.active + i)) continue;
+    const BatchInst& I = A.inst[i];
+    const int j = u - pre[i];
+    ResidArgs ra = I.resid;
+    ra.first = first;
+    double ar = 0.0, ab = 0.0, aq = 0.0;
+    const long long plane = (long long)ra.nx * ra.ny;
+    for (int x = c.lane; x < ra.nx; x += 32) {
+      if (copy_back) {
+        for (int k = I.fe_lo; k <= I.fe_hi; ++k) {
+          const long long t = k * plane + (long long)j * ra.nx + x;
+          I.P[t] = I.Pbuf[t];
+        }
+      }
+      resid_column<T>(ra, x, j, ar, ab, aq);
+    }
+    ar = wsum(ar); ab = wsum(ab); aq = wsum(aq);
+    if (c.lane == 0) {
+      A.partials[3 * u] = ar;
+      A.partials[3 * u + 1] = ab;
+      A.partials[3 * u + 2] = aq;
+    }
+  }
+}
+
+// Per-instance convergence decision: one warp per instance, fixed-order sums.
+template <typename T>
+__device__ void phase_decide(const Ctx<T>& c, int first) {
+  const BatchArgs& A = c.A;
+  for (int i = c.gwarp; i < A.ninst; i += c.nwarps) {
+    if (!ld_flag(A.active + i)) continue;
+    double sr = 0.0, sb = 0.0, sq = 0.0;
+    for (int u = A.pre[i] + c.lane; u < A.pre[i + 1]; u += 32) {
+      sr += A.partials[3 * u];
+      sb += A.partials[3 * u + 1];
+      sq += A.partials[3 * u + 2];
+    }
+    sr = wsum(sr); sb = wsum(sb); sq = wsum(sq);
+    if (c.lane == 0) {
+      const int cond = decide(A.inst[i].resid.stats, sr, sb, sq, first, A.tol, A.max_cycles, 0);
+      A.active[i] = cond;
+    }
+  }
+}
+
+// smoothing sweep of one colour at level l of every active instance with l < tail_first
+template <typename T>
+__device__ void phase_smooth(const Ctx<T>& c, int l, int color, int zero_init, int fuse_update) {
+  const BatchArgs& A = c.A;
+  const int* pre = A.pre + (1 + l) * (A.ninst + 1);
+  const int total = pre[A.ninst];
+  const int R = A.rows_per_unit;
+  for (int u = c.gwarp; u < total; u += c.nwarps) {
+    const int i = find_inst(pre, A.ninst, u);
+    if (!ld_flag(A.active + i)) continue;
+    const BatchInst& I = A.inst[i];
+    const LevelDesc L = A.lv[I.lv_off + l];
+    const int nrc = (L.ny + R - 1) / R;
+    const int q = u - pre[i];
+    const int k = q / nrc, j0 = (q - k * nrc) * R;
+    Upd up{nullptr, 0.0, 0};
+    if (fuse_update) up = Upd{I.phi, I.clamp, ld_flag(&I.resid.stats->zero_phi)};
+    const int hx = (L.nx + 1) >> 1;
+    for (int j = j0; j < j0 + R && j < L.ny; ++j)
+      for (int ip = c.lane; ip < hx; ip += 32) smooth_pair(c.mg, L, ip, j, k, color, zero_init, up);
+  }
+}
+
+// restriction (op 0) or prolongation (op 1) between levels l and l+1
+template <typename T>
+__device__ void phase_transfer(const Ctx<T>& c, int l, int op) {
+  const BatchArgs& A = c.A;
+  const int* pre = A.pre + (1 + A.Ldown + l) * (A.ninst + 1);
+  const int total = pre[A.ninst];
+  const int R = A.rows_per_unit;
+  for (int u = c.gwarp; u < total; u += c.nwarps) {
+    const int i = find_inst(pre, A.ninst, u);
+    if (!ld_flag(A.active + i)) continue;
+    const BatchInst& I = A.inst[i];
+    const LevelDesc F = A.lv[I.lv_off + l], Cc = A.lv[I.lv_off + l + 1];
+    const int nrc = (Cc.ny + R - 1) / R;
+    const int q = u - pre[i];
+    const int K = q / nrc, J0 = (q - K * nrc) * R;
+    for (int J = J0; J < J0 + R && J < Cc.ny; ++J)
+      for (int I0 = c.lane; I0 < Cc.nx; I0 += 32) {
+        if (op == 0) restrict_cell(c.mg, F, Cc, I0, J, K);
+        else prolong_cell(c.mg, F, Cc, I0, J, K, 0);
+      }
+  }
+}
+
+// the tail levels of every active instance: one block per instance
+template <typename T>
+__device__ void phase_tail(const Ctx<T>& c, unsigned char* smem) {
+  const BatchArgs& A = c.A;
+  for (int i = blockIdx.x; i < A.ninst; i += gridDim.x) {
+    if (!ld_flag(A.active + i)) continue;
+    const BatchInst& I = A.inst[i];
+    TailArgs t{A.lvt + I.lvt_off, I.nlev_tail, I.tail_elems, I.tail_base, A.nu1, A.nu2,
+               I.bottom_sweeps, 0};
+    tail_vcycle<T>(c.mg, t, smem);
+  }
+}
+
+// phi += e for instances whose update is not folded into a sweep (all levels in the tail)
+template <typename T>
+__device__ void phase_update(const Ctx<T>& c) {
+  const BatchArgs& A = c.A;
+  const int* pre = A.pre;
+  const int total = pre[A.ninst];
+  for (int u = c.gwarp; u < total; u += c.nwarps) {
+    const int i = find_inst(pre, A.ninst, u);
+    const BatchInst& I = A.inst[i];
+    if (!ld_flag(A.active + i) || I.tail_first != 0) continue;
+    const int j = u - pre[i];
+    const LevelDesc L = A.lv[I.lv_off];
+    const Upd up{I.phi, I.clamp, ld_flag(&I.resid.stats->zero_phi)};
+    for (int k = 0; k < L.nz; ++k)
+      for (int x = c.lane; x < L.nx; x += 32) {
+        const long long id = L.off + ((long long)k * L.ny + j) * L.nx + x;
+        apply_update(up, id - L.off, c.mg.e[id]);
+      }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512, 1) batch_kernel(BatchArgs A) {
+  extern __shared__ __align__(16) unsigned char bsmem[];
+  MGArgs<T> mg;
+  mg.e = static_cast<T*>(A.e);
+  mg.r = static_cast<T*>(A.r);
+  mg.s = static_cast<T*>(A.s);
+  mg.coef = static_cast<const PlaneCoef<T>*>(A.coef);
+  mg.lv = A.lv;
+  const int lane = threadIdx.x & 31;
+  const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const Ctx<T> c{A, mg, lane, gwarp, nwarps};
+  const int nsteps = A.mode == 1 ? 1 : *A.nsteps;
+  int nbar = 0;
+#define FX_BAR()                                                                    \
+  do {                                                                              \
+    ++nbar;                                                                         \
+    if (!grid_barrier(A.bar, A.status, kBarrierSpinCycles, A.dbg, nbar)) {          \
+      if (A.dbg && threadIdx.x == 0) A.dbg[8 + blockIdx.x] = -nbar;                 \
+      return;                                                                       \
+    }                                                                               \
+  } while (0)
+  for (int step = 0; step < nsteps; ++step) {
+    // every instance takes part in the step; the barrier before the reset keeps
+    // it from racing with slower blocks still reading the previous step's flags
+    if (step > 0) FX_BAR();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.ninst; i += gridDim.x * blockDim.x)
+      A.active[i] = 1;
+    FX_BAR();
+    phase_tdgl(c, A.mode == 1 ? 3 : 0);          // Step 1a (or the RHS of the current P)
+    FX_BAR();
+    for (int cyc = 0;; ++cyc) {
+      phase_resid(c, cyc == 0, A.mode == 0 && cyc == 0);
+      FX_BAR();
+      phase_decide(c, cyc == 0);
+      FX_BAR();
+      int any = 0;
+      for (int i = 0; i < A.ninst; ++i) any |= ld_flag(A.active + i);
+      if (!any) break;
+      // one V-cycle on the active instances
+      for (int l = 0; l < A.Ldown; ++l) {
+        for (int sw = 0; sw < A.nu1; ++sw) {
+          phase_smooth(c, l, 0, sw == 0, 0);
+          FX_BAR();
+          phase_smooth(c, l, 1, 0, 0);
+          FX_BAR();
+        }
+        phase_transfer(c, l, 0);
+        FX_BAR();
+      }
+      phase_tail(c, bsmem);
+      FX_BAR();
+      for (int l = A.Ldown - 1; l >= 0; --l) {
+        phase_transfer(c, l, 1);
+        FX_BAR();
+        for (int sw = 0; sw < A.nu2; ++sw) {
+          phase_smooth(c, l, 0, 0, 0);
+          FX_BAR();
+          phase_smooth(c, l, 1, 0, l == 0 && sw == A.nu2 - 1);
+          FX_BAR();
+        }
+      }
+      if (A.any_full_tail || A.nu2 == 0) {
+        phase_update(c);
+        FX_BAR();
+      }
+    }
+    if (A.mode == 0 && blockIdx.x == 0)
+      for (int i = threadIdx.x; i < A.ninst; i += blockDim.x) A.inst[i].resid.stats->steps += 1;
+  }
+  if (A.dbg && threadIdx.x == 0) A.dbg[8 + blockIdx.x] = nbar;
+#undef FX_BAR
+}
+
+// Failure-detection check: block 1 never arrives, so block 0's bounded wait
+// must run out and record FERROX_ETIMEOUT.
+__global__ void barrier_timeout_kernel(GridBar* gb, int* status, long long limit) {
+  if (blockIdx.x == 1) return;
+  grid_barrier(gb, status, limit);
+}
+
+}  // namespace
+
+cudaError_t launch_barrier_timeout(GridBar* gb, int* status, long long limit, cudaStream_t s) {
+  barrier_timeout_kernel<<<2, 32, 0, s>>>(gb, status, limit);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t batch_prepare(size_t smem) {
+  return cudaFuncSetAttribute(batch_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <typename T>
+cudaError_t batch_occupancy(int threads, size_t smem, int* blocks_per_sm) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, batch_kernel<T>, threads, smem);
+}
+
+template <typename T>
+cudaError_t launch_batch(const BatchArgs& a, int blocks, int threads, size_t smem, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, batch_kernel<T>, a);
+}
+
+template cudaError_t batch_prepare<double>(size_t);
+template cudaError_t batch_prepare<float>(size_t);
+template cudaError_t batch_occupancy<double>(int, size_t, int*);
+template cudaError_t batch_occupancy<float>(int, size_t, int*);
+template cudaError_t launch_batch<double>(const BatchArgs&, int, int, size_t, cudaStream_t);
+template cudaError_t launch_batch<float>(const BatchArgs&, int, int, size_t, cudaStream_t);
+
+}  // namespace fx

@@ -56,7 +56,10 @@ class Stats(C.Structure):
 EXPORTS = ["ferrox_init_geometry", "ferrox_set_bias", "ferrox_solve_poisson", "ferrox_tdgl_update",
            "ferrox_step", "ferrox_charge", "ferrox_sync_stats", "ferrox_clear_status",
            "ferrox_get_state", "ferrox_set_state", "ferrox_destroy", "ferrox_last_error",
-           "ferrox_level_shape", "ferrox_profile_step", "ferrox_tdgl_update_static"]
+           "ferrox_level_shape", "ferrox_profile_step", "ferrox_tdgl_update_static",
+           "ferrox_init_batch", "ferrox_batch_set_bias", "ferrox_batch_solve_poisson",
+           "ferrox_batch_step", "ferrox_batch_charge", "ferrox_batch_stats", "ferrox_batch_tuning",
+           "ferrox_batch_destroy", "ferrox_batch_last_error", "ferrox_check_wait_timeout"]
 
 KERNEL_CLASSES = ["tdgl", "resid", "smooth_fine", "smooth_coarse", "restrict", "prolong", "tail",
                   "update", "copy"]
@@ -90,8 +93,20 @@ def load(path: str = LIB_PATH):
     lib.ferrox_profile_step.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int)]
     lib.ferrox_tdgl_update_static.argtypes = [C.POINTER(Geometry), C.c_double, C.c_double,
                                               C.c_double, vp, vp, vp]
+    lib.ferrox_init_batch.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(Geometry),
+                                      C.POINTER(Numerics), vp, vp, vp]
+    lib.ferrox_batch_set_bias.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    lib.ferrox_batch_solve_poisson.argtypes = [vp]
+    lib.ferrox_batch_step.argtypes = [vp, C.c_int]
+    lib.ferrox_batch_charge.argtypes = [vp, C.POINTER(Charge)]
+    lib.ferrox_batch_stats.argtypes = [vp, C.POINTER(Stats)]
+    lib.ferrox_batch_tuning.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    lib.ferrox_batch_destroy.argtypes = [vp]
+    lib.ferrox_batch_last_error.argtypes = [vp]
+    lib.ferrox_batch_last_error.restype = C.c_char_p
+    lib.ferrox_check_wait_timeout.argtypes = [C.c_double, C.POINTER(C.c_int), vp]
     for name in EXPORTS:
-        if name != "ferrox_last_error":
+        if name not in ("ferrox_last_error", "ferrox_batch_last_error"):
             getattr(lib, name).restype = st
     _lib = lib
     return lib
@@ -244,3 +259,102 @@ class Device:
             self.close()
         except Exception:
             pass
+
+
+class Batch:
+    """n independent device stacks advanced by one persistent launch per call.
+
+    geoms: list of geometry dicts (ncomp = 1); P0s: list of (1, Nz, Ny, Nx) arrays.
+    The state lives in two packed torch tensors (instances back to back)."""
+
+    def __init__(self, geoms, P0s, numerics, stream=None, device="cuda:0"):
+        import torch
+        self.lib = load()
+        self.geoms = geoms
+        self.shapes = [(sum(l["ncells"] for l in g["layers"]), g["ny"], g["nx"]) for g in geoms]
+        self.sizes = [int(np.prod(s)) for s in self.shapes]
+        self.offsets = np.concatenate([[0], np.cumsum(self.sizes)]).astype(np.int64)
+        flat = np.concatenate([np.asarray(p, dtype=np.float64).ravel() for p in P0s])
+        self.P = torch.as_tensor(flat, device=device).contiguous().clone()
+        self.phi = torch.zeros_like(self.P)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.P.device)
+        self._layers = [make_layers(g["layers"]) for g in geoms]
+        garr = (Geometry * len(geoms))()
+        for q, g in enumerate(geoms):
+            garr[q] = Geometry(g["nx"], g["ny"], g["h"], len(g["layers"]), self._layers[q], g["pbc"],
+                               g["lam"], 1)
+        self._garr = garr
+        self.numerics = numerics
+        self.ctx = C.c_void_p()
+        rc = self.lib.ferrox_init_batch(C.byref(self.ctx), len(geoms), garr, C.byref(numerics),
+                                        C.c_void_p(self.P.data_ptr()), C.c_void_p(self.phi.data_ptr()),
+                                        C.c_void_p(self.stream.cuda_stream))
+        if rc != FERROX_OK:
+            raise FerroxError(rc, self.lib.ferrox_batch_last_error(None).decode())
+
+    def _ck(self, rc):
+        if rc != FERROX_OK:
+            raise FerroxError(rc, self.lib.ferrox_batch_last_error(self.ctx).decode())
+
+    def set_bias(self, v_bottom, v_top):
+        n = len(self.geoms)
+        vb = (C.c_double * n)(*[float(v) for v in np.broadcast_to(v_bottom, n)])
+        vt = (C.c_double * n)(*[float(v) for v in np.broadcast_to(v_top, n)])
+        self._ck(self.lib.ferrox_batch_set_bias(self.ctx, vb, vt))
+
+    def solve_poisson(self):
+        self._ck(self.lib.ferrox_batch_solve_poisson(self.ctx))
+
+    def step(self, n=1):
+        self._ck(self.lib.ferrox_batch_step(self.ctx, int(n)))
+
+    def stats(self, check=True):
+        n = len(self.geoms)
+        out = (Stats * n)()
+        rc = self.lib.ferrox_batch_stats(self.ctx, out)
+        if check:
+            self._ck(rc)
+        return [{k: getattr(o, k) for k, _ in Stats._fields_} for o in out]
+
+    def charge(self):
+        n = len(self.geoms)
+        out = (Charge * n)()
+        self._ck(self.lib.ferrox_batch_charge(self.ctx, out))
+        return [{k: getattr(o, k) for k, _ in Charge._fields_} for o in out]
+
+    def tuning(self):
+        t, r, b = C.c_int(), C.c_int(), C.c_int()
+        rc = self.lib.ferrox_batch_tuning(self.ctx, C.byref(t), C.byref(r), C.byref(b))
+        return dict(threads=t.value, rows_per_unit=r.value, blocks=b.value, tuned=rc == FERROX_OK)
+
+    def state(self, i):
+        """(P, phi) of instance i as numpy arrays (synchronises)."""
+        import torch
+        torch.cuda.synchronize()
+        a, b = self.offsets[i], self.offsets[i + 1]
+        shp = self.shapes[i]
+        return (self.P[a:b].cpu().numpy().reshape((1,) + shp), self.phi[a:b].cpu().numpy().reshape(shp))
+
+    def close(self):
+        if self.ctx:
+            self.lib.ferrox_batch_destroy(self.ctx)
+            self.ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def check_wait_timeout(seconds=0.2, stream=None):
+    """Run the bounded-wait check; returns the status the device recorded."""
+    import torch
+    lib = load()
+    st = stream if stream is not None else torch.cuda.current_stream()
+    out = C.c_int(-1)
+    rc = lib.ferrox_check_wait_timeout(float(seconds), C.byref(out), C.c_void_p(st.cuda_stream))
+    if rc != FERROX_OK:
+        raise FerroxError(rc, lib.ferrox_batch_last_error(None).decode())
+    return out.value
+

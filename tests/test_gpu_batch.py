@@ -1,0 +1,103 @@
+"""Batched persistent engine (one cooperative launch per call) on the GPU.
+
+Every instance of a batch of uneven lateral sizes and biases must follow the
+same trajectory as the oracle run of that instance alone, and as the
+single-instance GPU path, within the tolerances of the single-instance tests.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import tdgl, diagnostics
+from paper_2210_15668_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def small_batch(n=6, seed=3):
+    rng = np.random.default_rng(seed)
+    sizes = rng.choice([32, 48, 64], size=n)
+    biases = rng.uniform(-2.0, 2.0, size=n)
+    geoms = [I.make_geometry(int(s), int(s), I.mfim_stack(16)) for s in sizes]
+    P0s = [I.random_polarization(g, seed=100 + i) for i, g in enumerate(geoms)]
+    return geoms, P0s, biases
+
+
+@pytest.mark.parametrize("precision,tol,bound", [(0, 1e-12, 1e-9), (1, 1e-12, 1e-9), (1, 1e-10, 2e-8)])
+def test_batch_matches_oracle_per_instance(precision, tol, bound):
+    from paper_2210_15668_gb300 import ferrox
+    geoms, P0s, biases = small_batch()
+    num = ferrox.make_numerics(4e-13, tol=tol, precision=precision)
+    B = ferrox.Batch(geoms, P0s, num)
+    B.set_bias(np.zeros(len(geoms)), biases)
+    B.solve_poisson()
+    steps = 20
+    B.step(steps)
+    st = B.stats()
+    tune = B.tuning()
+    assert tune["tuned"] and tune["threads"] in (256, 512) and tune["rows_per_unit"] in (1, 2, 4)
+    charges = B.charge()
+    for i, g in enumerate(geoms):
+        pl = oracle.planes(g)
+        Po, phio = tdgl.run(P0s[i], pl, g, 4e-13, 0.0, biases[i], steps)
+        Pg, phig = B.state(i)
+        assert st[i]["status"] == 0 and st[i]["steps"] == steps
+        assert rel_l2(Pg, Po) <= bound and rel_l2(phig, phio) <= bound, (i, rel_l2(Pg, Po))
+        qo = diagnostics.charges(phio, Po, pl, g, 0.0, biases[i])
+        assert abs(charges[i]["sigma_top"] - qo["sigma_top"]) <= 1e-7 * abs(qo["sigma_top"])
+    B.close()
+
+
+def test_batch_matches_single_instance_gpu_path():
+    from paper_2210_15668_gb300 import ferrox
+    geoms, P0s, biases = small_batch(n=4, seed=5)
+    num = ferrox.make_numerics(4e-13, tol=1e-10, precision=1)
+    B = ferrox.Batch(geoms, P0s, num)
+    B.set_bias(np.zeros(len(geoms)), biases)
+    B.solve_poisson()
+    B.step(10)
+    sb = B.stats()
+    for i, g in enumerate(geoms):
+        d = ferrox.Device(g, P0s[i], numerics=ferrox.make_numerics(4e-13, tol=1e-10, precision=1))
+        d.set_bias(0.0, biases[i])
+        d.solve_poisson()
+        d.step(10)
+        Ps, phis = d.get_state()
+        Pb, phib = B.state(i)
+        assert rel_l2(Pb, Ps) <= 1e-10 and rel_l2(phib, phis) <= 1e-10
+        assert abs(d.stats()["cycles"] - sb[i]["cycles"]) <= 2
+        d.close()
+    B.close()
+
+
+def test_instances_drop_out_independently():
+    """A zero-bias, zero-polarization instance converges at once while the others iterate."""
+    from paper_2210_15668_gb300 import ferrox
+    geoms, P0s, biases = small_batch(n=3, seed=7)
+    P0s[1] = np.zeros_like(P0s[1])
+    biases = np.array([1.5, 0.0, -1.0])
+    B = ferrox.Batch(geoms, P0s, ferrox.make_numerics(4e-13, precision=1))
+    B.set_bias(np.zeros(3), biases)
+    B.solve_poisson()
+    st = B.stats()
+    assert st[1]["last_cycles"] == 0 and st[0]["last_cycles"] > 0 and st[2]["last_cycles"] > 0
+    assert np.all(B.state(1)[1] == 0.0)
+    B.close()
+
+
+def test_bounded_wait_reports_timeout():
+    """A grid barrier that one block never reaches ends with FERROX_ETIMEOUT."""
+    from paper_2210_15668_gb300 import ferrox
+    assert ferrox.check_wait_timeout(0.2) == ferrox.FERROX_ETIMEOUT
+    # the context stays usable afterwards
+    g = I.make_geometry(16, 16, I.mfim_stack(8, n_fe=4))
+    d = ferrox.Device(g, I.random_polarization(g, seed=1))
+    d.set_bias(0.0, 0.3)
+    d.solve_poisson()
+    assert d.stats()["status"] == 0
+    d.close()
