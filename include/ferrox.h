@@ -97,6 +97,10 @@ typedef struct {
   int max_cycles;   /* V-cycles (outer iterations) allowed per solve */
   int precision;    /* FERROX_FP64 or FERROX_MIXED */
   int bottom_sweeps;/* sweeps on the coarsest level (0: default) */
+  int guess;        /* initial potential of each step's solve: 0 = the previous step's
+                       potential (Step 1b of the Methods), 1 = linear extrapolation in
+                       time 2 Phi^n - Phi^{n-1}.  The solve stops on the same residual
+                       test either way; only the number of V-cycles changes. */
 } ferrox_numerics;
 
 typedef struct {
@@ -174,7 +178,7 @@ enum {
   FERROX_K_PROLONG = 5,   /* prolongation + correction */
   FERROX_K_TAIL = 6,      /* single-CTA V-cycle over the smallest levels */
   FERROX_K_UPDATE = 7,    /* phi += correction */
-  FERROX_K_COPY = 8,      /* copy of the new polarization into the caller's array */
+  FERROX_K_COPY = 8,      /* copy of the new polarization; initial-guess extrapolation */
   FERROX_K_COUNT = 9
 };
 

@@ -63,6 +63,7 @@ struct ferrox_ctx {
   double* b = nullptr;
   double* Pbuf = nullptr;
   double* Fbuf = nullptr;
+  double* phi_prev = nullptr;         // previous step's potential (guess = 1)
   void* e_arena = nullptr;
   void* r_arena = nullptr;
   void* s_arena = nullptr;
@@ -445,17 +446,21 @@ ferrox_status build_graphs_t(ferrox_ctx* ctx) {
   FX_CK(cudaGraphInstantiate(&ctx->ge_tdgl, ctx->gr_tdgl, 0));
   // full time step
   FX_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+  const long long N = (long long)ctx->nx * ctx->ny * ctx->nz;
   if (ctx->num.order == 1) {
     launch_tdgl(tdgl_args(ctx, 0), s);                 // Step 1a
     FX_CK(enqueue_copy_back(ctx, s));
+    if (ctx->num.guess == 1) launch_extrapolate(ctx->phi, ctx->phi_prev, N, s);
     if ((rc = capture_solve<T>(ctx, s)) != FERROX_OK) return rc;   // Step 1b
   } else {
     launch_tdgl(tdgl_args(ctx, 1), s);                 // Step 1a (P* to scratch, f(P^n) kept)
+    if (ctx->num.guess == 1) launch_extrapolate(ctx->phi, ctx->phi_prev, N, s);
     if ((rc = capture_solve<T>(ctx, s)) != FERROX_OK) return rc;   // Step 1b: Phi*
     launch_tdgl(tdgl_args(ctx, 2), s);                 // Step 2a: P^{n+1} into the caller's P
     if ((rc = capture_solve<T>(ctx, s)) != FERROX_OK) return rc;   // Step 2b
   }
-  launch_stats_step(ctx->stats_d, 1, tdgl_launches(ctx) * ctx->num.order + 1, s);
+  launch_stats_step(ctx->stats_d, 1,
+                    tdgl_launches(ctx) * ctx->num.order + 1 + (ctx->num.guess == 1 ? 1 : 0), s);
   FX_CK(cudaGetLastError());
   FX_CK(cudaStreamEndCapture(s, &ctx->gr_step));
   FX_CK(cudaGraphInstantiate(&ctx->ge_step, ctx->gr_step, 0));
@@ -499,17 +504,21 @@ ferrox_status profile_step_t(ferrox_ctx* ctx, double* ms, int* count) {
     return FERROX_OK;
   };
   ferrox_status rc;
+  const long long N = (long long)ctx->nx * ctx->ny * ctx->nz;
   if (ctx->num.order == 1) {
     tm(FERROX_K_TDGL, [&] { launch_tdgl(tdgl_args(ctx, 0), s); });
     tm(FERROX_K_COPY, [&] { enqueue_copy_back(ctx, s); });
+    if (ctx->num.guess == 1) tm(FERROX_K_COPY, [&] { launch_extrapolate(ctx->phi, ctx->phi_prev, N, s); });
     if ((rc = solve()) != FERROX_OK) return rc;
   } else {
     tm(FERROX_K_TDGL, [&] { launch_tdgl(tdgl_args(ctx, 1), s); });
+    if (ctx->num.guess == 1) tm(FERROX_K_COPY, [&] { launch_extrapolate(ctx->phi, ctx->phi_prev, N, s); });
     if ((rc = solve()) != FERROX_OK) return rc;
     tm(FERROX_K_TDGL, [&] { launch_tdgl(tdgl_args(ctx, 2), s); });
     if ((rc = solve()) != FERROX_OK) return rc;
   }
-  launch_stats_step(ctx->stats_d, 1, tdgl_launches(ctx) * ctx->num.order + 1, s);
+  launch_stats_step(ctx->stats_d, 1,
+                    tdgl_launches(ctx) * ctx->num.order + 1 + (ctx->num.guess == 1 ? 1 : 0), s);
   FX_CK(cudaGetLastError());
   FX_CK(cudaStreamSynchronize(s));
   for (int k = 0; k < FERROX_K_COUNT; ++k) { ms[k] = 0.0; count[k] = 0; }
@@ -531,7 +540,7 @@ void release(ferrox_ctx* c) {
   cudaGraph_t gr[3] = {c->gr_step, c->gr_solve, c->gr_tdgl};
   for (auto g : ge) if (g) cudaGraphExecDestroy(g);
   for (auto g : gr) if (g) cudaGraphDestroy(g);
-  void* ptrs[] = {c->b, c->Pbuf, c->Fbuf, c->e_arena, c->r_arena, c->s_arena, c->coef, c->coef0,
+  void* ptrs[] = {c->b, c->Pbuf, c->Fbuf, c->phi_prev, c->e_arena, c->r_arena, c->s_arena, c->coef, c->coef0,
                   c->planes_d, c->lv_d, c->lvt_d, c->params_d, c->stats_d, c->partials_d, c->charge_d,
                   c->charge_part_d};
   for (void* p : ptrs) if (p) cudaFree(p);
@@ -575,6 +584,7 @@ ferrox_status validate(const ferrox_geometry* g, const ferrox_numerics* n, const
   if (n->max_cycles < 1) return bad("max_cycles must be >= 1");
   if (n->precision != FERROX_FP64 && n->precision != FERROX_MIXED) return bad("unknown precision");
   if (n->bottom_sweeps < 0) return bad("bottom_sweeps must be >= 0");
+  if (n->guess != 0 && n->guess != 1) return bad("guess must be 0 or 1");
   return FERROX_OK;
 }
 
@@ -621,6 +631,10 @@ ferrox_status ferrox_init_geometry(ferrox_ctx** out, const ferrox_geometry* geom
   FX_INIT_CK(cudaMalloc(&ctx->b, N * sizeof(double)));
   FX_INIT_CK(cudaMalloc(&ctx->Pbuf, ctx->ncomp * N * sizeof(double)));
   if (ctx->num.order == 2) FX_INIT_CK(cudaMalloc(&ctx->Fbuf, ctx->ncomp * N * sizeof(double)));
+  if (ctx->num.guess == 1) {
+    FX_INIT_CK(cudaMalloc(&ctx->phi_prev, N * sizeof(double)));
+    FX_INIT_CK(cudaMemset(ctx->phi_prev, 0, N * sizeof(double)));
+  }
   FX_INIT_CK(cudaMalloc(&ctx->e_arena, ctx->arena * tsz));
   FX_INIT_CK(cudaMalloc(&ctx->r_arena, ctx->arena * tsz));
   if (ctx->has_sc) FX_INIT_CK(cudaMalloc(&ctx->s_arena, ctx->arena * tsz));
@@ -686,6 +700,9 @@ ferrox_status ferrox_solve_poisson(ferrox_ctx* ctx) {
   launch_tdgl(tdgl_args(ctx, 3), ctx->stream);
   FX_CK(cudaGetLastError());
   FX_CK(cudaGraphLaunch(ctx->ge_solve, ctx->stream));
+  if (ctx->num.guess == 1)   // no history yet: the first step starts from this potential
+    FX_CK(cudaMemcpyAsync(ctx->phi_prev, ctx->phi, (size_t)ctx->nx * ctx->ny * ctx->nz * sizeof(double),
+                          cudaMemcpyDeviceToDevice, ctx->stream));
   return FERROX_OK;
 }
 
@@ -791,8 +808,12 @@ ferrox_status ferrox_set_state(ferrox_ctx* ctx, const double* P_host, const doub
   if (P_host)
     FX_CK(cudaMemcpyAsync(ctx->P, P_host, ctx->ncomp * N * sizeof(double), cudaMemcpyHostToDevice,
                           ctx->stream));
-  if (phi_host)
+  if (phi_host) {
     FX_CK(cudaMemcpyAsync(ctx->phi, phi_host, N * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    if (ctx->num.guess == 1)   // a new state has no history
+      FX_CK(cudaMemcpyAsync(ctx->phi_prev, ctx->phi, N * sizeof(double), cudaMemcpyDeviceToDevice,
+                            ctx->stream));
+  }
   return FERROX_OK;
 }
 
@@ -879,7 +900,8 @@ struct ferrox_batch {
 namespace {
 
 std::mutex g_tune_mu;
-std::vector<std::pair<std::string, std::pair<int, int>>> g_tune_cache;
+struct TuneChoice { int threads, rows, bps; };
+std::vector<std::pair<std::string, TuneChoice>> g_tune_cache;
 
 ferrox_status bfail(ferrox_batch* b, ferrox_status s, const std::string& m) {
   if (b) b->err = m; else g_init_error = m;
@@ -935,7 +957,7 @@ cudaError_t batch_launch(ferrox_batch* B, int mode, cudaStream_t s) {
                   : launch_batch<double>(a, B->blocks, B->threads, B->smem, s);
 }
 
-ferrox_status batch_configure(ferrox_batch* B, int threads, int R) {
+ferrox_status batch_configure(ferrox_batch* B, int threads, int R, int bps = 1) {
   int per_sm = 0;
   FX_BCK(B->mixed ? batch_occupancy<float>(threads, B->smem, &per_sm)
                   : batch_occupancy<double>(threads, B->smem, &per_sm));
@@ -945,9 +967,9 @@ ferrox_status batch_configure(ferrox_batch* B, int threads, int R) {
   FX_BCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   B->threads = threads;
   B->rows_per_unit = R;
-  // one CTA per SM: every block of the persistent launch is resident whatever
-  // shared-memory carveout the driver picks, so the grid barriers can complete
-  B->blocks = sms;
+  // bps CTAs per SM, never more than the occupancy calculation allows (the
+  // cooperative launch then guarantees they are all resident together)
+  B->blocks = sms * std::min(bps, per_sm);
   const std::vector<int> pre = batch_prefix(B, R);
   FX_BCK(cudaMemcpy(B->pre, pre.data(), pre.size() * sizeof(int), cudaMemcpyHostToDevice));
   return FERROX_OK;
@@ -966,7 +988,7 @@ ferrox_status batch_autotune(ferrox_batch* B) {
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     for (auto& kv : g_tune_cache)
-      if (kv.first == key) return batch_configure(B, kv.second.first, kv.second.second);
+      if (kv.first == key) return batch_configure(B, kv.second.threads, kv.second.rows, kv.second.bps);
   }
   const size_t bytes = (size_t)B->cells * sizeof(double);
   cudaStream_t s = B->stream;
@@ -981,11 +1003,16 @@ ferrox_status batch_autotune(ferrox_batch* B) {
   FX_BCK(cudaEventCreate(&e0));
   FX_BCK(cudaEventCreate(&e1));
   float best = 1e30f;
-  int bt = 512, bR = 1;
-  const int cand_t[2] = {256, 512}, cand_R[3] = {1, 2, 4};
+  int bt = 512, bR = 1, bB = 1;
+  const int cand_t[2] = {256, 512}, cand_R[3] = {1, 2, 4}, cand_b[2] = {1, 2};
+  for (int bi = 0; bi < 2; ++bi)
   for (int ti = 0; ti < 2; ++ti)
     for (int ri = 0; ri < 3; ++ri) {
-      ferrox_status rc = batch_configure(B, cand_t[ti], cand_R[ri]);
+      int per_sm = 0;
+      FX_BCK(B->mixed ? batch_occupancy<float>(cand_t[ti], B->smem, &per_sm)
+                      : batch_occupancy<double>(cand_t[ti], B->smem, &per_sm));
+      if (cand_b[bi] > per_sm) continue;
+      ferrox_status rc = batch_configure(B, cand_t[ti], cand_R[ri], cand_b[bi]);
       if (rc != FERROX_OK) return rc;
       FX_BCK(cudaEventRecord(e0, s));
       FX_BCK(batch_launch(B, 0, s));
@@ -996,7 +1023,7 @@ ferrox_status batch_autotune(ferrox_batch* B) {
       int gst = 0;
       FX_BCK(cudaMemcpy(&gst, B->status, sizeof(int), cudaMemcpyDeviceToHost));
       if (gst != 0) return bfail(B, (ferrox_status)gst, "batch kernel failed while tuning");
-      if (ms < best) { best = ms; bt = cand_t[ti]; bR = cand_R[ri]; }
+      if (ms < best) { best = ms; bt = cand_t[ti]; bR = cand_R[ri]; bB = cand_b[bi]; }
       FX_BCK(cudaMemcpyAsync(B->P, B->backup, bytes, cudaMemcpyDeviceToDevice, s));
       FX_BCK(cudaMemcpyAsync(B->phi, B->backup + B->cells, bytes, cudaMemcpyDeviceToDevice, s));
       FX_BCK(cudaMemcpyAsync(B->stats, st0.data(), B->n * sizeof(DevStats), cudaMemcpyHostToDevice, s));
@@ -1006,9 +1033,9 @@ ferrox_status batch_autotune(ferrox_batch* B) {
   cudaEventDestroy(e1);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune_cache.push_back({key, {bt, bR}});
+    g_tune_cache.push_back({key, {bt, bR, bB}});
   }
-  return batch_configure(B, bt, bR);
+  return batch_configure(B, bt, bR, bB);
 }
 
 ferrox_status batch_build_graphs(ferrox_batch* B) {

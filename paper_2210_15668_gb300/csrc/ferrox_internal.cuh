@@ -20,6 +20,19 @@ constexpr int kTailThreads = 1024;
 constexpr int kTailMaxSmem = 200 * 1024; // shared memory available to the tail CTA
 constexpr int kResidBX = 32, kResidBY = 8; // residual: one thread per (x, y) column
 
+// Copy of a read-only table entry through the read-only data path (8-byte
+// loads); fields the caller never uses are removed by the compiler.
+template <typename S>
+__device__ __forceinline__ S ldg_struct(const S* p) {
+  static_assert(sizeof(S) % 8 == 0, "table entries are padded to 8 bytes");
+  S out;
+  const unsigned long long* src = reinterpret_cast<const unsigned long long*>(p);
+  unsigned long long* dst = reinterpret_cast<unsigned long long*>(&out);
+#pragma unroll
+  for (int q = 0; q < (int)(sizeof(S) / 8); ++q) dst[q] = __ldg(src + q);
+  return out;
+}
+
 // ---- per-plane data of the fine level (device, read-only during a step) -------------
 struct PlaneTDGL {
   int fe;          // ferroelectric plane
@@ -222,6 +235,7 @@ cudaError_t batch_occupancy(int threads, size_t smem, int* blocks_per_sm);
 template <typename T>
 cudaError_t launch_batch(const BatchArgs& a, int blocks, int threads, size_t smem, cudaStream_t s);
 void launch_set_params(DevParams* p, double v_bot, double v_top, cudaStream_t s);
+void launch_extrapolate(double* phi, double* prev, long long n, cudaStream_t s);
 void launch_stats_step(DevStats* st, int nsteps, int launches, cudaStream_t s);
 
 }  // namespace fx

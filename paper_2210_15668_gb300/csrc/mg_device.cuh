@@ -57,7 +57,7 @@ __device__ __forceinline__ void smooth_pair(const MGArgs<T>& a, const LevelDesc&
   const int par = (j + k + color) & 1;
   const int i = 2 * ip + par;
   const int i2 = 2 * ip + (par ^ 1);
-  const PlaneCoef<T> c = a.coef[L.coef_off + k];
+  const PlaneCoef<T> c = ldg_struct(a.coef + L.coef_off + k);
   T ev = T(0);
   long long id = -1;
   if (i < L.nx) {
@@ -83,7 +83,7 @@ __device__ __forceinline__ void smooth_pair(const MGArgs<T>& a, const LevelDesc&
 template <typename T>
 __device__ __forceinline__ T cell_residual(const MGArgs<T>& a, const LevelDesc& L, int i, int j,
                                            int k) {
-  const PlaneCoef<T> c = a.coef[L.coef_off + k];
+  const PlaneCoef<T> c = ldg_struct(a.coef + L.coef_off + k);
   const long long id = lidx(L, i, j, k);
   T num = gs_numerator(a.e, a.r, c, L, i, j, k, id);   // r + couplings * neighbours
   T d = c.has_s ? c.diag + a.s[id] : c.diag;
@@ -204,7 +204,7 @@ __device__ void tail_vcycle(const MGArgs<T>& g, const TailArgs& t, unsigned char
   MGArgs<T> a;
   a.e = se; a.r = sr; a.s = ss; a.coef = g.coef; a.lv = lv;
   for (int l = 0; l + 1 < t.nlev; ++l) {
-    const LevelDesc F = lv[l], C = lv[l + 1];
+    const LevelDesc F = ldg_struct(lv + l), C = ldg_struct(lv + l + 1);
     tail_smooth(a, F, t.nu1, 1);
     const int nc = (int)C.ncell;
     for (int q = threadIdx.x; q < nc; q += blockDim.x)
@@ -213,7 +213,7 @@ __device__ void tail_vcycle(const MGArgs<T>& g, const TailArgs& t, unsigned char
   }
   tail_smooth(a, lv[t.nlev - 1], t.bottom_sweeps, 1);
   for (int l = t.nlev - 2; l >= 0; --l) {
-    const LevelDesc F = lv[l], C = lv[l + 1];
+    const LevelDesc F = ldg_struct(lv + l), C = ldg_struct(lv + l + 1);
     const int nc = (int)C.ncell;
     for (int q = threadIdx.x; q < nc; q += blockDim.x)
       prolong_cell(a, F, C, q % C.nx, (q / C.nx) % C.ny, q / (C.nx * C.ny), t.constant);
@@ -267,8 +267,8 @@ __device__ __forceinline__ void resid_column(const ResidArgs& a, int i, int j, d
   for (int k = 0; k < nz; ++k) {
     const long long t = k * plane + col;
     const double pu = (k < nz - 1) ? phi[t + plane] : 0.0;
-    const PlaneCoef<double> c = a.coef0[k];
-    const PlaneTDGL& pt = a.planes[k];
+    const PlaneCoef<double> c = ldg_struct(a.coef0 + k);
+    const PlaneTDGL pt = ldg_struct(a.planes + k);
     const double sx = phi[t + dxm] + phi[t + dxp];
     const double sy = phi[t + dym] + phi[t + dyp];
     double off = c.cx * sx;

@@ -114,7 +114,7 @@ __device__ void phase_tdgl(const Ctx<T>& c, int mode) {
   const int total = pre[A.ninst];
   for (int u = c.gwarp; u < total; u += c.nwarps) {
     const int i = find_inst(pre, A.ninst, u);
-    const BatchInst& I = A.inst[i];
+    const BatchInst I = ldg_struct(A.inst + i);
     TDGLArgs t = I.tdgl;
     t.mode = mode;
     const int j = u - pre[i];
@@ -131,7 +131,7 @@ __device__ void phase_resid(const Ctx<T>& c, int first, int copy_back) {
   for (int u = c.gwarp; u < total; u += c.nwarps) {
     const int i = find_inst(pre, A.ninst, u);
     if (!ld_flag(A.active + i)) continue;
-    const BatchInst& I = A.inst[i];
+    const BatchInst I = ldg_struct(A.inst + i);
     const int j = u - pre[i];
     ResidArgs ra = I.resid;
     ra.first = first;
@@ -185,8 +185,8 @@ __device__ void phase_smooth(const Ctx<T>& c, int l, int color, int zero_init, i
   for (int u = c.gwarp; u < total; u += c.nwarps) {
     const int i = find_inst(pre, A.ninst, u);
     if (!ld_flag(A.active + i)) continue;
-    const BatchInst& I = A.inst[i];
-    const LevelDesc L = A.lv[I.lv_off + l];
+    const BatchInst I = ldg_struct(A.inst + i);
+    const LevelDesc L = ldg_struct(A.lv + I.lv_off + l);
     const int nrc = (L.ny + R - 1) / R;
     const int q = u - pre[i];
     const int k = q / nrc, j0 = (q - k * nrc) * R;
@@ -208,8 +208,8 @@ __device__ void phase_transfer(const Ctx<T>& c, int l, int op) {
   for (int u = c.gwarp; u < total; u += c.nwarps) {
     const int i = find_inst(pre, A.ninst, u);
     if (!ld_flag(A.active + i)) continue;
-    const BatchInst& I = A.inst[i];
-    const LevelDesc F = A.lv[I.lv_off + l], Cc = A.lv[I.lv_off + l + 1];
+    const BatchInst I = ldg_struct(A.inst + i);
+    const LevelDesc F = ldg_struct(A.lv + I.lv_off + l), Cc = ldg_struct(A.lv + I.lv_off + l + 1);
     const int nrc = (Cc.ny + R - 1) / R;
     const int q = u - pre[i];
     const int K = q / nrc, J0 = (q - K * nrc) * R;
@@ -227,7 +227,7 @@ __device__ void phase_tail(const Ctx<T>& c, unsigned char* smem) {
   const BatchArgs& A = c.A;
   for (int i = blockIdx.x; i < A.ninst; i += gridDim.x) {
     if (!ld_flag(A.active + i)) continue;
-    const BatchInst& I = A.inst[i];
+    const BatchInst I = ldg_struct(A.inst + i);
     TailArgs t{A.lvt + I.lvt_off, I.nlev_tail, I.tail_elems, I.tail_base, A.nu1, A.nu2,
                I.bottom_sweeps, 0};
     tail_vcycle<T>(c.mg, t, smem);
@@ -242,10 +242,10 @@ __device__ void phase_update(const Ctx<T>& c) {
   const int total = pre[A.ninst];
   for (int u = c.gwarp; u < total; u += c.nwarps) {
     const int i = find_inst(pre, A.ninst, u);
-    const BatchInst& I = A.inst[i];
+    const BatchInst I = ldg_struct(A.inst + i);
     if (!ld_flag(A.active + i) || I.tail_first != 0) continue;
     const int j = u - pre[i];
-    const LevelDesc L = A.lv[I.lv_off];
+    const LevelDesc L = ldg_struct(A.lv + I.lv_off);
     const Upd up{I.phi, I.clamp, ld_flag(&I.resid.stats->zero_phi)};
     for (int k = 0; k < L.nz; ++k)
       for (int x = c.lane; x < L.nx; x += 32) {

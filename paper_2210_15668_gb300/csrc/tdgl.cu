@@ -122,6 +122,17 @@ __global__ void charge_finalize(const double* partials, double* out) {
   }
 }
 
+// phi <- 2 phi - phi_prev, phi_prev <- phi (initial guess of the next solve)
+__global__ void __launch_bounds__(256) extrapolate_kernel(double* __restrict__ phi,
+                                                          double* __restrict__ prev, long long n) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const double v = phi[t];
+    phi[t] = fma(2.0, v, -prev[t]);
+    prev[t] = v;
+  }
+}
+
 __global__ void set_params_kernel(DevParams* p, double v_bot, double v_top) {
   p->v_bot = v_bot;
   p->v_top = v_top;
@@ -148,6 +159,12 @@ void launch_tdgl(const TDGLArgs& a, cudaStream_t s) {
 void launch_charge(const ChargeArgs& a, cudaStream_t s) {
   charge_kernel<<<kChargeBlocks, 256, 0, s>>>(a);
   charge_finalize<<<1, 32, 0, s>>>(a.partials, a.out);
+}
+
+void launch_extrapolate(double* phi, double* prev, long long n, cudaStream_t s) {
+  long long b = (n + 255) / 256;
+  if (b > 152LL * 16) b = 152LL * 16;
+  extrapolate_kernel<<<(int)b, 256, 0, s>>>(phi, prev, n);
 }
 
 void launch_set_params(DevParams* p, double v_bot, double v_top, cudaStream_t s) {

@@ -24,8 +24,8 @@ __device__ __forceinline__ double force_z(const TDGLArgs& a, const PlaneTDGL& pt
   const double P = Pz[t];
   const double lat = (Pz[t - i + im] + Pz[t - i + ip]) +
                      (Pz[t + (long long)(jm - j) * a.nx] + Pz[t + (long long)(jp - j) * a.nx]);
-  const bool fe_dn = k > 0 && planes[k - 1].fe;
-  const bool fe_up = k < a.nz - 1 && planes[k + 1].fe;
+  const bool fe_dn = k > 0 && __ldg(&planes[k - 1].fe);
+  const bool fe_up = k < a.nz - 1 && __ldg(&planes[k + 1].fe);
   const double Pdn = fe_dn ? Pz[t - plane] : 0.0;
   const double Pup = fe_up ? Pz[t + plane] : 0.0;
   const double ph = phi[t];
@@ -38,7 +38,7 @@ __device__ __forceinline__ double force_z(const TDGLArgs& a, const PlaneTDGL& pt
   if (k == a.nz - 1) {
     phif_up = v_top;
   } else {
-    const PlaneTDGL& pu = planes[k + 1];
+    const PlaneTDGL pu = ldg_struct(planes + k + 1);
     phif_up = fma(pu.fw_L, ph, pu.fw_R * phi[t + plane]) - pu.fpc * (Pup - P);
   }
   const double lap = fma(-4.0, P, lat) * a.inv_h2;
@@ -63,8 +63,8 @@ __device__ __forceinline__ double force_xy(const TDGLArgs& a, const PlaneTDGL& p
   const long long tp = comp == 0 ? t - i + ip : t + (long long)(jp - j) * a.nx;
   const double lat = (Pc[t - i + im] + Pc[t - i + ip]) +
                      (Pc[t + (long long)(jm - j) * a.nx] + Pc[t + (long long)(jp - j) * a.nx]);
-  const bool fe_dn = k > 0 && planes[k - 1].fe;
-  const bool fe_up = k < a.nz - 1 && planes[k + 1].fe;
+  const bool fe_dn = k > 0 && __ldg(&planes[k - 1].fe);
+  const bool fe_up = k < a.nz - 1 && __ldg(&planes[k + 1].fe);
   const double Pdn = fe_dn ? Pc[t - plane] : 0.0;
   const double Pup = fe_up ? Pc[t + plane] : 0.0;
   const double lap = fma(-4.0, P, lat) * a.inv_h2;
@@ -91,12 +91,14 @@ __device__ __forceinline__ double advance(const TDGLArgs& a, long long idx, doub
 __device__ __forceinline__ double rhs_value(const TDGLArgs& a, const PlaneTDGL* planes, int k,
                                             double pn_dn, double pn, double pn_up, double v_bot,
                                             double v_top) {
-  const double Pf_dn = (k == 0) ? pn : fma(planes[k].fw_R, pn_dn, planes[k].fw_L * pn);
-  const double Pf_up =
-      (k == a.nz - 1) ? pn : fma(planes[k + 1].fw_R, pn, planes[k + 1].fw_L * pn_up);
+  const double Pf_dn =
+      (k == 0) ? pn : fma(__ldg(&planes[k].fw_R), pn_dn, __ldg(&planes[k].fw_L) * pn);
+  const double Pf_up = (k == a.nz - 1)
+                           ? pn
+                           : fma(__ldg(&planes[k + 1].fw_R), pn, __ldg(&planes[k + 1].fw_L) * pn_up);
   double b = -(Pf_up - Pf_dn) * a.b_scale;
-  if (k == 0) b = fma(planes[0].lift, v_bot, b);
-  if (k == a.nz - 1) b = fma(planes[a.nz - 1].lift, v_top, b);
+  if (k == 0) b = fma(__ldg(&planes[0].lift), v_bot, b);
+  if (k == a.nz - 1) b = fma(__ldg(&planes[a.nz - 1].lift), v_top, b);
   return b;
 }
 
@@ -116,7 +118,7 @@ __device__ __forceinline__ void tdgl_column(const TDGLArgs& a, int i, int j) {
   for (int k = a.kd_lo; k <= a.kd_hi + 1; ++k) {
     double pn = 0.0;
     if (k <= a.kd_hi) {
-      const PlaneTDGL& pt = planes[k];
+      const PlaneTDGL pt = ldg_struct(planes + k);
       if (pt.fe && a.mode == 3) {
         pn = Pz_in[k * plane + col];          // right-hand side of the current P only
       } else if (pt.fe) {

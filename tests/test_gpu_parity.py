@@ -252,3 +252,26 @@ def test_profile_step_equals_graph_step(precision):
         assert d.stats()["steps"] == 3
         d.close()
     assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_extrapolated_initial_guess_same_answer_fewer_cycles(precision):
+    """guess = 1 (2 phi^n - phi^{n-1}) changes where each solve starts, not where it
+    stops: the trajectory stays within the solver tolerance of the oracle."""
+    cfg = I.mfim_small()
+    geom = cfg["geom"]
+    pl = oracle.planes(geom)
+    P0 = I.random_polarization(geom, cfg["seed"])
+    Po, phio = tdgl.run(P0, pl, geom, cfg["dt"], 0.0, 0.5, 30)
+    cycles = []
+    for guess in (0, 1):
+        d = _dev(geom, P0, tol=1e-12, precision=precision, v=(0.0, 0.5), guess=guess)
+        d.solve_poisson()
+        d.step(30)
+        Pg, phig = d.get_state()
+        st = d.stats()
+        assert st["status"] == 0
+        assert rel_l2(Pg, Po) <= 1e-9 and rel_l2(phig, phio) <= 1e-9
+        cycles.append(st["cycles"])
+        d.close()
+    assert cycles[1] < cycles[0], cycles
