@@ -301,6 +301,8 @@ def run_ours(args, ws, rank, local):
         fast = {"precision": "mixed", "guess": "extrapolated", "value": ws * cells * K / (t4 / 1e3) / 1e6,
                 "ms_per_step": t4 / K, "vcycles_per_step": (s41["cycles"] - s40["cycles"]) / K}
         d4.close()
+    learned = None if (args.no_compare or args.no_learned) else run_learned(args, ws, cfg, geom, P0, cells,
+                                                                            sweep, timed_run)
     batch = None if args.no_batch else run_batch_qv(args, ws)
     mixed_v = value if prec_main == ferrox.MIXED else (other or {}).get("value")
     fp64_v = value if prec_main == ferrox.FP64 else (other or {}).get("value")
@@ -344,12 +346,53 @@ def run_ours(args, ws, rank, local):
             "vs_plain_fp64": (mixed_v / fp64_v) if (mixed_v and fp64_v) else None,
             "other_precision": other, "fast_form": fast,
             "vs_plain_fp64_fast_form": (fast["value"] / fp64_v) if (fast and fp64_v) else None,
-            "batch_qv": batch, "e2e": e2e, "cpu_baseline": cpu, "clocks": ck}
+            "learned_form": learned, "batch_qv": batch, "e2e": e2e, "cpu_baseline": cpu, "clocks": ck}
     if rank == 0:
         print(json.dumps(line))
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+# --------------------------------------------------------------- learned warm start -----
+
+def run_learned(args, ws, cfg, geom, P0, cells, sweep, timed_run):
+    """Mixed form + extrapolated guess + the learned warm start: snapshots recorded on
+    the workload itself (bias points of the sweep), GPU training, then timed steps."""
+    import numpy as np
+    import torch
+
+    from paper_2210_15668_gb300 import ferrox
+    num = ferrox.make_numerics(cfg["dt"], order=1, tol=1e-10, precision=ferrox.MIXED,
+                               max_cycles=200, guess=1)
+    d = ferrox.Device(geom, P0, numerics=num)
+    lv = d.levels()[2]
+    net = ferrox.NN(lv[2], lv[1], lv[0], capacity=args.nn_snapshots, seed=7)
+    d.set_bias(0.0, sweep[0])
+    d.solve_poisson()
+    d.attach_nn(net, 1)
+    t0 = time.perf_counter()
+    for k in range(args.nn_snapshots):
+        if k % 25 == 0:
+            d.set_bias(0.0, sweep[(k // 25) % len(sweep)])
+        d.step(1)
+    losses = net.train(epochs=args.nn_epochs, lr=3e-4, batch=8)
+    torch.cuda.synchronize()
+    prep = time.perf_counter() - t0
+    d.attach_nn(None, 0)
+    d.set_bias(0.0, sweep[0])
+    d.attach_nn(net, 2)
+    K = args.steps
+    t, s0, s1, _ = timed_run(d, K, args.warmup)
+    t = reduce_max(t, ws)
+    out = {"precision": "mixed", "guess": "extrapolated + learned", "value": ws * cells * K / (t / 1e3) / 1e6,
+           "ms_per_step": t / K, "vcycles_per_step": (s1["cycles"] - s0["cycles"]) / K,
+           "snapshots": args.nn_snapshots, "epochs": args.nn_epochs,
+           "train_loss_first_last": [float(losses[0]), float(losses[-1])],
+           "collect_and_train_s": prep, "params": 79.5e3}
+    d.close()
+    net.close()
+    return out
 
 
 # ------------------------------------------------------- batched Q-V sweep workload -----
@@ -456,6 +499,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--nn-snapshots", type=int, default=300)
+    ap.add_argument("--nn-epochs", type=int, default=20)
     ap.add_argument("--batch-steps", type=int, default=50)
     args = ap.parse_args()
     if args.warmup < 3:

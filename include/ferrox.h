@@ -242,6 +242,48 @@ ferrox_status ferrox_batch_destroy(ferrox_batch* b);
 ferrox_status ferrox_check_wait_timeout(double seconds, int* status_out, void* cuda_stream);
 const char* ferrox_batch_last_error(const ferrox_batch* b);
 
+/* ---- learned warm start ------------------------------------------------------------------
+ * Not in the paper (the workloads add it).  A small 3-D U-Net (about 80k
+ * parameters; BF16 weights and activations, FP32 accumulation on the tensor
+ * cores) acts on multigrid level 2 (the fine grid coarsened 2x2x2 twice).  It
+ * maps the restricted initial residual of each solve (scaled by its rms) and
+ * per-plane material, height and bias features to the restricted error of the
+ * initial guess; the prediction is prolongated and added to the guess before
+ * the multigrid cycles.  Multigrid still runs to the residual test, so the
+ * network can change the number of cycles, never the converged answer.
+ * Training data are snapshots the solver records in collect mode.
+ * Weights: per layer [27][Cin][Cout] FP32 (tap = 9 dz + 3 dy + dx), layers
+ * (16,16) (16,16) (16,32) (32,32) (48,16) (16,16); biases [Cout]. */
+typedef struct ferrox_nn ferrox_nn; /* opaque */
+
+/* A network for a D x H x W grid (all even) with a store for `capacity`
+ * snapshots; the caller supplies the initial weights and biases (host FP32). */
+ferrox_status ferrox_nn_create(ferrox_nn** out, int D, int H, int W, int capacity,
+                               const float* weights, const float* biases, void* cuda_stream);
+/* y_dev[m] = output channel 0 for input x_dev[m][16] (device FP32 arrays). */
+ferrox_status ferrox_nn_forward(ferrox_nn* nn, const float* x_dev, float* y_dev);
+/* Forward, mean-squared error against t_dev[m], backward: gradients accumulate. */
+ferrox_status ferrox_nn_loss_grad(ferrox_nn* nn, const float* x_dev, const float* t_dev,
+                                  float* loss_host);
+/* Copy weights, biases and accumulated gradients to host arrays (any may be NULL). */
+ferrox_status ferrox_nn_params(ferrox_nn* nn, float* w, float* b, float* gw, float* gb);
+ferrox_status ferrox_nn_set_params(ferrox_nn* nn, const float* w, const float* b);
+/* One Adam update (beta1 0.9, beta2 0.999, eps 1e-8) from the accumulated gradients,
+ * which are then cleared. */
+ferrox_status ferrox_nn_adam_step(ferrox_nn* nn, double lr);
+ferrox_status ferrox_nn_snapshot_count(const ferrox_nn* nn, int* count);
+/* `epochs` passes over the stored snapshots, an Adam step every `batch` of them;
+ * loss_per_epoch (host, may be NULL) receives the mean loss of each epoch. */
+ferrox_status ferrox_nn_train(ferrox_nn* nn, int epochs, double lr, int batch,
+                              float* loss_per_epoch);
+ferrox_status ferrox_nn_destroy(ferrox_nn* nn);
+const char* ferrox_nn_last_error(const ferrox_nn* nn);
+/* Attach a network to a context: mode 0 detaches, 1 records one snapshot per
+ * ferrox_step (order 1; the steps then run without a CUDA graph), 2 applies the
+ * network before every predictor solve (captured in the step graph).  The
+ * network grid must equal the context's level-2 grid. */
+ferrox_status ferrox_attach_nn(ferrox_ctx* ctx, ferrox_nn* nn, int mode);
+
 /* Limits of ferrox_tdgl_update_static (sizes of its file-scope scratch array). */
 #define FERROX_STATIC_MAX_CELLS 262144
 #define FERROX_STATIC_MAX_PLANES 512

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libferrox.so")
-SOURCES = ["engine.cu", "multigrid.cu", "tdgl.cu", "persistent.cu"]
+SOURCES = ["engine.cu", "multigrid.cu", "tdgl.cu", "persistent.cu", "nn.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 # The persistent engine exchanges data between CTAs of one launch through global

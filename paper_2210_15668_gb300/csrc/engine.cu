@@ -82,6 +82,16 @@ struct ferrox_ctx {
   cudaGraph_t gr_step = nullptr, gr_solve = nullptr, gr_tdgl = nullptr;
   cudaGraphExec_t ge_step = nullptr, ge_solve = nullptr, ge_tdgl = nullptr;
   double v_bot = 0.0, v_top = 0.0;
+  // learned warm start
+  ferrox_nn* nn = nullptr;
+  int nn_mode = 0;                 // 0 off, 1 collect snapshots, 2 use before each solve
+  int nn_level = 2;
+  double* nn_scale = nullptr;
+  double* phi_guess = nullptr;
+  float* nn_pf = nullptr;          // per-plane features of the network level
+  DevStats* nn_stats = nullptr;    // zeroed status for the prediction update
+  cudaGraph_t gr_step_nn = nullptr;
+  cudaGraphExec_t ge_step_nn = nullptr;
   std::string err;
 };
 
@@ -467,6 +477,91 @@ ferrox_status build_graphs_t(ferrox_ctx* ctx) {
   return FERROX_OK;
 }
 
+// ---- learned warm start --------------------------------------------------------------------
+
+// restricted initial residual -> network features (into x) and its rms (nn_scale)
+template <typename T>
+void enqueue_nn_features(ferrox_ctx* c, cudaStream_t s, __nv_bfloat16* x) {
+  ResidArgs a{};
+  a.phi = c->phi; a.b = c->b; a.planes = c->planes_d; a.coef0 = c->coef0; a.params = c->params_d;
+  a.nx = c->nx; a.ny = c->ny; a.nz = c->nz;
+  a.r_out = c->r_arena;
+  a.s_out = c->has_sc ? c->s_arena : nullptr;
+  a.stats = c->stats_d;
+  a.no_stats = 1;
+  launch_resid<T>(a, s);
+  T* r = static_cast<T*>(c->r_arena);
+  nn_bridge_restrict<T>(r, c->lv, c->nn_level, s);
+  nn_bridge_scale<T>(r, c->lv[c->nn_level], c->nn_scale, s);
+  nn_bridge_features<T>(r, c->lv[c->nn_level], c->nn_pf, c->nn_scale, c->params_d, x, s);
+}
+
+// network prediction of the coarse error, prolongated and added to phi
+template <typename T>
+void enqueue_nn_prelude(ferrox_ctx* c, cudaStream_t s) {
+  enqueue_nn_features<T>(c, s, nn_input(c->nn));
+  nn_run_forward(c->nn, s);
+  const size_t tsz = sizeof(T);
+  const int lv = c->nn_level;
+  cudaMemsetAsync(c->e_arena, 0, (size_t)c->lv[lv].off * tsz, s);
+  T* e = static_cast<T*>(c->e_arena);
+  nn_bridge_apply<T>(nn_output(c->nn), c->lv[lv], c->nn_scale, e, s);
+  MGArgs<T> a = mg_args<T>(c);
+  for (int l = lv - 1; l >= 0; --l) launch_prolong<T>(a, c->lv[l], c->lv[l + 1], 0, s);
+  launch_update<T>(c->phi, e, (long long)c->nx * c->ny * c->nz, c->nn_stats, update_clamp(c), s);
+}
+
+template <typename T>
+ferrox_status build_nn_graph_t(ferrox_ctx* ctx) {
+  cudaStream_t s = ctx->cap1;
+  ferrox_status rc;
+  const long long N = (long long)ctx->nx * ctx->ny * ctx->nz;
+  FX_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+  if (ctx->num.order == 1) {
+    launch_tdgl(tdgl_args(ctx, 0), s);
+    FX_CK(enqueue_copy_back(ctx, s));
+    if (ctx->num.guess == 1) launch_extrapolate(ctx->phi, ctx->phi_prev, N, s);
+    enqueue_nn_prelude<T>(ctx, s);
+    if ((rc = capture_solve<T>(ctx, s)) != FERROX_OK) return rc;
+  } else {
+    launch_tdgl(tdgl_args(ctx, 1), s);
+    if (ctx->num.guess == 1) launch_extrapolate(ctx->phi, ctx->phi_prev, N, s);
+    enqueue_nn_prelude<T>(ctx, s);
+    if ((rc = capture_solve<T>(ctx, s)) != FERROX_OK) return rc;
+    launch_tdgl(tdgl_args(ctx, 2), s);
+    if ((rc = capture_solve<T>(ctx, s)) != FERROX_OK) return rc;
+  }
+  launch_stats_step(ctx->stats_d, 1, 0, s);
+  FX_CK(cudaGetLastError());
+  FX_CK(cudaStreamEndCapture(s, &ctx->gr_step_nn));
+  FX_CK(cudaGraphInstantiate(&ctx->ge_step_nn, ctx->gr_step_nn, 0));
+  return FERROX_OK;
+}
+
+// one step that also records a (features, target) snapshot into the network's store
+template <typename T>
+ferrox_status collect_step_t(ferrox_ctx* ctx) {
+  cudaStream_t s = ctx->stream;
+  const long long N = (long long)ctx->nx * ctx->ny * ctx->nz;
+  if (ctx->num.order != 1) return fail(ctx, FERROX_EINVAL, "snapshot collection runs order-1 steps");
+  const int slot = nn_next_slot(ctx->nn);
+  const LevelDesc& L = ctx->lv[ctx->nn_level];
+  launch_tdgl(tdgl_args(ctx, 0), s);
+  FX_CK(enqueue_copy_back(ctx, s));
+  if (ctx->num.guess == 1) launch_extrapolate(ctx->phi, ctx->phi_prev, N, s);
+  enqueue_nn_features<T>(ctx, s, nn_snap_x(ctx->nn) + (size_t)slot * L.ncell * 16);
+  FX_CK(cudaMemcpyAsync(ctx->phi_guess, ctx->phi, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  FX_CK(cudaGraphLaunch(ctx->ge_solve, s));
+  T* e = static_cast<T*>(ctx->e_arena);
+  nn_bridge_guess_error<T>(ctx->phi, ctx->phi_guess, N, e, s);
+  nn_bridge_restrict<T>(e, ctx->lv, ctx->nn_level, s);
+  nn_bridge_target<T>(e, L, ctx->nn_scale, nn_snap_t(ctx->nn) + (size_t)slot * L.ncell, s);
+  launch_stats_step(ctx->stats_d, 1, 0, s);
+  FX_CK(cudaGetLastError());
+  nn_note_snapshots(ctx->nn, 1);
+  return FERROX_OK;
+}
+
 // ---- eager, event-timed step (per-kernel breakdown) -------------------------------------
 struct EventTimer {
   cudaStream_t s;
@@ -536,12 +631,12 @@ ferrox_status profile_step_t(ferrox_ctx* ctx, double* ms, int* count) {
 void release(ferrox_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
-  cudaGraphExec_t ge[3] = {c->ge_step, c->ge_solve, c->ge_tdgl};
-  cudaGraph_t gr[3] = {c->gr_step, c->gr_solve, c->gr_tdgl};
+  cudaGraphExec_t ge[4] = {c->ge_step, c->ge_solve, c->ge_tdgl, c->ge_step_nn};
+  cudaGraph_t gr[4] = {c->gr_step, c->gr_solve, c->gr_tdgl, c->gr_step_nn};
   for (auto g : ge) if (g) cudaGraphExecDestroy(g);
   for (auto g : gr) if (g) cudaGraphDestroy(g);
   void* ptrs[] = {c->b, c->Pbuf, c->Fbuf, c->phi_prev, c->e_arena, c->r_arena, c->s_arena, c->coef, c->coef0,
-                  c->planes_d, c->lv_d, c->lvt_d, c->params_d, c->stats_d, c->partials_d, c->charge_d,
+                  c->planes_d, c->lv_d, c->lvt_d, c->nn_scale, c->phi_guess, c->nn_pf, c->nn_stats, c->params_d, c->stats_d, c->partials_d, c->charge_d,
                   c->charge_part_d};
   for (void* p : ptrs) if (p) cudaFree(p);
   if (c->host_pinned) cudaFreeHost(c->host_pinned);
@@ -715,7 +810,66 @@ ferrox_status ferrox_tdgl_update(ferrox_ctx* ctx) {
 ferrox_status ferrox_step(ferrox_ctx* ctx, int nsteps) {
   if (!ctx) return fail(nullptr, FERROX_EINVAL, "null context");
   if (nsteps < 0) return fail(ctx, FERROX_EINVAL, "nsteps < 0");
-  for (int q = 0; q < nsteps; ++q) FX_CK(cudaGraphLaunch(ctx->ge_step, ctx->stream));
+  for (int q = 0; q < nsteps; ++q) {
+    if (ctx->nn_mode == 1) {
+      const ferrox_status rc = ctx->num.precision == FERROX_MIXED ? collect_step_t<float>(ctx)
+                                                                 : collect_step_t<double>(ctx);
+      if (rc != FERROX_OK) return rc;
+    } else if (ctx->nn_mode == 2) {
+      FX_CK(cudaGraphLaunch(ctx->ge_step_nn, ctx->stream));
+    } else {
+      FX_CK(cudaGraphLaunch(ctx->ge_step, ctx->stream));
+    }
+  }
+  return FERROX_OK;
+}
+
+ferrox_status ferrox_attach_nn(ferrox_ctx* ctx, ferrox_nn* nn, int mode) {
+  if (!ctx) return fail(nullptr, FERROX_EINVAL, "null context");
+  if (mode < 0 || mode > 2 || (mode > 0 && !nn)) return fail(ctx, FERROX_EINVAL, "bad mode or network");
+  FX_CK(cudaStreamSynchronize(ctx->stream));
+  if (mode == 0) { ctx->nn_mode = 0; ctx->nn = nullptr; return FERROX_OK; }
+  const int l = ctx->nn_level;
+  if ((int)ctx->lv.size() <= l) return fail(ctx, FERROX_EINVAL, "the hierarchy has no network level");
+  for (int q = 0; q < l; ++q)
+    if (!(ctx->lv[q].crx && ctx->lv[q].cry && ctx->lv[q].crz))
+      return fail(ctx, FERROX_EINVAL, "the network level must be reached by full 2x2x2 coarsening");
+  const NNGrid g = nn_grid(nn);
+  const LevelDesc& L = ctx->lv[l];
+  if (g.D != L.nz || g.H != L.ny || g.W != L.nx)
+    return fail(ctx, FERROX_EINVAL, "network grid does not match the network level of this context");
+  if (mode == 1 && nn_capacity(nn) < 1) return fail(ctx, FERROX_EINVAL, "network has no snapshot store");
+  if (!ctx->nn_scale) {
+    FX_CK(cudaMalloc(&ctx->nn_scale, sizeof(double)));
+    FX_CK(cudaMalloc(&ctx->phi_guess, (size_t)ctx->nx * ctx->ny * ctx->nz * sizeof(double)));
+    FX_CK(cudaMalloc(&ctx->nn_stats, sizeof(DevStats)));
+    FX_CK(cudaMemset(ctx->nn_stats, 0, sizeof(DevStats)));
+    std::vector<float> pf(4 * L.nz);
+    const int fz = ctx->nz / L.nz;
+    for (int K = 0; K < L.nz; ++K) {
+      double eps = 0.0, fe = 0.0, sc = 0.0;
+      for (int k = K * fz; k < (K + 1) * fz; ++k) {
+        eps += ctx->epsr[k];
+        fe += ctx->planes[k].fe;
+        sc += ctx->planes[k].sc;
+      }
+      pf[4 * K] = (float)(eps / fz / 24.0);
+      pf[4 * K + 1] = (float)(fe / fz);
+      pf[4 * K + 2] = (float)(sc / fz);
+      pf[4 * K + 3] = (float)((K + 0.5) / L.nz);
+    }
+    FX_CK(cudaMalloc(&ctx->nn_pf, pf.size() * sizeof(float)));
+    FX_CK(cudaMemcpy(ctx->nn_pf, pf.data(), pf.size() * sizeof(float), cudaMemcpyHostToDevice));
+  }
+  ctx->nn = nn;
+  ctx->nn_mode = mode;
+  if (mode == 2) {
+    if (ctx->ge_step_nn) { cudaGraphExecDestroy(ctx->ge_step_nn); ctx->ge_step_nn = nullptr; }
+    if (ctx->gr_step_nn) { cudaGraphDestroy(ctx->gr_step_nn); ctx->gr_step_nn = nullptr; }
+    const ferrox_status rc = ctx->num.precision == FERROX_MIXED ? build_nn_graph_t<float>(ctx)
+                                                               : build_nn_graph_t<double>(ctx);
+    if (rc != FERROX_OK) { ctx->nn_mode = 0; return rc; }
+  }
   return FERROX_OK;
 }
 

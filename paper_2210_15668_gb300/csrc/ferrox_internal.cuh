@@ -107,7 +107,7 @@ struct ResidArgs {
   int set_cond;        // call cudaGraphSetConditional
   unsigned long long cond_handle;
   int launches_per_cycle;  // kernels of one outer iteration (V-cycle + update + resid)
-  int pad;
+  int no_stats;            // write r (and s) only: no norms, no decision
 };
 
 // ---- launchers (kernels.cu / tdgl.cu) ------------------------------------------------
@@ -185,6 +185,53 @@ struct ChargeArgs {
   double* partials;
 };
 void launch_charge(const ChargeArgs& a, cudaStream_t s);
+
+// ---- learned warm-start network (nn.cu) -----------------------------------------------
+struct NNGrid {
+  int D, H, W;
+};
+}  // namespace fx
+#include <cuda_bf16.h>
+#include <string>
+#include <vector>
+#include <algorithm>
+struct ferrox_nn;
+namespace fx {
+void nn_conv_fwd(const __nv_bfloat16* in, int cin, const __nv_bfloat16* wk, const float* bias,
+                 int cout, NNGrid g, int relu, __nv_bfloat16* out_bf, float* out_f, cudaStream_t s);
+void nn_conv_wgrad(const __nv_bfloat16* in, int cin, const __nv_bfloat16* dout, int cout, NNGrid g,
+                   float* gw, float* gb, cudaStream_t s);
+void nn_pool2(const __nv_bfloat16* in, NNGrid f, int C, __nv_bfloat16* out, cudaStream_t s);
+void nn_upcat(const __nv_bfloat16* a4, const __nv_bfloat16* s1, NNGrid f, __nv_bfloat16* cat, cudaStream_t s);
+void nn_mask(const float* d, const __nv_bfloat16* act, long long n, __nv_bfloat16* out, cudaStream_t s);
+void nn_up_grad(const float* dcat, const __nv_bfloat16* a4, NNGrid f, __nv_bfloat16* out, cudaStream_t s);
+void nn_skip_grad(const float* dcat, const float* dp, const __nv_bfloat16* s1, NNGrid f,
+                  __nv_bfloat16* out, cudaStream_t s);
+void nn_mse(const float* y, const float* tgt, int M, __nv_bfloat16* dy, float* loss, cudaStream_t s);
+void nn_adam(float* p, float* g, float* m, float* v, int n, float lr, int step, cudaStream_t s);
+void nn_pack(const float* w, int cin, int cout, __nv_bfloat16* wk, __nv_bfloat16* wb, cudaStream_t s);
+__nv_bfloat16* nn_input(ferrox_nn* N);
+const float* nn_output(ferrox_nn* N);
+void nn_run_forward(ferrox_nn* N, cudaStream_t s);
+NNGrid nn_grid(const ferrox_nn* N);
+int nn_capacity(const ferrox_nn* N);
+__nv_bfloat16* nn_snap_x(ferrox_nn* N);
+float* nn_snap_t(ferrox_nn* N);
+void nn_note_snapshots(ferrox_nn* N, int added);
+int nn_next_slot(const ferrox_nn* N);
+template <typename T>
+void nn_bridge_restrict(T* arena, const std::vector<LevelDesc>& lv, int to, cudaStream_t s);
+template <typename T>
+void nn_bridge_scale(const T* arena, const LevelDesc& L, double* scale, cudaStream_t s);
+template <typename T>
+void nn_bridge_features(const T* r, const LevelDesc& L, const float* pf, const double* scale,
+                        const DevParams* prm, __nv_bfloat16* x, cudaStream_t s);
+template <typename T>
+void nn_bridge_apply(const float* y, const LevelDesc& L, const double* scale, T* e, cudaStream_t s);
+template <typename T>
+void nn_bridge_guess_error(const double* phi, const double* guess, long long n, T* e0, cudaStream_t s);
+template <typename T>
+void nn_bridge_target(const T* e, const LevelDesc& L, const double* scale, float* tgt, cudaStream_t s);
 
 // ---- persistent batched engine (persistent.cu) ---------------------------------------
 constexpr long long kBarrierSpinCycles = 2000000000LL;  // ~1 s at 2 GHz: a wait never hangs

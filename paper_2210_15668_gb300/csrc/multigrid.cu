@@ -71,6 +71,7 @@ __global__ void __launch_bounds__(kResidBX* kResidBY) resid_kernel(ResidArgs a) 
   const int j = blockIdx.y * kResidBY + threadIdx.y;
   double acc_r = 0.0, acc_b = 0.0, acc_rho = 0.0;
   if (i < a.nx && j < a.ny) resid_column<T>(a, i, j, acc_r, acc_b, acc_rho);
+  if (a.no_stats) return;
   block_sum3(acc_r, acc_b, acc_rho);
   __shared__ bool last;
   const int nblk = gridDim.x * gridDim.y;

@@ -59,7 +59,10 @@ EXPORTS = ["ferrox_init_geometry", "ferrox_set_bias", "ferrox_solve_poisson", "f
            "ferrox_level_shape", "ferrox_profile_step", "ferrox_tdgl_update_static",
            "ferrox_init_batch", "ferrox_batch_set_bias", "ferrox_batch_solve_poisson",
            "ferrox_batch_step", "ferrox_batch_charge", "ferrox_batch_stats", "ferrox_batch_tuning",
-           "ferrox_batch_destroy", "ferrox_batch_last_error", "ferrox_check_wait_timeout"]
+           "ferrox_batch_destroy", "ferrox_batch_last_error", "ferrox_check_wait_timeout",
+           "ferrox_nn_create", "ferrox_nn_forward", "ferrox_nn_loss_grad", "ferrox_nn_params",
+           "ferrox_nn_set_params", "ferrox_nn_adam_step", "ferrox_nn_snapshot_count", "ferrox_nn_train",
+           "ferrox_nn_destroy", "ferrox_nn_last_error", "ferrox_attach_nn"]
 
 KERNEL_CLASSES = ["tdgl", "resid", "smooth_fine", "smooth_coarse", "restrict", "prolong", "tail",
                   "update", "copy"]
@@ -105,8 +108,9 @@ def load(path: str = LIB_PATH):
     lib.ferrox_batch_last_error.argtypes = [vp]
     lib.ferrox_batch_last_error.restype = C.c_char_p
     lib.ferrox_check_wait_timeout.argtypes = [C.c_double, C.POINTER(C.c_int), vp]
+    lib.ferrox_attach_nn.argtypes = [vp, vp, C.c_int]
     for name in EXPORTS:
-        if name not in ("ferrox_last_error", "ferrox_batch_last_error"):
+        if name not in ("ferrox_last_error", "ferrox_batch_last_error", "ferrox_nn_last_error"):
             getattr(lib, name).restype = st
     _lib = lib
     return lib
@@ -239,6 +243,10 @@ class Device:
         self._ck(self.lib.ferrox_profile_step(self.ctx, ms, cnt))
         return {KERNEL_CLASSES[k]: (ms[k], cnt[k]) for k in range(n)}
 
+    def attach_nn(self, net, mode):
+        """mode 0: detach; 1: collect snapshots each step; 2: apply before each solve."""
+        self._ck(self.lib.ferrox_attach_nn(self.ctx, net.ctx if net is not None else None, int(mode)))
+
     def levels(self):
         n = C.c_int()
         nx, ny, nz = C.c_int(), C.c_int(), C.c_int()
@@ -358,3 +366,123 @@ def check_wait_timeout(seconds=0.2, stream=None):
         raise FerroxError(rc, lib.ferrox_batch_last_error(None).decode())
     return out.value
 
+
+
+NN_LAYERS = [(16, 16), (16, 16), (16, 32), (32, 32), (48, 16), (16, 16)]
+
+
+def nn_param_sizes():
+    return [27 * ci * co for ci, co in NN_LAYERS], [co for _, co in NN_LAYERS]
+
+
+def nn_init_params(seed):
+    """He-normal initial weights (math layout [27][Cin][Cout] per layer) and zero biases."""
+    rng = np.random.default_rng(seed)
+    ws = [rng.standard_normal((27, ci, co)) * np.sqrt(2.0 / (27 * ci)) for ci, co in NN_LAYERS]
+    bs = [np.zeros(co) for _, co in NN_LAYERS]
+    return ws, bs
+
+
+class NN:
+    """The learned warm-start network on one grid (channels-last, 16 input channels)."""
+
+    def __init__(self, D, H, W, capacity=0, params=None, seed=0, stream=None):
+        import torch
+        self.lib = load()
+        lib = self.lib
+        if not getattr(lib, "_nn_declared", False):
+            vp = C.c_void_p
+            fp = C.POINTER(C.c_float)
+            lib.ferrox_nn_create.argtypes = [C.POINTER(vp), C.c_int, C.c_int, C.c_int, C.c_int, fp, fp, vp]
+            lib.ferrox_nn_forward.argtypes = [vp, vp, vp]
+            lib.ferrox_nn_loss_grad.argtypes = [vp, vp, vp, fp]
+            lib.ferrox_nn_params.argtypes = [vp, fp, fp, fp, fp]
+            lib.ferrox_nn_set_params.argtypes = [vp, fp, fp]
+            lib.ferrox_nn_adam_step.argtypes = [vp, C.c_double]
+            lib.ferrox_nn_snapshot_count.argtypes = [vp, C.POINTER(C.c_int)]
+            lib.ferrox_nn_train.argtypes = [vp, C.c_int, C.c_double, C.c_int, fp]
+            lib.ferrox_nn_destroy.argtypes = [vp]
+            lib.ferrox_nn_last_error.argtypes = [vp]
+            lib.ferrox_nn_last_error.restype = C.c_char_p
+            for n in ("ferrox_nn_create", "ferrox_nn_forward", "ferrox_nn_loss_grad", "ferrox_nn_params",
+                      "ferrox_nn_set_params", "ferrox_nn_adam_step", "ferrox_nn_snapshot_count",
+                      "ferrox_nn_train", "ferrox_nn_destroy"):
+                getattr(lib, n).restype = C.c_int
+            lib._nn_declared = True
+        self.shape = (D, H, W)
+        self.M = D * H * W
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        ws, bs = params if params is not None else nn_init_params(seed)
+        wflat = np.concatenate([np.asarray(w, np.float32).ravel() for w in ws])
+        bflat = np.concatenate([np.asarray(b, np.float32).ravel() for b in bs])
+        self.ctx = C.c_void_p()
+        rc = lib.ferrox_nn_create(C.byref(self.ctx), D, H, W, capacity,
+                                  wflat.ctypes.data_as(C.POINTER(C.c_float)),
+                                  bflat.ctypes.data_as(C.POINTER(C.c_float)), C.c_void_p(self.stream.cuda_stream))
+        if rc != FERROX_OK:
+            raise FerroxError(rc, lib.ferrox_nn_last_error(None).decode())
+
+    def _ck(self, rc):
+        if rc != FERROX_OK:
+            raise FerroxError(rc, self.lib.ferrox_nn_last_error(self.ctx).decode())
+
+    def forward(self, x):
+        """x: float32 CUDA tensor [M, 16] -> float32 CUDA tensor [M] (output channel 0)."""
+        import torch
+        y = torch.empty(self.M, dtype=torch.float32, device=x.device)
+        self._ck(self.lib.ferrox_nn_forward(self.ctx, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr())))
+        return y
+
+    def loss_grad(self, x, t):
+        out = C.c_float()
+        self._ck(self.lib.ferrox_nn_loss_grad(self.ctx, C.c_void_p(x.data_ptr()), C.c_void_p(t.data_ptr()),
+                                              C.byref(out)))
+        return out.value
+
+    def params(self):
+        nw, nb = nn_param_sizes()
+        w = np.empty(sum(nw), np.float32); b = np.empty(sum(nb), np.float32)
+        gw = np.empty(sum(nw), np.float32); gb = np.empty(sum(nb), np.float32)
+        fp = C.POINTER(C.c_float)
+        self._ck(self.lib.ferrox_nn_params(self.ctx, w.ctypes.data_as(fp), b.ctypes.data_as(fp),
+                                           gw.ctypes.data_as(fp), gb.ctypes.data_as(fp)))
+        return _split(w, nw), _split(b, nb), _split(gw, nw), _split(gb, nb)
+
+    def set_params(self, ws, bs):
+        fp = C.POINTER(C.c_float)
+        wf = np.concatenate([np.asarray(w, np.float32).ravel() for w in ws])
+        bf = np.concatenate([np.asarray(b, np.float32).ravel() for b in bs])
+        self._ck(self.lib.ferrox_nn_set_params(self.ctx, wf.ctypes.data_as(fp), bf.ctypes.data_as(fp)))
+
+    def adam_step(self, lr):
+        self._ck(self.lib.ferrox_nn_adam_step(self.ctx, float(lr)))
+
+    def snapshot_count(self):
+        n = C.c_int()
+        self._ck(self.lib.ferrox_nn_snapshot_count(self.ctx, C.byref(n)))
+        return n.value
+
+    def train(self, epochs, lr, batch=8):
+        losses = np.zeros(max(epochs, 1), np.float32)
+        self._ck(self.lib.ferrox_nn_train(self.ctx, int(epochs), float(lr), int(batch),
+                                          losses.ctypes.data_as(C.POINTER(C.c_float))))
+        return losses[:epochs]
+
+    def close(self):
+        if self.ctx:
+            self.lib.ferrox_nn_destroy(self.ctx)
+            self.ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _split(flat, sizes):
+    out, o = [], 0
+    for n in sizes:
+        out.append(flat[o:o + n])
+        o += n
+    return out

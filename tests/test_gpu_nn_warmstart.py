@@ -1,0 +1,70 @@
+"""The learned warm start inside the solver: collect snapshots, train on the GPU
+with the library's own kernels, then run with and without the network.
+
+The network may only change how many V-cycles a solve needs: both runs stop on
+the same residual test, so their trajectories agree to the solver tolerance.
+The test reports the gain (cycles per step with / without) and bounds any loss.
+"""
+import numpy as np
+import pytest
+
+from paper_2210_15668_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def test_learned_warm_start_gain_and_same_answer():
+    from paper_2210_15668_gb300 import ferrox
+    cfg = I.mfim_small()
+    geom = cfg["geom"]
+    P0 = I.random_polarization(geom, cfg["seed"])
+    num = ferrox.make_numerics(4e-13, tol=1e-12, precision=1, guess=1)
+    d = ferrox.Device(geom, P0, numerics=num)
+    D, H, W = d.levels()[2][2], d.levels()[2][1], d.levels()[2][0]
+    net = ferrox.NN(D, H, W, capacity=160, seed=11)
+    d.set_bias(0.0, -1.0)
+    d.solve_poisson()
+    d.attach_nn(net, 1)
+    for k in range(160):
+        if k % 20 == 0:
+            d.set_bias(0.0, [-1.0, -0.5, 0.0, 0.5, 1.0, 0.75, 0.25, -0.25][k // 20])
+        d.step(1)
+    assert net.snapshot_count() == 160
+    P_c, phi_c = d.get_state()
+    d.close()
+    losses = net.train(epochs=30, lr=3e-4, batch=8)
+    assert np.all(np.isfinite(losses))
+    assert losses[-5:].mean() < losses[:5].mean(), losses
+
+    out = {}
+    for mode in (0, 2):
+        e = ferrox.Device(geom, P_c, numerics=num, phi0=phi_c)
+        e.set_bias(0.0, 0.6)
+        e.solve_poisson()
+        if mode == 2:
+            e.attach_nn(net, 2)
+        s0 = e.stats()
+        e.step(40)
+        s1 = e.stats()
+        assert s1["status"] == 0
+        out[mode] = (e.get_state(), (s1["cycles"] - s0["cycles"]) / 40)
+        e.close()
+    (Pa, phia), ca = out[0]
+    (Pb, phib), cb = out[2]
+    print(f"V-cycles per step: without network {ca:.2f}, with network {cb:.2f}")
+    assert np.linalg.norm(Pa - Pb) <= 1e-9 * np.linalg.norm(Pa)
+    assert np.linalg.norm(phia - phib) <= 1e-9 * np.linalg.norm(phia)
+    assert cb <= 1.5 * ca + 1.0
+    net.close()
+
+
+def test_attach_rejects_a_network_of_the_wrong_grid():
+    from paper_2210_15668_gb300 import ferrox
+    geom = I.make_geometry(64, 64, I.mfim_stack(16))
+    d = ferrox.Device(geom, I.random_polarization(geom, seed=1))
+    net = ferrox.NN(4, 8, 8, capacity=4)
+    with pytest.raises(ferrox.FerroxError, match="EINVAL"):
+        d.attach_nn(net, 2)
+    d.close()
+    net.close()
