@@ -34,6 +34,7 @@ sys.path.insert(0, ROOT)
 METRIC = "Mcell-steps/s incl. Poisson to 1e-10 residual; HBM % of peak; vs plain FP64"
 UNIT = "Mcell-steps/s"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x DFMA/clk/SM x flop/FMA x max clock
+FP64_PEAK_GINSTR = 152 * 2 * 2.070                 # FP64 pipe instructions per second (G/s)
 HBM_FALLBACK_GBS = 6800.0
 
 
@@ -124,6 +125,10 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------- algorithmic work -------
+
+# FP64 pipe instructions per unit of work (the FP64 forms are bound by this pipe)
+FP64_INSTR = {"smooth_fine": 7.0, "resid": 10.0, "tdgl": 30.0, "restrict": 8.0, "prolong": 4.5}
+
 
 def kernel_work(kind, cells, fe_cells, dyn_cells, tsz):
     """Algorithmic (bytes, flops) of ONE launch of a kernel class on the fine level.
@@ -257,10 +262,14 @@ def run_ours(args, ws, rank, local):
             traffic = tj.get("per_launch_bytes", {}).get(f"{args.precision}:{dom}")
     share = dom_ms / step_ms if step_ms else None
     if fp64_kernel:
-        roof = {"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "share_of_step": share,
-                "frac": tfl / FP64_PEAK_TFLOPS if tfl else None, "traffic": traffic,
-                "kernel": dom, "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
+        units = {"smooth_fine": 0.5 * cells, "resid": cells, "tdgl": fe_cells, "restrict": cells,
+                 "prolong": cells}.get(dom, cells)
+        gi = FP64_INSTR.get(dom, 0.0) * units / avg_s / 1e9
+        roof = {"bound": "alu", "achieved": gi, "peak": FP64_PEAK_GINSTR, "unit": "G FP64-instr/s",
+                "share_of_step": share, "frac": gi / FP64_PEAK_GINSTR, "traffic": traffic,
+                "kernel": dom, "peak_source": "derived: 152 SMs x 2 FP64 instr/clk x 2.07 GHz",
+                "work": f"{FP64_INSTR.get(dom, 0.0)} FP64 instructions per unit",
+                "flop_view": {"achieved_tflops": tfl, "peak_tflops": FP64_PEAK_TFLOPS},
                 "hbm_view": {"achieved_gbs": gbs, "peak_gbs": hbm_peak,
                              "frac": gbs / hbm_peak if gbs else None, "peak_source": peak_src}}
     else:

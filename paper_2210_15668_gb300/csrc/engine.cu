@@ -706,6 +706,10 @@ ferrox_status ferrox_init_geometry(ferrox_ctx** out, const ferrox_geometry* geom
   ctx->phi = phi_dev;
   if ((rc = build_planes(ctx)) != FERROX_OK) { ctx->err = g_init_error; release(ctx); return rc; }
   build_levels(ctx);
+  if (ctx->arena >= (1LL << 31)) {   // the multigrid kernels index the arenas with 32-bit integers
+    release(ctx);
+    return fail(nullptr, FERROX_EINVAL, "grid too large: the multigrid arenas exceed 2^31 elements");
+  }
 
   const bool mixed = ctx->num.precision == FERROX_MIXED;
   const size_t tsz = mixed ? sizeof(float) : sizeof(double);
@@ -1292,6 +1296,10 @@ ferrox_status ferrox_init_batch(ferrox_batch** out, int n, const ferrox_geometry
   }
   B->cells = cells;
   B->arena = arena;
+  if (arena >= (1LL << 31)) {
+    batch_release(B);
+    return bfail(nullptr, FERROX_EINVAL, "batch too large: the multigrid arenas exceed 2^31 elements");
+  }
   // with any semiconductor instance every tail carries the shift array too
   const bool any_sc = std::any_of(B->plans.begin(), B->plans.end(), [](const BatchPlan& p) { return p.c.has_sc; });
   for (const auto& p : B->plans)

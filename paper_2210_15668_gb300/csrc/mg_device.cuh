@@ -10,22 +10,23 @@
 namespace fx {
 namespace dev {
 
-__device__ __forceinline__ long long lidx(const LevelDesc& L, int i, int j, int k) {
-  return L.off + ((long long)k * L.ny + j) * L.nx + i;
+// arenas hold fewer than 2^31 elements (checked at init), so 32-bit indices suffice
+__device__ __forceinline__ int lidx(const LevelDesc& L, int i, int j, int k) {
+  return (int)L.off + (k * L.ny + j) * L.nx + i;
 }
 
 // (r + sum of couplings * neighbours) of one cell; the Gauss-Seidel numerator.
 template <typename T>
 __device__ __forceinline__ T gs_numerator(const T* e, const T* r, const PlaneCoef<T>& c,
-                                          const LevelDesc& L, int i, int j, int k, long long id) {
+                                          const LevelDesc& L, int i, int j, int k, int id) {
   const int im = (i == 0) ? L.nx - 1 : i - 1;
   const int ip = (i == L.nx - 1) ? 0 : i + 1;
   const int jm = (j == 0) ? L.ny - 1 : j - 1;
   const int jp = (j == L.ny - 1) ? 0 : j + 1;
-  const long long row = id - i;
-  const long long plane = (long long)L.nx * L.ny;
+  const int row = id - i;
+  const int plane = L.nx * L.ny;
   T sx = e[row + im] + e[row + ip];
-  T sy = e[id + (long long)(jm - j) * L.nx] + e[id + (long long)(jp - j) * L.nx];
+  T sy = e[id + (jm - j) * L.nx] + e[id + (jp - j) * L.nx];
   T ed = (k > 0) ? e[id - plane] : T(0);
   T eu = (k < L.nz - 1) ? e[id + plane] : T(0);
   T acc = r[id];
@@ -43,7 +44,7 @@ struct Upd {
 };
 
 template <typename T>
-__device__ __forceinline__ void apply_update(const Upd& u, long long idx, T e) {
+__device__ __forceinline__ void apply_update(const Upd& u, int idx, T e) {
   if (u.zero) u.phi[idx] = 0.0;
   else u.phi[idx] += fmin(fmax((double)e, -u.clamp), u.clamp);
 }
@@ -59,7 +60,7 @@ __device__ __forceinline__ void smooth_pair(const MGArgs<T>& a, const LevelDesc&
   const int i2 = 2 * ip + (par ^ 1);
   const PlaneCoef<T> c = ldg_struct(a.coef + L.coef_off + k);
   T ev = T(0);
-  long long id = -1;
+  int id = -1;
   if (i < L.nx) {
     id = lidx(L, i, j, k);
     if (zero_init) {
@@ -72,7 +73,7 @@ __device__ __forceinline__ void smooth_pair(const MGArgs<T>& a, const LevelDesc&
     a.e[id] = ev;
   }
   if (i2 < L.nx) {
-    const long long id2 = lidx(L, i2, j, k);
+    const int id2 = lidx(L, i2, j, k);
     if (zero_init) a.e[id2] = T(0);
     if (u.phi) apply_update(u, id2 - L.off, a.e[id2]);
   }
@@ -84,7 +85,7 @@ template <typename T>
 __device__ __forceinline__ T cell_residual(const MGArgs<T>& a, const LevelDesc& L, int i, int j,
                                            int k) {
   const PlaneCoef<T> c = ldg_struct(a.coef + L.coef_off + k);
-  const long long id = lidx(L, i, j, k);
+  const int id = lidx(L, i, j, k);
   T num = gs_numerator(a.e, a.r, c, L, i, j, k, id);   // r + couplings * neighbours
   T d = c.has_s ? c.diag + a.s[id] : c.diag;
   return fma(-d, a.e[id], num);
@@ -103,7 +104,7 @@ __device__ __forceinline__ void restrict_cell(const MGArgs<T>& a, const LevelDes
         if (a.s) ssum += a.s[lidx(F, i0 + di, j0 + dj, k0 + dk)];
       }
   const T inv = T(1) / T(nxc * nyc * nzc);
-  const long long idc = lidx(C, I, J, K);
+  const int idc = lidx(C, I, J, K);
   a.r[idc] = sum * inv;
   if (a.s) a.s[idc] = ssum * inv;
 }
@@ -159,7 +160,7 @@ __device__ __forceinline__ void prolong_cell(const MGArgs<T>& a, const LevelDesc
       }
       const int fj = F.cry ? 2 * J + b : J, fk = F.crz ? 2 * K + c : K;
       if (F.crx) {
-        const long long f0 = lidx(F, 2 * I, fj, fk);
+        const int f0 = lidx(F, 2 * I, fj, fk);
         e[f0] += fma(T(0.75), Y[1], T(0.25) * Y[0]);
         e[f0 + 1] += fma(T(0.75), Y[1], T(0.25) * Y[2]);
       } else {
