@@ -35,7 +35,12 @@ constexpr double kKB = 1.380649e-23;
 
 std::string g_init_error;
 
+// programmatic dependent launch on (1) unless graph capture rejected it (0)
+int g_pdl = 1;
+
 }  // namespace
+
+int fx::pdl_enabled() { return g_pdl; }
 
 struct ferrox_ctx {
   // geometry and numerics
@@ -777,6 +782,22 @@ ferrox_status ferrox_init_geometry(ferrox_ctx** out, const ferrox_geometry* geom
   FX_INIT_CK(cudaMemcpy(ctx->params_d, &p0, sizeof(p0), cudaMemcpyHostToDevice));
   FX_INIT_CK(cudaDeviceSynchronize());
   rc = mixed ? build_graphs_t<float>(ctx) : build_graphs_t<double>(ctx);
+  if (rc != FERROX_OK && g_pdl) {
+    // graph capture without programmatic edges (same kernels, plain dependencies)
+    cudaGetLastError();
+    for (auto* g : {&ctx->ge_step, &ctx->ge_solve, &ctx->ge_tdgl})
+      if (*g) { cudaGraphExecDestroy(*g); *g = nullptr; }
+    for (auto* g : {&ctx->gr_step, &ctx->gr_solve, &ctx->gr_tdgl})
+      if (*g) { cudaGraphDestroy(*g); *g = nullptr; }
+    cudaStreamCaptureStatus cs;
+    if (cudaStreamIsCapturing(ctx->cap1, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+      cudaGraph_t junk;
+      cudaStreamEndCapture(ctx->cap1, &junk);
+      if (junk) cudaGraphDestroy(junk);
+    }
+    g_pdl = 0;
+    rc = mixed ? build_graphs_t<float>(ctx) : build_graphs_t<double>(ctx);
+  }
   if (rc != FERROX_OK) return cleanup(rc);
 #undef FX_INIT_CK
   *out = ctx;

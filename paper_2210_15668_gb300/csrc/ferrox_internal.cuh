@@ -11,7 +11,36 @@
 
 #include "../../include/ferrox.h"
 
+#include <utility>
+
 namespace fx {
+
+// Programmatic dependent launch: each solver kernel first waits for the kernel
+// before it to complete (its memory visible), then lets the next one be
+// scheduled, so consecutive launches overlap their dispatch with the tail of
+// the previous kernel.  Without the launch attribute both are no-ops.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+int pdl_enabled();
+
+template <typename... K, typename... A>
+inline cudaError_t launch_k(void (*kern)(K...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                            A&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<A>(args)...);
+}
 
 constexpr int kMaxLevels = 24;
 constexpr int kTailMaxCells = 4096;     // levels at or below this size run in one CTA (FP32)

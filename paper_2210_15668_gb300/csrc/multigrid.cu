@@ -34,6 +34,7 @@ using namespace dev;
 template <typename T>
 __global__ void __launch_bounds__(256) smooth_kernel(MGArgs<T> a, LevelDesc L, int color,
                                                      int zero_init, Upd u, const DevStats* st) {
+  pdl_enter();
   const int ip = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z;
@@ -44,6 +45,7 @@ __global__ void __launch_bounds__(256) smooth_kernel(MGArgs<T> a, LevelDesc L, i
 
 template <typename T>
 __global__ void __launch_bounds__(256) restrict_kernel(MGArgs<T> a, LevelDesc F, LevelDesc C) {
+  pdl_enter();
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = blockIdx.y * blockDim.y + threadIdx.y;
   if (I >= C.nx || J >= C.ny) return;
@@ -53,6 +55,7 @@ __global__ void __launch_bounds__(256) restrict_kernel(MGArgs<T> a, LevelDesc F,
 template <typename T>
 __global__ void __launch_bounds__(256) prolong_kernel(MGArgs<T> a, LevelDesc F, LevelDesc C,
                                                       int constant) {
+  pdl_enter();
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = blockIdx.y * blockDim.y + threadIdx.y;
   if (I >= C.nx || J >= C.ny) return;
@@ -62,11 +65,13 @@ __global__ void __launch_bounds__(256) prolong_kernel(MGArgs<T> a, LevelDesc F, 
 template <typename T>
 __global__ void __launch_bounds__(kTailThreads) tail_kernel(MGArgs<T> g, TailArgs t) {
   extern __shared__ __align__(16) unsigned char tail_smem[];
+  pdl_enter();
   tail_vcycle<T>(g, t, tail_smem);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kResidBX* kResidBY) resid_kernel(ResidArgs a) {
+  pdl_enter();
   const int i = blockIdx.x * kResidBX + threadIdx.x;
   const int j = blockIdx.y * kResidBY + threadIdx.y;
   double acc_r = 0.0, acc_b = 0.0, acc_rho = 0.0;
@@ -108,6 +113,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) update_kernel(double* __restrict__ phi, const T* __restrict__ e0,
                                                      long long n, const DevStats* stats,
                                                      double clamp) {
+  pdl_enter();
   const Upd u{phi, clamp, stats->zero_phi};
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
        t += (long long)gridDim.x * blockDim.x)
@@ -134,14 +140,14 @@ void launch_smooth(const MGArgs<T>& a, const LevelDesc& L, int color, int zero_i
   Upd u{nullptr, 0.0, 0};
   const DevStats* st = nullptr;
   if (upd) { u.phi = upd->phi; u.clamp = upd->clamp; st = upd->stats; }
-  smooth_kernel<T><<<grid, block, 0, s>>>(a, L, color, zero_init, u, st);
+  launch_k(smooth_kernel<T>, grid, block, 0, s, a, L, color, zero_init, u, st);
 }
 
 template <typename T>
 void launch_restrict(const MGArgs<T>& a, const LevelDesc& F, const LevelDesc& C, cudaStream_t s) {
   dim3 block, grid;
   block_shape(C.nx, C.ny, block, grid, C.nz);
-  restrict_kernel<T><<<grid, block, 0, s>>>(a, F, C);
+  launch_k(restrict_kernel<T>, grid, block, 0, s, a, F, C);
 }
 
 template <typename T>
@@ -149,7 +155,7 @@ void launch_prolong(const MGArgs<T>& a, const LevelDesc& F, const LevelDesc& C, 
                     cudaStream_t s) {
   dim3 block, grid;
   block_shape(C.nx, C.ny, block, grid, C.nz);
-  prolong_kernel<T><<<grid, block, 0, s>>>(a, F, C, constant);
+  launch_k(prolong_kernel<T>, grid, block, 0, s, a, F, C, constant);
 }
 
 template <typename T>
@@ -164,14 +170,14 @@ cudaError_t tail_prepare(size_t smem) {
 
 template <typename T>
 void launch_tail(const MGArgs<T>& a, const TailArgs& t, size_t smem, cudaStream_t s) {
-  tail_kernel<T><<<1, kTailThreads, smem, s>>>(a, t);
+  launch_k(tail_kernel<T>, dim3(1), dim3(kTailThreads), smem, s, a, t);
 }
 
 template <typename T>
 void launch_resid(const ResidArgs& a, cudaStream_t s) {
   dim3 block(kResidBX, kResidBY);
   dim3 grid((a.nx + kResidBX - 1) / kResidBX, (a.ny + kResidBY - 1) / kResidBY);
-  resid_kernel<T><<<grid, block, 0, s>>>(a);
+  launch_k(resid_kernel<T>, grid, block, 0, s, a);
 }
 
 template <typename T>
@@ -179,7 +185,7 @@ void launch_update(double* phi, const T* e0, long long n, const DevStats* stats,
                    cudaStream_t s) {
   long long b = (n + 255) / 256;
   if (b > 152LL * 16) b = 152LL * 16;
-  update_kernel<T><<<(int)b, 256, 0, s>>>(phi, e0, n, stats, clamp);
+  launch_k(update_kernel<T>, dim3((int)b), dim3(256), 0, s, phi, e0, n, stats, clamp);
 }
 
 #define FX_INST(T)                                                                              \

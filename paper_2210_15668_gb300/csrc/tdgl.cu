@@ -27,6 +27,7 @@ constexpr int kBX = 32, kBY = 8;
 using namespace dev;
 
 __global__ void __launch_bounds__(kBX* kBY) tdgl_kernel(TDGLArgs a) {
+  pdl_enter();
   const int i = blockIdx.x * kBX + threadIdx.x;
   const int j = blockIdx.y * kBY + threadIdx.y;
   if (i >= a.nx || j >= a.ny) return;
@@ -125,6 +126,7 @@ __global__ void charge_finalize(const double* partials, double* out) {
 // phi <- 2 phi - phi_prev, phi_prev <- phi (initial guess of the next solve)
 __global__ void __launch_bounds__(256) extrapolate_kernel(double* __restrict__ phi,
                                                           double* __restrict__ prev, long long n) {
+  pdl_enter();
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
        t += (long long)gridDim.x * blockDim.x) {
     const double v = phi[t];
@@ -139,6 +141,7 @@ __global__ void set_params_kernel(DevParams* p, double v_bot, double v_top) {
 }
 
 __global__ void stats_step_kernel(DevStats* st, int n, int launches) {
+  pdl_enter();
   st->steps += n;
   st->launches += launches;
 }
@@ -152,7 +155,7 @@ void launch_tdgl(const TDGLArgs& a, cudaStream_t s) {
     rhs3_kernel<<<grid, block, 0, s>>>(a, a.P_in);
     return;
   }
-  tdgl_kernel<<<grid, block, 0, s>>>(a);
+  launch_k(tdgl_kernel, grid, block, 0, s, a);
   if (a.ncomp == 3) rhs3_kernel<<<grid, block, 0, s>>>(a, a.P_out);
 }
 
@@ -164,7 +167,7 @@ void launch_charge(const ChargeArgs& a, cudaStream_t s) {
 void launch_extrapolate(double* phi, double* prev, long long n, cudaStream_t s) {
   long long b = (n + 255) / 256;
   if (b > 152LL * 16) b = 152LL * 16;
-  extrapolate_kernel<<<(int)b, 256, 0, s>>>(phi, prev, n);
+  launch_k(extrapolate_kernel, dim3((int)b), dim3(256), 0, s, phi, prev, n);
 }
 
 void launch_set_params(DevParams* p, double v_bot, double v_top, cudaStream_t s) {
@@ -172,7 +175,7 @@ void launch_set_params(DevParams* p, double v_bot, double v_top, cudaStream_t s)
 }
 
 void launch_stats_step(DevStats* st, int nsteps, int launches, cudaStream_t s) {
-  stats_step_kernel<<<1, 1, 0, s>>>(st, nsteps, launches);
+  launch_k(stats_step_kernel, dim3(1), dim3(1), 0, s, st, nsteps, launches);
 }
 
 }  // namespace fx
