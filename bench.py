@@ -161,6 +161,13 @@ def workload_config(name):
     cfg["label"] = "mfim_256x256x32 Q-V sweep (first steps at -2 V), seed 1"
     if name == "mfim_256x256x32":
         return cfg
+    if name in ("mfism_256x256x64", "mfism_512x512x128"):
+        m = I.mfism_mixed() if name == "mfism_256x256x64" else I.mfism_large()
+        m["sweep"] = [m["v_top"]]
+        m["steps_per_point"] = 10 ** 9
+        m["label"] = (f"{name} MFISM (p-Si N_A 1e24, n_i 1e16, 300 K; damped Newton), "
+                      f"seed {m['seed']}, 0 V")
+        return m
     if name.startswith("mfim_"):
         nx, ny, nz = (int(v) for v in name[5:].split("x"))
         cfg["geom"] = I.make_geometry(nx, ny, I.mfim_stack(nz))
@@ -193,7 +200,8 @@ def run_ours(args, ws, rank, local):
     sweep, per_point = cfg["sweep"], cfg["steps_per_point"]
 
     def make(precision):
-        num = ferrox.make_numerics(cfg["dt"], order=1, tol=1e-10, precision=precision, max_cycles=200)
+        num = ferrox.make_numerics(cfg["dt"], order=1, tol=1e-10, precision=precision, max_cycles=200,
+                                   guess=args.guess)
         d = ferrox.Device(geom, P0, numerics=num)
         d.set_bias(0.0, sweep[0])
         d.solve_poisson()                                  # Step 0 (untimed)
@@ -232,6 +240,12 @@ def run_ours(args, ws, rank, local):
 
     prec_main = ferrox.MIXED if args.precision == "mixed" else ferrox.FP64
     dev = make(prec_main)
+    learned_main = None
+    if args.learned:
+        learned_main = train_network_on(args, ferrox, I)
+        lv2 = dev.levels()[2]
+        dev._net = ferrox.NN(lv2[2], lv2[1], lv2[0], params=learned_main["params"])
+        dev.attach_nn(dev._net, 2)
     clocks = ClockSampler(local) if rank == 0 else None
     t_ms, st0, st1, ck = timed_run(dev, args.steps, args.warmup, clocks)
     t_max = reduce_max(t_ms, ws)
@@ -346,11 +360,13 @@ def run_ours(args, ws, rank, local):
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if prec_main == ferrox.FP64 else "f32+f64",
             "data": "synthetic",
-            "config": {"workload": cfg["label"],
+            "config": {"workload": cfg["label"], "guess": args.guess,
                        "cells": cells, "tol": 1e-10, "order": 1,
                        "precision": args.precision, "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": f"replicas x{ws}"},
             "vcycles_per_step": cycles_per_step, "gpu_launches": launches,
+            "learned_main": None if learned_main is None else
+            {k: v for k, v in learned_main.items() if k != "params"},
             "roofline": roof, "kernel_breakdown_ms_one_step": breakdown,
             "vs_plain_fp64": (mixed_v / fp64_v) if (mixed_v and fp64_v) else None,
             "other_precision": other, "fast_form": fast,
@@ -402,6 +418,39 @@ def run_learned(args, ws, cfg, geom, P0, cells, sweep, timed_run):
     d.close()
     net.close()
     return out
+
+
+def train_network_on(args, ferrox, I):
+    """Collect snapshots on the 256x256x32 MFIM and 256x256x64 MFISM workloads and
+    train one network on both (the weights carry over between grids: the network
+    is fully convolutional)."""
+    import torch
+    params, losses, t0 = None, [], time.perf_counter()
+    for name in ("mfim_256x256x32", "mfism_256x256x64"):
+        cfg = workload_config(name)
+        g = cfg["geom"]
+        num = ferrox.make_numerics(cfg["dt"], order=1, tol=1e-10, precision=ferrox.MIXED, guess=1)
+        d = ferrox.Device(g, I.random_polarization(g, cfg["seed"]), numerics=num)
+        lv = d.levels()[2]
+        net = ferrox.NN(lv[2], lv[1], lv[0], capacity=args.nn_snapshots,
+                        params=params if params is not None else ferrox.nn_init_params(7))
+        sweep = cfg["sweep"]
+        d.set_bias(0.0, sweep[0])
+        d.solve_poisson()
+        d.attach_nn(net, 1)
+        for k in range(args.nn_snapshots):
+            if len(sweep) > 1 and k % 25 == 0:
+                d.set_bias(0.0, sweep[(k // 25) % len(sweep)])
+            d.step(1)
+        losses += [float(x) for x in net.train(epochs=args.nn_epochs, lr=3e-4, batch=8)]
+        w, b, _, _ = net.params()
+        params = ([wi.reshape(27, ci, co) for wi, (ci, co) in zip(w, ferrox.NN_LAYERS)], b)
+        d.close()
+        net.close()
+    torch.cuda.synchronize()
+    return {"params": params, "snapshots_per_workload": args.nn_snapshots, "epochs": args.nn_epochs,
+            "train_loss_first_last": [losses[0], losses[-1]],
+            "collect_and_train_s": time.perf_counter() - t0}
 
 
 # ------------------------------------------------------- batched Q-V sweep workload -----
@@ -509,6 +558,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--guess", type=int, choices=[0, 1], default=0,
+                    help="initial potential of each solve: 0 previous (paper), 1 extrapolated")
+    ap.add_argument("--learned", action="store_true",
+                    help="attach a network trained on the 256^2 x 32 MFIM and 256^2 x 64 MFISM snapshots")
     ap.add_argument("--nn-snapshots", type=int, default=300)
     ap.add_argument("--nn-epochs", type=int, default=20)
     ap.add_argument("--batch-steps", type=int, default=50)
