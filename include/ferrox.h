@@ -240,6 +240,16 @@ ferrox_status ferrox_batch_destroy(ferrox_batch* b);
  * after about `seconds` (<= 5) of SM clock and records the status, which is
  * written to *status_out (FERROX_ETIMEOUT when the limit works).  Synchronises. */
 ferrox_status ferrox_check_wait_timeout(double seconds, int* status_out, void* cuda_stream);
+
+/* The carrier exponentials of the residual kernel on their own: ep_dev[i] =
+ * e^{u_dev[i]}, em_dev[i] = e^{-u_dev[i]} (device FP64 arrays of n).  The
+ * Boltzmann densities n0 e^{phi/V_T} and p0 e^{-phi/V_T} of the carrier model
+ * (Sec. II) are formed from this pair; both share one table-driven argument
+ * reduction (Tang 1989), within about 1.3 ulp for |u| < 700 and equal to exp()
+ * beyond.  n = 0 launches nothing.  Synchronises the stream; FERROX_EINVAL for
+ * n < 0 or a null pointer with n > 0. */
+ferrox_status ferrox_carrier_exp(const double* u_dev, double* ep_dev, double* em_dev, long long n,
+                                 void* cuda_stream);
 const char* ferrox_batch_last_error(const ferrox_batch* b);
 
 /* ---- learned warm start ------------------------------------------------------------------

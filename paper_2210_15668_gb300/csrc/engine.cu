@@ -60,6 +60,7 @@ struct ferrox_ctx {
   long long tail_elems = 0;
   size_t tail_smem = 0;
   int resid_blocks = 0;
+  int resid_kchunk = 0;   // planes per z chunk of the residual kernel
   // device memory
   cudaStream_t stream = nullptr;
   cudaStream_t cap1 = nullptr, cap2 = nullptr;
@@ -368,6 +369,7 @@ void enqueue_resid(ferrox_ctx* c, cudaStream_t s, int first, int set_cond,
   a.r_out = c->r_arena;
   a.s_out = c->has_sc ? c->s_arena : nullptr;
   a.partials = c->partials_d;
+  a.kchunk = c->resid_kchunk;
   a.stats = c->stats_d;
   a.tol = c->num.tol;
   a.max_cycles = c->num.max_cycles;
@@ -494,6 +496,7 @@ void enqueue_nn_features(ferrox_ctx* c, cudaStream_t s, __nv_bfloat16* x) {
   a.s_out = c->has_sc ? c->s_arena : nullptr;
   a.stats = c->stats_d;
   a.no_stats = 1;
+  a.kchunk = c->resid_kchunk;
   launch_resid<T>(a, s);
   T* r = static_cast<T*>(c->r_arena);
   nn_bridge_restrict<T>(r, c->lv, c->nn_level, s);
@@ -719,7 +722,15 @@ ferrox_status ferrox_init_geometry(ferrox_ctx** out, const ferrox_geometry* geom
   const bool mixed = ctx->num.precision == FERROX_MIXED;
   const size_t tsz = mixed ? sizeof(float) : sizeof(double);
   plan_tail(ctx, tsz);
-  ctx->resid_blocks = ((ctx->nx + kResidBX - 1) / kResidBX) * ((ctx->ny + kResidBY - 1) / kResidBY);
+  {
+    // residual grid: split the columns into z chunks (halving, at least 4 planes
+    // each) until there are about four waves of blocks on 152 SMs
+    const int bxy = ((ctx->nx + kResidBX - 1) / kResidBX) * ((ctx->ny + kResidBY - 1) / kResidBY);
+    int zc = 1;
+    while ((long long)bxy * zc < 4LL * 152 * 3 && ctx->nz / (2 * zc) >= 4) zc *= 2;
+    ctx->resid_kchunk = (ctx->nz + zc - 1) / zc;
+    ctx->resid_blocks = bxy * ((ctx->nz + ctx->resid_kchunk - 1) / ctx->resid_kchunk);
+  }
   const long long N = (long long)ctx->nx * ctx->ny * ctx->nz;
   auto cleanup = [&](ferrox_status s) { g_init_error = ctx->err; release(ctx); return s; };
 #define FX_INIT_CK(call)                                                                     \
@@ -1409,7 +1420,7 @@ ferrox_status ferrox_init_batch(ferrox_batch** out, int n, const ferrox_geometry
     ra.partials = nullptr;
     ra.stats = B->stats + i;
     ra.tol = num->tol; ra.max_cycles = num->max_cycles; ra.first = 1; ra.set_cond = 0;
-    ra.cond_handle = 0; ra.launches_per_cycle = 0;
+    ra.cond_handle = 0; ra.launches_per_cycle = 0; ra.kchunk = c.nz;
   }
   FX_BINIT(cudaMemcpy(B->coef, coefT.data(), coefT.size(), cudaMemcpyHostToDevice));
   FX_BINIT(cudaMemcpy(B->coef0, coef0.data(), coef0.size() * sizeof(PlaneCoef<double>), cudaMemcpyHostToDevice));
@@ -1557,6 +1568,16 @@ ferrox_status ferrox_check_wait_timeout(double seconds, int* status_out, void* c
   FX_BCK(cudaStreamSynchronize(s));
   cudaFree(gb);
   cudaFree(st);
+  return FERROX_OK;
+}
+
+ferrox_status ferrox_carrier_exp(const double* u_dev, double* ep_dev, double* em_dev, long long n,
+                                 void* cuda_stream) {
+  ferrox_batch* B = nullptr;
+  if (n < 0 || (n > 0 && (!u_dev || !ep_dev || !em_dev))) return bfail(nullptr, FERROX_EINVAL, "bad argument");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  FX_BCK(launch_carrier_exp(u_dev, ep_dev, em_dev, n, s));
+  FX_BCK(cudaStreamSynchronize(s));
   return FERROX_OK;
 }
 

@@ -137,6 +137,7 @@ struct ResidArgs {
   unsigned long long cond_handle;
   int launches_per_cycle;  // kernels of one outer iteration (V-cycle + update + resid)
   int no_stats;            // write r (and s) only: no norms, no decision
+  int kchunk;              // planes per z chunk of the multi-block kernel (grid.z chunks)
 };
 
 // ---- launchers (kernels.cu / tdgl.cu) ------------------------------------------------
@@ -304,6 +305,7 @@ struct BatchArgs {
 };
 
 cudaError_t launch_barrier_timeout(GridBar* gb, int* status, long long limit, cudaStream_t s);
+cudaError_t launch_carrier_exp(const double* u, double* ep, double* em, long long n, cudaStream_t s);
 template <typename T>
 cudaError_t batch_prepare(size_t smem);
 template <typename T>

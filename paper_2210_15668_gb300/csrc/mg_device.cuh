@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include "carrier_exp.cuh"
 #include "ferrox_internal.cuh"
 
 namespace fx {
@@ -172,17 +173,33 @@ __device__ __forceinline__ void prolong_cell(const MGArgs<T>& a, const LevelDesc
 
 // ---- single-CTA tail: the smallest levels in shared memory ---------------------------
 
+// Division by a level constant d without the integer divide sequence: with
+// m = ceil(2^32 / d) = floor((2^32 - 1) / d) + 1 (one 32-bit divide per call),
+// floor(t m / 2^32) = floor(t / d) for all t < 2^16 and d <= 2^16 (Granlund and
+// Montgomery, PLDI 1994: the error t (m d - 2^32) / d stays below 2^32 / d).
+// The tail's shared-memory budget keeps every tail level below 2^16 cells, so
+// all indices of a tail sweep are in range.
+static_assert(kTailMaxSmem / (2 * sizeof(float)) < 65536, "tail indices must stay below 2^16");
+
+__device__ __forceinline__ unsigned long long magic32(unsigned d) {
+  return (unsigned long long)(0xFFFFFFFFu / d) + 1ull;
+}
+__device__ __forceinline__ int div32(int t, unsigned long long m) {
+  return (int)(((unsigned long long)(unsigned)t * m) >> 32);
+}
+
 template <typename T>
 __device__ void tail_smooth(const MGArgs<T>& a, const LevelDesc& L, int sweeps, int zero_first) {
   const int hx = (L.nx + 1) >> 1;
   const int items = hx * L.ny * L.nz;
+  const unsigned long long mx = magic32(hx), my = magic32(L.ny);
   const Upd none{nullptr, 0.0, 0};
   for (int sw = 0; sw < sweeps; ++sw)
     for (int color = 0; color < 2; ++color) {
       const int zi = (zero_first && sw == 0 && color == 0);
       for (int t = threadIdx.x; t < items; t += blockDim.x) {
-        const int ip = t % hx, rest = t / hx;
-        smooth_pair(a, L, ip, rest % L.ny, rest / L.ny, color, zi, none);
+        const int rest = div32(t, mx), k = div32(rest, my);
+        smooth_pair(a, L, t - rest * hx, rest - k * L.ny, k, color, zi, none);
       }
       __syncthreads();
     }
@@ -208,16 +225,22 @@ __device__ void tail_vcycle(const MGArgs<T>& g, const TailArgs& t, unsigned char
     const LevelDesc F = ldg_struct(lv + l), C = ldg_struct(lv + l + 1);
     tail_smooth(a, F, t.nu1, 1);
     const int nc = (int)C.ncell;
-    for (int q = threadIdx.x; q < nc; q += blockDim.x)
-      restrict_cell(a, F, C, q % C.nx, (q / C.nx) % C.ny, q / (C.nx * C.ny));
+    const unsigned long long mx = magic32(C.nx), my = magic32(C.ny);
+    for (int q = threadIdx.x; q < nc; q += blockDim.x) {
+      const int rest = div32(q, mx), K = div32(rest, my);
+      restrict_cell(a, F, C, q - rest * C.nx, rest - K * C.ny, K);
+    }
     __syncthreads();
   }
   tail_smooth(a, lv[t.nlev - 1], t.bottom_sweeps, 1);
   for (int l = t.nlev - 2; l >= 0; --l) {
     const LevelDesc F = ldg_struct(lv + l), C = ldg_struct(lv + l + 1);
     const int nc = (int)C.ncell;
-    for (int q = threadIdx.x; q < nc; q += blockDim.x)
-      prolong_cell(a, F, C, q % C.nx, (q / C.nx) % C.ny, q / (C.nx * C.ny), t.constant);
+    const unsigned long long mx = magic32(C.nx), my = magic32(C.ny);
+    for (int q = threadIdx.x; q < nc; q += blockDim.x) {
+      const int rest = div32(q, mx), K = div32(rest, my);
+      prolong_cell(a, F, C, q - rest * C.nx, rest - K * C.ny, K, t.constant);
+    }
     __syncthreads();
     tail_smooth(a, F, t.nu2, 0);
   }
@@ -227,6 +250,19 @@ __device__ void tail_vcycle(const MGArgs<T>& g, const TailArgs& t, unsigned char
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
+}
+
+// Block sum of one value; result valid in thread 0.
+__device__ __forceinline__ void block_sum1(double& x) {
+  __shared__ double sh1[32];
+  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+  const int nthr = blockDim.x * blockDim.y;
+  x = warp_sum(x);
+  const int w = tid >> 5, l = tid & 31;
+  if (l == 0) sh1[w] = x;
+  __syncthreads();
+  if (w == 0) x = warp_sum(l < ((nthr + 31) >> 5) ? sh1[l] : 0.0);
+  __syncthreads();
 }
 
 // Block sum of three values; result valid in thread 0.
@@ -248,11 +284,13 @@ __device__ __forceinline__ void block_sum3(double& x, double& y, double& z) {
   __syncthreads();
 }
 
-// FP64 residual of one (x, y) column, marching up the planes with a register
-// window; accumulates r^2, b^2 (first residual of a solve only) and rho^2.
-template <typename T>
-__device__ __forceinline__ void resid_column(const ResidArgs& a, int i, int j, double& acc_r,
-                                             double& acc_b, double& acc_rho) {
+// FP64 residual of planes [k0, k1) of one (x, y) column, marching up with a
+// register window; accumulates r^2, b^2 (first residual of a solve only) and
+// rho^2.  SC = false compiles out the carrier term (stacks without a
+// semiconductor layer).
+template <typename T, bool SC = true>
+__device__ __forceinline__ void resid_column(const ResidArgs& a, int i, int j, int k0, int k1,
+                                             double& acc_r, double& acc_b, double& acc_rho) {
   const int nx = a.nx, ny = a.ny, nz = a.nz;
   const long long plane = (long long)nx * ny;
   T* r_out = static_cast<T*>(a.r_out);
@@ -264,18 +302,15 @@ __device__ __forceinline__ void resid_column(const ResidArgs& a, int i, int j, d
   const long long dyp = (long long)((j == ny - 1) ? 0 : j + 1) * nx - (long long)j * nx;
   const double* phi = a.phi;
   const long long col = (long long)j * nx + i;
-  double pd = 0.0, pc = phi[col];
-  for (int k = 0; k < nz; ++k) {
+  double pd = k0 > 0 ? phi[(long long)(k0 - 1) * plane + col] : 0.0;
+  double pc = phi[(long long)k0 * plane + col];
+  for (int k = k0; k < k1; ++k) {
     const long long t = k * plane + col;
     const double pu = (k < nz - 1) ? phi[t + plane] : 0.0;
     const PlaneCoef<double> c = ldg_struct(a.coef0 + k);
     const PlaneTDGL pt = ldg_struct(a.planes + k);
     const double sx = phi[t + dxm] + phi[t + dxp];
     const double sy = phi[t + dym] + phi[t + dyp];
-    double off = c.cx * sx;
-    off = fma(c.cy, sy, off);
-    off = fma(c.czlo, pd, off);
-    off = fma(c.czhi, pu, off);
     double bb;
     if (pt.b_dyn) {
       bb = a.b[t];
@@ -285,15 +320,21 @@ __device__ __forceinline__ void resid_column(const ResidArgs& a, int i, int j, d
       if (k == nz - 1) bb += pt.lift * v_top;
     }
     double rho = 0.0;
-    if (pt.sc) {
-      const double u = pc * pt.inv_vt;
-      const double n = pt.n0 * exp(u);
-      const double p = pt.p0 * exp(-u);
+    if (SC && pt.sc) {
+      double ep, em;
+      exp_pm(pc * pt.inv_vt, ep, em);
+      const double n = pt.n0 * ep;
+      const double p = pt.p0 * em;
       rho = pt.kq * (p - n + pt.Nnet);
       if (s_out) s_out[t] = (T)(pt.kq * (n + p) * pt.inv_vt);
       acc_rho = fma(rho, rho, acc_rho);
     }
-    const double r = (bb + rho) - fma(c.diag, pc, -off);
+    // r = b + rho - A phi = (b + rho) - diag phi + couplings * neighbours
+    double r = fma(-c.diag, pc, SC ? bb + rho : bb);
+    r = fma(c.czhi, pu, r);
+    r = fma(c.czlo, pd, r);
+    r = fma(c.cy, sy, r);
+    r = fma(c.cx, sx, r);
     r_out[t] = (T)r;
     acc_r = fma(r, r, acc_r);
     if (a.first) acc_b = fma(bb, bb, acc_b);

@@ -69,18 +69,25 @@ __global__ void __launch_bounds__(kTailThreads) tail_kernel(MGArgs<T> g, TailArg
   tail_vcycle<T>(g, t, tail_smem);
 }
 
-template <typename T>
+// grid (x chunk, row chunk, z chunk): block z owns planes [z kchunk, (z+1) kchunk)
+template <typename T, bool SC>
 __global__ void __launch_bounds__(kResidBX* kResidBY) resid_kernel(ResidArgs a) {
   pdl_enter();
   const int i = blockIdx.x * kResidBX + threadIdx.x;
   const int j = blockIdx.y * kResidBY + threadIdx.y;
+  const int k0 = blockIdx.z * a.kchunk;
+  const int k1 = min(a.nz, k0 + a.kchunk);
   double acc_r = 0.0, acc_b = 0.0, acc_rho = 0.0;
-  if (i < a.nx && j < a.ny) resid_column<T>(a, i, j, acc_r, acc_b, acc_rho);
+  if (i < a.nx && j < a.ny) resid_column<T, SC>(a, i, j, k0, k1, acc_r, acc_b, acc_rho);
   if (a.no_stats) return;
-  block_sum3(acc_r, acc_b, acc_rho);
+  // ||b||^2 is summed on the first residual of a solve only, ||rho||^2 with carriers only
+  if (SC || a.first)
+    block_sum3(acc_r, acc_b, acc_rho);
+  else
+    block_sum1(acc_r);
   __shared__ bool last;
-  const int nblk = gridDim.x * gridDim.y;
-  const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+  const int nblk = gridDim.x * gridDim.y * gridDim.z;
+  const int bid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   if (tid == 0) {
     a.partials[bid] = acc_r;
@@ -176,8 +183,12 @@ void launch_tail(const MGArgs<T>& a, const TailArgs& t, size_t smem, cudaStream_
 template <typename T>
 void launch_resid(const ResidArgs& a, cudaStream_t s) {
   dim3 block(kResidBX, kResidBY);
-  dim3 grid((a.nx + kResidBX - 1) / kResidBX, (a.ny + kResidBY - 1) / kResidBY);
-  launch_k(resid_kernel<T>, grid, block, 0, s, a);
+  dim3 grid((a.nx + kResidBX - 1) / kResidBX, (a.ny + kResidBY - 1) / kResidBY,
+            (a.nz + a.kchunk - 1) / a.kchunk);
+  if (a.s_out)
+    launch_k(resid_kernel<T, true>, grid, block, 0, s, a);
+  else
+    launch_k(resid_kernel<T, false>, grid, block, 0, s, a);
 }
 
 template <typename T>
@@ -186,6 +197,28 @@ void launch_update(double* phi, const T* e0, long long n, const DevStats* stats,
   long long b = (n + 255) / 256;
   if (b > 152LL * 16) b = 152LL * 16;
   launch_k(update_kernel<T>, dim3((int)b), dim3(256), 0, s, phi, e0, n, stats, clamp);
+}
+
+// e^{+u}, e^{-u} of n arguments with the carrier routine of the residual kernel
+// (grid-stride; exposed so its error can be checked on its own)
+__global__ void __launch_bounds__(256) carrier_exp_kernel(const double* __restrict__ u,
+                                                          double* __restrict__ ep,
+                                                          double* __restrict__ em, long long n) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) {
+    double a, b;
+    exp_pm(u[i], a, b);
+    ep[i] = a;
+    em[i] = b;
+  }
+}
+
+cudaError_t launch_carrier_exp(const double* u, double* ep, double* em, long long n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  long long b = (n + 255) / 256;
+  if (b > 152LL * 8) b = 152LL * 8;
+  carrier_exp_kernel<<<(int)b, 256, 0, s>>>(u, ep, em, n);
+  return cudaGetLastError();
 }
 
 #define FX_INST(T)                                                                              \

@@ -144,7 +144,7 @@ __device__ void phase_resid(const Ctx<T>& c, int first, int copy_back) {
           I.P[t] = I.Pbuf[t];
         }
       }
-      resid_column<T>(ra, x, j, ar, ab, aq);
+      resid_column<T>(ra, x, j, 0, ra.nz, ar, ab, aq);
     }
     ar = wsum(ar); ab = wsum(ab); aq = wsum(aq);
     if (c.lane == 0) {

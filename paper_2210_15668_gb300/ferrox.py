@@ -60,6 +60,7 @@ EXPORTS = ["ferrox_init_geometry", "ferrox_set_bias", "ferrox_solve_poisson", "f
            "ferrox_init_batch", "ferrox_batch_set_bias", "ferrox_batch_solve_poisson",
            "ferrox_batch_step", "ferrox_batch_charge", "ferrox_batch_stats", "ferrox_batch_tuning",
            "ferrox_batch_destroy", "ferrox_batch_last_error", "ferrox_check_wait_timeout",
+           "ferrox_carrier_exp",
            "ferrox_nn_create", "ferrox_nn_forward", "ferrox_nn_loss_grad", "ferrox_nn_params",
            "ferrox_nn_set_params", "ferrox_nn_adam_step", "ferrox_nn_snapshot_count", "ferrox_nn_train",
            "ferrox_nn_destroy", "ferrox_nn_last_error", "ferrox_attach_nn"]
@@ -108,6 +109,7 @@ def load(path: str = LIB_PATH):
     lib.ferrox_batch_last_error.argtypes = [vp]
     lib.ferrox_batch_last_error.restype = C.c_char_p
     lib.ferrox_check_wait_timeout.argtypes = [C.c_double, C.POINTER(C.c_int), vp]
+    lib.ferrox_carrier_exp.argtypes = [vp, vp, vp, C.c_longlong, vp]
     lib.ferrox_attach_nn.argtypes = [vp, vp, C.c_int]
     for name in EXPORTS:
         if name not in ("ferrox_last_error", "ferrox_batch_last_error", "ferrox_nn_last_error"):
@@ -366,6 +368,22 @@ def check_wait_timeout(seconds=0.2, stream=None):
         raise FerroxError(rc, lib.ferrox_batch_last_error(None).decode())
     return out.value
 
+
+def carrier_exp(u, stream=None):
+    """(e^u, e^-u) of a CUDA FP64 tensor, by the residual kernel's carrier routine."""
+    import torch
+    lib = load()
+    if not (u.is_cuda and u.dtype == torch.float64):
+        raise TypeError("u must be a CUDA float64 tensor")
+    u = u.contiguous()
+    st = stream if stream is not None else torch.cuda.current_stream()
+    ep = torch.empty_like(u)
+    em = torch.empty_like(u)
+    rc = lib.ferrox_carrier_exp(C.c_void_p(u.data_ptr()), C.c_void_p(ep.data_ptr()),
+                                C.c_void_p(em.data_ptr()), u.numel(), C.c_void_p(st.cuda_stream))
+    if rc != FERROX_OK:
+        raise FerroxError(rc, lib.ferrox_batch_last_error(None).decode())
+    return ep, em
 
 
 NN_LAYERS = [(16, 16), (16, 16), (16, 32), (32, 32), (48, 16), (16, 16)]
