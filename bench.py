@@ -201,7 +201,7 @@ def run_ours(args, ws, rank, local):
 
     def make(precision):
         num = ferrox.make_numerics(cfg["dt"], order=1, tol=1e-10, precision=precision, max_cycles=200,
-                                   guess=args.guess)
+                                   guess=args.guess, nu1=args.nu1, nu2=args.nu2)
         d = ferrox.Device(geom, P0, numerics=num)
         d.set_bias(0.0, sweep[0])
         d.solve_poisson()                                  # Step 0 (untimed)
@@ -360,7 +360,7 @@ def run_ours(args, ws, rank, local):
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if prec_main == ferrox.FP64 else "f32+f64",
             "data": "synthetic",
-            "config": {"workload": cfg["label"], "guess": args.guess,
+            "config": {"workload": cfg["label"], "guess": args.guess, "nu1": args.nu1, "nu2": args.nu2,
                        "cells": cells, "tol": 1e-10, "order": 1,
                        "precision": args.precision, "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": f"replicas x{ws}"},
@@ -558,6 +558,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--nu1", type=int, default=2, help="pre-smoothing sweeps per level")
+    ap.add_argument("--nu2", type=int, default=2, help="post-smoothing sweeps per level")
     ap.add_argument("--guess", type=int, choices=[0, 1], default=0,
                     help="initial potential of each solve: 0 previous (paper), 1 extrapolated")
     ap.add_argument("--learned", action="store_true",

@@ -332,7 +332,7 @@ void enqueue_vcycle(ferrox_ctx* c, cudaStream_t s, W wrap = W()) {
       wrap(ks, [&] { launch_smooth<T>(a, c->lv[l], 0, sw == 0, nullptr, s); });
       wrap(ks, [&] { launch_smooth<T>(a, c->lv[l], 1, 0, nullptr, s); });
     }
-    wrap(FERROX_K_RESTRICT, [&] { launch_restrict<T>(a, c->lv[l], c->lv[l + 1], s); });
+    wrap(FERROX_K_RESTRICT, [&] { launch_restrict<T>(a, c->lv[l], c->lv[l + 1], nu1, s); });
   }
   TailArgs ta{c->lvt_d, L - lt + 1, c->tail_elems, c->lv[lt].off, nu1, nu2, c->num.bottom_sweeps,
               constant};

@@ -170,7 +170,8 @@ template <typename T>
 void launch_smooth(const MGArgs<T>& a, const LevelDesc& L, int color, int zero_init,
                    const UpdateArgs* upd, cudaStream_t s);
 template <typename T>
-void launch_restrict(const MGArgs<T>& a, const LevelDesc& F, const LevelDesc& C, cudaStream_t s);
+void launch_restrict(const MGArgs<T>& a, const LevelDesc& F, const LevelDesc& C, int nu1,
+                     cudaStream_t s);
 template <typename T>
 void launch_prolong(const MGArgs<T>& a, const LevelDesc& F, const LevelDesc& C, int constant,
                     cudaStream_t s);

@@ -92,17 +92,29 @@ __device__ __forceinline__ T cell_residual(const MGArgs<T>& a, const LevelDesc& 
   return fma(-d, a.e[id], num);
 }
 
+// A red/black pre-smoothing ends with the black colour ((i + j + k) odd), whose
+// cells were just relaxed against red neighbours that have not changed since:
+// their residual is zero up to rounding.  With skip_black set, restriction
+// sums the residuals of the red children only (half the arithmetic).  The
+// colouring is a proper 2-colouring only if every periodic lateral size is
+// even (or 1); black_residual_zero() tells the callers when that holds.
+__host__ __device__ __forceinline__ int black_residual_zero(const LevelDesc& F, int nu1) {
+  return nu1 > 0 && (F.nx == 1 || !(F.nx & 1)) && (F.ny == 1 || !(F.ny & 1));
+}
+
 template <typename T>
 __device__ __forceinline__ void restrict_cell(const MGArgs<T>& a, const LevelDesc& F,
-                                              const LevelDesc& C, int I, int J, int K) {
+                                              const LevelDesc& C, int I, int J, int K,
+                                              int skip_black = 0) {
   const int nxc = F.crx ? 2 : 1, nyc = F.cry ? 2 : 1, nzc = F.crz ? 2 : 1;
   const int i0 = F.crx ? 2 * I : I, j0 = F.cry ? 2 * J : J, k0 = F.crz ? 2 * K : K;
   T sum = T(0), ssum = T(0);
   for (int dk = 0; dk < nzc; ++dk)
     for (int dj = 0; dj < nyc; ++dj)
       for (int di = 0; di < nxc; ++di) {
-        sum += cell_residual(a, F, i0 + di, j0 + dj, k0 + dk);
-        if (a.s) ssum += a.s[lidx(F, i0 + di, j0 + dj, k0 + dk)];
+        const int i = i0 + di, j = j0 + dj, k = k0 + dk;
+        if (!(skip_black && ((i + j + k) & 1))) sum += cell_residual(a, F, i, j, k);
+        if (a.s) ssum += a.s[lidx(F, i, j, k)];
       }
   const T inv = T(1) / T(nxc * nyc * nzc);
   const int idc = lidx(C, I, J, K);
@@ -226,9 +238,10 @@ __device__ void tail_vcycle(const MGArgs<T>& g, const TailArgs& t, unsigned char
     tail_smooth(a, F, t.nu1, 1);
     const int nc = (int)C.ncell;
     const unsigned long long mx = magic32(C.nx), my = magic32(C.ny);
+    const int skip = black_residual_zero(F, t.nu1);
     for (int q = threadIdx.x; q < nc; q += blockDim.x) {
       const int rest = div32(q, mx), K = div32(rest, my);
-      restrict_cell(a, F, C, q - rest * C.nx, rest - K * C.ny, K);
+      restrict_cell(a, F, C, q - rest * C.nx, rest - K * C.ny, K, skip);
     }
     __syncthreads();
   }

@@ -44,12 +44,13 @@ __global__ void __launch_bounds__(256) smooth_kernel(MGArgs<T> a, LevelDesc L, i
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) restrict_kernel(MGArgs<T> a, LevelDesc F, LevelDesc C) {
+__global__ void __launch_bounds__(256) restrict_kernel(MGArgs<T> a, LevelDesc F, LevelDesc C,
+                                                       int skip_black) {
   pdl_enter();
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = blockIdx.y * blockDim.y + threadIdx.y;
   if (I >= C.nx || J >= C.ny) return;
-  restrict_cell(a, F, C, I, J, (int)blockIdx.z);
+  restrict_cell(a, F, C, I, J, (int)blockIdx.z, skip_black);
 }
 
 template <typename T>
@@ -151,10 +152,11 @@ void launch_smooth(const MGArgs<T>& a, const LevelDesc& L, int color, int zero_i
 }
 
 template <typename T>
-void launch_restrict(const MGArgs<T>& a, const LevelDesc& F, const LevelDesc& C, cudaStream_t s) {
+void launch_restrict(const MGArgs<T>& a, const LevelDesc& F, const LevelDesc& C, int nu1,
+                     cudaStream_t s) {
   dim3 block, grid;
   block_shape(C.nx, C.ny, block, grid, C.nz);
-  launch_k(restrict_kernel<T>, grid, block, 0, s, a, F, C);
+  launch_k(restrict_kernel<T>, grid, block, 0, s, a, F, C, black_residual_zero(F, nu1));
 }
 
 template <typename T>
@@ -224,7 +226,7 @@ cudaError_t launch_carrier_exp(const double* u, double* ep, double* em, long lon
 #define FX_INST(T)                                                                              \
   template void launch_smooth<T>(const MGArgs<T>&, const LevelDesc&, int, int,                  \
                                  const UpdateArgs*, cudaStream_t);                              \
-  template void launch_restrict<T>(const MGArgs<T>&, const LevelDesc&, const LevelDesc&,        \
+  template void launch_restrict<T>(const MGArgs<T>&, const LevelDesc&, const LevelDesc&, int,   \
                                    cudaStream_t);                                               \
   template void launch_prolong<T>(const MGArgs<T>&, const LevelDesc&, const LevelDesc&, int,    \
                                   cudaStream_t);                                                \

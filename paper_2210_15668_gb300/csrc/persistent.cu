@@ -215,7 +215,7 @@ __device__ void phase_transfer(const Ctx<T>& c, int l, int op) {
     const int K = q / nrc, J0 = (q - K * nrc) * R;
     for (int J = J0; J < J0 + R && J < Cc.ny; ++J)
       for (int I0 = c.lane; I0 < Cc.nx; I0 += 32) {
-        if (op == 0) restrict_cell(c.mg, F, Cc, I0, J, K);
+        if (op == 0) restrict_cell(c.mg, F, Cc, I0, J, K, black_residual_zero(F, A.nu1));
         else prolong_cell(c.mg, F, Cc, I0, J, K, 0);
       }
   }
