@@ -201,7 +201,7 @@ def run_ours(args, ws, rank, local):
 
     def make(precision):
         num = ferrox.make_numerics(cfg["dt"], order=1, tol=1e-10, precision=precision, max_cycles=200,
-                                   guess=args.guess, nu1=args.nu1, nu2=args.nu2)
+                                   guess=args.guess, nu1=args.nu1, nu2=args.nu2, inner=args.inner)
         d = ferrox.Device(geom, P0, numerics=num)
         d.set_bias(0.0, sweep[0])
         d.solve_poisson()                                  # Step 0 (untimed)
@@ -360,11 +360,12 @@ def run_ours(args, ws, rank, local):
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if prec_main == ferrox.FP64 else "f32+f64",
             "data": "synthetic",
-            "config": {"workload": cfg["label"], "guess": args.guess, "nu1": args.nu1, "nu2": args.nu2,
+            "config": {"workload": cfg["label"], "guess": args.guess, "nu1": args.nu1, "nu2": args.nu2, "inner": args.inner,
                        "cells": cells, "tol": 1e-10, "order": 1,
                        "precision": args.precision, "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": f"replicas x{ws}"},
-            "vcycles_per_step": cycles_per_step, "gpu_launches": launches,
+            "vcycles_per_step": cycles_per_step * max(1, args.inner),
+            "outer_iterations_per_step": cycles_per_step, "gpu_launches": launches,
             "learned_main": None if learned_main is None else
             {k: v for k, v in learned_main.items() if k != "params"},
             "roofline": roof, "kernel_breakdown_ms_one_step": breakdown,
@@ -558,6 +559,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--inner", type=int, default=1, help="V-cycles per outer (FP64) iteration")
     ap.add_argument("--nu1", type=int, default=2, help="pre-smoothing sweeps per level")
     ap.add_argument("--nu2", type=int, default=2, help="post-smoothing sweeps per level")
     ap.add_argument("--guess", type=int, choices=[0, 1], default=0,

@@ -101,6 +101,12 @@ typedef struct {
                        potential (Step 1b of the Methods), 1 = linear extrapolation in
                        time 2 Phi^n - Phi^{n-1}.  The solve stops on the same residual
                        test either way; only the number of V-cycles changes. */
+  int inner;        /* V-cycles per outer (defect-correction / Newton) iteration; 0 or 1:
+                       one, the plain method.  The first starts from a zero correction,
+                       the others continue it on the same right-hand side and Newton
+                       shift, and phi is corrected once after the last: fewer FP64
+                       residuals (and carrier exponentials) per solve.  The stopping
+                       test is unchanged.  The batched engine takes 0 or 1 only. */
 } ferrox_numerics;
 
 typedef struct {

@@ -320,8 +320,14 @@ struct NoWrap {
 
 // One V-cycle on the correction equation; `wrap(kind, launch)` lets the profiler
 // bracket each launch with events (identity when capturing graphs).
+// V-cycles per outer iteration (numerics.inner; 0 means 1)
+int inner_cycles(const ferrox_ctx* c) { return c->num.inner > 1 ? c->num.inner : 1; }
+
+// first: the fine level starts from a zero correction; last: phi += e rides on
+// the last fine-level sweep
 template <typename T, typename W = NoWrap>
-void enqueue_vcycle(ferrox_ctx* c, cudaStream_t s, W wrap = W()) {
+void enqueue_vcycle(ferrox_ctx* c, cudaStream_t s, W wrap = W(), bool first = true,
+                    bool last = true) {
   MGArgs<T> a = mg_args<T>(c);
   const int nu1 = c->num.nu1, nu2 = c->num.nu2;
   const int constant = 0;
@@ -329,7 +335,8 @@ void enqueue_vcycle(ferrox_ctx* c, cudaStream_t s, W wrap = W()) {
   for (int l = 0; l < lt; ++l) {
     const int ks = l == 0 ? FERROX_K_SMOOTH0 : FERROX_K_SMOOTHC;
     for (int sw = 0; sw < nu1; ++sw) {
-      wrap(ks, [&] { launch_smooth<T>(a, c->lv[l], 0, sw == 0, nullptr, s); });
+      const int zero = sw == 0 && (first || l > 0);
+      wrap(ks, [&] { launch_smooth<T>(a, c->lv[l], 0, zero, nullptr, s); });
       wrap(ks, [&] { launch_smooth<T>(a, c->lv[l], 1, 0, nullptr, s); });
     }
     wrap(FERROX_K_RESTRICT, [&] { launch_restrict<T>(a, c->lv[l], c->lv[l + 1], nu1, s); });
@@ -342,11 +349,18 @@ void enqueue_vcycle(ferrox_ctx* c, cudaStream_t s, W wrap = W()) {
     const int ks = l == 0 ? FERROX_K_SMOOTH0 : FERROX_K_SMOOTHC;
     wrap(FERROX_K_PROLONG, [&] { launch_prolong<T>(a, c->lv[l], c->lv[l + 1], constant, s); });
     for (int sw = 0; sw < nu2; ++sw) {
-      const bool fuse = (l == 0 && sw == nu2 - 1);   // phi += e folded into the last sweep
+      const bool fuse = last && l == 0 && sw == nu2 - 1;   // phi += e folded into the last sweep
       wrap(ks, [&] { launch_smooth<T>(a, c->lv[l], 0, 0, nullptr, s); });
       wrap(ks, [&] { launch_smooth<T>(a, c->lv[l], 1, 0, fuse ? &upd : nullptr, s); });
     }
   }
+}
+
+// the V-cycles of one outer iteration
+template <typename T, typename W = NoWrap>
+void enqueue_cycles(ferrox_ctx* c, cudaStream_t s, W wrap = W()) {
+  const int q = inner_cycles(c);
+  for (int i = 0; i < q; ++i) enqueue_vcycle<T>(c, s, wrap, i == 0, i == q - 1);
 }
 
 // the fine-level update is a separate kernel only when it cannot ride on a sweep
@@ -355,7 +369,8 @@ bool separate_update(const ferrox_ctx* c) { return c->tail_first == 0 || c->num.
 // kernels launched by one outer iteration: V-cycle, (update), residual
 int launches_per_cycle(const ferrox_ctx* c) {
   const int lt = c->tail_first;
-  return lt * (2 * c->num.nu1 + 1 + 1 + 2 * c->num.nu2) + 1 + (separate_update(c) ? 1 : 0) + 1;
+  return inner_cycles(c) * (lt * (2 * c->num.nu1 + 1 + 1 + 2 * c->num.nu2) + 1) +
+         (separate_update(c) ? 1 : 0) + 1;
 }
 
 int tdgl_launches(const ferrox_ctx* c) { return c->ncomp == 3 ? 2 : 1; }
@@ -436,7 +451,7 @@ ferrox_status capture_solve(ferrox_ctx* ctx, cudaStream_t s) {
   cudaGraph_t body = cp.conditional.phGraph_out[0];
   FX_CK(cudaStreamBeginCaptureToGraph(ctx->cap2, body, nullptr, nullptr, 0,
                                       cudaStreamCaptureModeRelaxed));
-  enqueue_vcycle<T>(ctx, ctx->cap2);
+  enqueue_cycles<T>(ctx, ctx->cap2);
   enqueue_update<T>(ctx, ctx->cap2);
   enqueue_resid<T>(ctx, ctx->cap2, 0, 1, (unsigned long long)h);
   FX_CK(cudaGetLastError());
@@ -600,7 +615,7 @@ ferrox_status profile_step_t(ferrox_ctx* ctx, double* ms, int* count) {
       int cond;
       std::memcpy(&cond, ctx->host_pinned, sizeof(int));
       if (!cond) break;
-      enqueue_vcycle<T>(ctx, s, std::ref(tm));
+      enqueue_cycles<T>(ctx, s, std::ref(tm));
       if (separate_update(ctx)) tm(FERROX_K_UPDATE, [&] { enqueue_update<T>(ctx, s); });
       tm(FERROX_K_RESID, [&] { enqueue_resid<T>(ctx, s, 0, 0, 0ULL); });
     }
@@ -687,6 +702,7 @@ ferrox_status validate(const ferrox_geometry* g, const ferrox_numerics* n, const
   if (n->max_cycles < 1) return bad("max_cycles must be >= 1");
   if (n->precision != FERROX_FP64 && n->precision != FERROX_MIXED) return bad("unknown precision");
   if (n->bottom_sweeps < 0) return bad("bottom_sweeps must be >= 0");
+  if (n->inner < 0 || n->inner > 16) return bad("inner must be in 0..16");
   if (n->guess != 0 && n->guess != 1) return bad("guess must be 0 or 1");
   return FERROX_OK;
 }
@@ -1279,6 +1295,7 @@ ferrox_status ferrox_init_batch(ferrox_batch** out, int n, const ferrox_geometry
     if (geoms[i].ncomp != 1) return bfail(nullptr, FERROX_EINVAL, "batched instances are uniaxial (ncomp = 1)");
   }
   if (num->order != 1) return bfail(nullptr, FERROX_EINVAL, "the batched engine runs order-1 steps");
+  if (num->inner > 1) return bfail(nullptr, FERROX_EINVAL, "the batched engine runs one V-cycle per outer iteration");
   ferrox_batch* B = new ferrox_batch();
   B->n = n;
   B->num = *num;
