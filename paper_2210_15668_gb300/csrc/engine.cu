@@ -181,7 +181,8 @@ void plan_tail(ferrox_ctx* c, size_t elem_size) {
   c->tail_smem = (size_t)c->tail_elems * elem_size * narr;
   if (c->num.bottom_sweeps == 0) {     // enough sweeps to solve the coarsest level
     const LevelDesc& B = c->lv.back();
-    c->num.bottom_sweeps = std::min(64, 2 * (B.nx + B.ny + B.nz));
+    // one cell: a single update is the exact solve (more sweeps repeat it)
+    c->num.bottom_sweeps = B.ncell == 1 ? 1 : std::min(64, 2 * (B.nx + B.ny + B.nz));
   }
 }
 
