@@ -348,7 +348,9 @@ void enqueue_vcycle(ferrox_ctx* c, cudaStream_t s, W wrap = W(), bool first = tr
   const UpdateArgs upd{c->phi, c->stats_d, update_clamp(c)};
   for (int l = lt - 1; l >= 0; --l) {
     const int ks = l == 0 ? FERROX_K_SMOOTH0 : FERROX_K_SMOOTHC;
-    wrap(FERROX_K_PROLONG, [&] { launch_prolong<T>(a, c->lv[l], c->lv[l + 1], constant, s); });
+    // the tiled form where FP64 arithmetic bounds the launch: the fine level
+    const bool tiled = sizeof(T) == sizeof(double) && l == 0;
+    wrap(FERROX_K_PROLONG, [&] { launch_prolong<T>(a, c->lv[l], c->lv[l + 1], constant, s, tiled); });
     for (int sw = 0; sw < nu2; ++sw) {
       const bool fuse = last && l == 0 && sw == nu2 - 1;   // phi += e folded into the last sweep
       wrap(ks, [&] { launch_smooth<T>(a, c->lv[l], 0, 0, nullptr, s); });

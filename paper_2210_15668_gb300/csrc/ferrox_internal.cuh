@@ -177,7 +177,7 @@ void launch_restrict(const MGArgs<T>& a, const LevelDesc& F, const LevelDesc& C,
                      cudaStream_t s);
 template <typename T>
 void launch_prolong(const MGArgs<T>& a, const LevelDesc& F, const LevelDesc& C, int constant,
-                    cudaStream_t s);
+                    cudaStream_t s, bool tiled = false);
 template <typename T>
 size_t tail_smem_bytes(long long elems, bool has_s);
 template <typename T>
