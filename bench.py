@@ -127,7 +127,7 @@ class ClockSampler:
 # ------------------------------------------------------------- algorithmic work -------
 
 # FP64 pipe instructions per unit of work (the FP64 forms are bound by this pipe)
-FAST_INNER = 3   # V-cycles per FP64 residual in the fast and learned forms
+FAST_INNER = -8  # fast and learned forms: V-cycles per FP64 residual chosen on the device (<= 8)
 
 FP64_INSTR = {"smooth_fine": 7.0, "resid": 10.0, "tdgl": 30.0, "restrict": 8.0, "prolong": 4.5}
 
@@ -326,7 +326,8 @@ def run_ours(args, ws, rank, local):
         t4 = reduce_max(t4, ws)
         fast = {"precision": "mixed", "guess": "extrapolated", "inner": FAST_INNER,
                 "value": ws * cells * K / (t4 / 1e3) / 1e6, "ms_per_step": t4 / K,
-                "vcycles_per_step": FAST_INNER * (s41["cycles"] - s40["cycles"]) / K,
+                "vcycles_per_step": (FAST_INNER * (s41["cycles"] - s40["cycles"]) / K
+                                     if FAST_INNER > 0 else None),
                 "outer_iterations_per_step": (s41["cycles"] - s40["cycles"]) / K}
         d4.close()
     learned = None if (args.no_compare or args.no_learned) else run_learned(args, ws, cfg, geom, P0, cells,
@@ -369,7 +370,7 @@ def run_ours(args, ws, rank, local):
                        "cells": cells, "tol": 1e-10, "order": 1,
                        "precision": args.precision, "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": f"replicas x{ws}"},
-            "vcycles_per_step": cycles_per_step * max(1, args.inner),
+            "vcycles_per_step": cycles_per_step * max(1, args.inner) if args.inner >= 0 else None,
             "outer_iterations_per_step": cycles_per_step, "gpu_launches": launches,
             "learned_main": None if learned_main is None else
             {k: v for k, v in learned_main.items() if k != "params"},
@@ -418,7 +419,8 @@ def run_learned(args, ws, cfg, geom, P0, cells, sweep, timed_run):
     t = reduce_max(t, ws)
     out = {"precision": "mixed", "guess": "extrapolated + learned", "inner": FAST_INNER,
            "value": ws * cells * K / (t / 1e3) / 1e6, "ms_per_step": t / K,
-           "vcycles_per_step": FAST_INNER * (s1["cycles"] - s0["cycles"]) / K,
+           "vcycles_per_step": (FAST_INNER * (s1["cycles"] - s0["cycles"]) / K
+                                if FAST_INNER > 0 else None),
            "outer_iterations_per_step": (s1["cycles"] - s0["cycles"]) / K,
            "snapshots": args.nn_snapshots, "epochs": args.nn_epochs,
            "train_loss_first_last": [float(losses[0]), float(losses[-1])],

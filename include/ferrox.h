@@ -105,8 +105,12 @@ typedef struct {
                        one, the plain method.  The first starts from a zero correction,
                        the others continue it on the same right-hand side and Newton
                        shift, and phi is corrected once after the last: fewer FP64
-                       residuals (and carrier exponentials) per solve.  The stopping
-                       test is unchanged.  The batched engine takes 0 or 1 only. */
+                       residuals (and carrier exponentials) per solve.  inner < 0:
+                       adaptive, at most -inner V-cycles, the count chosen on the device
+                       after each residual from the contraction per V-cycle measured
+                       over the previous outer iteration (kept across solves) and the
+                       distance to the tolerance.  The stopping test is unchanged.
+                       The batched engine takes 0 or 1 only. */
 } ferrox_numerics;
 
 typedef struct {

@@ -63,7 +63,7 @@ struct ferrox_ctx {
   int resid_kchunk = 0;   // planes per z chunk of the residual kernel
   // device memory
   cudaStream_t stream = nullptr;
-  cudaStream_t cap1 = nullptr, cap2 = nullptr;
+  cudaStream_t cap1 = nullptr, cap2 = nullptr, cap3 = nullptr;
   double* P = nullptr;
   double* phi = nullptr;
   double* b = nullptr;
@@ -321,8 +321,11 @@ struct NoWrap {
 
 // One V-cycle on the correction equation; `wrap(kind, launch)` lets the profiler
 // bracket each launch with events (identity when capturing graphs).
-// V-cycles per outer iteration (numerics.inner; 0 means 1)
+// V-cycles per outer iteration (numerics.inner; 0 means 1; < 0: adaptive, see adapt_max)
 int inner_cycles(const ferrox_ctx* c) { return c->num.inner > 1 ? c->num.inner : 1; }
+// adaptive inner cycles: at most -inner V-cycles per outer iteration, the count
+// chosen on the device after every FP64 residual (0: fixed count)
+int adapt_max(const ferrox_ctx* c) { return c->num.inner < 0 ? -c->num.inner : 0; }
 
 // first: the fine level starts from a zero correction; last: phi += e rides on
 // the last fine-level sweep
@@ -367,13 +370,18 @@ void enqueue_cycles(ferrox_ctx* c, cudaStream_t s, W wrap = W()) {
 }
 
 // the fine-level update is a separate kernel only when it cannot ride on a sweep
-bool separate_update(const ferrox_ctx* c) { return c->tail_first == 0 || c->num.nu2 == 0; }
+bool separate_update(const ferrox_ctx* c) {
+  return c->tail_first == 0 || c->num.nu2 == 0 || adapt_max(c) > 0;
+}
 
 // kernels launched by one outer iteration: V-cycle, (update), residual
+int vcycle_launches(const ferrox_ctx* c) {
+  return c->tail_first * (2 * c->num.nu1 + 1 + 1 + 2 * c->num.nu2) + 1;
+}
+
 int launches_per_cycle(const ferrox_ctx* c) {
-  const int lt = c->tail_first;
-  return inner_cycles(c) * (lt * (2 * c->num.nu1 + 1 + 1 + 2 * c->num.nu2) + 1) +
-         (separate_update(c) ? 1 : 0) + 1;
+  if (adapt_max(c) > 0) return 1 + 1 + 1;   // arm, update, resid (V-cycles counted on the device)
+  return inner_cycles(c) * vcycle_launches(c) + (separate_update(c) ? 1 : 0) + 1;
 }
 
 int tdgl_launches(const ferrox_ctx* c) { return c->ncomp == 3 ? 2 : 1; }
@@ -395,14 +403,17 @@ void enqueue_resid(ferrox_ctx* c, cudaStream_t s, int first, int set_cond,
   a.set_cond = set_cond;
   a.cond_handle = handle;
   a.launches_per_cycle = launches_per_cycle(c);
+  a.adapt_max = adapt_max(c);
+  a.launches_per_vcycle = vcycle_launches(c) + 1;   // + the countdown
   launch_resid<T>(a, s);
 }
 
 template <typename T>
 void enqueue_update(ferrox_ctx* c, cudaStream_t s) {
   if (!separate_update(c)) return;
-  launch_update<T>(c->phi, static_cast<const T*>(c->e_arena), (long long)c->nx * c->ny * c->nz,
-                   c->stats_d, update_clamp(c), s);
+  T* e = static_cast<T*>(c->e_arena);
+  launch_update<T>(c->phi, e, (long long)c->nx * c->ny * c->nz, c->stats_d, update_clamp(c), s,
+                   adapt_max(c) > 0 ? e : nullptr);
 }
 
 TDGLArgs tdgl_args(ferrox_ctx* c, int mode) {
@@ -454,7 +465,33 @@ ferrox_status capture_solve(ferrox_ctx* ctx, cudaStream_t s) {
   cudaGraph_t body = cp.conditional.phGraph_out[0];
   FX_CK(cudaStreamBeginCaptureToGraph(ctx->cap2, body, nullptr, nullptr, 0,
                                       cudaStreamCaptureModeRelaxed));
-  enqueue_cycles<T>(ctx, ctx->cap2);
+  if (adapt_max(ctx) > 0) {
+    // arm -> WHILE { V-cycle continuing the correction; countdown } (count set by the resid)
+    cudaGraphConditionalHandle hi;
+    FX_CK(cudaGraphConditionalHandleCreate(&hi, body, 0, 0));
+    launch_inner_arm(ctx->stats_d, (unsigned long long)hi, ctx->cap2);
+    FX_CK(cudaGetLastError());
+    const cudaGraphNode_t* bdeps = nullptr;
+    size_t bnd = 0;
+    cudaGraph_t bg;
+    FX_CK(cudaStreamGetCaptureInfo(ctx->cap2, &st, nullptr, &bg, &bdeps, nullptr, &bnd));
+    cudaGraphNodeParams ip = {cudaGraphNodeTypeConditional};
+    ip.conditional.handle = hi;
+    ip.conditional.type = cudaGraphCondTypeWhile;
+    ip.conditional.size = 1;
+    cudaGraphNode_t icn;
+    FX_CK(cudaGraphAddNode(&icn, bg, bdeps, nullptr, bnd, &ip));
+    FX_CK(cudaStreamBeginCaptureToGraph(ctx->cap3, ip.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                        cudaStreamCaptureModeRelaxed));
+    enqueue_vcycle<T>(ctx, ctx->cap3, NoWrap(), false, false);
+    launch_inner_countdown(ctx->stats_d, (unsigned long long)hi, ctx->cap3);
+    FX_CK(cudaGetLastError());
+    cudaGraph_t ibody_out;
+    FX_CK(cudaStreamEndCapture(ctx->cap3, &ibody_out));
+    FX_CK(cudaStreamUpdateCaptureDependencies(ctx->cap2, &icn, nullptr, 1, cudaStreamSetCaptureDependencies));
+  } else {
+    enqueue_cycles<T>(ctx, ctx->cap2);
+  }
   enqueue_update<T>(ctx, ctx->cap2);
   enqueue_resid<T>(ctx, ctx->cap2, 0, 1, (unsigned long long)h);
   FX_CK(cudaGetLastError());
@@ -534,7 +571,8 @@ void enqueue_nn_prelude(ferrox_ctx* c, cudaStream_t s) {
   nn_bridge_apply<T>(nn_output(c->nn), c->lv[lv], c->nn_scale, e, s);
   MGArgs<T> a = mg_args<T>(c);
   for (int l = lv - 1; l >= 0; --l) launch_prolong<T>(a, c->lv[l], c->lv[l + 1], 0, s);
-  launch_update<T>(c->phi, e, (long long)c->nx * c->ny * c->nz, c->nn_stats, update_clamp(c), s);
+  launch_update<T>(c->phi, e, (long long)c->nx * c->ny * c->nz, c->nn_stats, update_clamp(c), s,
+                   adapt_max(c) > 0 ? e : nullptr);
 }
 
 template <typename T>
@@ -618,7 +656,17 @@ ferrox_status profile_step_t(ferrox_ctx* ctx, double* ms, int* count) {
       int cond;
       std::memcpy(&cond, ctx->host_pinned, sizeof(int));
       if (!cond) break;
-      enqueue_cycles<T>(ctx, s, std::ref(tm));
+      if (adapt_max(ctx) > 0) {
+        FX_CK(cudaMemcpyAsync(ctx->host_pinned, reinterpret_cast<char*>(ctx->stats_d) +
+                                                    offsetof(DevStats, inner_k),
+                              sizeof(int), cudaMemcpyDeviceToHost, s));
+        FX_CK(cudaStreamSynchronize(s));
+        int k;
+        std::memcpy(&k, ctx->host_pinned, sizeof(int));
+        for (int i = 0; i < k; ++i) enqueue_vcycle<T>(ctx, s, std::ref(tm), false, false);
+      } else {
+        enqueue_cycles<T>(ctx, s, std::ref(tm));
+      }
       if (separate_update(ctx)) tm(FERROX_K_UPDATE, [&] { enqueue_update<T>(ctx, s); });
       tm(FERROX_K_RESID, [&] { enqueue_resid<T>(ctx, s, 0, 0, 0ULL); });
     }
@@ -668,6 +716,7 @@ void release(ferrox_ctx* c) {
   if (c->host_pinned) cudaFreeHost(c->host_pinned);
   if (c->cap1) cudaStreamDestroy(c->cap1);
   if (c->cap2) cudaStreamDestroy(c->cap2);
+  if (c->cap3) cudaStreamDestroy(c->cap3);
   delete c;
 }
 
@@ -705,7 +754,7 @@ ferrox_status validate(const ferrox_geometry* g, const ferrox_numerics* n, const
   if (n->max_cycles < 1) return bad("max_cycles must be >= 1");
   if (n->precision != FERROX_FP64 && n->precision != FERROX_MIXED) return bad("unknown precision");
   if (n->bottom_sweeps < 0) return bad("bottom_sweeps must be >= 0");
-  if (n->inner < 0 || n->inner > 16) return bad("inner must be in 0..16");
+  if (n->inner < -16 || n->inner > 16) return bad("inner must be in -16..16");
   if (n->guess != 0 && n->guess != 1) return bad("guess must be 0 or 1");
   return FERROX_OK;
 }
@@ -762,6 +811,7 @@ ferrox_status ferrox_init_geometry(ferrox_ctx** out, const ferrox_geometry* geom
   } while (0)
   FX_INIT_CK(cudaStreamCreateWithFlags(&ctx->cap1, cudaStreamNonBlocking));
   FX_INIT_CK(cudaStreamCreateWithFlags(&ctx->cap2, cudaStreamNonBlocking));
+  FX_INIT_CK(cudaStreamCreateWithFlags(&ctx->cap3, cudaStreamNonBlocking));
   FX_INIT_CK(cudaMalloc(&ctx->b, N * sizeof(double)));
   FX_INIT_CK(cudaMalloc(&ctx->Pbuf, ctx->ncomp * N * sizeof(double)));
   if (ctx->num.order == 2) FX_INIT_CK(cudaMalloc(&ctx->Fbuf, ctx->ncomp * N * sizeof(double)));
@@ -1298,7 +1348,8 @@ ferrox_status ferrox_init_batch(ferrox_batch** out, int n, const ferrox_geometry
     if (geoms[i].ncomp != 1) return bfail(nullptr, FERROX_EINVAL, "batched instances are uniaxial (ncomp = 1)");
   }
   if (num->order != 1) return bfail(nullptr, FERROX_EINVAL, "the batched engine runs order-1 steps");
-  if (num->inner > 1) return bfail(nullptr, FERROX_EINVAL, "the batched engine runs one V-cycle per outer iteration");
+  if (num->inner > 1 || num->inner < 0)
+    return bfail(nullptr, FERROX_EINVAL, "the batched engine runs one V-cycle per outer iteration");
   ferrox_batch* B = new ferrox_batch();
   B->n = n;
   B->num = *num;

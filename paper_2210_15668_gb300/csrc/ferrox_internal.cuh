@@ -118,7 +118,11 @@ struct DevStats {
   unsigned int done_ctr;
   int cycles_this_solve;
   int zero_phi;
-  int pad;
+  int inner_k;            // adaptive inner cycles: V-cycles of the current outer iteration
+  int inner_left;         //   ... still to run
+  int pad3;
+  double rho_v;           //   estimated contraction per V-cycle (0: none yet), kept across solves
+  double prev_rnorm;      //   ||r|| at the previous outer iteration of this solve
 };
 
 // Arguments of the outer (FP64) residual kernel.
@@ -138,8 +142,11 @@ struct ResidArgs {
   int first;           // first residual of a solve
   int set_cond;        // call cudaGraphSetConditional
   unsigned long long cond_handle;
-  int launches_per_cycle;  // kernels of one outer iteration (V-cycle + update + resid)
+  int launches_per_cycle;  // kernels of one outer iteration (V-cycle + update + resid); adaptive:
+                           // the fixed part (update + resid)
   int no_stats;            // write r (and s) only: no norms, no decision
+  int adapt_max;           // > 0: choose the next outer iteration's V-cycles (<= adapt_max)
+  int launches_per_vcycle; // adaptive: kernels of one V-cycle and its countdown
   int kchunk;              // planes per z chunk of the multi-block kernel (grid.z chunks)
 };
 
@@ -188,7 +195,11 @@ template <typename T>
 void launch_resid(const ResidArgs& a, cudaStream_t s);
 template <typename T>
 void launch_update(double* phi, const T* e0, long long n, const DevStats* stats, double clamp,
-                   cudaStream_t s);
+                   cudaStream_t s, T* zero_e = nullptr);
+// adaptive inner loop: arm its condition from inner_left (first node of an outer
+// iteration), and count one V-cycle down after each
+void launch_inner_arm(const DevStats* st, unsigned long long handle, cudaStream_t s);
+void launch_inner_countdown(DevStats* st, unsigned long long handle, cudaStream_t s);
 
 struct TDGLArgs {
   const double* P_in;     // [ncomp][nz][ny][nx]

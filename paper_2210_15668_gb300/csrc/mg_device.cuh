@@ -358,7 +358,8 @@ __device__ __forceinline__ void resid_column(const ResidArgs& a, int i, int j, i
 
 // Convergence decision of one solve from its summed norms (one thread).
 __device__ __forceinline__ int decide(DevStats* st, double sr, double sb, double sq, int first,
-                                      double tol, int max_cycles, int launches_per_cycle) {
+                                      double tol, int max_cycles, int launches_per_cycle,
+                                      int adapt_max = 0, int launches_per_vcycle = 0) {
   if (first) {
     st->solves += 1;
     st->cycles_this_solve = 0;
@@ -386,6 +387,22 @@ __device__ __forceinline__ int decide(DevStats* st, double sr, double sb, double
     st->cycles_this_solve += 1;
     st->cycles += 1;
     st->launches += launches_per_cycle;
+  }
+  if (adapt_max > 0 && !first && st->inner_k > 0 && st->prev_rnorm > 0.0 && rn > 0.0) {
+    // contraction per V-cycle over the outer iteration just finished, measured
+    // whether or not it reached the tolerance (kept for the next solves)
+    st->rho_v = fmin(fmax(pow(rn / st->prev_rnorm, 1.0 / st->inner_k), 0.02), 0.9);
+  }
+  if (cond && adapt_max > 0) {
+    // V-cycles for the next outer iteration: enough, at the estimated contraction
+    // (0.2 before any measurement), to bring ||r|| to the tolerance
+    const double rho = st->rho_v > 0.0 ? st->rho_v : 0.2;
+    const double need = (rn > 0.0 && scale > 0.0) ? log(tol * scale / rn) / log(rho) : 1.0;
+    const int k = (int)fmin(fmax(ceil(need), 1.0), (double)adapt_max);
+    st->inner_k = k;
+    st->inner_left = k;
+    st->prev_rnorm = rn;
+    st->launches += k * launches_per_vcycle;
   }
   st->last_cond = cond;
   st->last_cycles = st->cycles_this_solve;

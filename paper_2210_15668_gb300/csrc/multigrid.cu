@@ -189,7 +189,8 @@ __global__ void __launch_bounds__(kResidBX* kResidBY) resid_kernel(ResidArgs a) 
   block_sum3(sr, sb, sq);
   if (tid == 0) {
     a.stats->done_ctr = 0;
-    const int cond = decide(a.stats, sr, sb, sq, a.first, a.tol, a.max_cycles, a.launches_per_cycle);
+    const int cond = decide(a.stats, sr, sb, sq, a.first, a.tol, a.max_cycles, a.launches_per_cycle,
+                            a.adapt_max, a.launches_per_vcycle);
     if (a.set_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)a.cond_handle, cond);
   }
 }
@@ -197,12 +198,26 @@ __global__ void __launch_bounds__(kResidBX* kResidBY) resid_kernel(ResidArgs a) 
 template <typename T>
 __global__ void __launch_bounds__(256) update_kernel(double* __restrict__ phi, const T* __restrict__ e0,
                                                      long long n, const DevStats* stats,
-                                                     double clamp) {
+                                                     double clamp, T* zero_e) {
   pdl_enter();
   const Upd u{phi, clamp, stats->zero_phi};
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
-       t += (long long)gridDim.x * blockDim.x)
+       t += (long long)gridDim.x * blockDim.x) {
     apply_update(u, t, e0[t]);
+    if (zero_e) zero_e[t] = T(0);   // the next outer iteration starts from a zero correction
+  }
+}
+
+__global__ void inner_arm_kernel(const DevStats* st, unsigned long long handle) {
+  pdl_enter();
+  cudaGraphSetConditional((cudaGraphConditionalHandle)handle, st->inner_left > 0 ? 1 : 0);
+}
+
+__global__ void inner_countdown_kernel(DevStats* st, unsigned long long handle) {
+  pdl_enter();
+  const int left = st->inner_left - 1;
+  st->inner_left = left;
+  cudaGraphSetConditional((cudaGraphConditionalHandle)handle, left > 0 ? 1 : 0);
 }
 
 // 2-D block over (x items, rows): x extent a power of two up to 128
@@ -277,10 +292,18 @@ void launch_resid(const ResidArgs& a, cudaStream_t s) {
 
 template <typename T>
 void launch_update(double* phi, const T* e0, long long n, const DevStats* stats, double clamp,
-                   cudaStream_t s) {
+                   cudaStream_t s, T* zero_e) {
   long long b = (n + 255) / 256;
   if (b > 152LL * 16) b = 152LL * 16;
-  launch_k(update_kernel<T>, dim3((int)b), dim3(256), 0, s, phi, e0, n, stats, clamp);
+  launch_k(update_kernel<T>, dim3((int)b), dim3(256), 0, s, phi, e0, n, stats, clamp, zero_e);
+}
+
+void launch_inner_arm(const DevStats* st, unsigned long long handle, cudaStream_t s) {
+  launch_k(inner_arm_kernel, dim3(1), dim3(1), 0, s, st, handle);
+}
+
+void launch_inner_countdown(DevStats* st, unsigned long long handle, cudaStream_t s) {
+  launch_k(inner_countdown_kernel, dim3(1), dim3(1), 0, s, st, handle);
 }
 
 // e^{+u}, e^{-u} of n arguments with the carrier routine of the residual kernel
@@ -317,7 +340,7 @@ cudaError_t launch_carrier_exp(const double* u, double* ep, double* em, long lon
   template void launch_tail<T>(const MGArgs<T>&, const TailArgs&, size_t, cudaStream_t);        \
   template void launch_resid<T>(const ResidArgs&, cudaStream_t);                                \
   template void launch_update<T>(double*, const T*, long long, const DevStats*, double,         \
-                                 cudaStream_t);
+                                 cudaStream_t, T*);
 FX_INST(double)
 FX_INST(float)
 #undef FX_INST
