@@ -240,7 +240,7 @@ def run_ours(args, ws, rank, local):
         st1 = d.stats()
         return t_ms, st0, st1, ck
 
-    prec_main = ferrox.MIXED if args.precision == "mixed" else ferrox.FP64
+    prec_main = {"mixed": ferrox.MIXED, "fp64": ferrox.FP64, "fp64_defect": ferrox.FP64_DEFECT}[args.precision]
     dev = make(prec_main)
     learned_main = None
     if args.learned:
@@ -254,6 +254,7 @@ def run_ours(args, ws, rank, local):
     K = args.steps
     value = ws * cells * K / (t_max / 1e3) / 1e6
     cycles_per_step = (st1["cycles"] - st0["cycles"]) / K
+    vcycles_per_step = (st1["vcycles"] - st0["vcycles"]) / K
     launches = st1["launches"] - st0["launches"]
 
     # per-kernel breakdown of one step (eager, event-timed) -> roofline of the dominant kernel
@@ -269,7 +270,7 @@ def run_ours(args, ws, rank, local):
     avg_s = dom_ms / max(dom_n, 1) / 1e3
     gbs = by / avg_s / 1e9 if by else None
     tfl = fl / avg_s / 1e12 if fl else None
-    fp64_kernel = prec_main == ferrox.FP64 or dom in ("resid", "tdgl", "update")
+    fp64_kernel = prec_main != ferrox.MIXED or dom in ("resid", "tdgl", "update")
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if os.path.exists(tpath):
@@ -305,7 +306,7 @@ def run_ours(args, ws, rank, local):
         v2 = ws * cells * K / (t2 / 1e3) / 1e6
         prof2 = d2.profile_step()
         other = {"precision": "fp64" if prec_o == ferrox.FP64 else "mixed", "value": v2,
-                 "ms_per_step": t2 / K, "vcycles_per_step": (s21["cycles"] - s20["cycles"]) / K,
+                 "ms_per_step": t2 / K, "vcycles_per_step": (s21["vcycles"] - s20["vcycles"]) / K,
                  "kernel_breakdown_ms_one_step": {k: {"ms": round(v[0], 4), "launches": v[1]}
                                                   for k, v in prof2.items() if v[1]}}
         d2.close()
@@ -326,15 +327,14 @@ def run_ours(args, ws, rank, local):
         t4 = reduce_max(t4, ws)
         fast = {"precision": "mixed", "guess": "extrapolated", "inner": FAST_INNER,
                 "value": ws * cells * K / (t4 / 1e3) / 1e6, "ms_per_step": t4 / K,
-                "vcycles_per_step": (FAST_INNER * (s41["cycles"] - s40["cycles"]) / K
-                                     if FAST_INNER > 0 else None),
+                "vcycles_per_step": (s41["vcycles"] - s40["vcycles"]) / K,
                 "outer_iterations_per_step": (s41["cycles"] - s40["cycles"]) / K}
         d4.close()
     learned = None if (args.no_compare or args.no_learned) else run_learned(args, ws, cfg, geom, P0, cells,
                                                                             sweep, timed_run)
     batch = None if args.no_batch else run_batch_qv(args, ws)
     mixed_v = value if prec_main == ferrox.MIXED else (other or {}).get("value")
-    fp64_v = value if prec_main == ferrox.FP64 else (other or {}).get("value")
+    fp64_v = value if prec_main != ferrox.MIXED else (other or {}).get("value")
 
     # end to end through the public API with host buffers (pinned), copies inside the region
     e2e = None
@@ -364,13 +364,13 @@ def run_ours(args, ws, rank, local):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K,
             "warmup": args.warmup, "ms_per_step": t_max / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if prec_main == ferrox.FP64 else "f32+f64",
+            "dtype": "f64" if prec_main != ferrox.MIXED else "f32+f64",
             "data": "synthetic",
             "config": {"workload": cfg["label"], "guess": args.guess, "nu1": args.nu1, "nu2": args.nu2, "inner": args.inner,
                        "cells": cells, "tol": 1e-10, "order": 1,
                        "precision": args.precision, "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": f"replicas x{ws}"},
-            "vcycles_per_step": cycles_per_step * max(1, args.inner) if args.inner >= 0 else None,
+            "vcycles_per_step": vcycles_per_step,
             "outer_iterations_per_step": cycles_per_step, "gpu_launches": launches,
             "learned_main": None if learned_main is None else
             {k: v for k, v in learned_main.items() if k != "params"},
@@ -419,8 +419,7 @@ def run_learned(args, ws, cfg, geom, P0, cells, sweep, timed_run):
     t = reduce_max(t, ws)
     out = {"precision": "mixed", "guess": "extrapolated + learned", "inner": FAST_INNER,
            "value": ws * cells * K / (t / 1e3) / 1e6, "ms_per_step": t / K,
-           "vcycles_per_step": (FAST_INNER * (s1["cycles"] - s0["cycles"]) / K
-                                if FAST_INNER > 0 else None),
+           "vcycles_per_step": (s1["vcycles"] - s0["vcycles"]) / K,
            "outer_iterations_per_step": (s1["cycles"] - s0["cycles"]) / K,
            "snapshots": args.nn_snapshots, "epochs": args.nn_epochs,
            "train_loss_first_last": [float(losses[0]), float(losses[-1])],
@@ -560,7 +559,10 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "mixed", "fp64_defect"], default="fp64",
+                    help="fp64: V-cycles on phi (residual norm fused into the restriction); "
+                         "fp64_defect: FP64 V-cycles on the correction equation; mixed: FP32 "
+                         "V-cycles in FP64 defect correction")
     ap.add_argument("--workload", default="mfim_256x256x32",
                     help="mfim_256x256x32 (the benchmark) or mfim_NXxNYxNZ (profiling copies)")
     ap.add_argument("--e2e-steps", type=int, default=200)

@@ -61,8 +61,17 @@ enum { FERROX_PBC_FREE = 0, FERROX_PBC_ZERO = 1, FERROX_PBC_LAMBDA = 2 };
 
 /* Arithmetic of the Poisson solve: FP64 multigrid, or FP32 multigrid cycles
  * inside an FP64 defect-correction loop (FP64 residual, potential, norms and
- * carrier exponentials).  Both stop on the same FP64 residual test. */
-enum { FERROX_FP64 = 0, FERROX_MIXED = 1 };
+ * carrier exponentials).  All stop on the same FP64 residual test.
+ *   FERROX_FP64: V-cycles on phi itself, the residual norm fused into the
+ *     fine-level restriction after the pre-smoothing (the test accepts phi after
+ *     that pre-smoothing), when the stack has no semiconductor layer, inner is
+ *     0 or 1 and the fine level coarsens in x, y and z; otherwise as
+ *     FERROX_FP64_DEFECT.
+ *   FERROX_FP64_DEFECT: FP64 V-cycles on the correction equation inside the
+ *     defect-correction (Newton) loop, the residual computed by its own kernel
+ *     before every V-cycle.
+ * The batched engine runs the defect-correction form for FERROX_FP64. */
+enum { FERROX_FP64 = 0, FERROX_MIXED = 1, FERROX_FP64_DEFECT = 2 };
 
 /* One planar layer (Table 1 lists the parameters).  Only the fields of its
  * kind are read: Landau/gradient/kinetic data for FE, carrier data for SC. */
@@ -95,7 +104,7 @@ typedef struct {
   double tol;       /* stop when ||r||_2 <= tol * max(||b||_2, ||rho||_2); e.g. 1e-10 */
   int nu1, nu2;     /* pre/post red-black Gauss-Seidel sweeps per V-cycle level */
   int max_cycles;   /* V-cycles (outer iterations) allowed per solve */
-  int precision;    /* FERROX_FP64 or FERROX_MIXED */
+  int precision;    /* FERROX_FP64, FERROX_MIXED or FERROX_FP64_DEFECT */
   int bottom_sweeps;/* sweeps on the coarsest level (0: default) */
   int guess;        /* initial potential of each step's solve: 0 = the previous step's
                        potential (Step 1b of the Methods), 1 = linear extrapolation in
@@ -129,6 +138,8 @@ typedef struct {
   int last_cycles;         /* V-cycles of the most recent solve */
   double last_rel_res;     /* ||r|| / max(||b||, ||rho||) at the end of that solve */
   int status;              /* sticky device status (ferrox_status) */
+  long long vcycles;       /* V-cycles run, all solves, inner cycles included (= cycles when
+                              numerics.inner is 0 or 1) */
 } ferrox_stats;
 
 /* Create a context (a1: per-plane material tables, multigrid hierarchy, CUDA

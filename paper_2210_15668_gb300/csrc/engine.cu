@@ -61,6 +61,8 @@ struct ferrox_ctx {
   size_t tail_smem = 0;
   int resid_blocks = 0;
   int resid_kchunk = 0;   // planes per z chunk of the residual kernel
+  bool direct = false;    // FP64 V-cycles on phi itself (see direct_form)
+  int check_blocks = 0;   // blocks of the direct form's fused residual + restriction + norm
   // device memory
   cudaStream_t stream = nullptr;
   cudaStream_t cap1 = nullptr, cap2 = nullptr, cap3 = nullptr;
@@ -329,14 +331,14 @@ int adapt_max(const ferrox_ctx* c) { return c->num.inner < 0 ? -c->num.inner : 0
 
 // first: the fine level starts from a zero correction; last: phi += e rides on
 // the last fine-level sweep
+// levels l0 .. L of one V-cycle (l0 = 1: the coarse part of the direct form)
 template <typename T, typename W = NoWrap>
-void enqueue_vcycle(ferrox_ctx* c, cudaStream_t s, W wrap = W(), bool first = true,
-                    bool last = true) {
+void enqueue_levels(ferrox_ctx* c, cudaStream_t s, W wrap, int l0, bool first, bool last) {
   MGArgs<T> a = mg_args<T>(c);
   const int nu1 = c->num.nu1, nu2 = c->num.nu2;
   const int constant = 0;
   const int lt = c->tail_first, L = (int)c->lv.size() - 1;
-  for (int l = 0; l < lt; ++l) {
+  for (int l = l0; l < lt; ++l) {
     const int ks = l == 0 ? FERROX_K_SMOOTH0 : FERROX_K_SMOOTHC;
     for (int sw = 0; sw < nu1; ++sw) {
       const int zero = sw == 0 && (first || l > 0);
@@ -349,7 +351,7 @@ void enqueue_vcycle(ferrox_ctx* c, cudaStream_t s, W wrap = W(), bool first = tr
               constant};
   wrap(FERROX_K_TAIL, [&] { launch_tail<T>(a, ta, c->tail_smem, s); });
   const UpdateArgs upd{c->phi, c->stats_d, update_clamp(c)};
-  for (int l = lt - 1; l >= 0; --l) {
+  for (int l = lt - 1; l >= l0; --l) {
     const int ks = l == 0 ? FERROX_K_SMOOTH0 : FERROX_K_SMOOTHC;
     // the tiled form where FP64 arithmetic bounds the launch: the fine level
     const bool tiled = sizeof(T) == sizeof(double) && l == 0;
@@ -360,6 +362,86 @@ void enqueue_vcycle(ferrox_ctx* c, cudaStream_t s, W wrap = W(), bool first = tr
       wrap(ks, [&] { launch_smooth<T>(a, c->lv[l], 1, 0, fuse ? &upd : nullptr, s); });
     }
   }
+}
+
+template <typename T, typename W = NoWrap>
+void enqueue_vcycle(ferrox_ctx* c, cudaStream_t s, W wrap = W(), bool first = true,
+                    bool last = true) {
+  enqueue_levels<T>(c, s, wrap, 0, first, last);
+}
+
+// ---- direct FP64 form: V-cycles on phi itself -------------------------------------
+// The fine level relaxes A phi = b in place (b holds the whole right-hand side:
+// the TDGL update writes its planes, launch_static_b the electrode lift of the
+// others); the residual b - A phi after the pre-smoothing is restricted and its
+// norm decides convergence in the same kernel, so no separate residual pass,
+// correction array or update runs on the fine level.  Used for FP64 stacks
+// without carriers (no Newton shift), one V-cycle per check and a fine level
+// coarsened in all three directions (the tiled prolongation writes phi).
+bool direct_form(const ferrox_ctx* c) {
+  return c->num.precision == FERROX_FP64 && !c->has_sc && c->num.inner <= 1 &&
+         c->num.inner >= 0 && c->tail_first >= 1 && c->lv.size() >= 2 && c->lv[0].crx &&
+         c->lv[0].cry && c->lv[0].crz;
+}
+
+MGArgs<double> fine_args(ferrox_ctx* c) {
+  MGArgs<double> a = mg_args<double>(c);
+  a.e = c->phi;   // level 0 has arena offset 0
+  a.r = c->b;
+  a.s = nullptr;
+  return a;
+}
+
+// nu1 red/black sweep pairs on phi; zst: honour the solve's b = 0 flag (phi = 0)
+template <typename W>
+void enqueue_fine_sweeps(ferrox_ctx* c, cudaStream_t s, W wrap, int nu, const DevStats* zst) {
+  const MGArgs<double> fa = fine_args(c);
+  for (int sw = 0; sw < nu; ++sw) {
+    wrap(FERROX_K_SMOOTH0, [&] { launch_smooth<double>(fa, c->lv[0], 0, 0, nullptr, s, zst); });
+    wrap(FERROX_K_SMOOTH0, [&] { launch_smooth<double>(fa, c->lv[0], 1, 0, nullptr, s, zst); });
+  }
+}
+
+// kernels of one loop iteration of the direct form (= one V-cycle)
+int vcycle_launches(const ferrox_ctx* c);
+
+template <typename W>
+void enqueue_check(ferrox_ctx* c, cudaStream_t s, W wrap, int first, int set_cond,
+                   unsigned long long handle) {
+  CheckArgs ck{};
+  ck.partials = c->partials_d;
+  ck.stats = c->stats_d;
+  ck.tol = c->num.tol;
+  ck.max_cycles = c->num.max_cycles;
+  ck.first = first;
+  ck.set_cond = set_cond;
+  ck.launches_per_cycle = vcycle_launches(c);
+  ck.cond_handle = handle;
+  ck.first_launches = 2 * c->num.nu1 + 1;
+  const MGArgs<double> fa = fine_args(c);
+  double* rc = static_cast<double*>(c->r_arena);
+  wrap(FERROX_K_RESID, [&] { launch_restrict_check(fa, rc, c->lv[0], c->lv[1], c->num.nu1, ck, s); });
+}
+
+// prologue of a solve: pre-smoothing and the first check
+template <typename W = NoWrap>
+void enqueue_direct_prologue(ferrox_ctx* c, cudaStream_t s, W wrap, int set_cond,
+                             unsigned long long handle) {
+  enqueue_fine_sweeps(c, s, wrap, c->num.nu1, nullptr);
+  enqueue_check(c, s, wrap, 1, set_cond, handle);
+}
+
+// one loop iteration: the coarse levels, their correction prolongated into phi,
+// post-smoothing, the next pre-smoothing and check
+template <typename W = NoWrap>
+void enqueue_direct_cycle(ferrox_ctx* c, cudaStream_t s, W wrap, int set_cond,
+                          unsigned long long handle) {
+  enqueue_levels<double>(c, s, wrap, 1, true, false);
+  MGArgs<double> a = mg_args<double>(c);
+  wrap(FERROX_K_PROLONG, [&] { launch_prolong<double>(a, c->lv[0], c->lv[1], 0, s, true, c->phi); });
+  enqueue_fine_sweeps(c, s, wrap, c->num.nu2, c->stats_d);
+  enqueue_fine_sweeps(c, s, wrap, c->num.nu1, c->stats_d);
+  enqueue_check(c, s, wrap, 0, set_cond, handle);
 }
 
 // the V-cycles of one outer iteration
@@ -380,6 +462,7 @@ int vcycle_launches(const ferrox_ctx* c) {
 }
 
 int launches_per_cycle(const ferrox_ctx* c) {
+  if (c->direct) return vcycle_launches(c);
   if (adapt_max(c) > 0) return 1 + 1 + 1;   // arm, update, resid (V-cycles counted on the device)
   return inner_cycles(c) * vcycle_launches(c) + (separate_update(c) ? 1 : 0) + 1;
 }
@@ -405,6 +488,7 @@ void enqueue_resid(ferrox_ctx* c, cudaStream_t s, int first, int set_cond,
   a.launches_per_cycle = launches_per_cycle(c);
   a.adapt_max = adapt_max(c);
   a.launches_per_vcycle = vcycle_launches(c) + 1;   // + the countdown
+  a.inner_fixed = inner_cycles(c);
   launch_resid<T>(a, s);
 }
 
@@ -453,7 +537,10 @@ ferrox_status capture_solve(ferrox_ctx* ctx, cudaStream_t s) {
   FX_CK(cudaStreamGetCaptureInfo(s, &st, nullptr, &g, nullptr, nullptr, nullptr));
   cudaGraphConditionalHandle h;
   FX_CK(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
-  enqueue_resid<T>(ctx, s, 1, 1, (unsigned long long)h);
+  if (ctx->direct)
+    enqueue_direct_prologue(ctx, s, NoWrap(), 1, (unsigned long long)h);
+  else
+    enqueue_resid<T>(ctx, s, 1, 1, (unsigned long long)h);
   FX_CK(cudaGetLastError());
   FX_CK(cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, nullptr, &nd));
   cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
@@ -465,6 +552,14 @@ ferrox_status capture_solve(ferrox_ctx* ctx, cudaStream_t s) {
   cudaGraph_t body = cp.conditional.phGraph_out[0];
   FX_CK(cudaStreamBeginCaptureToGraph(ctx->cap2, body, nullptr, nullptr, 0,
                                       cudaStreamCaptureModeRelaxed));
+  if (ctx->direct) {
+    enqueue_direct_cycle(ctx, ctx->cap2, NoWrap(), 1, (unsigned long long)h);
+    FX_CK(cudaGetLastError());
+    cudaGraph_t body_out;
+    FX_CK(cudaStreamEndCapture(ctx->cap2, &body_out));
+    FX_CK(cudaStreamUpdateCaptureDependencies(s, &cn, nullptr, 1, cudaStreamSetCaptureDependencies));
+    return FERROX_OK;
+  }
   if (adapt_max(ctx) > 0) {
     // arm -> WHILE { V-cycle continuing the correction; countdown } (count set by the resid)
     cudaGraphConditionalHandle hi;
@@ -647,6 +742,20 @@ ferrox_status profile_step_t(ferrox_ctx* ctx, double* ms, int* count) {
   cudaStream_t s = ctx->stream;
   EventTimer tm{s, {}};
   auto solve = [&]() -> ferrox_status {
+    if (ctx->direct) {
+      enqueue_direct_prologue(ctx, s, std::ref(tm), 0, 0ULL);
+      for (int guard = 0; guard <= ctx->num.max_cycles + 1; ++guard) {
+        FX_CK(cudaMemcpyAsync(ctx->host_pinned, reinterpret_cast<char*>(ctx->stats_d) +
+                                                    offsetof(DevStats, last_cond),
+                              sizeof(int), cudaMemcpyDeviceToHost, s));
+        FX_CK(cudaStreamSynchronize(s));
+        int cond;
+        std::memcpy(&cond, ctx->host_pinned, sizeof(int));
+        if (!cond) break;
+        enqueue_direct_cycle(ctx, s, std::ref(tm), 0, 0ULL);
+      }
+      return FERROX_OK;
+    }
     tm(FERROX_K_RESID, [&] { enqueue_resid<T>(ctx, s, 1, 0, 0ULL); });
     for (int guard = 0; guard <= ctx->num.max_cycles + 1; ++guard) {
       FX_CK(cudaMemcpyAsync(ctx->host_pinned, reinterpret_cast<char*>(ctx->stats_d) +
@@ -752,7 +861,9 @@ ferrox_status validate(const ferrox_geometry* g, const ferrox_numerics* n, const
   if (!(n->tol > 0.0)) return bad("tol must be > 0");
   if (n->nu1 < 1 || n->nu2 < 0) return bad("need nu1 >= 1 and nu2 >= 0");
   if (n->max_cycles < 1) return bad("max_cycles must be >= 1");
-  if (n->precision != FERROX_FP64 && n->precision != FERROX_MIXED) return bad("unknown precision");
+  if (n->precision != FERROX_FP64 && n->precision != FERROX_MIXED &&
+      n->precision != FERROX_FP64_DEFECT)
+    return bad("unknown precision");
   if (n->bottom_sweeps < 0) return bad("bottom_sweeps must be >= 0");
   if (n->inner < -16 || n->inner > 16) return bad("inner must be in -16..16");
   if (n->guess != 0 && n->guess != 1) return bad("guess must be 0 or 1");
@@ -799,6 +910,11 @@ ferrox_status ferrox_init_geometry(ferrox_ctx** out, const ferrox_geometry* geom
     ctx->resid_kchunk = (ctx->nz + zc - 1) / zc;
     ctx->resid_blocks = bxy * ((ctx->nz + ctx->resid_kchunk - 1) / ctx->resid_kchunk);
   }
+  ctx->direct = direct_form(ctx);
+  if (ctx->direct) {
+    const dim3 g = check_grid(ctx->lv[1]);
+    ctx->check_blocks = (int)(g.x * g.y * g.z);
+  }
   const long long N = (long long)ctx->nx * ctx->ny * ctx->nz;
   auto cleanup = [&](ferrox_status s) { g_init_error = ctx->err; release(ctx); return s; };
 #define FX_INIT_CK(call)                                                                     \
@@ -826,7 +942,9 @@ ferrox_status ferrox_init_geometry(ferrox_ctx** out, const ferrox_geometry* geom
   FX_INIT_CK(cudaMalloc(&ctx->lv_d, ctx->lv.size() * sizeof(LevelDesc)));
   FX_INIT_CK(cudaMalloc(&ctx->params_d, sizeof(DevParams)));
   FX_INIT_CK(cudaMalloc(&ctx->stats_d, sizeof(DevStats)));
-  FX_INIT_CK(cudaMalloc(&ctx->partials_d, 3 * (size_t)ctx->resid_blocks * sizeof(double)));
+  FX_INIT_CK(cudaMalloc(&ctx->partials_d, std::max(3 * (size_t)ctx->resid_blocks,
+                                                    2 * (size_t)ctx->check_blocks) *
+                                               sizeof(double)));
   FX_INIT_CK(cudaMalloc(&ctx->lvt_d, ctx->lv_tail.size() * sizeof(LevelDesc)));
   FX_INIT_CK(cudaMemcpy(ctx->lvt_d, ctx->lv_tail.data(), ctx->lv_tail.size() * sizeof(LevelDesc),
                         cudaMemcpyHostToDevice));
@@ -890,6 +1008,8 @@ ferrox_status ferrox_set_bias(ferrox_ctx* ctx, double v_bottom, double v_top) {
   ctx->v_bot = v_bottom;
   ctx->v_top = v_top;
   launch_set_params(ctx->params_d, v_bottom, v_top, ctx->stream);
+  if (ctx->direct)
+    launch_static_b(ctx->b, ctx->planes_d, ctx->params_d, ctx->nx, ctx->ny, ctx->nz, ctx->stream);
   FX_CK(cudaGetLastError());
   return FERROX_OK;
 }
@@ -995,6 +1115,7 @@ ferrox_status ferrox_sync_stats(ferrox_ctx* ctx, ferrox_stats* out) {
   out->launches = st.launches;
   out->solves = st.solves;
   out->cycles = st.cycles;
+  out->vcycles = st.vcycles;
   out->last_cycles = st.last_cycles;
   out->last_rel_res = st.last_rel;
   out->status = st.status;
@@ -1567,6 +1688,7 @@ ferrox_status ferrox_batch_stats(ferrox_batch* B, ferrox_stats* out) {
     out[i].launches = st[i].steps;
     out[i].solves = st[i].solves;
     out[i].cycles = st[i].cycles;
+    out[i].vcycles = st[i].vcycles;
     out[i].last_cycles = st[i].last_cycles;
     out[i].last_rel_res = st[i].last_rel;
     out[i].status = gst ? gst : st[i].status;

@@ -123,6 +123,7 @@ struct DevStats {
   int pad3;
   double rho_v;           //   estimated contraction per V-cycle (0: none yet), kept across solves
   double prev_rnorm;      //   ||r|| at the previous outer iteration of this solve
+  long long vcycles;      // V-cycles run, all solves (inner cycles included)
 };
 
 // Arguments of the outer (FP64) residual kernel.
@@ -148,6 +149,7 @@ struct ResidArgs {
   int adapt_max;           // > 0: choose the next outer iteration's V-cycles (<= adapt_max)
   int launches_per_vcycle; // adaptive: kernels of one V-cycle and its countdown
   int kchunk;              // planes per z chunk of the multi-block kernel (grid.z chunks)
+  int inner_fixed;         // fixed V-cycles per outer iteration (when adapt_max == 0)
 };
 
 // ---- launchers (kernels.cu / tdgl.cu) ------------------------------------------------
@@ -176,15 +178,33 @@ struct TailArgs {
   int nu1, nu2, bottom_sweeps, constant;
 };
 
+// Direct FP64 form (V-cycle on phi itself): the fused fine-level residual +
+// restriction + norm that takes the convergence decision
+struct CheckArgs {
+  double* partials;        // 2 per block of the check grid
+  DevStats* stats;
+  double tol;
+  int max_cycles;
+  int first;               // first check of a solve (sums ||b||^2)
+  int set_cond;
+  int launches_per_cycle;  // kernels of one loop iteration (one V-cycle)
+  unsigned long long cond_handle;
+  int first_launches;      // kernels before the first check (pre-smoothing + the check)
+  int pad;
+};
+
 template <typename T>
 void launch_smooth(const MGArgs<T>& a, const LevelDesc& L, int color, int zero_init,
-                   const UpdateArgs* upd, cudaStream_t s);
+                   const UpdateArgs* upd, cudaStream_t s, const DevStats* zero_stats = nullptr);
+dim3 check_grid(const LevelDesc& C);
+void launch_restrict_check(const MGArgs<double>& fa, double* rc, const LevelDesc& F,
+                           const LevelDesc& C, int nu1, const CheckArgs& ck, cudaStream_t s);
 template <typename T>
 void launch_restrict(const MGArgs<T>& a, const LevelDesc& F, const LevelDesc& C, int nu1,
                      cudaStream_t s);
 template <typename T>
 void launch_prolong(const MGArgs<T>& a, const LevelDesc& F, const LevelDesc& C, int constant,
-                    cudaStream_t s, bool tiled = false);
+                    cudaStream_t s, bool tiled = false, T* fine = nullptr);
 template <typename T>
 size_t tail_smem_bytes(long long elems, bool has_s);
 template <typename T>
@@ -328,6 +348,8 @@ cudaError_t batch_occupancy(int threads, size_t smem, int* blocks_per_sm);
 template <typename T>
 cudaError_t launch_batch(const BatchArgs& a, int blocks, int threads, size_t smem, cudaStream_t s);
 void launch_set_params(DevParams* p, double v_bot, double v_top, cudaStream_t s);
+void launch_static_b(double* b, const PlaneTDGL* planes, const DevParams* prm, int nx, int ny,
+                     int nz, cudaStream_t s);
 void launch_extrapolate(double* phi, double* prev, long long n, cudaStream_t s);
 void launch_stats_step(DevStats* st, int nsteps, int launches, cudaStream_t s);
 

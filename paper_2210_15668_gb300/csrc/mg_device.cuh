@@ -102,10 +102,16 @@ __host__ __device__ __forceinline__ int black_residual_zero(const LevelDesc& F, 
   return nu1 > 0 && (F.nx == 1 || !(F.nx & 1)) && (F.ny == 1 || !(F.ny & 1));
 }
 
-template <typename T>
-__device__ __forceinline__ void restrict_cell(const MGArgs<T>& a, const LevelDesc& F,
-                                              const LevelDesc& C, int I, int J, int K,
-                                              int skip_black = 0) {
+// Residual of the children of coarse cell (I, J, K) on level F (arrays of `fa`),
+// their mean written to the coarse right-hand side rc (and the mean Newton shift
+// to sc).  NORM also accumulates the squared residuals of the children it
+// computes into rr and, with want_b, the squared right-hand sides of all
+// children into bb (the direct FP64 form's stopping test).
+template <typename T, bool NORM = false>
+__device__ __forceinline__ void restrict_children(const MGArgs<T>& fa, T* rc, T* sc,
+                                                  const LevelDesc& F, const LevelDesc& C, int I,
+                                                  int J, int K, int skip_black, double& rr,
+                                                  double& bb, int want_b) {
   const int nxc = F.crx ? 2 : 1, nyc = F.cry ? 2 : 1, nzc = F.crz ? 2 : 1;
   const int i0 = F.crx ? 2 * I : I, j0 = F.cry ? 2 * J : J, k0 = F.crz ? 2 * K : K;
   T sum = T(0), ssum = T(0);
@@ -113,13 +119,29 @@ __device__ __forceinline__ void restrict_cell(const MGArgs<T>& a, const LevelDes
     for (int dj = 0; dj < nyc; ++dj)
       for (int di = 0; di < nxc; ++di) {
         const int i = i0 + di, j = j0 + dj, k = k0 + dk;
-        if (!(skip_black && ((i + j + k) & 1))) sum += cell_residual(a, F, i, j, k);
-        if (a.s) ssum += a.s[lidx(F, i, j, k)];
+        if (!(skip_black && ((i + j + k) & 1))) {
+          const T r = cell_residual(fa, F, i, j, k);
+          sum += r;
+          if (NORM) rr = fma((double)r, (double)r, rr);
+        }
+        if (NORM && want_b) {
+          const double b = fa.r[lidx(F, i, j, k)];
+          bb = fma(b, b, bb);
+        }
+        if (sc) ssum += fa.s[lidx(F, i, j, k)];
       }
   const T inv = T(1) / T(nxc * nyc * nzc);
   const int idc = lidx(C, I, J, K);
-  a.r[idc] = sum * inv;
-  if (a.s) a.s[idc] = ssum * inv;
+  rc[idc] = sum * inv;
+  if (sc) sc[idc] = ssum * inv;
+}
+
+template <typename T>
+__device__ __forceinline__ void restrict_cell(const MGArgs<T>& a, const LevelDesc& F,
+                                              const LevelDesc& C, int I, int J, int K,
+                                              int skip_black = 0) {
+  double rr = 0.0, bb = 0.0;
+  restrict_children<T, false>(a, a.r, a.s, F, C, I, J, K, skip_black, rr, bb, 0);
 }
 
 // Prolongation + correction for the children of coarse cell (I, J, K).
@@ -359,7 +381,8 @@ __device__ __forceinline__ void resid_column(const ResidArgs& a, int i, int j, i
 // Convergence decision of one solve from its summed norms (one thread).
 __device__ __forceinline__ int decide(DevStats* st, double sr, double sb, double sq, int first,
                                       double tol, int max_cycles, int launches_per_cycle,
-                                      int adapt_max = 0, int launches_per_vcycle = 0) {
+                                      int adapt_max = 0, int launches_per_vcycle = 0,
+                                      int inner_fixed = 1) {
   if (first) {
     st->solves += 1;
     st->cycles_this_solve = 0;
@@ -387,6 +410,7 @@ __device__ __forceinline__ int decide(DevStats* st, double sr, double sb, double
     st->cycles_this_solve += 1;
     st->cycles += 1;
     st->launches += launches_per_cycle;
+    if (adapt_max <= 0) st->vcycles += inner_fixed;
   }
   if (adapt_max > 0 && !first && st->inner_k > 0 && st->prev_rnorm > 0.0 && rn > 0.0) {
     // contraction per V-cycle over the outer iteration just finished, measured
@@ -403,6 +427,7 @@ __device__ __forceinline__ int decide(DevStats* st, double sr, double sb, double
     st->inner_left = k;
     st->prev_rnorm = rn;
     st->launches += k * launches_per_vcycle;
+    st->vcycles += k;
   }
   st->last_cond = cond;
   st->last_cycles = st->cycles_this_solve;

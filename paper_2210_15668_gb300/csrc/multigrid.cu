@@ -31,14 +31,22 @@ using namespace dev;
 
 // ---- multi-block kernels (3-D grids: x chunk, row chunk, plane) ----------------------
 
+// zst (direct FP64 form, sweeps on phi itself): when the solve found b = 0 with
+// no carrier charge (zero_phi), write the solution phi = 0 instead of relaxing
 template <typename T>
 __global__ void __launch_bounds__(256) smooth_kernel(MGArgs<T> a, LevelDesc L, int color,
-                                                     int zero_init, Upd u, const DevStats* st) {
+                                                     int zero_init, Upd u, const DevStats* st,
+                                                     const DevStats* zst) {
   pdl_enter();
   const int ip = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z;
   if (ip >= ((L.nx + 1) >> 1) || j >= L.ny) return;
+  if (zst && zst->zero_phi) {
+    const int i = 2 * ip + ((j + k + color) & 1);
+    if (i < L.nx) a.e[lidx(L, i, j, k)] = T(0);
+    return;
+  }
   if (u.phi) u.zero = st->zero_phi;
   smooth_pair(a, L, ip, j, k, color, zero_init, u);
 }
@@ -51,6 +59,57 @@ __global__ void __launch_bounds__(256) restrict_kernel(MGArgs<T> a, LevelDesc F,
   const int J = blockIdx.y * blockDim.y + threadIdx.y;
   if (I >= C.nx || J >= C.ny) return;
   restrict_cell(a, F, C, I, J, (int)blockIdx.z, skip_black);
+}
+
+// Direct FP64 form: the fine level's residual b - A phi after the pre-smoothing,
+// restricted to the first coarse level (8-child mean, red children only when the
+// black residuals vanish) and its squared norm summed on the way; the last block
+// sums the per-block partials in a fixed order, takes the convergence decision
+// (||r|| <= tol ||b||, ||b||^2 summed on the first check of a solve) and sets the
+// loop condition.  phi after the pre-smoothing is the iterate the test accepts.
+template <typename T>
+__global__ void __launch_bounds__(256) restrict_check_kernel(MGArgs<T> fa, T* rc, LevelDesc F,
+                                                             LevelDesc C, int skip_black,
+                                                             CheckArgs ck) {
+  pdl_enter();
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+  double rr = 0.0, bb = 0.0, zz = 0.0;
+  if (I < C.nx && J < C.ny)
+    restrict_children<T, true>(fa, rc, nullptr, F, C, I, J, (int)blockIdx.z, skip_black, rr, bb,
+                               ck.first);
+  if (ck.first)
+    block_sum3(rr, bb, zz);
+  else
+    block_sum1(rr);
+  __shared__ bool last;
+  const int nblk = gridDim.x * gridDim.y * gridDim.z;
+  const int bid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  if (tid == 0) {
+    ck.partials[bid] = rr;
+    ck.partials[nblk + bid] = ck.first ? bb : 0.0;
+    __threadfence();
+    const unsigned int prev = atomicAdd(&ck.stats->done_ctr, 1u);
+    last = (prev == (unsigned)nblk - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double sr = 0.0, sb = 0.0;
+  const volatile double* P = ck.partials;
+  for (int q = tid; q < nblk; q += blockDim.x * blockDim.y) {
+    sr += P[q];
+    sb += P[nblk + q];
+  }
+  block_sum3(sr, sb, zz);
+  if (tid == 0) {
+    ck.stats->done_ctr = 0;
+    const int cond = decide(ck.stats, sr, sb, 0.0, ck.first, ck.tol, ck.max_cycles,
+                            ck.launches_per_cycle);
+    if (ck.first) ck.stats->launches += ck.first_launches - 1;   // decide counted one
+    if (ck.set_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)ck.cond_handle, cond);
+  }
 }
 
 template <typename T>
@@ -76,7 +135,7 @@ constexpr int kPX = 32, kPY = 8, kPZ = 4;   // coarse columns (x, y) and planes 
 
 template <typename T>
 __global__ void __launch_bounds__(kPX* kPY) prolong_tiled_kernel(MGArgs<T> a, LevelDesc F,
-                                                                LevelDesc C) {
+                                                                LevelDesc C, T* fine) {
   pdl_enter();
   __shared__ T sE[kPY + 2][kPX + 2];     // coarse e of one plane: tile + periodic halo
   __shared__ T sY[2 * kPY][kPX + 2];     // interpolated in y: fine rows x coarse columns
@@ -86,6 +145,7 @@ __global__ void __launch_bounds__(kPX* kPY) prolong_tiled_kernel(MGArgs<T> a, Le
   const bool own = I < C.nx && J < C.ny;
   const int K0 = blockIdx.z * kPZ, K1 = min(C.nz, K0 + kPZ);
   T* e = a.e;
+  T* ef = fine ? fine : e + F.off;       // the level's corrections, or phi (direct form)
   auto plane_xy = [&](int K, T out[4]) {
     __syncthreads();                     // the previous plane's readers are done with sE, sY
     for (int q = tid; q < (kPY + 2) * (kPX + 2); q += kPX * kPY) {
@@ -127,7 +187,7 @@ __global__ void __launch_bounds__(kPX* kPY) prolong_tiled_kernel(MGArgs<T> a, Le
     if (own) {
 #pragma unroll
       for (int b = 0; b < 2; ++b) {
-        T* lo = e + F.off + ((long long)(2 * K) * F.ny + 2 * J + b) * F.nx + 2 * I;
+        T* lo = ef + ((long long)(2 * K) * F.ny + 2 * J + b) * F.nx + 2 * I;
         T* hi = lo + (long long)F.ny * F.nx;
         lo[0] += fma(T(0.75), xc[2 * b], T(0.25) * xm[2 * b]);
         lo[1] += fma(T(0.75), xc[2 * b + 1], T(0.25) * xm[2 * b + 1]);
@@ -190,7 +250,7 @@ __global__ void __launch_bounds__(kResidBX* kResidBY) resid_kernel(ResidArgs a) 
   if (tid == 0) {
     a.stats->done_ctr = 0;
     const int cond = decide(a.stats, sr, sb, sq, a.first, a.tol, a.max_cycles, a.launches_per_cycle,
-                            a.adapt_max, a.launches_per_vcycle);
+                            a.adapt_max, a.launches_per_vcycle, a.inner_fixed);
     if (a.set_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)a.cond_handle, cond);
   }
 }
@@ -234,13 +294,27 @@ void block_shape(int nxi, int ny, dim3& block, dim3& grid, int nz) {
 
 template <typename T>
 void launch_smooth(const MGArgs<T>& a, const LevelDesc& L, int color, int zero_init,
-                   const UpdateArgs* upd, cudaStream_t s) {
+                   const UpdateArgs* upd, cudaStream_t s, const DevStats* zero_stats) {
   dim3 block, grid;
   block_shape((L.nx + 1) >> 1, L.ny, block, grid, L.nz);
   Upd u{nullptr, 0.0, 0};
   const DevStats* st = nullptr;
   if (upd) { u.phi = upd->phi; u.clamp = upd->clamp; st = upd->stats; }
-  launch_k(smooth_kernel<T>, grid, block, 0, s, a, L, color, zero_init, u, st);
+  launch_k(smooth_kernel<T>, grid, block, 0, s, a, L, color, zero_init, u, st, zero_stats);
+}
+
+dim3 check_grid(const LevelDesc& C) {
+  dim3 block, grid;
+  block_shape(C.nx, C.ny, block, grid, C.nz);
+  return grid;
+}
+
+void launch_restrict_check(const MGArgs<double>& fa, double* rc, const LevelDesc& F,
+                           const LevelDesc& C, int nu1, const CheckArgs& ck, cudaStream_t s) {
+  dim3 block, grid;
+  block_shape(C.nx, C.ny, block, grid, C.nz);
+  launch_k(restrict_check_kernel<double>, grid, block, 0, s, fa, rc, F, C,
+           black_residual_zero(F, nu1), ck);
 }
 
 template <typename T>
@@ -253,10 +327,10 @@ void launch_restrict(const MGArgs<T>& a, const LevelDesc& F, const LevelDesc& C,
 
 template <typename T>
 void launch_prolong(const MGArgs<T>& a, const LevelDesc& F, const LevelDesc& C, int constant,
-                    cudaStream_t s, bool tiled) {
-  if (tiled && F.crx && F.cry && F.crz && !constant) {
+                    cudaStream_t s, bool tiled, T* fine) {
+  if (fine || (tiled && F.crx && F.cry && F.crz && !constant)) {
     const dim3 grid((C.nx + kPX - 1) / kPX, (C.ny + kPY - 1) / kPY, (C.nz + kPZ - 1) / kPZ);
-    launch_k(prolong_tiled_kernel<T>, grid, dim3(kPX, kPY), 0, s, a, F, C);
+    launch_k(prolong_tiled_kernel<T>, grid, dim3(kPX, kPY), 0, s, a, F, C, fine);
     return;
   }
   dim3 block, grid;
@@ -330,11 +404,11 @@ cudaError_t launch_carrier_exp(const double* u, double* ep, double* em, long lon
 
 #define FX_INST(T)                                                                              \
   template void launch_smooth<T>(const MGArgs<T>&, const LevelDesc&, int, int,                  \
-                                 const UpdateArgs*, cudaStream_t);                              \
+                                 const UpdateArgs*, cudaStream_t, const DevStats*);             \
   template void launch_restrict<T>(const MGArgs<T>&, const LevelDesc&, const LevelDesc&, int,   \
                                    cudaStream_t);                                               \
   template void launch_prolong<T>(const MGArgs<T>&, const LevelDesc&, const LevelDesc&, int,    \
-                                  cudaStream_t, bool);                                                \
+                                  cudaStream_t, bool, T*);                                      \
   template size_t tail_smem_bytes<T>(long long, bool);                                          \
   template cudaError_t tail_prepare<T>(size_t);                                                 \
   template void launch_tail<T>(const MGArgs<T>&, const TailArgs&, size_t, cudaStream_t);        \

@@ -140,6 +140,25 @@ __global__ void set_params_kernel(DevParams* p, double v_bot, double v_top) {
   p->v_top = v_top;
 }
 
+// The electrode lift of the boundary planes whose right-hand side no TDGL update
+// writes (b of the other static planes stays zero), so that b holds the whole
+// right-hand side for the direct FP64 form's sweeps on phi.
+__global__ void static_b_kernel(double* b, const PlaneTDGL* planes, const DevParams* prm, int nx,
+                                int ny, int nz) {
+  const long long plane = (long long)nx * ny;
+  const int side = blockIdx.y;               // 0: bottom plane, 1: top plane
+  const int k = side == 0 ? 0 : nz - 1;
+  if (side == 1 && nz == 1) return;          // one plane: written once, both lifts
+  const PlaneTDGL& pt = planes[k];
+  if (pt.b_dyn) return;
+  double v = 0.0;
+  if (k == 0) v += pt.lift * prm->v_bot;
+  if (k == nz - 1) v += pt.lift * prm->v_top;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < plane;
+       t += (long long)gridDim.x * blockDim.x)
+    b[k * plane + t] = v;
+}
+
 __global__ void stats_step_kernel(DevStats* st, int n, int launches) {
   pdl_enter();
   st->steps += n;
@@ -172,6 +191,13 @@ void launch_extrapolate(double* phi, double* prev, long long n, cudaStream_t s) 
 
 void launch_set_params(DevParams* p, double v_bot, double v_top, cudaStream_t s) {
   set_params_kernel<<<1, 1, 0, s>>>(p, v_bot, v_top);
+}
+
+void launch_static_b(double* b, const PlaneTDGL* planes, const DevParams* prm, int nx, int ny,
+                     int nz, cudaStream_t s) {
+  long long blocks = ((long long)nx * ny + 255) / 256;
+  if (blocks > 152) blocks = 152;
+  static_b_kernel<<<dim3((int)blocks, 2), 256, 0, s>>>(b, planes, prm, nx, ny, nz);
 }
 
 void launch_stats_step(DevStats* st, int nsteps, int launches, cudaStream_t s) {

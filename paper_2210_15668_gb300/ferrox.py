@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libferrox.so")
 
 FERROX_OK, FERROX_EINVAL, FERROX_ENOMEM, FERROX_ECUDA = 0, 1, 2, 3
 FERROX_ENOCONV, FERROX_ENONFINITE, FERROX_ETIMEOUT, FERROX_ESTATE = 4, 5, 6, 7
-FP64, MIXED = 0, 1
+FP64, MIXED, FP64_DEFECT = 0, 1, 2
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "ENONFINITE",
                 6: "ETIMEOUT", 7: "ESTATE"}
 
@@ -50,7 +50,8 @@ class Charge(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("steps", C.c_longlong), ("launches", C.c_longlong), ("solves", C.c_longlong),
                 ("cycles", C.c_longlong),
-                ("last_cycles", C.c_int), ("last_rel_res", C.c_double), ("status", C.c_int)]
+                ("last_cycles", C.c_int), ("last_rel_res", C.c_double), ("status", C.c_int),
+                ("vcycles", C.c_longlong)]
 
 
 EXPORTS = ["ferrox_init_geometry", "ferrox_set_bias", "ferrox_solve_poisson", "ferrox_tdgl_update",

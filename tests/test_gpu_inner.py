@@ -34,6 +34,8 @@ def test_inner_cycles_mfim(precision):
     b = run(geom, P0, precision, 2, 10, 0.8)
     assert a[2]["status"] == 0 and b[2]["status"] == 0
     assert b[2]["cycles"] < a[2]["cycles"]            # fewer outer iterations
+    assert a[2]["vcycles"] == a[2]["cycles"]
+    assert b[2]["vcycles"] == 2 * b[2]["cycles"]
     assert np.linalg.norm(b[1] - a[1]) <= 1e-9 * np.linalg.norm(a[1])
     assert np.linalg.norm(b[0] - a[0]) <= 1e-9 * np.linalg.norm(a[0])
 
@@ -65,6 +67,7 @@ def test_adaptive_inner_cycles_mfim(precision):
     b = run(geom, P0, precision, -8, 10, 0.8)
     assert a[2]["status"] == 0 and b[2]["status"] == 0
     assert b[2]["cycles"] < a[2]["cycles"]            # fewer FP64 residuals
+    assert b[2]["cycles"] <= b[2]["vcycles"] <= 8 * b[2]["cycles"]
     assert np.linalg.norm(b[1] - a[1]) <= 1e-9 * np.linalg.norm(a[1])
     assert np.linalg.norm(b[0] - a[0]) <= 1e-9 * np.linalg.norm(a[0])
 
