@@ -62,6 +62,8 @@ struct ferrox_ctx {
   int resid_blocks = 0;
   int resid_kchunk = 0;   // planes per z chunk of the residual kernel
   bool direct = false;    // FP64 V-cycles on phi itself (see direct_form)
+  int dense_lev = -1;     // tail level solved by its inverse (-1: none)
+  void* dense_d = nullptr;
   int check_blocks = 0;   // blocks of the direct form's fused residual + restriction + norm
   // device memory
   cudaStream_t stream = nullptr;
@@ -186,6 +188,67 @@ void plan_tail(ferrox_ctx* c, size_t elem_size) {
     // one cell: a single update is the exact solve (more sweeps repeat it)
     c->num.bottom_sweeps = B.ncell == 1 ? 1 : std::min(64, 2 * (B.nx + B.ny + B.nz));
   }
+}
+
+// The first tail level of at most kDenseMax cells (and more than one) is solved
+// exactly by its inverse in stacks without carriers (no Newton shift on the
+// diagonal, so the operator is fixed for the context's lifetime).
+int dense_level(const ferrox_ctx* c) {
+  if (c->has_sc) return -1;
+  for (size_t l = 0; l < c->lv_tail.size(); ++l)
+    if (c->lv_tail[l].ncell <= kDenseMax) return c->lv_tail[l].ncell > 1 ? (int)l : -1;
+  return -1;
+}
+
+// Inverse of the level operator (diag - couplings, periodic in x and y, the
+// electrode couplings on the diagonal) as the smoother sees it, from the
+// precision-T coefficients; Gauss-Jordan elimination with partial pivoting in
+// FP64, rounded to T.
+template <typename T>
+std::vector<T> dense_inverse(const std::vector<PlaneCoef<T>>& coef, const LevelDesc& L) {
+  const int n = (int)L.ncell;
+  std::vector<double> A((size_t)n * n, 0.0), X((size_t)n * n, 0.0);
+  auto id = [&](int i, int j, int k) { return (k * L.ny + j) * L.nx + i; };
+  for (int k = 0; k < L.nz; ++k)
+    for (int j = 0; j < L.ny; ++j)
+      for (int i = 0; i < L.nx; ++i) {
+        const PlaneCoef<T>& p = coef[L.coef_off + k];
+        double* row = &A[(size_t)id(i, j, k) * n];
+        row[id(i, j, k)] += (double)p.diag;
+        if (L.nx > 1) {
+          row[id((i + L.nx - 1) % L.nx, j, k)] -= (double)p.cx;
+          row[id((i + 1) % L.nx, j, k)] -= (double)p.cx;
+        }
+        if (L.ny > 1) {
+          row[id(i, (j + L.ny - 1) % L.ny, k)] -= (double)p.cy;
+          row[id(i, (j + 1) % L.ny, k)] -= (double)p.cy;
+        }
+        if (k > 0) row[id(i, j, k - 1)] -= (double)p.czlo;
+        if (k < L.nz - 1) row[id(i, j, k + 1)] -= (double)p.czhi;
+      }
+  for (int q = 0; q < n; ++q) X[(size_t)q * n + q] = 1.0;
+  for (int col = 0; col < n; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < n; ++r)
+      if (std::fabs(A[(size_t)r * n + col]) > std::fabs(A[(size_t)piv * n + col])) piv = r;
+    if (piv != col)
+      for (int q = 0; q < n; ++q) {
+        std::swap(A[(size_t)piv * n + q], A[(size_t)col * n + q]);
+        std::swap(X[(size_t)piv * n + q], X[(size_t)col * n + q]);
+      }
+    const double d = A[(size_t)col * n + col];
+    for (int q = 0; q < n; ++q) { A[(size_t)col * n + q] /= d; X[(size_t)col * n + q] /= d; }
+    for (int r = 0; r < n; ++r) {
+      if (r == col) continue;
+      const double f = A[(size_t)r * n + col];
+      if (f == 0.0) continue;
+      for (int q = 0; q < n; ++q) {
+        A[(size_t)r * n + q] -= f * A[(size_t)col * n + q];
+        X[(size_t)r * n + q] -= f * X[(size_t)col * n + q];
+      }
+    }
+  }
+  return std::vector<T>(X.begin(), X.end());
 }
 
 template <typename T>
@@ -348,7 +411,7 @@ void enqueue_levels(ferrox_ctx* c, cudaStream_t s, W wrap, int l0, bool first, b
     wrap(FERROX_K_RESTRICT, [&] { launch_restrict<T>(a, c->lv[l], c->lv[l + 1], nu1, s); });
   }
   TailArgs ta{c->lvt_d, L - lt + 1, c->tail_elems, c->lv[lt].off, nu1, nu2, c->num.bottom_sweeps,
-              constant};
+              constant, c->dense_d, c->dense_lev, 0};
   wrap(FERROX_K_TAIL, [&] { launch_tail<T>(a, ta, c->tail_smem, s); });
   const UpdateArgs upd{c->phi, c->stats_d, update_clamp(c)};
   for (int l = lt - 1; l >= l0; --l) {
@@ -820,7 +883,7 @@ void release(ferrox_ctx* c) {
   for (auto g : gr) if (g) cudaGraphDestroy(g);
   void* ptrs[] = {c->b, c->Pbuf, c->Fbuf, c->phi_prev, c->e_arena, c->r_arena, c->s_arena, c->coef, c->coef0,
                   c->planes_d, c->lv_d, c->lvt_d, c->nn_scale, c->phi_guess, c->nn_pf, c->nn_stats, c->params_d, c->stats_d, c->partials_d, c->charge_d,
-                  c->charge_part_d};
+                  c->charge_part_d, c->dense_d};
   for (void* p : ptrs) if (p) cudaFree(p);
   if (c->host_pinned) cudaFreeHost(c->host_pinned);
   if (c->cap1) cudaStreamDestroy(c->cap1);
@@ -956,15 +1019,28 @@ ferrox_status ferrox_init_geometry(ferrox_ctx** out, const ferrox_geometry* geom
   FX_INIT_CK(cudaMalloc(&ctx->coef0, ctx->nz * sizeof(PlaneCoef<double>)));
   FX_INIT_CK(cudaMemcpy(ctx->coef0, c64.data(), ctx->nz * sizeof(PlaneCoef<double>),
                         cudaMemcpyHostToDevice));
+  ctx->dense_lev = dense_level(ctx);
   if (mixed) {
     auto c32 = level_coefficients<float>(ctx);
     FX_INIT_CK(cudaMalloc(&ctx->coef, c32.size() * sizeof(PlaneCoef<float>)));
     FX_INIT_CK(cudaMemcpy(ctx->coef, c32.data(), c32.size() * sizeof(PlaneCoef<float>),
                           cudaMemcpyHostToDevice));
+    if (ctx->dense_lev >= 0) {
+      const auto inv = dense_inverse<float>(c32, ctx->lv_tail[ctx->dense_lev]);
+      FX_INIT_CK(cudaMalloc(&ctx->dense_d, inv.size() * sizeof(float)));
+      FX_INIT_CK(cudaMemcpy(ctx->dense_d, inv.data(), inv.size() * sizeof(float),
+                            cudaMemcpyHostToDevice));
+    }
   } else {
     FX_INIT_CK(cudaMalloc(&ctx->coef, c64.size() * sizeof(PlaneCoef<double>)));
     FX_INIT_CK(cudaMemcpy(ctx->coef, c64.data(), c64.size() * sizeof(PlaneCoef<double>),
                           cudaMemcpyHostToDevice));
+    if (ctx->dense_lev >= 0) {
+      const auto inv = dense_inverse<double>(c64, ctx->lv_tail[ctx->dense_lev]);
+      FX_INIT_CK(cudaMalloc(&ctx->dense_d, inv.size() * sizeof(double)));
+      FX_INIT_CK(cudaMemcpy(ctx->dense_d, inv.data(), inv.size() * sizeof(double),
+                            cudaMemcpyHostToDevice));
+    }
   }
   FX_INIT_CK(cudaMemcpy(ctx->planes_d, ctx->planes.data(), ctx->nz * sizeof(PlaneTDGL),
                         cudaMemcpyHostToDevice));

@@ -49,6 +49,7 @@ constexpr int kMaxLevels = 24;
 constexpr int kTailMaxCells = 4096;     // levels at or below this size run in one CTA (FP32)
 constexpr int kTailMaxCellsFP64 = 512;  // the same for FP64 corrections
 constexpr int kTailThreads = 1024;
+constexpr int kDenseMax = 64;           // a tail level of at most this many cells is solved by its inverse
 constexpr int kTailMaxSmem = 200 * 1024; // shared memory available to the tail CTA
 constexpr int kResidBX = 32, kResidBY = 8; // residual: one thread per (x, y) column
 
@@ -176,6 +177,9 @@ struct TailArgs {
   long long elems;      // elements per tail array in shared memory
   long long base;       // arena offset of the first tail level
   int nu1, nu2, bottom_sweeps, constant;
+  const void* dense;    // T[n * n]: inverse of the operator of tail level dense_lev (null: none)
+  int dense_lev;
+  int pad;
 };
 
 // Direct FP64 form (V-cycle on phi itself): the fused fine-level residual +

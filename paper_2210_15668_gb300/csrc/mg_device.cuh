@@ -205,6 +205,42 @@ __device__ __forceinline__ void prolong_cell(const MGArgs<T>& a, const LevelDesc
   }
 }
 
+// Prolongation + correction of one fine cell (i, j, k) of F: the separable
+// trilinear interpolation of prolong_cell (z, then y, then x, the same
+// operations in the same order), evaluated per fine cell, so that a tiny level
+// spreads its arithmetic over one thread per fine cell.
+template <typename T>
+__device__ __forceinline__ void prolong_fine(const MGArgs<T>& a, const LevelDesc& F,
+                                             const LevelDesc& C, int i, int j, int k,
+                                             int constant) {
+  T* e = a.e;
+  const int I = F.crx ? i >> 1 : i, J = F.cry ? j >> 1 : j, K = F.crz ? k >> 1 : k;
+  if (constant) {
+    e[lidx(F, i, j, k)] += e[lidx(C, I, J, K)];
+    return;
+  }
+  // the coarse neighbour on the child's side in each coarsened direction
+  const int I2 = !F.crx ? I : (i & 1) ? (I + 1 == C.nx ? 0 : I + 1) : (I == 0 ? C.nx - 1 : I - 1);
+  const int J2 = !F.cry ? J : (j & 1) ? (J + 1 == C.ny ? 0 : J + 1) : (J == 0 ? C.ny - 1 : J - 1);
+  const int K2 = (k & 1) ? K + 1 : K - 1;   // outside [0, C.nz): electrode ghost (-e)
+  auto zcol = [&](int x, int y) -> T {
+    const T c0 = e[lidx(C, x, y, K)];
+    if (!F.crz) return c0;
+    return (K2 >= 0 && K2 < C.nz) ? fma(T(0.75), c0, T(0.25) * e[lidx(C, x, y, K2)])
+                                  : T(0.5) * c0;
+  };
+  const T z11 = zcol(I, J);
+  T y1 = z11, y2 = T(0);
+  if (F.cry) y1 = fma(T(0.75), z11, T(0.25) * zcol(I, J2));
+  if (F.crx) {
+    const T z21 = zcol(I2, J);
+    y2 = F.cry ? fma(T(0.75), z21, T(0.25) * zcol(I2, J2)) : z21;
+    e[lidx(F, i, j, k)] += fma(T(0.75), y1, T(0.25) * y2);
+  } else {
+    e[lidx(F, i, j, k)] += y1;
+  }
+}
+
 // ---- single-CTA tail: the smallest levels in shared memory ---------------------------
 
 // Division by a level constant d without the integer divide sequence: with
@@ -239,8 +275,28 @@ __device__ void tail_smooth(const MGArgs<T>& a, const LevelDesc& L, int sweeps, 
     }
 }
 
+// e = A^-1 r on a level of n <= kDenseMax cells: the inverse (row-major, computed
+// on the host in FP64) times r, four lanes per row and a fixed-order reduction.
+template <typename T>
+__device__ void tail_dense(const T* __restrict__ inv, int n, const T* r, T* e) {
+  const int tid = threadIdx.x;
+  if ((tid >> 5) < ((4 * n + 31) >> 5)) {   // whole warps, for the shuffles
+    const int row = tid >> 2, p = tid & 3;
+    T acc = T(0);
+    if (row < n)
+      for (int c = p; c < n; c += 4) acc = fma(__ldg(inv + row * n + c), r[c], acc);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    if (row < n && p == 0) e[row] = acc;
+  }
+  __syncthreads();
+}
+
 // A complete V-cycle over the tail levels of one instance, by one CTA, with the
 // level arrays in shared memory (smem holds 2 or 3 arrays of t.elems values).
+// With t.dense the level t.dense_lev is solved exactly by its inverse and the
+// levels below it are not visited; otherwise the coarsest level is relaxed
+// t.bottom_sweeps times.
 template <typename T>
 __device__ void tail_vcycle(const MGArgs<T>& g, const TailArgs& t, unsigned char* tail_smem) {
   T* se = reinterpret_cast<T*>(tail_smem);
@@ -255,7 +311,8 @@ __device__ void tail_vcycle(const MGArgs<T>& g, const TailArgs& t, unsigned char
   __syncthreads();
   MGArgs<T> a;
   a.e = se; a.r = sr; a.s = ss; a.coef = g.coef; a.lv = lv;
-  for (int l = 0; l + 1 < t.nlev; ++l) {
+  const int bottom = t.dense ? t.dense_lev : t.nlev - 1;
+  for (int l = 0; l < bottom; ++l) {
     const LevelDesc F = ldg_struct(lv + l), C = ldg_struct(lv + l + 1);
     tail_smooth(a, F, t.nu1, 1);
     const int nc = (int)C.ncell;
@@ -267,14 +324,19 @@ __device__ void tail_vcycle(const MGArgs<T>& g, const TailArgs& t, unsigned char
     }
     __syncthreads();
   }
-  tail_smooth(a, lv[t.nlev - 1], t.bottom_sweeps, 1);
-  for (int l = t.nlev - 2; l >= 0; --l) {
+  if (t.dense) {
+    const LevelDesc B = ldg_struct(lv + bottom);
+    tail_dense(static_cast<const T*>(t.dense), (int)B.ncell, sr + B.off, se + B.off);
+  } else {
+    tail_smooth(a, lv[bottom], t.bottom_sweeps, 1);
+  }
+  for (int l = bottom - 1; l >= 0; --l) {
     const LevelDesc F = ldg_struct(lv + l), C = ldg_struct(lv + l + 1);
-    const int nc = (int)C.ncell;
-    const unsigned long long mx = magic32(C.nx), my = magic32(C.ny);
-    for (int q = threadIdx.x; q < nc; q += blockDim.x) {
-      const int rest = div32(q, mx), K = div32(rest, my);
-      prolong_cell(a, F, C, q - rest * C.nx, rest - K * C.ny, K, t.constant);
+    const int nf = (int)F.ncell;
+    const unsigned long long mx = magic32(F.nx), my = magic32(F.ny);
+    for (int q = threadIdx.x; q < nf; q += blockDim.x) {
+      const int rest = div32(q, mx), k = div32(rest, my);
+      prolong_fine(a, F, C, q - rest * F.nx, rest - k * F.ny, k, t.constant);
     }
     __syncthreads();
     tail_smooth(a, F, t.nu2, 0);

@@ -280,11 +280,20 @@ __global__ void inner_countdown_kernel(DevStats* st, unsigned long long handle) 
   cudaGraphSetConditional((cudaGraphConditionalHandle)handle, left > 0 ? 1 : 0);
 }
 
+// threads per block: 256, halved to 128 when the grid would hold fewer than two
+// blocks per SM, so small levels spread over more SMs (their FP64 arithmetic,
+// at 2 DFMA per clock per SM, bounds them)
+int spread_threads(long long items) {
+  int t = 256;
+  while (t > 128 && items < 2LL * 152 * t) t >>= 1;
+  return t;
+}
+
 // 2-D block over (x items, rows): x extent a power of two up to 128
-void block_shape(int nxi, int ny, dim3& block, dim3& grid, int nz) {
+void block_shape(int nxi, int ny, dim3& block, dim3& grid, int nz, int threads = 256) {
   int bx = 1;
-  while (bx < nxi && bx < 128) bx <<= 1;
-  int by = 256 / bx;
+  while (bx < nxi && bx < 128 && bx < threads) bx <<= 1;
+  int by = threads / bx;
   if (by > ny) { by = 1; while (by < ny) by <<= 1; }
   block = dim3(bx, by, 1);
   grid = dim3((nxi + bx - 1) / bx, (ny + by - 1) / by, nz);
@@ -296,7 +305,8 @@ template <typename T>
 void launch_smooth(const MGArgs<T>& a, const LevelDesc& L, int color, int zero_init,
                    const UpdateArgs* upd, cudaStream_t s, const DevStats* zero_stats) {
   dim3 block, grid;
-  block_shape((L.nx + 1) >> 1, L.ny, block, grid, L.nz);
+  block_shape((L.nx + 1) >> 1, L.ny, block, grid, L.nz,
+              spread_threads((long long)((L.nx + 1) >> 1) * L.ny * L.nz));
   Upd u{nullptr, 0.0, 0};
   const DevStats* st = nullptr;
   if (upd) { u.phi = upd->phi; u.clamp = upd->clamp; st = upd->stats; }
@@ -321,7 +331,7 @@ template <typename T>
 void launch_restrict(const MGArgs<T>& a, const LevelDesc& F, const LevelDesc& C, int nu1,
                      cudaStream_t s) {
   dim3 block, grid;
-  block_shape(C.nx, C.ny, block, grid, C.nz);
+  block_shape(C.nx, C.ny, block, grid, C.nz, spread_threads(C.ncell));
   launch_k(restrict_kernel<T>, grid, block, 0, s, a, F, C, black_residual_zero(F, nu1));
 }
 
@@ -334,7 +344,7 @@ void launch_prolong(const MGArgs<T>& a, const LevelDesc& F, const LevelDesc& C, 
     return;
   }
   dim3 block, grid;
-  block_shape(C.nx, C.ny, block, grid, C.nz);
+  block_shape(C.nx, C.ny, block, grid, C.nz, spread_threads(C.ncell));
   launch_k(prolong_kernel<T>, grid, block, 0, s, a, F, C, constant);
 }
 
