@@ -421,6 +421,7 @@ def run_learned(args, ws, cfg, geom, P0, cells, sweep, timed_run):
            "value": ws * cells * K / (t / 1e3) / 1e6, "ms_per_step": t / K,
            "vcycles_per_step": (s1["vcycles"] - s0["vcycles"]) / K,
            "outer_iterations_per_step": (s1["cycles"] - s0["cycles"]) / K,
+           "corrections_rejected": s1["nn_rejected"] - s0["nn_rejected"],
            "snapshots": args.nn_snapshots, "epochs": args.nn_epochs,
            "train_loss_first_last": [float(losses[0]), float(losses[-1])],
            "collect_and_train_s": prep, "params": 79.5e3}

@@ -140,6 +140,7 @@ typedef struct {
   int status;              /* sticky device status (ferrox_status) */
   long long vcycles;       /* V-cycles run, all solves, inner cycles included (= cycles when
                               numerics.inner is 0 or 1) */
+  long long nn_rejected;   /* learned corrections rejected because they did not lower ||r|| */
 } ferrox_stats;
 
 /* Create a context (a1: per-plane material tables, multigrid hierarchy, CUDA
@@ -280,8 +281,12 @@ const char* ferrox_batch_last_error(const ferrox_batch* b);
  * maps the restricted initial residual of each solve (scaled by its rms) and
  * per-plane material, height and bias features to the restricted error of the
  * initial guess; the prediction is prolongated and added to the guess before
- * the multigrid cycles.  Multigrid still runs to the residual test, so the
- * network can change the number of cycles, never the converged answer.
+ * the multigrid cycles.  The corrected guess is kept only if its residual norm
+ * is below the guess's (or already meets the test); otherwise the solve
+ * restarts from the saved guess (stats.nn_rejected counts these).  Multigrid
+ * still runs to the residual test, so the network can change the number of
+ * cycles, never the converged answer.  Learned steps run the defect-correction
+ * form of the solve.
  * Training data are snapshots the solver records in collect mode.
  * Weights: per layer [27][Cin][Cout] FP32 (tap = 9 dz + 3 dy + dx), layers
  * (16,16) (16,16) (16,32) (32,32) (48,16) (16,16); biases [Cout]. */

@@ -534,8 +534,11 @@ int tdgl_launches(const ferrox_ctx* c) { return c->ncomp == 3 ? 2 : 1; }
 
 template <typename T>
 void enqueue_resid(ferrox_ctx* c, cudaStream_t s, int first, int set_cond,
-                   unsigned long long handle) {
+                   unsigned long long handle, const double* reject_ref = nullptr,
+                   unsigned long long reject_handle = 0) {
   ResidArgs a{};
+  a.reject_ref = reject_ref;
+  a.reject_handle = reject_handle;
   a.phi = c->phi; a.b = c->b; a.planes = c->planes_d; a.coef0 = c->coef0; a.params = c->params_d;
   a.nx = c->nx; a.ny = c->ny; a.nz = c->nz;
   a.r_out = c->r_arena;
@@ -590,9 +593,11 @@ cudaError_t enqueue_copy_back(ferrox_ctx* c, cudaStream_t s) {
   return cudaSuccess;
 }
 
-// resid (sets the condition) -> WHILE { V-cycle; update; resid } on the capturing stream s
+// resid (sets the condition) -> WHILE { V-cycle; update; resid } on the capturing stream s.
+// guard: phi holds a learned correction of the guess saved in phi_guess; the first
+// residual rejects it unless it lowered ||r||, and then IF { phi = guess; resid } runs.
 template <typename T>
-ferrox_status capture_solve(ferrox_ctx* ctx, cudaStream_t s) {
+ferrox_status capture_solve(ferrox_ctx* ctx, cudaStream_t s, bool guard = false) {
   cudaStreamCaptureStatus st;
   cudaGraph_t g;
   const cudaGraphNode_t* deps = nullptr;
@@ -600,10 +605,34 @@ ferrox_status capture_solve(ferrox_ctx* ctx, cudaStream_t s) {
   FX_CK(cudaStreamGetCaptureInfo(s, &st, nullptr, &g, nullptr, nullptr, nullptr));
   cudaGraphConditionalHandle h;
   FX_CK(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
-  if (ctx->direct)
+  if (guard) {
+    cudaGraphConditionalHandle hr;
+    FX_CK(cudaGraphConditionalHandleCreate(&hr, g, 0, cudaGraphCondAssignDefault));
+    enqueue_resid<T>(ctx, s, 1, 1, (unsigned long long)h, ctx->nn_scale + 1,
+                     (unsigned long long)hr);
+    FX_CK(cudaGetLastError());
+    FX_CK(cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, nullptr, &nd));
+    cudaGraphNodeParams ip = {cudaGraphNodeTypeConditional};
+    ip.conditional.handle = hr;
+    ip.conditional.type = cudaGraphCondTypeIf;
+    ip.conditional.size = 1;
+    cudaGraphNode_t ifn;
+    FX_CK(cudaGraphAddNode(&ifn, g, deps, nullptr, nd, &ip));
+    FX_CK(cudaStreamBeginCaptureToGraph(ctx->cap2, ip.conditional.phGraph_out[0], nullptr, nullptr,
+                                        0, cudaStreamCaptureModeRelaxed));
+    FX_CK(cudaMemcpyAsync(ctx->phi, ctx->phi_guess,
+                          (size_t)ctx->nx * ctx->ny * ctx->nz * sizeof(double),
+                          cudaMemcpyDeviceToDevice, ctx->cap2));
+    enqueue_resid<T>(ctx, ctx->cap2, 1, 1, (unsigned long long)h);
+    FX_CK(cudaGetLastError());
+    cudaGraph_t if_out;
+    FX_CK(cudaStreamEndCapture(ctx->cap2, &if_out));
+    FX_CK(cudaStreamUpdateCaptureDependencies(s, &ifn, nullptr, 1, cudaStreamSetCaptureDependencies));
+  } else if (ctx->direct) {
     enqueue_direct_prologue(ctx, s, NoWrap(), 1, (unsigned long long)h);
-  else
+  } else {
     enqueue_resid<T>(ctx, s, 1, 1, (unsigned long long)h);
+  }
   FX_CK(cudaGetLastError());
   FX_CK(cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, nullptr, &nd));
   cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
@@ -708,7 +737,8 @@ void enqueue_nn_features(ferrox_ctx* c, cudaStream_t s, __nv_bfloat16* x) {
   a.r_out = c->r_arena;
   a.s_out = c->has_sc ? c->s_arena : nullptr;
   a.stats = c->stats_d;
-  a.no_stats = 1;
+  a.partials = c->partials_d;
+  a.norm_out = c->nn_scale + 1;   // ||r|| of the guess, for the check of the correction
   a.kchunk = c->resid_kchunk;
   launch_resid<T>(a, s);
   T* r = static_cast<T*>(c->r_arena);
@@ -720,6 +750,8 @@ void enqueue_nn_features(ferrox_ctx* c, cudaStream_t s, __nv_bfloat16* x) {
 // network prediction of the coarse error, prolongated and added to phi
 template <typename T>
 void enqueue_nn_prelude(ferrox_ctx* c, cudaStream_t s) {
+  cudaMemcpyAsync(c->phi_guess, c->phi, (size_t)c->nx * c->ny * c->nz * sizeof(double),
+                  cudaMemcpyDeviceToDevice, s);
   enqueue_nn_features<T>(c, s, nn_input(c->nn));
   nn_run_forward(c->nn, s);
   const size_t tsz = sizeof(T);
@@ -734,27 +766,39 @@ void enqueue_nn_prelude(ferrox_ctx* c, cudaStream_t s) {
 }
 
 template <typename T>
-ferrox_status build_nn_graph_t(ferrox_ctx* ctx) {
-  cudaStream_t s = ctx->cap1;
+ferrox_status capture_nn_step(ferrox_ctx* ctx, cudaStream_t s) {
   ferrox_status rc;
   const long long N = (long long)ctx->nx * ctx->ny * ctx->nz;
-  FX_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
   if (ctx->num.order == 1) {
     launch_tdgl(tdgl_args(ctx, 0), s);
     FX_CK(enqueue_copy_back(ctx, s));
     if (ctx->num.guess == 1) launch_extrapolate(ctx->phi, ctx->phi_prev, N, s);
     enqueue_nn_prelude<T>(ctx, s);
-    if ((rc = capture_solve<T>(ctx, s)) != FERROX_OK) return rc;
+    if ((rc = capture_solve<T>(ctx, s, true)) != FERROX_OK) return rc;
   } else {
     launch_tdgl(tdgl_args(ctx, 1), s);
     if (ctx->num.guess == 1) launch_extrapolate(ctx->phi, ctx->phi_prev, N, s);
     enqueue_nn_prelude<T>(ctx, s);
-    if ((rc = capture_solve<T>(ctx, s)) != FERROX_OK) return rc;
+    if ((rc = capture_solve<T>(ctx, s, true)) != FERROX_OK) return rc;
     launch_tdgl(tdgl_args(ctx, 2), s);
     if ((rc = capture_solve<T>(ctx, s)) != FERROX_OK) return rc;
   }
   launch_stats_step(ctx->stats_d, 1, 0, s);
   FX_CK(cudaGetLastError());
+  return FERROX_OK;
+}
+
+// The learned step runs the defect-correction form (its first residual is the
+// check of the correction), also where plain FP64 solves use the direct form.
+template <typename T>
+ferrox_status build_nn_graph_t(ferrox_ctx* ctx) {
+  cudaStream_t s = ctx->cap1;
+  FX_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+  const bool direct = ctx->direct;
+  ctx->direct = false;
+  const ferrox_status rc = capture_nn_step<T>(ctx, s);
+  ctx->direct = direct;
+  if (rc != FERROX_OK) return rc;
   FX_CK(cudaStreamEndCapture(s, &ctx->gr_step_nn));
   FX_CK(cudaGraphInstantiate(&ctx->ge_step_nn, ctx->gr_step_nn, 0));
   return FERROX_OK;
@@ -1141,7 +1185,7 @@ ferrox_status ferrox_attach_nn(ferrox_ctx* ctx, ferrox_nn* nn, int mode) {
     return fail(ctx, FERROX_EINVAL, "network grid does not match the network level of this context");
   if (mode == 1 && nn_capacity(nn) < 1) return fail(ctx, FERROX_EINVAL, "network has no snapshot store");
   if (!ctx->nn_scale) {
-    FX_CK(cudaMalloc(&ctx->nn_scale, sizeof(double)));
+    FX_CK(cudaMalloc(&ctx->nn_scale, 2 * sizeof(double)));   // rms of r, ||r|| of the guess
     FX_CK(cudaMalloc(&ctx->phi_guess, (size_t)ctx->nx * ctx->ny * ctx->nz * sizeof(double)));
     FX_CK(cudaMalloc(&ctx->nn_stats, sizeof(DevStats)));
     FX_CK(cudaMemset(ctx->nn_stats, 0, sizeof(DevStats)));
@@ -1192,6 +1236,7 @@ ferrox_status ferrox_sync_stats(ferrox_ctx* ctx, ferrox_stats* out) {
   out->solves = st.solves;
   out->cycles = st.cycles;
   out->vcycles = st.vcycles;
+  out->nn_rejected = st.nn_rejected;
   out->last_cycles = st.last_cycles;
   out->last_rel_res = st.last_rel;
   out->status = st.status;
@@ -1765,6 +1810,7 @@ ferrox_status ferrox_batch_stats(ferrox_batch* B, ferrox_stats* out) {
     out[i].solves = st[i].solves;
     out[i].cycles = st[i].cycles;
     out[i].vcycles = st[i].vcycles;
+    out[i].nn_rejected = 0;
     out[i].last_cycles = st[i].last_cycles;
     out[i].last_rel_res = st[i].last_rel;
     out[i].status = gst ? gst : st[i].status;

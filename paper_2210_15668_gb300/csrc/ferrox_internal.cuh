@@ -125,6 +125,7 @@ struct DevStats {
   double rho_v;           //   estimated contraction per V-cycle (0: none yet), kept across solves
   double prev_rnorm;      //   ||r|| at the previous outer iteration of this solve
   long long vcycles;      // V-cycles run, all solves (inner cycles included)
+  long long nn_rejected;  // learned corrections rejected (they did not lower ||r||)
 };
 
 // Arguments of the outer (FP64) residual kernel.
@@ -151,6 +152,10 @@ struct ResidArgs {
   int launches_per_vcycle; // adaptive: kernels of one V-cycle and its countdown
   int kchunk;              // planes per z chunk of the multi-block kernel (grid.z chunks)
   int inner_fixed;         // fixed V-cycles per outer iteration (when adapt_max == 0)
+  double* norm_out;        // store ||r|| here instead of taking a decision
+  const double* reject_ref;          // ||r|| of the guess before a learned correction: the
+  unsigned long long reject_handle;  // first residual sets this IF condition to 1 when
+                                     // the corrected guess is no better (reject it)
 };
 
 // ---- launchers (kernels.cu / tdgl.cu) ------------------------------------------------

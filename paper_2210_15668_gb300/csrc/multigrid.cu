@@ -51,6 +51,59 @@ __global__ void __launch_bounds__(256) smooth_kernel(MGArgs<T> a, LevelDesc L, i
   smooth_pair(a, L, ip, j, k, color, zero_init, u);
 }
 
+// A plain colour sweep (no zero start, no fused update) with KZ planes per
+// thread: the loads of all KZ cells are issued before their arithmetic, so each
+// thread keeps KZ independent chains in flight.  Same operations in the same
+// order as smooth_pair.
+template <typename T, int KZ>
+__global__ void __launch_bounds__(256) smooth_kz_kernel(MGArgs<T> a, LevelDesc L, int color,
+                                                        const DevStats* zst) {
+  pdl_enter();
+  const int ip = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k0 = blockIdx.z * KZ;
+  if (ip >= ((L.nx + 1) >> 1) || j >= L.ny) return;
+  const bool zero = zst && zst->zero_phi;
+  const int plane = L.nx * L.ny;
+  const int dym = ((j == 0) ? L.ny - 1 : j - 1) - j, dyp = ((j == L.ny - 1) ? 0 : j + 1) - j;
+  int ids[KZ];
+  T v[KZ][7];   // r, x-, x+, y-, y+, z-, z+
+  PlaneCoef<T> c[KZ];
+#pragma unroll
+  for (int q = 0; q < KZ; ++q) {
+    const int k = k0 + q;
+    const int i = 2 * ip + ((j + k + color) & 1);
+    ids[q] = (k < L.nz && i < L.nx) ? lidx(L, i, j, k) : -1;
+    if (ids[q] < 0 || zero) continue;
+    const int id = ids[q];
+    const int im = (i == 0) ? L.nx - 1 : i - 1;
+    const int ipp = (i == L.nx - 1) ? 0 : i + 1;
+    c[q] = ldg_struct(a.coef + L.coef_off + k);
+    v[q][0] = a.r[id];
+    v[q][1] = a.e[id - i + im];
+    v[q][2] = a.e[id - i + ipp];
+    v[q][3] = a.e[id + dym * L.nx];
+    v[q][4] = a.e[id + dyp * L.nx];
+    v[q][5] = (k > 0) ? a.e[id - plane] : T(0);
+    v[q][6] = (k < L.nz - 1) ? a.e[id + plane] : T(0);
+  }
+#pragma unroll
+  for (int q = 0; q < KZ; ++q) {
+    const int id = ids[q];
+    if (id < 0) continue;
+    if (zero) {
+      a.e[id] = T(0);
+      continue;
+    }
+    T acc = v[q][0];
+    acc = fma(c[q].cx, v[q][1] + v[q][2], acc);
+    acc = fma(c[q].cy, v[q][3] + v[q][4], acc);
+    acc = fma(c[q].czlo, v[q][5], acc);
+    acc = fma(c[q].czhi, v[q][6], acc);
+    a.e[id] = c[q].has_s ? acc / (c[q].diag + a.s[id]) : acc * c[q].invdiag;
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) restrict_kernel(MGArgs<T> a, LevelDesc F, LevelDesc C,
                                                        int skip_black) {
@@ -249,6 +302,24 @@ __global__ void __launch_bounds__(kResidBX* kResidBY) resid_kernel(ResidArgs a) 
   block_sum3(sr, sb, sq);
   if (tid == 0) {
     a.stats->done_ctr = 0;
+    if (a.norm_out) {
+      *a.norm_out = sqrt(sr);
+      return;
+    }
+    if (a.reject_ref) {
+      // keep a learned correction only if it lowered ||r|| or already meets the
+      // test; a rejected one leaves the statistics to the residual of the restored
+      // guess (the IF body), which also sets the loop condition
+      const double rn = sqrt(sr), scale = fmax(sqrt(sb), sqrt(sq));
+      const bool met = rn <= a.tol * scale;
+      const int reject = !isfinite(rn) || !isfinite(scale) || (!(rn < *a.reject_ref) && !met);
+      cudaGraphSetConditional((cudaGraphConditionalHandle)a.reject_handle, reject);
+      if (reject) {
+        a.stats->nn_rejected += 1;
+        a.stats->launches += 1;
+        return;
+      }
+    }
     const int cond = decide(a.stats, sr, sb, sq, a.first, a.tol, a.max_cycles, a.launches_per_cycle,
                             a.adapt_max, a.launches_per_vcycle, a.inner_fixed);
     if (a.set_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)a.cond_handle, cond);
@@ -304,6 +375,19 @@ void block_shape(int nxi, int ny, dim3& block, dim3& grid, int nz, int threads =
 template <typename T>
 void launch_smooth(const MGArgs<T>& a, const LevelDesc& L, int color, int zero_init,
                    const UpdateArgs* upd, cudaStream_t s, const DevStats* zero_stats) {
+  if (!zero_init && !upd) {
+    // plain sweeps: two planes per thread on large FP32 levels (more loads in
+    // flight for an issue-bound sweep), one elsewhere (FP64 arithmetic bounds it)
+    const int kz = (sizeof(T) == sizeof(float) && L.ncell >= (1LL << 20)) ? 2 : 1;
+    dim3 block, grid;
+    block_shape((L.nx + 1) >> 1, L.ny, block, grid, (L.nz + kz - 1) / kz,
+                spread_threads((long long)((L.nx + 1) >> 1) * L.ny * ((L.nz + kz - 1) / kz)));
+    if (kz == 2)
+      launch_k(smooth_kz_kernel<T, 2>, grid, block, 0, s, a, L, color, zero_stats);
+    else
+      launch_k(smooth_kz_kernel<T, 1>, grid, block, 0, s, a, L, color, zero_stats);
+    return;
+  }
   dim3 block, grid;
   block_shape((L.nx + 1) >> 1, L.ny, block, grid, L.nz,
               spread_threads((long long)((L.nx + 1) >> 1) * L.ny * L.nz));

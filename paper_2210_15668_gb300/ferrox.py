@@ -51,7 +51,7 @@ class Stats(C.Structure):
     _fields_ = [("steps", C.c_longlong), ("launches", C.c_longlong), ("solves", C.c_longlong),
                 ("cycles", C.c_longlong),
                 ("last_cycles", C.c_int), ("last_rel_res", C.c_double), ("status", C.c_int),
-                ("vcycles", C.c_longlong)]
+                ("vcycles", C.c_longlong), ("nn_rejected", C.c_longlong)]
 
 
 EXPORTS = ["ferrox_init_geometry", "ferrox_set_bias", "ferrox_solve_poisson", "ferrox_tdgl_update",

@@ -48,11 +48,13 @@ def test_learned_warm_start_gain_and_same_answer():
         e.step(40)
         s1 = e.stats()
         assert s1["status"] == 0
-        out[mode] = (e.get_state(), (s1["cycles"] - s0["cycles"]) / 40)
+        out[mode] = (e.get_state(), (s1["cycles"] - s0["cycles"]) / 40, s1["nn_rejected"])
         e.close()
-    (Pa, phia), ca = out[0]
-    (Pb, phib), cb = out[2]
-    print(f"V-cycles per step: without network {ca:.2f}, with network {cb:.2f}")
+    (Pa, phia), ca, _ = out[0]
+    (Pb, phib), cb, rej = out[2]
+    print(f"V-cycles per step: without network {ca:.2f}, with network {cb:.2f}; "
+          f"corrections rejected {rej} of 40")
+    assert rej < 40
     assert np.linalg.norm(Pa - Pb) <= 1e-9 * np.linalg.norm(Pa)
     assert np.linalg.norm(phia - phib) <= 1e-9 * np.linalg.norm(phia)
     assert cb <= 1.5 * ca + 1.0
@@ -68,3 +70,46 @@ def test_attach_rejects_a_network_of_the_wrong_grid():
         d.attach_nn(net, 2)
     d.close()
     net.close()
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_a_correction_that_raises_the_residual_is_rejected(precision):
+    """A network whose output is dominated by a large constant makes the corrected
+    guess worse: every correction is rejected and each solve restarts from the
+    saved guess.  In the mixed form (the same solve with or without a network)
+    the run is then bit-identical to the run without the network; plain FP64
+    contexts solve learned steps in the defect-correction form, so there the two
+    agree to the solver tolerance."""
+    from paper_2210_15668_gb300 import ferrox
+    cfg = I.mfim_small()
+    geom = cfg["geom"]
+    P0 = I.random_polarization(geom, cfg["seed"])
+    num = ferrox.make_numerics(4e-13, tol=1e-12, precision=precision, guess=1)
+    ws, bs = ferrox.nn_init_params(3)
+    bs[-1] = bs[-1] + 1e3
+    out = {}
+    for mode in (0, 2):
+        e = ferrox.Device(geom, P0, numerics=num)
+        e.set_bias(0.0, 0.5)
+        e.solve_poisson()
+        net = None
+        if mode == 2:
+            lv2 = e.levels()[2]
+            net = ferrox.NN(lv2[2], lv2[1], lv2[0], params=(ws, bs))
+            e.attach_nn(net, 2)
+        e.step(10)
+        st = e.stats()
+        assert st["status"] == 0
+        out[mode] = (e.get_state(), st)
+        e.close()
+        if net is not None:
+            net.close()
+    (Pa, phia), sa = out[0]
+    (Pb, phib), sb = out[2]
+    assert sa["nn_rejected"] == 0 and sb["nn_rejected"] == 10
+    if precision == 1:
+        assert np.array_equal(Pa, Pb) and np.array_equal(phia, phib)
+        assert sa["cycles"] == sb["cycles"] and sa["vcycles"] == sb["vcycles"]
+    else:
+        assert np.linalg.norm(phia - phib) <= 1e-9 * np.linalg.norm(phia)
+        assert np.linalg.norm(Pa - Pb) <= 1e-9 * np.linalg.norm(Pa)

@@ -50,7 +50,7 @@ def test_struct_layouts_match_header(lib):
     from paper_2210_15668_gb300 import ferrox
     assert ctypes.sizeof(ferrox.Layer) == 8 + 14 * 8
     assert ctypes.sizeof(ferrox.Numerics) == 8 + 4 + 4 + 8 + 5 * 4 + 4 + 4 + 4
-    assert ctypes.sizeof(ferrox.Stats) == 4 * 8 + 8 + 8 + 8 + 8
+    assert ctypes.sizeof(ferrox.Stats) == 4 * 8 + 8 + 8 + 8 + 8 + 8
 
 
 def test_init_rejects_bad_arguments_without_gpu(lib):
