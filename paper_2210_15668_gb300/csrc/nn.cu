@@ -84,6 +84,9 @@ __global__ void __launch_bounds__(128) conv_fwd_kernel(const bf16* __restrict__ 
   const unsigned* inw = reinterpret_cast<const unsigned*>(in);
   const unsigned* ww = reinterpret_cast<const unsigned*>(wk);
   const int cin2 = cin >> 1;
+  // unrolled over a 3x3 slab of taps: their gathers are all in flight before the
+  // MMAs that consume them (the layer is latency-bound at these sizes)
+#pragma unroll 9
   for (int tap = 0; tap < 27; ++tap) {
     const int n0 = val[0] ? nb_index(zr[0], yr[0], xr[0], tap, g) : -1;
     const int n1 = val[1] ? nb_index(zr[1], yr[1], xr[1], tap, g) : -1;
