@@ -554,6 +554,29 @@ def run_reference(args, ws, rank):
     print(json.dumps(line))
 
 
+def run_nn_forward(args):
+    """Event-timed forwards of the warm-start network (random weights) on the
+    benchmark stack's level-2 grid, 64 x 64 x 8, from a seeded input."""
+    import torch
+    from paper_2210_15668_gb300 import ferrox
+    D, H, W = 8, 64, 64
+    net = ferrox.NN(D, H, W, seed=3)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.randn(D * H * W, 16, device="cuda", dtype=torch.float32, generator=g)
+    for _ in range(args.warmup):
+        net.forward(x)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        net.forward(x)
+    b.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"nn_forward_us": a.elapsed_time(b) / args.steps * 1e3, "grid": [D, H, W],
+                      "forwards": args.steps}))
+    net.close()
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -583,11 +606,16 @@ def main():
     ap.add_argument("--nn-snapshots", type=int, default=300)
     ap.add_argument("--nn-epochs", type=int, default=20)
     ap.add_argument("--batch-steps", type=int, default=50)
+    ap.add_argument("--nn-forward", action="store_true",
+                    help="time only the network forward on the 64x64x8 level of the benchmark "
+                         "stack (--steps forwards; for profiling the convolution kernels)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     ws, rank, local = dist_env()
-    if args.impl == "reference":
+    if args.nn_forward:
+        run_nn_forward(args)
+    elif args.impl == "reference":
         run_reference(args, ws, rank)
     else:
         run_ours(args, ws, rank, local)

@@ -2,7 +2,7 @@
 // multigrid level).  Activations are channels-last BF16 ([voxel][channel]);
 // convolutions are implicit GEMMs on the BF16 tensor cores with FP32
 // accumulation (mma.sync m16n8k16): M = voxels (16 per warp), N = output
-// channels, K = 27 taps x input channels.  3x3x3 stencils are periodic in x
+// channels, K = 27 taps x input channels, split over three warps per voxel tile.  3x3x3 stencils are periodic in x
 // and y and zero-padded in z, like the device.  Gradients with respect to the
 // input use the same kernel with the taps flipped and the channel matrices
 // transposed (the adjoint convolution); gradients with respect to the weights
@@ -57,18 +57,23 @@ __device__ __forceinline__ void voxel_zyx(int m, const NNGrid& g, int& z, int& y
 }
 
 // out[m][co] = act(bias[co] + sum_tap sum_ci in[nb(m, tap)][ci] w[tap][ci][co]),
-// weights in the kernel layout wk[tap][co][ci] (BF16).
+// weights in the kernel layout wk[tap][co][ci] (BF16).  A block holds kConvTiles
+// tiles of 16 voxels; the three warps of a tile (threadIdx.z) split the 27 taps
+// by z offset (9 each), so every warp's chain of dependent gathers is one slab,
+// and the partial sums meet in shared memory in a fixed order (slab 0 + slab 1
+// + slab 2).
+constexpr int kConvTiles = 4;
+
 template <int COUT>
-__global__ void __launch_bounds__(128) conv_fwd_kernel(const bf16* __restrict__ in, int cin,
-                                                       const bf16* __restrict__ wk,
-                                                       const float* __restrict__ bias, NNGrid g,
-                                                       int relu, bf16* __restrict__ out_bf,
-                                                       float* __restrict__ out_f) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(32 * kConvTiles * 3) conv_fwd_kernel(
+    const bf16* __restrict__ in, int cin, const bf16* __restrict__ wk,
+    const float* __restrict__ bias, NNGrid g, int relu, bf16* __restrict__ out_bf,
+    float* __restrict__ out_f) {
+  __shared__ float part[2][kConvTiles][COUT / 8][4][32];
+  const int lane = threadIdx.x, tile = threadIdx.y, slab = threadIdx.z;
   const int M = g.D * g.H * g.W;
-  const int m0 = warp * 16;
-  if (m0 >= M) return;
+  const int m0 = (blockIdx.x * kConvTiles + tile) * 16;
+  const bool active = m0 < M;
   const int gq = lane >> 2, tq = lane & 3;
   int zr[2], yr[2], xr[2];
   bool val[2];
@@ -84,27 +89,42 @@ __global__ void __launch_bounds__(128) conv_fwd_kernel(const bf16* __restrict__ 
   const unsigned* inw = reinterpret_cast<const unsigned*>(in);
   const unsigned* ww = reinterpret_cast<const unsigned*>(wk);
   const int cin2 = cin >> 1;
-  // unrolled over a 3x3 slab of taps: their gathers are all in flight before the
-  // MMAs that consume them (the layer is latency-bound at these sizes)
-#pragma unroll 9
-  for (int tap = 0; tap < 27; ++tap) {
-    const int n0 = val[0] ? nb_index(zr[0], yr[0], xr[0], tap, g) : -1;
-    const int n1 = val[1] ? nb_index(zr[1], yr[1], xr[1], tap, g) : -1;
-    for (int c0 = 0; c0 < cin; c0 += 16) {
-      const int off = (c0 >> 1) + tq;
-      unsigned a[4];
-      a[0] = n0 >= 0 ? __ldg(inw + (size_t)n0 * cin2 + off) : 0u;
-      a[1] = n1 >= 0 ? __ldg(inw + (size_t)n1 * cin2 + off) : 0u;
-      a[2] = n0 >= 0 ? __ldg(inw + (size_t)n0 * cin2 + off + 4) : 0u;
-      a[3] = n1 >= 0 ? __ldg(inw + (size_t)n1 * cin2 + off + 4) : 0u;
+  if (active) {
+    // the slab's nine taps unrolled: their gathers are all in flight before the
+    // MMAs that consume them (the layer is latency-bound at these sizes)
 #pragma unroll
-      for (int j = 0; j < COUT / 8; ++j) {
-        const unsigned* wp = ww + (size_t)(tap * COUT + j * 8 + gq) * cin2 + off;
-        const unsigned b[2] = {__ldg(wp), __ldg(wp + 4)};
-        mma_bf16(acc[j], a, b);
+    for (int t = 0; t < 9; ++t) {
+      const int tap = slab * 9 + t;
+      const int n0 = val[0] ? nb_index(zr[0], yr[0], xr[0], tap, g) : -1;
+      const int n1 = val[1] ? nb_index(zr[1], yr[1], xr[1], tap, g) : -1;
+      for (int c0 = 0; c0 < cin; c0 += 16) {
+        const int off = (c0 >> 1) + tq;
+        unsigned a[4];
+        a[0] = n0 >= 0 ? __ldg(inw + (size_t)n0 * cin2 + off) : 0u;
+        a[1] = n1 >= 0 ? __ldg(inw + (size_t)n1 * cin2 + off) : 0u;
+        a[2] = n0 >= 0 ? __ldg(inw + (size_t)n0 * cin2 + off + 4) : 0u;
+        a[3] = n1 >= 0 ? __ldg(inw + (size_t)n1 * cin2 + off + 4) : 0u;
+#pragma unroll
+        for (int j = 0; j < COUT / 8; ++j) {
+          const unsigned* wp = ww + (size_t)(tap * COUT + j * 8 + gq) * cin2 + off;
+          const unsigned b[2] = {__ldg(wp), __ldg(wp + 4)};
+          mma_bf16(acc[j], a, b);
+        }
       }
     }
   }
+  if (slab > 0) {
+#pragma unroll
+    for (int j = 0; j < COUT / 8; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) part[slab - 1][tile][j][q][lane] = acc[j][q];
+  }
+  __syncthreads();
+  if (slab > 0 || !active) return;
+#pragma unroll
+  for (int j = 0; j < COUT / 8; ++j)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[j][q] = (acc[j][q] + part[0][tile][j][q][lane]) + part[1][tile][j][q][lane];
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
     if (!val[r]) continue;
@@ -328,11 +348,12 @@ int grid1(long long n, int threads) {
 void nn_conv_fwd(const bf16* in, int cin, const bf16* wk, const float* bias, int cout, NNGrid g,
                  int relu, bf16* out_bf, float* out_f, cudaStream_t s) {
   const int M = g.D * g.H * g.W;
-  const int warps = (M + 15) / 16;
-  const int blocks = (warps + 3) / 4;
-  if (cout == 16) conv_fwd_kernel<16><<<blocks, 128, 0, s>>>(in, cin, wk, bias, g, relu, out_bf, out_f);
-  else if (cout == 32) conv_fwd_kernel<32><<<blocks, 128, 0, s>>>(in, cin, wk, bias, g, relu, out_bf, out_f);
-  else if (cout == 48) conv_fwd_kernel<48><<<blocks, 128, 0, s>>>(in, cin, wk, bias, g, relu, out_bf, out_f);
+  const int tiles = (M + 15) / 16;
+  const int blocks = (tiles + kConvTiles - 1) / kConvTiles;
+  const dim3 block(32, kConvTiles, 3);
+  if (cout == 16) conv_fwd_kernel<16><<<blocks, block, 0, s>>>(in, cin, wk, bias, g, relu, out_bf, out_f);
+  else if (cout == 32) conv_fwd_kernel<32><<<blocks, block, 0, s>>>(in, cin, wk, bias, g, relu, out_bf, out_f);
+  else if (cout == 48) conv_fwd_kernel<48><<<blocks, block, 0, s>>>(in, cin, wk, bias, g, relu, out_bf, out_f);
 }
 
 void nn_conv_wgrad(const bf16* in, int cin, const bf16* dout, int cout, NNGrid g, float* gw,
