@@ -165,6 +165,63 @@ __global__ void __launch_bounds__(256) restrict_check_kernel(MGArgs<T> fa, T* rc
   }
 }
 
+// Restriction with four threads per coarse cell (consecutive lanes): each sums
+// the residuals of its children (positions q and q + 4 of the up to 2x2x2
+// children, red only when the black residuals vanish), and two shuffles add the
+// four partial sums ((s0 + s1) + (s2 + s3)).  The dependent chain per thread is
+// one or two residuals instead of four to eight, for levels whose launch
+// latency, not arithmetic, bounds the restriction.
+template <typename T>
+__global__ void __launch_bounds__(256) restrict4_kernel(MGArgs<T> a, LevelDesc F, LevelDesc C,
+                                                        int skip_black) {
+  pdl_enter();
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int q = (int)(t & 3);
+  const long long cell = t >> 2;
+  const bool own = cell < C.ncell;
+  const int nxc = F.crx ? 2 : 1, nyc = F.cry ? 2 : 1, nzc = F.crz ? 2 : 1;
+  const int nch = nxc * nyc * nzc;
+  int I = 0, J = 0, K = 0;
+  if (own) {
+    const int rest = (int)(cell / C.nx);
+    I = (int)(cell - (long long)rest * C.nx);
+    K = rest / C.ny;
+    J = rest - K * C.ny;
+  }
+  T sum = T(0), ssum = T(0);
+  if (own) {
+    for (int c = q; c < nch; c += 4) {
+      const int di = c % nxc, dj = (c / nxc) % nyc, dk = c / (nxc * nyc);
+      const int i = F.crx ? 2 * I + di : I, j = F.cry ? 2 * J + dj : J, k = F.crz ? 2 * K + dk : K;
+      if (!(skip_black && ((i + j + k) & 1))) sum += cell_residual(a, F, i, j, k);
+      if (a.s) ssum += a.s[lidx(F, i, j, k)];
+    }
+  }
+  sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+  sum += __shfl_xor_sync(0xffffffffu, sum, 2);
+  if (a.s) {
+    ssum += __shfl_xor_sync(0xffffffffu, ssum, 1);
+    ssum += __shfl_xor_sync(0xffffffffu, ssum, 2);
+  }
+  if (own && q == 0) {
+    const T inv = T(1) / T(nch);
+    const int idc = lidx(C, I, J, K);
+    a.r[idc] = sum * inv;
+    if (a.s) a.s[idc] = ssum * inv;
+  }
+}
+
+// Prolongation + correction with one thread per fine cell (prolong_fine).
+template <typename T>
+__global__ void __launch_bounds__(256) prolong_fine_kernel(MGArgs<T> a, LevelDesc F, LevelDesc C,
+                                                           int constant) {
+  pdl_enter();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= F.nx || j >= F.ny) return;
+  prolong_fine(a, F, C, i, j, (int)blockIdx.z, constant);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) prolong_kernel(MGArgs<T> a, LevelDesc F, LevelDesc C,
                                                       int constant) {
@@ -414,6 +471,14 @@ void launch_restrict_check(const MGArgs<double>& fa, double* rc, const LevelDesc
 template <typename T>
 void launch_restrict(const MGArgs<T>& a, const LevelDesc& F, const LevelDesc& C, int nu1,
                      cudaStream_t s) {
+  if (sizeof(T) == sizeof(double)) {
+    // FP64: four threads per coarse cell (FP64 latency bounds the small levels;
+    // measured +0.4% FP64, -2.6% in the FP32 form, which keeps one thread)
+    const long long threads = 4 * C.ncell;
+    launch_k(restrict4_kernel<T>, dim3((unsigned)((threads + 255) / 256)), dim3(256), 0, s, a, F, C,
+             black_residual_zero(F, nu1));
+    return;
+  }
   dim3 block, grid;
   block_shape(C.nx, C.ny, block, grid, C.nz, spread_threads(C.ncell));
   launch_k(restrict_kernel<T>, grid, block, 0, s, a, F, C, black_residual_zero(F, nu1));
@@ -425,6 +490,15 @@ void launch_prolong(const MGArgs<T>& a, const LevelDesc& F, const LevelDesc& C, 
   if (fine || (tiled && F.crx && F.cry && F.crz && !constant)) {
     const dim3 grid((C.nx + kPX - 1) / kPX, (C.ny + kPY - 1) / kPY, (C.nz + kPZ - 1) / kPZ);
     launch_k(prolong_tiled_kernel<T>, grid, dim3(kPX, kPY), 0, s, a, F, C, fine);
+    return;
+  }
+  if (sizeof(T) == sizeof(double)) {
+    // FP64: one thread per fine cell, a 15-operation chain instead of 84 per
+    // coarse cell (measured +1.8% FP64, -2.9% in the FP32 form, which keeps the
+    // per-coarse-cell kernel)
+    dim3 block, grid;
+    block_shape(F.nx, F.ny, block, grid, F.nz, spread_threads(F.ncell));
+    launch_k(prolong_fine_kernel<T>, grid, block, 0, s, a, F, C, constant);
     return;
   }
   dim3 block, grid;
