@@ -250,6 +250,8 @@ def run_ours(args, ws, rank, local):
         dev.attach_nn(dev._net, 2)
     clocks = ClockSampler(local) if rank == 0 else None
     t_ms, st0, st1, ck = timed_run(dev, args.steps, args.warmup, clocks)
+    if learned_main is not None:
+        learned_main["corrections_rejected"] = st1["nn_rejected"] - st0["nn_rejected"]
     t_max = reduce_max(t_ms, ws)
     K = args.steps
     value = ws * cells * K / (t_max / 1e3) / 1e6
@@ -431,12 +433,12 @@ def run_learned(args, ws, cfg, geom, P0, cells, sweep, timed_run):
 
 
 def train_network_on(args, ferrox, I):
-    """Collect snapshots on the 256x256x32 MFIM and 256x256x64 MFISM workloads and
-    train one network on both (the weights carry over between grids: the network
-    is fully convolutional)."""
+    """Collect snapshots on the --nn-train-on workloads (default: the 256x256x32 MFIM
+    and 256x256x64 MFISM) and train one network on all of them (the weights carry
+    over between grids: the network is fully convolutional)."""
     import torch
     params, losses, t0 = None, [], time.perf_counter()
-    for name in ("mfim_256x256x32", "mfism_256x256x64"):
+    for name in args.nn_train_on.split(","):
         cfg = workload_config(name)
         g = cfg["geom"]
         num = ferrox.make_numerics(cfg["dt"], order=1, tol=1e-10, precision=ferrox.MIXED, guess=1)
@@ -604,6 +606,8 @@ def main():
     ap.add_argument("--learned", action="store_true",
                     help="attach a network trained on the 256^2 x 32 MFIM and 256^2 x 64 MFISM snapshots")
     ap.add_argument("--nn-snapshots", type=int, default=300)
+    ap.add_argument("--nn-train-on", default="mfim_256x256x32,mfism_256x256x64",
+                    help="workloads whose snapshots train the --learned network (comma list)")
     ap.add_argument("--nn-epochs", type=int, default=20)
     ap.add_argument("--batch-steps", type=int, default=50)
     ap.add_argument("--nn-forward", action="store_true",
