@@ -381,6 +381,25 @@ __device__ __forceinline__ void block_sum3(double& x, double& y, double& z) {
   __syncthreads();
 }
 
+// FP64 -> FP32 store of the outer residual (mixed form) by integer truncation:
+// sign, rebiased exponent and the top 23 mantissa bits, rounding toward zero
+// (within 1 FP32 ulp; the FP64 defect correction absorbs it).  Magnitudes below
+// the FP32 normal range store a signed zero, above it (and NaN) infinity; the
+// norms and the convergence decision use the FP64 value.  The conversion
+// instruction would run on the FP64 pipe that bounds this kernel.
+template <typename T>
+__device__ __forceinline__ T narrow_resid(double x) {
+  if (sizeof(T) == sizeof(float)) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+    const int e = (int)((b >> 52) & 0x7ff) - 1023 + 127;
+    if (e <= 0) return (T)__uint_as_float(sign);
+    if (e >= 255) return (T)__uint_as_float(sign | 0x7f800000u);
+    return (T)__uint_as_float(sign | ((unsigned)e << 23) | (unsigned)((b >> 29) & 0x7fffffu));
+  }
+  return (T)x;
+}
+
 // FP64 residual of planes [k0, k1) of one (x, y) column, marching up with a
 // register window; accumulates r^2, b^2 (first residual of a solve only) and
 // rho^2.  SC = false compiles out the carrier term (stacks without a
@@ -432,7 +451,7 @@ __device__ __forceinline__ void resid_column(const ResidArgs& a, int i, int j, i
     r = fma(c.czlo, pd, r);
     r = fma(c.cy, sy, r);
     r = fma(c.cx, sx, r);
-    r_out[t] = (T)r;
+    r_out[t] = narrow_resid<T>(r);
     acc_r = fma(r, r, acc_r);
     if (a.first) acc_b = fma(bb, bb, acc_b);
     pd = pc;
