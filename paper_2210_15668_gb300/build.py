@@ -19,10 +19,11 @@ LIB = os.path.join(OUT_DIR, "libferrox.so")
 SOURCES = ["engine.cu", "multigrid.cu", "tdgl.cu", "persistent.cu", "nn.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
-# The persistent engine exchanges data between CTAs of one launch through global
-# memory; its loads are cached in L2 only (the coherence point), never in the
-# per-SM L1, so a CTA cannot read a line another SM has since rewritten.
-PER_FILE_FLAGS = {"persistent.cu": ["-Xptxas", "-dlcm=cg"]}
+# Per-file extra flags.  The persistent engine needs none: CTAs of one launch
+# exchange data only across its grid barrier, whose fence / acquire sequence is
+# the cooperative-groups grid synchronisation pattern under which ordinary
+# (L1-cached) loads observe every store made before the barrier.
+PER_FILE_FLAGS: dict[str, list[str]] = {}
 
 
 def nvcc() -> str:
