@@ -1373,6 +1373,7 @@ struct ferrox_batch {
   void* r = nullptr;
   void* s = nullptr;
   void* coef = nullptr;
+  void* dense = nullptr;              // T: inverses of the instances' dense tail levels
   PlaneCoef<double>* coef0 = nullptr;
   PlaneTDGL* planes = nullptr;
   LevelDesc* lv = nullptr;
@@ -1444,6 +1445,7 @@ BatchArgs batch_args(ferrox_batch* B, int mode) {
   BatchArgs a{};
   a.inst = B->inst; a.ninst = B->n; a.mode = mode; a.nsteps = B->nsteps_d;
   a.e = B->e; a.r = B->r; a.s = B->s; a.coef = B->coef; a.lv = B->lv; a.lvt = B->lvt;
+  a.dense = B->dense;
   a.pre = B->pre; a.Ldown = B->Ldown; a.partials = B->partials; a.active = B->active;
   a.bar = B->bar; a.status = B->status; a.tol = B->num.tol; a.max_cycles = B->num.max_cycles;
   a.nu1 = B->num.nu1; a.nu2 = B->num.nu2; a.rows_per_unit = B->rows_per_unit;
@@ -1565,7 +1567,7 @@ void batch_release(ferrox_batch* B) {
   if (B->ge_solve) cudaGraphExecDestroy(B->ge_solve);
   if (B->gr_step) cudaGraphDestroy(B->gr_step);
   if (B->gr_solve) cudaGraphDestroy(B->gr_solve);
-  void* ptrs[] = {B->b, B->Pbuf, B->backup, B->e, B->r, B->s, B->coef, B->coef0, B->planes, B->lv,
+  void* ptrs[] = {B->b, B->Pbuf, B->backup, B->e, B->r, B->s, B->coef, B->dense, B->coef0, B->planes, B->lv,
                   B->lvt, B->pre, B->partials, B->active, B->bar, B->status, B->nsteps_d, B->dbg, B->params,
                   B->stats, B->inst, B->charge_part, B->charge_out};
   for (void* p : ptrs) if (p) cudaFree(p);
@@ -1688,7 +1690,7 @@ ferrox_status ferrox_init_batch(ferrox_batch** out, int n, const ferrox_geometry
   FX_BINIT(cudaMalloc(&B->charge_out, (size_t)n * 8 * sizeof(double)));
   FX_BINIT(cudaMallocHost(&B->host_pinned, (size_t)n * 8 * sizeof(double) + 64));
   // tables
-  std::vector<unsigned char> coefT;
+  std::vector<unsigned char> coefT, denseT;
   std::vector<PlaneCoef<double>> coef0;
   std::vector<PlaneTDGL> planes;
   std::vector<LevelDesc> lv, lvt;
@@ -1698,13 +1700,26 @@ ferrox_status ferrox_init_batch(ferrox_batch** out, int n, const ferrox_geometry
     ferrox_ctx& c = p.c;
     auto c64 = level_coefficients<double>(&c);
     for (int k = 0; k < c.nz; ++k) coef0.push_back(c64[k]);
+    const int dl = dense_level(&c);
+    inst[i].dense_lev = dl;
+    inst[i].dense_off = (long long)(denseT.size() / tsz);
     if (B->mixed) {
       auto c32 = level_coefficients<float>(&c);
       const unsigned char* q = reinterpret_cast<const unsigned char*>(c32.data());
       coefT.insert(coefT.end(), q, q + c32.size() * sizeof(PlaneCoef<float>));
+      if (dl >= 0) {
+        const auto inv = dense_inverse<float>(c32, c.lv_tail[dl]);
+        const unsigned char* d = reinterpret_cast<const unsigned char*>(inv.data());
+        denseT.insert(denseT.end(), d, d + inv.size() * sizeof(float));
+      }
     } else {
       const unsigned char* q = reinterpret_cast<const unsigned char*>(c64.data());
       coefT.insert(coefT.end(), q, q + c64.size() * sizeof(PlaneCoef<double>));
+      if (dl >= 0) {
+        const auto inv = dense_inverse<double>(c64, c.lv_tail[dl]);
+        const unsigned char* d = reinterpret_cast<const unsigned char*>(inv.data());
+        denseT.insert(denseT.end(), d, d + inv.size() * sizeof(double));
+      }
     }
     planes.insert(planes.end(), c.planes.begin(), c.planes.end());
     for (auto L : c.lv) { L.off += p.arena_off; L.coef_off += p.coef_off; lv.push_back(L); }
@@ -1736,6 +1751,10 @@ ferrox_status ferrox_init_batch(ferrox_batch** out, int n, const ferrox_geometry
     ra.cond_handle = 0; ra.launches_per_cycle = 0; ra.kchunk = c.nz;
   }
   FX_BINIT(cudaMemcpy(B->coef, coefT.data(), coefT.size(), cudaMemcpyHostToDevice));
+  if (!denseT.empty()) {
+    FX_BINIT(cudaMalloc(&B->dense, denseT.size()));
+    FX_BINIT(cudaMemcpy(B->dense, denseT.data(), denseT.size(), cudaMemcpyHostToDevice));
+  }
   FX_BINIT(cudaMemcpy(B->coef0, coef0.data(), coef0.size() * sizeof(PlaneCoef<double>), cudaMemcpyHostToDevice));
   FX_BINIT(cudaMemcpy(B->planes, planes.data(), planes.size() * sizeof(PlaneTDGL), cudaMemcpyHostToDevice));
   FX_BINIT(cudaMemcpy(B->lv, lv.data(), lv.size() * sizeof(LevelDesc), cudaMemcpyHostToDevice));

@@ -324,6 +324,9 @@ struct BatchInst {
   int fe_lo, fe_hi;
   int lv_off, nlev, tail_first, lvt_off, nlev_tail, bottom_sweeps;
   long long tail_elems, tail_base;
+  long long dense_off;  // element offset of the instance's tail inverse in BatchArgs::dense
+  int dense_lev;        // tail level solved by that inverse (-1: relaxed bottom level)
+  int pad2;
 };
 
 struct BatchArgs {
@@ -337,6 +340,7 @@ struct BatchArgs {
   const void* coef;     // PlaneCoef<T> of all levels of all instances
   const LevelDesc* lv;  // levels of all instances (arena offsets)
   const LevelDesc* lvt; // tail levels of all instances (shared-memory offsets)
+  const void* dense;    // T: inverses of the instances' dense tail levels
   const int* pre;       // unit prefix tables: rows, smoothing rows per level, coarse rows per level
   int Ldown;            // deepest multi-block level count over instances
   double* partials;     // 3 per row unit

@@ -229,7 +229,9 @@ __device__ void phase_tail(const Ctx<T>& c, unsigned char* smem) {
     if (!ld_flag(A.active + i)) continue;
     const BatchInst I = ldg_struct(A.inst + i);
     TailArgs t{A.lvt + I.lvt_off, I.nlev_tail, I.tail_elems, I.tail_base, A.nu1, A.nu2,
-               I.bottom_sweeps, 0};
+               I.bottom_sweeps, 0,
+               I.dense_lev >= 0 ? static_cast<const T*>(A.dense) + I.dense_off : nullptr,
+               I.dense_lev, 0};
     tail_vcycle<T>(c.mg, t, smem);
   }
 }
