@@ -64,6 +64,7 @@ struct ferrox_ctx {
   bool direct = false;    // FP64 V-cycles on phi itself (see direct_form)
   int dense_lev = -1;     // tail level solved by its inverse (-1: none)
   void* dense_d = nullptr;
+  void* dense_wide_d = nullptr;   // FP64: inverse of the first tail level, solved instead of the tail
   int check_blocks = 0;   // blocks of the direct form's fused residual + restriction + norm
   // device memory
   cudaStream_t stream = nullptr;
@@ -410,9 +411,18 @@ void enqueue_levels(ferrox_ctx* c, cudaStream_t s, W wrap, int l0, bool first, b
     }
     wrap(FERROX_K_RESTRICT, [&] { launch_restrict<T>(a, c->lv[l], c->lv[l + 1], nu1, s); });
   }
-  TailArgs ta{c->lvt_d, L - lt + 1, c->tail_elems, c->lv[lt].off, nu1, nu2, c->num.bottom_sweeps,
-              constant, c->dense_d, c->dense_lev, 0};
-  wrap(FERROX_K_TAIL, [&] { launch_tail<T>(a, ta, c->tail_smem, s); });
+  if (c->dense_wide_d) {
+    // the whole tail as one exact solve of its first level, spread over the SMs
+    const LevelDesc& B = c->lv[lt];
+    wrap(FERROX_K_TAIL, [&] {
+      launch_dense_solve<T>(static_cast<const T*>(c->dense_wide_d), (int)B.ncell, a.r + B.off,
+                            a.e + B.off, s);
+    });
+  } else {
+    TailArgs ta{c->lvt_d, L - lt + 1, c->tail_elems, c->lv[lt].off, nu1, nu2, c->num.bottom_sweeps,
+                constant, c->dense_d, c->dense_lev, 0};
+    wrap(FERROX_K_TAIL, [&] { launch_tail<T>(a, ta, c->tail_smem, s); });
+  }
   const UpdateArgs upd{c->phi, c->stats_d, update_clamp(c)};
   for (int l = lt - 1; l >= l0; --l) {
     const int ks = l == 0 ? FERROX_K_SMOOTH0 : FERROX_K_SMOOTHC;
@@ -927,7 +937,7 @@ void release(ferrox_ctx* c) {
   for (auto g : gr) if (g) cudaGraphDestroy(g);
   void* ptrs[] = {c->b, c->Pbuf, c->Fbuf, c->phi_prev, c->e_arena, c->r_arena, c->s_arena, c->coef, c->coef0,
                   c->planes_d, c->lv_d, c->lvt_d, c->nn_scale, c->phi_guess, c->nn_pf, c->nn_stats, c->params_d, c->stats_d, c->partials_d, c->charge_d,
-                  c->charge_part_d, c->dense_d};
+                  c->charge_part_d, c->dense_d, c->dense_wide_d};
   for (void* p : ptrs) if (p) cudaFree(p);
   if (c->host_pinned) cudaFreeHost(c->host_pinned);
   if (c->cap1) cudaStreamDestroy(c->cap1);
@@ -1079,6 +1089,13 @@ ferrox_status ferrox_init_geometry(ferrox_ctx** out, const ferrox_geometry* geom
     FX_INIT_CK(cudaMalloc(&ctx->coef, c64.size() * sizeof(PlaneCoef<double>)));
     FX_INIT_CK(cudaMemcpy(ctx->coef, c64.data(), c64.size() * sizeof(PlaneCoef<double>),
                           cudaMemcpyHostToDevice));
+    const LevelDesc& T0 = ctx->lv_tail[0];
+    if (!ctx->has_sc && T0.ncell > kDenseMax && T0.ncell <= kDenseWide) {
+      const auto inv = dense_inverse<double>(c64, T0);
+      FX_INIT_CK(cudaMalloc(&ctx->dense_wide_d, inv.size() * sizeof(double)));
+      FX_INIT_CK(cudaMemcpy(ctx->dense_wide_d, inv.data(), inv.size() * sizeof(double),
+                            cudaMemcpyHostToDevice));
+    }
     if (ctx->dense_lev >= 0) {
       const auto inv = dense_inverse<double>(c64, ctx->lv_tail[ctx->dense_lev]);
       FX_INIT_CK(cudaMalloc(&ctx->dense_d, inv.size() * sizeof(double)));

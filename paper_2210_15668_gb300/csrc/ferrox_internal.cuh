@@ -50,6 +50,8 @@ constexpr int kTailMaxCells = 4096;     // levels at or below this size run in o
 constexpr int kTailMaxCellsFP64 = 512;  // the same for FP64 corrections
 constexpr int kTailThreads = 1024;
 constexpr int kDenseMax = 64;           // a tail level of at most this many cells is solved by its inverse
+constexpr int kDenseWide = 512;         // FP64: a first tail level up to this size is solved by
+                                        // its inverse across the SMs instead of the tail V-cycle
 constexpr int kTailMaxSmem = 200 * 1024; // shared memory available to the tail CTA
 constexpr int kResidBX = 32, kResidBY = 8; // residual: one thread per (x, y) column
 
@@ -220,6 +222,9 @@ template <typename T>
 cudaError_t tail_prepare(size_t smem);
 template <typename T>
 void launch_tail(const MGArgs<T>& a, const TailArgs& t, size_t smem, cudaStream_t s);
+// e = inv r for one level (n x n dense inverse, one warp per row)
+template <typename T>
+void launch_dense_solve(const T* inv, int n, const T* r, T* e, cudaStream_t s);
 template <typename T>
 void launch_resid(const ResidArgs& a, cudaStream_t s);
 template <typename T>

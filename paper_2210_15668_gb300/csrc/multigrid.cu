@@ -383,6 +383,26 @@ __global__ void __launch_bounds__(kResidBX* kResidBY) resid_kernel(ResidArgs a) 
   }
 }
 
+// e = A^-1 r on one level by its dense inverse (row-major, n x n): one warp per
+// row, lanes over columns, a fixed-order shuffle reduction.  Used for a level
+// that replaces the single-CTA tail in the FP64 form: the matrix-vector product
+// spreads over the SMs where the tail's V-cycle would run on one.
+template <typename T>
+__global__ void __launch_bounds__(256) dense_solve_kernel(const T* __restrict__ inv, int n,
+                                                          const T* __restrict__ r,
+                                                          T* __restrict__ e) {
+  pdl_enter();
+  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  const T* a = inv + (size_t)row * n;
+  T acc = T(0);
+  for (int c = lane; c < n; c += 32) acc = fma(__ldg(a + c), r[c], acc);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) e[row] = acc;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) update_kernel(double* __restrict__ phi, const T* __restrict__ e0,
                                                      long long n, const DevStats* stats,
@@ -507,6 +527,11 @@ void launch_prolong(const MGArgs<T>& a, const LevelDesc& F, const LevelDesc& C, 
 }
 
 template <typename T>
+void launch_dense_solve(const T* inv, int n, const T* r, T* e, cudaStream_t s) {
+  launch_k(dense_solve_kernel<T>, dim3((unsigned)((n + 7) / 8)), dim3(256), 0, s, inv, n, r, e);
+}
+
+template <typename T>
 size_t tail_smem_bytes(long long elems, bool has_s) {
   return (size_t)elems * sizeof(T) * (has_s ? 3 : 2);
 }
@@ -580,6 +605,7 @@ cudaError_t launch_carrier_exp(const double* u, double* ep, double* em, long lon
   template size_t tail_smem_bytes<T>(long long, bool);                                          \
   template cudaError_t tail_prepare<T>(size_t);                                                 \
   template void launch_tail<T>(const MGArgs<T>&, const TailArgs&, size_t, cudaStream_t);        \
+  template void launch_dense_solve<T>(const T*, int, const T*, T*, cudaStream_t);               \
   template void launch_resid<T>(const ResidArgs&, cudaStream_t);                                \
   template void launch_update<T>(double*, const T*, long long, const DevStats*, double,         \
                                  cudaStream_t, T*);
