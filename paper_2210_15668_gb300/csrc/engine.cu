@@ -166,12 +166,16 @@ void build_levels(ferrox_ctx* c) {
 }
 
 // first level of the single-CTA tail: small enough in cells and in shared memory
-void plan_tail(ferrox_ctx* c, size_t elem_size) {
+// wide: the context solves a first tail level of 65..kDenseWide cells by its
+// inverse across the SMs (no carriers), so its tail may start there
+void plan_tail(ferrox_ctx* c, size_t elem_size, bool wide = false) {
   const int L = (int)c->lv.size() - 1;
   const int narr = c->has_sc ? 3 : 2;
   c->tail_first = L;
-  // one SM runs FP64 at 2 DFMA/clk, so in FP64 the tail starts at a smaller level
-  const long long max_cells = elem_size == sizeof(double) ? kTailMaxCellsFP64 : kTailMaxCells;
+  // one SM runs FP64 at 2 DFMA/clk, so in FP64 the tail starts at a smaller level;
+  // with the wide dense solve the FP32 form starts there too
+  const long long max_cells = (elem_size == sizeof(double) || (wide && !c->has_sc))
+                                  ? kTailMaxCellsFP64 : kTailMaxCells;
   for (int l = 0; l <= L; ++l) {
     const long long elems = c->arena - c->lv[l].off;
     if (c->lv[l].ncell <= max_cells && (size_t)elems * elem_size * narr <= (size_t)kTailMaxSmem) {
@@ -1017,7 +1021,7 @@ ferrox_status ferrox_init_geometry(ferrox_ctx** out, const ferrox_geometry* geom
 
   const bool mixed = ctx->num.precision == FERROX_MIXED;
   const size_t tsz = mixed ? sizeof(float) : sizeof(double);
-  plan_tail(ctx, tsz);
+  plan_tail(ctx, tsz, true);
   {
     // residual grid: split the columns into z chunks (halving, at least 4 planes
     // each) until there are about four waves of blocks on 152 SMs
@@ -1083,6 +1087,13 @@ ferrox_status ferrox_init_geometry(ferrox_ctx** out, const ferrox_geometry* geom
       const auto inv = dense_inverse<float>(c32, ctx->lv_tail[ctx->dense_lev]);
       FX_INIT_CK(cudaMalloc(&ctx->dense_d, inv.size() * sizeof(float)));
       FX_INIT_CK(cudaMemcpy(ctx->dense_d, inv.data(), inv.size() * sizeof(float),
+                            cudaMemcpyHostToDevice));
+    }
+    const LevelDesc& T0 = ctx->lv_tail[0];
+    if (!ctx->has_sc && T0.ncell > kDenseMax && T0.ncell <= kDenseWide) {
+      const auto inv = dense_inverse<float>(c32, T0);
+      FX_INIT_CK(cudaMalloc(&ctx->dense_wide_d, inv.size() * sizeof(float)));
+      FX_INIT_CK(cudaMemcpy(ctx->dense_wide_d, inv.data(), inv.size() * sizeof(float),
                             cudaMemcpyHostToDevice));
     }
   } else {

@@ -50,8 +50,9 @@ constexpr int kTailMaxCells = 4096;     // levels at or below this size run in o
 constexpr int kTailMaxCellsFP64 = 512;  // the same for FP64 corrections
 constexpr int kTailThreads = 1024;
 constexpr int kDenseMax = 64;           // a tail level of at most this many cells is solved by its inverse
-constexpr int kDenseWide = 512;         // FP64: a first tail level up to this size is solved by
-                                        // its inverse across the SMs instead of the tail V-cycle
+constexpr int kDenseWide = 512;         // a first tail level up to this size (stacks without
+                                        // carriers) is solved by its inverse across the SMs
+                                        // instead of the tail V-cycle
 constexpr int kTailMaxSmem = 200 * 1024; // shared memory available to the tail CTA
 constexpr int kResidBX = 32, kResidBY = 8; // residual: one thread per (x, y) column
 
