@@ -54,23 +54,28 @@ def test_batch_matches_oracle_per_instance(precision, tol, bound):
 
 
 def test_batch_matches_single_instance_gpu_path():
+    """The batched and the single-instance engines stop on the same residual test
+    but solve the coarsest levels differently (a shared-memory V-cycle against an
+    exact dense solve of the first tail level), so they agree to the solver
+    tolerance: at 1e-12, to 1e-10 after 10 steps."""
     from paper_2210_15668_gb300 import ferrox
     geoms, P0s, biases = small_batch(n=4, seed=5)
-    num = ferrox.make_numerics(4e-13, tol=1e-10, precision=1)
+    num = ferrox.make_numerics(4e-13, tol=1e-12, precision=1)
     B = ferrox.Batch(geoms, P0s, num)
     B.set_bias(np.zeros(len(geoms)), biases)
     B.solve_poisson()
     B.step(10)
     sb = B.stats()
     for i, g in enumerate(geoms):
-        d = ferrox.Device(g, P0s[i], numerics=ferrox.make_numerics(4e-13, tol=1e-10, precision=1))
+        d = ferrox.Device(g, P0s[i], numerics=ferrox.make_numerics(4e-13, tol=1e-12, precision=1))
         d.set_bias(0.0, biases[i])
         d.solve_poisson()
         d.step(10)
         Ps, phis = d.get_state()
         Pb, phib = B.state(i)
         assert rel_l2(Pb, Ps) <= 1e-10 and rel_l2(phib, phis) <= 1e-10
-        assert abs(d.stats()["cycles"] - sb[i]["cycles"]) <= 2
+        # the exact coarse solve of the single-instance engine needs no more cycles
+        assert d.stats()["cycles"] <= sb[i]["cycles"] + 2
         d.close()
     B.close()
 
