@@ -342,17 +342,20 @@ def run_ours(args, ws, rank, local):
     e2e = None
     if not args.no_e2e:
         d3 = make(prec_main)
-        Ph = torch.empty((1,) + (nz, geom["ny"], geom["nx"]), dtype=torch.float64).pin_memory().numpy()
+        # the state a step takes and returns: P on the ferroelectric film (zero
+        # elsewhere in the model) and phi, in pinned host memory
+        lo, hi = d3.fe_planes()
+        Ph = torch.empty((1, hi - lo + 1, geom["ny"], geom["nx"]), dtype=torch.float64).pin_memory().numpy()
         fh = torch.empty((nz, geom["ny"], geom["nx"]), dtype=torch.float64).pin_memory().numpy()
-        d3.get_state(Ph, fh)
+        d3.get_state_fe(Ph, fh)
         Ke = max(1, min(K, args.e2e_steps))
         torch.cuda.synchronize()
         barrier(ws)
         t0 = time.perf_counter()
         for s in range(Ke):
-            d3.set_state(Ph, fh)
+            d3.set_state_fe(Ph, fh)
             d3.step(1)
-            d3.get_state(Ph, fh)
+            d3.get_state_fe(Ph, fh)
         te = reduce_max(time.perf_counter() - t0, ws)
         e2e = {"value": ws * cells * Ke / te / 1e6, "unit": UNIT, "steps": Ke,
                "h2d_bytes_per_step": int(Ph.nbytes + fh.nbytes),

@@ -190,6 +190,17 @@ ferrox_status ferrox_clear_status(ferrox_ctx* ctx);
 ferrox_status ferrox_get_state(ferrox_ctx* ctx, double* P_host, double* phi_host);
 ferrox_status ferrox_set_state(ferrox_ctx* ctx, const double* P_host, const double* phi_host);
 
+/* The same copies with P restricted to the ferroelectric film, the planes
+ * fe_lo..fe_hi that ferrox_fe_planes reports: P_fe_host is
+ * [ncomp][fe_hi - fe_lo + 1][ny][nx].  Outside the film P is zero in the model
+ * (Methods, TDGL: the polarization belongs to the FE layer), so this is the whole
+ * state at a third of the bytes for the 10-of-32-plane stacks; the device planes
+ * outside the film keep their values (zero unless ferrox_set_state wrote others).
+ * Synchronisation as for ferrox_get_state / ferrox_set_state. */
+ferrox_status ferrox_fe_planes(const ferrox_ctx* ctx, int* fe_lo, int* fe_hi);
+ferrox_status ferrox_get_state_fe(ferrox_ctx* ctx, double* P_fe_host, double* phi_host);
+ferrox_status ferrox_set_state_fe(ferrox_ctx* ctx, const double* P_fe_host, const double* phi_host);
+
 /* Kernel classes reported by ferrox_profile_step. */
 enum {
   FERROX_K_TDGL = 0,      /* fused TDGL update + right-hand side */

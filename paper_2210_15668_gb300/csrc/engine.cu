@@ -1346,6 +1346,44 @@ ferrox_status ferrox_set_state(ferrox_ctx* ctx, const double* P_host, const doub
   return FERROX_OK;
 }
 
+ferrox_status ferrox_fe_planes(const ferrox_ctx* ctx, int* fe_lo, int* fe_hi) {
+  if (!ctx || !fe_lo || !fe_hi) return FERROX_EINVAL;
+  *fe_lo = ctx->fe_lo;
+  *fe_hi = ctx->fe_hi;
+  return FERROX_OK;
+}
+
+ferrox_status ferrox_get_state_fe(ferrox_ctx* ctx, double* P_fe_host, double* phi_host) {
+  if (!ctx) return fail(nullptr, FERROX_EINVAL, "null context");
+  const long long plane = (long long)ctx->nx * ctx->ny, N = plane * ctx->nz;
+  const long long nfe = (long long)(ctx->fe_hi - ctx->fe_lo + 1) * plane;
+  if (P_fe_host)
+    for (int q = 0; q < ctx->ncomp; ++q)
+      FX_CK(cudaMemcpyAsync(P_fe_host + q * nfe, ctx->P + q * N + ctx->fe_lo * plane,
+                            nfe * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  if (phi_host)
+    FX_CK(cudaMemcpyAsync(phi_host, ctx->phi, N * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  ferrox_stats st;
+  return ferrox_sync_stats(ctx, &st);
+}
+
+ferrox_status ferrox_set_state_fe(ferrox_ctx* ctx, const double* P_fe_host, const double* phi_host) {
+  if (!ctx) return fail(nullptr, FERROX_EINVAL, "null context");
+  const long long plane = (long long)ctx->nx * ctx->ny, N = plane * ctx->nz;
+  const long long nfe = (long long)(ctx->fe_hi - ctx->fe_lo + 1) * plane;
+  if (P_fe_host)
+    for (int q = 0; q < ctx->ncomp; ++q)
+      FX_CK(cudaMemcpyAsync(ctx->P + q * N + ctx->fe_lo * plane, P_fe_host + q * nfe,
+                            nfe * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  if (phi_host) {
+    FX_CK(cudaMemcpyAsync(ctx->phi, phi_host, N * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    if (ctx->num.guess == 1)   // a new state has no history
+      FX_CK(cudaMemcpyAsync(ctx->phi_prev, ctx->phi, N * sizeof(double), cudaMemcpyDeviceToDevice,
+                            ctx->stream));
+  }
+  return FERROX_OK;
+}
+
 ferrox_status ferrox_destroy(ferrox_ctx* ctx) {
   release(ctx);
   return FERROX_OK;

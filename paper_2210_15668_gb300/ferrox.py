@@ -56,7 +56,8 @@ class Stats(C.Structure):
 
 EXPORTS = ["ferrox_init_geometry", "ferrox_set_bias", "ferrox_solve_poisson", "ferrox_tdgl_update",
            "ferrox_step", "ferrox_charge", "ferrox_sync_stats", "ferrox_clear_status",
-           "ferrox_get_state", "ferrox_set_state", "ferrox_destroy", "ferrox_last_error",
+           "ferrox_get_state", "ferrox_set_state", "ferrox_fe_planes", "ferrox_get_state_fe",
+           "ferrox_set_state_fe", "ferrox_destroy", "ferrox_last_error",
            "ferrox_level_shape", "ferrox_profile_step", "ferrox_tdgl_update_static",
            "ferrox_init_batch", "ferrox_batch_set_bias", "ferrox_batch_solve_poisson",
            "ferrox_batch_step", "ferrox_batch_charge", "ferrox_batch_stats", "ferrox_batch_tuning",
@@ -91,6 +92,9 @@ def load(path: str = LIB_PATH):
     lib.ferrox_sync_stats.argtypes = [vp, C.POINTER(Stats)]
     lib.ferrox_get_state.argtypes = [vp, vp, vp]
     lib.ferrox_set_state.argtypes = [vp, vp, vp]
+    lib.ferrox_fe_planes.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    lib.ferrox_get_state_fe.argtypes = [vp, vp, vp]
+    lib.ferrox_set_state_fe.argtypes = [vp, vp, vp]
     lib.ferrox_last_error.argtypes = [vp]
     lib.ferrox_last_error.restype = C.c_char_p
     lib.ferrox_level_shape.argtypes = [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
@@ -237,6 +241,28 @@ class Device:
         pp = C.c_void_p(P_host.ctypes.data) if P_host is not None else None
         fp = C.c_void_p(phi_host.ctypes.data) if phi_host is not None else None
         self._ck(self.lib.ferrox_set_state(self.ctx, pp, fp))
+
+    def fe_planes(self):
+        """(fe_lo, fe_hi): the planes of the ferroelectric film (P is zero elsewhere)."""
+        lo, hi = C.c_int(), C.c_int()
+        self._ck(self.lib.ferrox_fe_planes(self.ctx, C.byref(lo), C.byref(hi)))
+        return lo.value, hi.value
+
+    def get_state_fe(self, P_fe_host=None, phi_host=None):
+        """Like get_state with P restricted to the film: [ncomp][fe_hi-fe_lo+1][ny][nx]."""
+        lo, hi = self.fe_planes()
+        P_fe_host = np.empty((self.ncomp, hi - lo + 1) + self.shape[1:]) if P_fe_host is None else P_fe_host
+        phi_host = np.empty(self.shape) if phi_host is None else phi_host
+        self._ck(self.lib.ferrox_get_state_fe(self.ctx, C.c_void_p(P_fe_host.ctypes.data),
+                                              C.c_void_p(phi_host.ctypes.data)))
+        return P_fe_host, phi_host
+
+    def set_state_fe(self, P_fe_host=None, phi_host=None):
+        """Asynchronous copy of the film's P and of phi (keep the arrays alive until the stream syncs)."""
+        self._keep = (P_fe_host, phi_host)
+        pp = C.c_void_p(P_fe_host.ctypes.data) if P_fe_host is not None else None
+        fp = C.c_void_p(phi_host.ctypes.data) if phi_host is not None else None
+        self._ck(self.lib.ferrox_set_state_fe(self.ctx, pp, fp))
 
     def profile_step(self):
         """One event-timed eager step: {kernel class: (total ms, launches)}."""

@@ -112,3 +112,29 @@ def test_direct_form_repeat_is_bit_identical_and_profile_matches():
         assert prof["resid"][1] >= 1 and prof["update"][1] == 0
         d.close()
     assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
+def test_film_state_copies_match_full_state():
+    """get_state_fe / set_state_fe move P of the ferroelectric film and phi; the
+    planes outside the film are zero, so a step from a film-only state equals the
+    step from the full state."""
+    from paper_2210_15668_gb300 import ferrox
+    geom = I.make_geometry(32, 32, I.mfim_stack(16))
+    P = I.random_polarization(geom, seed=41, amp=0.1)
+    d = _dev(geom, P, 0, tol=1e-12, v=(0.0, 0.7))
+    d.solve_poisson()
+    d.step(2)
+    lo, hi = d.fe_planes()
+    Pfe, phi_fe = d.get_state_fe()
+    Pf, phif = d.get_state()
+    assert np.array_equal(Pfe, Pf[:, lo:hi + 1]) and np.array_equal(phi_fe, phif)
+    assert not np.any(Pf[:, :lo]) and not np.any(Pf[:, hi + 1:])
+    d.step(3)
+    ref = d.get_state()
+    e = _dev(geom, np.zeros_like(P), 0, tol=1e-12, v=(0.0, 0.7))
+    e.set_state_fe(Pfe, phi_fe)
+    e.step(3)
+    out = e.get_state()
+    assert np.array_equal(out[0], ref[0]) and np.array_equal(out[1], ref[1])
+    d.close()
+    e.close()
