@@ -266,6 +266,10 @@ ferrox_status ferrox_batch_stats(ferrox_batch* b, ferrox_stats* out);
 /* The launch shape the autotuner chose (ESTATE before the first step). */
 ferrox_status ferrox_batch_tuning(const ferrox_batch* b, int* threads, int* rows_per_unit,
                                   int* blocks);
+/* CTA groups of the tuned launch: 1 when every CTA works on every instance
+ * behind one grid barrier; more when contiguous instance ranges run on their
+ * own CTAs behind their own barriers. */
+ferrox_status ferrox_batch_groups(const ferrox_batch* b, int* ngroups);
 ferrox_status ferrox_batch_destroy(ferrox_batch* b);
 
 /* Failure-detection check of the bounded device waits: a two-block launch in

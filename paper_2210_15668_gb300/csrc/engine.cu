@@ -1447,7 +1447,10 @@ struct ferrox_batch {
   int* pre = nullptr;
   double* partials = nullptr;
   int* active = nullptr;
-  GridBar* bar = nullptr;
+  GridBar* bar = nullptr;             // one per CTA group (n at most)
+  int* grp_d = nullptr;               // CTA prefix [n+1], then instance prefix [n+1]
+  int ngroups = 1;
+  bool grouped = false;
   int* status = nullptr;
   int* nsteps_d = nullptr;
   int* dbg = nullptr;
@@ -1468,7 +1471,7 @@ struct ferrox_batch {
 namespace {
 
 std::mutex g_tune_mu;
-struct TuneChoice { int threads, rows, bps; };
+struct TuneChoice { int threads, rows, bps, grouped; };
 std::vector<std::pair<std::string, TuneChoice>> g_tune_cache;
 
 ferrox_status bfail(ferrox_batch* b, ferrox_status s, const std::string& m) {
@@ -1514,6 +1517,7 @@ BatchArgs batch_args(ferrox_batch* B, int mode) {
   a.dense = B->dense;
   a.pre = B->pre; a.Ldown = B->Ldown; a.partials = B->partials; a.active = B->active;
   a.bar = B->bar; a.status = B->status; a.tol = B->num.tol; a.max_cycles = B->num.max_cycles;
+  a.grp_cta = B->grp_d; a.grp_inst = B->grp_d + (B->n + 1); a.ngroups = B->ngroups;
   a.nu1 = B->num.nu1; a.nu2 = B->num.nu2; a.rows_per_unit = B->rows_per_unit;
   a.any_full_tail = B->any_full_tail;
   a.dbg = B->dbg;
@@ -1526,7 +1530,65 @@ cudaError_t batch_launch(ferrox_batch* B, int mode, cudaStream_t s) {
                   : launch_batch<double>(a, B->blocks, B->threads, B->smem, s);
 }
 
-ferrox_status batch_configure(ferrox_batch* B, int threads, int R, int bps = 1) {
+// CTA groups.  grouped = false: one group, every CTA and instance.  grouped =
+// true: contiguous instance ranges of about cells / blocks cells each, and CTAs
+// shared out in proportion to their cells (at least one each), so instances of
+// different groups advance without waiting for each other at a barrier.
+void batch_groups(const ferrox_batch* B, int blocks, bool grouped, std::vector<int>& gcta,
+                  std::vector<int>& ginst) {
+  const int n = B->n;
+  gcta.assign(1, 0);
+  ginst.assign(1, 0);
+  if (!grouped || blocks < 2) {
+    gcta.push_back(blocks);
+    ginst.push_back(n);
+    return;
+  }
+  long long total = 0;
+  std::vector<long long> cells(n);
+  for (int i = 0; i < n; ++i) {
+    const ferrox_ctx& c = B->plans[i].c;
+    cells[i] = (long long)c.nx * c.ny * c.nz;
+    total += cells[i];
+  }
+  const double target = (double)total / blocks;
+  std::vector<long long> gcells;
+  long long acc = 0;
+  for (int i = 0; i < n; ++i) {
+    acc += cells[i];
+    if (acc >= target || i == n - 1) {
+      ginst.push_back(i + 1);
+      gcells.push_back(acc);
+      acc = 0;
+    }
+  }
+  while ((int)gcells.size() > blocks) {   // merge the last two groups
+    gcells[gcells.size() - 2] += gcells.back();
+    gcells.pop_back();
+    ginst.erase(ginst.end() - 2);
+  }
+  const int G = (int)gcells.size();
+  std::vector<int> k(G, 1);
+  std::vector<double> rem(G);
+  int left = blocks - G;
+  for (int q = 0; q < G; ++q) {
+    const double quota = (double)gcells[q] / total * blocks;
+    const int extra = std::max(0, std::min(left, (int)quota - 1));
+    k[q] += extra;
+    left -= extra;
+    rem[q] = quota - k[q];
+  }
+  while (left > 0) {   // largest remainder
+    int best = 0;
+    for (int q = 1; q < G; ++q) if (rem[q] > rem[best]) best = q;
+    k[best] += 1;
+    rem[best] -= 1.0;
+    --left;
+  }
+  for (int q = 0; q < G; ++q) gcta.push_back(gcta.back() + k[q]);
+}
+
+ferrox_status batch_configure(ferrox_batch* B, int threads, int R, int bps = 1, int grouped = 0) {
   int per_sm = 0;
   FX_BCK(B->mixed ? batch_occupancy<float>(threads, B->smem, &per_sm)
                   : batch_occupancy<double>(threads, B->smem, &per_sm));
@@ -1541,6 +1603,14 @@ ferrox_status batch_configure(ferrox_batch* B, int threads, int R, int bps = 1) 
   B->blocks = sms * std::min(bps, per_sm);
   const std::vector<int> pre = batch_prefix(B, R);
   FX_BCK(cudaMemcpy(B->pre, pre.data(), pre.size() * sizeof(int), cudaMemcpyHostToDevice));
+  std::vector<int> gcta, ginst;
+  batch_groups(B, B->blocks, grouped != 0, gcta, ginst);
+  B->grouped = grouped != 0;
+  B->ngroups = (int)gcta.size() - 1;
+  std::vector<int> g(2 * (B->n + 1), 0);
+  std::copy(gcta.begin(), gcta.end(), g.begin());
+  std::copy(ginst.begin(), ginst.end(), g.begin() + (B->n + 1));
+  FX_BCK(cudaMemcpy(B->grp_d, g.data(), g.size() * sizeof(int), cudaMemcpyHostToDevice));
   return FERROX_OK;
 }
 
@@ -1557,7 +1627,8 @@ ferrox_status batch_autotune(ferrox_batch* B) {
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     for (auto& kv : g_tune_cache)
-      if (kv.first == key) return batch_configure(B, kv.second.threads, kv.second.rows, kv.second.bps);
+      if (kv.first == key)
+        return batch_configure(B, kv.second.threads, kv.second.rows, kv.second.bps, kv.second.grouped);
   }
   const size_t bytes = (size_t)B->cells * sizeof(double);
   cudaStream_t s = B->stream;
@@ -1572,8 +1643,9 @@ ferrox_status batch_autotune(ferrox_batch* B) {
   FX_BCK(cudaEventCreate(&e0));
   FX_BCK(cudaEventCreate(&e1));
   float best = 1e30f;
-  int bt = 512, bR = 1, bB = 1;
+  int bt = 512, bR = 1, bB = 1, bG = 0;
   const int cand_t[2] = {256, 512}, cand_R[3] = {1, 2, 4}, cand_b[2] = {1, 2};
+  for (int gi = 0; gi < 2; ++gi)
   for (int bi = 0; bi < 2; ++bi)
   for (int ti = 0; ti < 2; ++ti)
     for (int ri = 0; ri < 3; ++ri) {
@@ -1581,7 +1653,7 @@ ferrox_status batch_autotune(ferrox_batch* B) {
       FX_BCK(B->mixed ? batch_occupancy<float>(cand_t[ti], B->smem, &per_sm)
                       : batch_occupancy<double>(cand_t[ti], B->smem, &per_sm));
       if (cand_b[bi] > per_sm) continue;
-      ferrox_status rc = batch_configure(B, cand_t[ti], cand_R[ri], cand_b[bi]);
+      ferrox_status rc = batch_configure(B, cand_t[ti], cand_R[ri], cand_b[bi], gi);
       if (rc != FERROX_OK) return rc;
       FX_BCK(cudaEventRecord(e0, s));
       FX_BCK(batch_launch(B, 0, s));
@@ -1592,7 +1664,7 @@ ferrox_status batch_autotune(ferrox_batch* B) {
       int gst = 0;
       FX_BCK(cudaMemcpy(&gst, B->status, sizeof(int), cudaMemcpyDeviceToHost));
       if (gst != 0) return bfail(B, (ferrox_status)gst, "batch kernel failed while tuning");
-      if (ms < best) { best = ms; bt = cand_t[ti]; bR = cand_R[ri]; bB = cand_b[bi]; }
+      if (ms < best) { best = ms; bt = cand_t[ti]; bR = cand_R[ri]; bB = cand_b[bi]; bG = gi; }
       FX_BCK(cudaMemcpyAsync(B->P, B->backup, bytes, cudaMemcpyDeviceToDevice, s));
       FX_BCK(cudaMemcpyAsync(B->phi, B->backup + B->cells, bytes, cudaMemcpyDeviceToDevice, s));
       FX_BCK(cudaMemcpyAsync(B->stats, st0.data(), B->n * sizeof(DevStats), cudaMemcpyHostToDevice, s));
@@ -1602,9 +1674,9 @@ ferrox_status batch_autotune(ferrox_batch* B) {
   cudaEventDestroy(e1);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune_cache.push_back({key, {bt, bR, bB}});
+    g_tune_cache.push_back({key, {bt, bR, bB, bG}});
   }
-  return batch_configure(B, bt, bR, bB);
+  return batch_configure(B, bt, bR, bB, bG);
 }
 
 ferrox_status batch_build_graphs(ferrox_batch* B) {
@@ -1634,7 +1706,7 @@ void batch_release(ferrox_batch* B) {
   if (B->gr_step) cudaGraphDestroy(B->gr_step);
   if (B->gr_solve) cudaGraphDestroy(B->gr_solve);
   void* ptrs[] = {B->b, B->Pbuf, B->backup, B->e, B->r, B->s, B->coef, B->dense, B->coef0, B->planes, B->lv,
-                  B->lvt, B->pre, B->partials, B->active, B->bar, B->status, B->nsteps_d, B->dbg, B->params,
+                  B->lvt, B->pre, B->partials, B->active, B->bar, B->grp_d, B->status, B->nsteps_d, B->dbg, B->params,
                   B->stats, B->inst, B->charge_part, B->charge_out};
   for (void* p : ptrs) if (p) cudaFree(p);
   if (B->host_pinned) cudaFreeHost(B->host_pinned);
@@ -1744,7 +1816,8 @@ ferrox_status ferrox_init_batch(ferrox_batch** out, int n, const ferrox_geometry
   FX_BINIT(cudaMalloc(&B->pre, (size_t)(1 + 2 * B->Ldown) * (n + 1) * sizeof(int)));
   FX_BINIT(cudaMalloc(&B->partials, (size_t)3 * B->nrows * sizeof(double)));
   FX_BINIT(cudaMalloc(&B->active, n * sizeof(int)));
-  FX_BINIT(cudaMalloc(&B->bar, sizeof(GridBar)));
+  FX_BINIT(cudaMalloc(&B->bar, (size_t)n * sizeof(GridBar)));
+  FX_BINIT(cudaMalloc(&B->grp_d, 2 * (size_t)(n + 1) * sizeof(int)));
   FX_BINIT(cudaMalloc(&B->status, sizeof(int)));
   FX_BINIT(cudaMalloc(&B->nsteps_d, sizeof(int)));
   FX_BINIT(cudaMalloc(&B->dbg, (8 + 1024) * sizeof(int)));
@@ -1831,7 +1904,7 @@ ferrox_status ferrox_init_batch(ferrox_batch** out, int n, const ferrox_geometry
   FX_BINIT(cudaMemset(B->e, 0, arena * tsz));
   FX_BINIT(cudaMemset(B->r, 0, arena * tsz));
   if (B->s) FX_BINIT(cudaMemset(B->s, 0, arena * tsz));
-  FX_BINIT(cudaMemset(B->bar, 0, sizeof(GridBar)));
+  FX_BINIT(cudaMemset(B->bar, 0, (size_t)n * sizeof(GridBar)));
   FX_BINIT(cudaMemset(B->status, 0, sizeof(int)));
   FX_BINIT(cudaMemset(B->stats, 0, n * sizeof(DevStats)));
   FX_BINIT(cudaMemset(B->params, 0, n * sizeof(DevParams)));
@@ -1950,6 +2023,12 @@ ferrox_status ferrox_batch_tuning(const ferrox_batch* B, int* threads, int* rows
   if (threads) *threads = B->threads;
   if (rows_per_unit) *rows_per_unit = B->rows_per_unit;
   if (blocks) *blocks = B->blocks;
+  return B->tuned ? FERROX_OK : FERROX_ESTATE;
+}
+
+ferrox_status ferrox_batch_groups(const ferrox_batch* B, int* ngroups) {
+  if (!B || !ngroups) return FERROX_EINVAL;
+  *ngroups = B->ngroups;
   return B->tuned ? FERROX_OK : FERROX_ESTATE;
 }
 

@@ -351,7 +351,11 @@ struct BatchArgs {
   int Ldown;            // deepest multi-block level count over instances
   double* partials;     // 3 per row unit
   int* active;          // per instance
-  GridBar* bar;
+  GridBar* bar;         // one barrier per CTA group
+  const int* grp_cta;   // CTA groups: group g owns CTAs [grp_cta[g], grp_cta[g+1]) ...
+  const int* grp_inst;  // ... and instances [grp_inst[g], grp_inst[g+1]); one group: the grid
+  int ngroups;
+  int pad3;
   int* status;          // global status (barrier time-out)
   double tol;
   int max_cycles, nu1, nu2, rows_per_unit, any_full_tail, pad;

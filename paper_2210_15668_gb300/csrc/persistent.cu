@@ -2,10 +2,12 @@
 // instances with uneven lateral sizes and biases) advanced by ONE cooperative
 // kernel launch.
 //
-// Every phase of the time step (TDGL update, FP64 residual, per-instance
-// convergence decision, each multigrid level's sweeps and transfers, the
-// shared-memory tail) runs over the work units of all instances at once; the
-// phases are separated by a grid barrier.  Each instance decides its own
+// The CTAs form groups, each owning a contiguous range of instances (one group
+// holding every instance and CTA is the plain grid form).  Every phase of the
+// time step (TDGL update, FP64 residual, per-instance convergence decision, each
+// multigrid level's sweeps and transfers, the shared-memory tail) runs over the
+// work units of the group's instances; the phases are separated by the group's
+// barrier, so groups advance independently.  Each instance decides its own
 // convergence and drops out of the remaining cycles when done.  Work units are
 // rows (or `rows_per_unit` consecutive rows) of one plane of one instance,
 // handled by one warp whose lanes run along x; the unit -> instance map is a
@@ -42,15 +44,16 @@ __device__ __forceinline__ void st_release(unsigned int* p, unsigned int v) {
 
 // Grid-wide barrier with a time limit.  Returns false (and records the status)
 // when the wait ran out or another block has already aborted.
-__device__ bool grid_barrier(GridBar* gb, int* status, long long limit = kBarrierSpinCycles,
-                             int* dbg = nullptr, int nbar = 0) {
+__device__ bool grid_barrier(GridBar* gb, int* status, unsigned int nblocks,
+                             long long limit = kBarrierSpinCycles, int* dbg = nullptr,
+                             int nbar = 0) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     ok = 1;
     __threadfence();
     const unsigned int gen = ld_acquire(&gb->gen);
-    if (atom_add_acq_rel(&gb->count, 1u) == gridDim.x - 1) {
+    if (atom_add_acq_rel(&gb->count, 1u) == nblocks - 1) {
       gb->count = 0;
       st_release(&gb->gen, gen + 1);
     } else {
@@ -97,11 +100,15 @@ __device__ __forceinline__ double wsum(double v) {
   return v;
 }
 
+// A CTA group advances its own instances [i_lo, i_hi) with its own barrier; the
+// warps of the group (gwarp of nwarps) share each phase's work units.
 template <typename T>
 struct Ctx {
   const BatchArgs& A;
   MGArgs<T> mg;
   int lane, gwarp, nwarps;
+  int i_lo, i_hi;       // the group's instances
+  int grank, ncta;      // this CTA's rank in the group, the group's CTAs
 };
 
 // ---- phases -----------------------------------------------------------------------------
@@ -111,8 +118,8 @@ template <typename T>
 __device__ void phase_tdgl(const Ctx<T>& c, int mode) {
   const BatchArgs& A = c.A;
   const int* pre = A.pre;   // space 0: rows
-  const int total = pre[A.ninst];
-  for (int u = c.gwarp; u < total; u += c.nwarps) {
+  const int total = pre[c.i_hi];
+  for (int u = pre[c.i_lo] + c.gwarp; u < total; u += c.nwarps) {
     const int i = find_inst(pre, A.ninst, u);
     const BatchInst I = ldg_struct(A.inst + i);
     TDGLArgs t = I.tdgl;
@@ -127,8 +134,8 @@ template <typename T>
 __device__ void phase_resid(const Ctx<T>& c, int first, int copy_back) {
   const BatchArgs& A = c.A;
   const int* pre = A.pre;
-  const int total = pre[A.ninst];
-  for (int u = c.gwarp; u < total; u += c.nwarps) {
+  const int total = pre[c.i_hi];
+  for (int u = pre[c.i_lo] + c.gwarp; u < total; u += c.nwarps) {
     const int i = find_inst(pre, A.ninst, u);
     if (!ld_flag(A.active + i)) continue;
     const BatchInst I = ldg_struct(A.inst + i);
@@ -159,7 +166,7 @@ __device__ void phase_resid(const Ctx<T>& c, int first, int copy_back) {
 template <typename T>
 __device__ void phase_decide(const Ctx<T>& c, int first) {
   const BatchArgs& A = c.A;
-  for (int i = c.gwarp; i < A.ninst; i += c.nwarps) {
+  for (int i = c.i_lo + c.gwarp; i < c.i_hi; i += c.nwarps) {
     if (!ld_flag(A.active + i)) continue;
     double sr = 0.0, sb = 0.0, sq = 0.0;
     for (int u = A.pre[i] + c.lane; u < A.pre[i + 1]; u += 32) {
@@ -180,9 +187,9 @@ template <typename T>
 __device__ void phase_smooth(const Ctx<T>& c, int l, int color, int zero_init, int fuse_update) {
   const BatchArgs& A = c.A;
   const int* pre = A.pre + (1 + l) * (A.ninst + 1);
-  const int total = pre[A.ninst];
+  const int total = pre[c.i_hi];
   const int R = A.rows_per_unit;
-  for (int u = c.gwarp; u < total; u += c.nwarps) {
+  for (int u = pre[c.i_lo] + c.gwarp; u < total; u += c.nwarps) {
     const int i = find_inst(pre, A.ninst, u);
     if (!ld_flag(A.active + i)) continue;
     const BatchInst I = ldg_struct(A.inst + i);
@@ -203,9 +210,9 @@ template <typename T>
 __device__ void phase_transfer(const Ctx<T>& c, int l, int op) {
   const BatchArgs& A = c.A;
   const int* pre = A.pre + (1 + A.Ldown + l) * (A.ninst + 1);
-  const int total = pre[A.ninst];
+  const int total = pre[c.i_hi];
   const int R = A.rows_per_unit;
-  for (int u = c.gwarp; u < total; u += c.nwarps) {
+  for (int u = pre[c.i_lo] + c.gwarp; u < total; u += c.nwarps) {
     const int i = find_inst(pre, A.ninst, u);
     if (!ld_flag(A.active + i)) continue;
     const BatchInst I = ldg_struct(A.inst + i);
@@ -225,7 +232,7 @@ __device__ void phase_transfer(const Ctx<T>& c, int l, int op) {
 template <typename T>
 __device__ void phase_tail(const Ctx<T>& c, unsigned char* smem) {
   const BatchArgs& A = c.A;
-  for (int i = blockIdx.x; i < A.ninst; i += gridDim.x) {
+  for (int i = c.i_lo + c.grank; i < c.i_hi; i += c.ncta) {
     if (!ld_flag(A.active + i)) continue;
     const BatchInst I = ldg_struct(A.inst + i);
     TailArgs t{A.lvt + I.lvt_off, I.nlev_tail, I.tail_elems, I.tail_base, A.nu1, A.nu2,
@@ -241,8 +248,8 @@ template <typename T>
 __device__ void phase_update(const Ctx<T>& c) {
   const BatchArgs& A = c.A;
   const int* pre = A.pre;
-  const int total = pre[A.ninst];
-  for (int u = c.gwarp; u < total; u += c.nwarps) {
+  const int total = pre[c.i_hi];
+  for (int u = pre[c.i_lo] + c.gwarp; u < total; u += c.nwarps) {
     const int i = find_inst(pre, A.ninst, u);
     const BatchInst I = ldg_struct(A.inst + i);
     if (!ld_flag(A.active + i) || I.tail_first != 0) continue;
@@ -267,24 +274,31 @@ __global__ void __launch_bounds__(512, 1) batch_kernel(BatchArgs A) {
   mg.coef = static_cast<const PlaneCoef<T>*>(A.coef);
   mg.lv = A.lv;
   const int lane = threadIdx.x & 31;
-  const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  const Ctx<T> c{A, mg, lane, gwarp, nwarps};
+  // this CTA's group: its CTAs, instances and barrier
+  const int g = find_inst(A.grp_cta, A.ngroups, (int)blockIdx.x);
+  const int cta_lo = A.grp_cta[g], ncta = A.grp_cta[g + 1] - cta_lo;
+  const int grank = (int)blockIdx.x - cta_lo;
+  GridBar* gbar = A.bar + g;
+  const int gwarp = (grank * (int)blockDim.x + (int)threadIdx.x) >> 5;
+  const int nwarps = (ncta * (int)blockDim.x) >> 5;
+  const Ctx<T> c{A, mg, lane, gwarp, nwarps, A.grp_inst[g], A.grp_inst[g + 1], grank, ncta};
   const int nsteps = A.mode == 1 ? 1 : *A.nsteps;
   int nbar = 0;
 #define FX_BAR()                                                                    \
   do {                                                                              \
     ++nbar;                                                                         \
-    if (!grid_barrier(A.bar, A.status, kBarrierSpinCycles, A.dbg, nbar)) {          \
+    if (!grid_barrier(gbar, A.status, (unsigned)ncta, kBarrierSpinCycles, A.dbg, nbar)) { \
       if (A.dbg && threadIdx.x == 0) A.dbg[8 + blockIdx.x] = -nbar;                 \
       return;                                                                       \
     }                                                                               \
   } while (0)
   for (int step = 0; step < nsteps; ++step) {
-    // every instance takes part in the step; the barrier before the reset keeps
-    // it from racing with slower blocks still reading the previous step's flags
+    // every instance of the group takes part in the step; the barrier before the
+    // reset keeps it from racing with slower blocks still reading the previous
+    // step's flags
     if (step > 0) FX_BAR();
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.ninst; i += gridDim.x * blockDim.x)
+    for (int i = c.i_lo + grank * (int)blockDim.x + (int)threadIdx.x; i < c.i_hi;
+         i += ncta * (int)blockDim.x)
       A.active[i] = 1;
     FX_BAR();
     phase_tdgl(c, A.mode == 1 ? 3 : 0);          // Step 1a (or the RHS of the current P)
@@ -295,7 +309,7 @@ __global__ void __launch_bounds__(512, 1) batch_kernel(BatchArgs A) {
       phase_decide(c, cyc == 0);
       FX_BAR();
       int any = 0;
-      for (int i = 0; i < A.ninst; ++i) any |= ld_flag(A.active + i);
+      for (int i = c.i_lo; i < c.i_hi; ++i) any |= ld_flag(A.active + i);
       if (!any) break;
       // one V-cycle on the active instances
       for (int l = 0; l < A.Ldown; ++l) {
@@ -325,8 +339,9 @@ __global__ void __launch_bounds__(512, 1) batch_kernel(BatchArgs A) {
         FX_BAR();
       }
     }
-    if (A.mode == 0 && blockIdx.x == 0)
-      for (int i = threadIdx.x; i < A.ninst; i += blockDim.x) A.inst[i].resid.stats->steps += 1;
+    if (A.mode == 0 && grank == 0)
+      for (int i = c.i_lo + (int)threadIdx.x; i < c.i_hi; i += blockDim.x)
+        A.inst[i].resid.stats->steps += 1;
   }
   if (A.dbg && threadIdx.x == 0) A.dbg[8 + blockIdx.x] = nbar;
 #undef FX_BAR
@@ -336,7 +351,7 @@ __global__ void __launch_bounds__(512, 1) batch_kernel(BatchArgs A) {
 // must run out and record FERROX_ETIMEOUT.
 __global__ void barrier_timeout_kernel(GridBar* gb, int* status, long long limit) {
   if (blockIdx.x == 1) return;
-  grid_barrier(gb, status, limit);
+  grid_barrier(gb, status, gridDim.x, limit);
 }
 
 }  // namespace
