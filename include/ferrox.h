@@ -270,6 +270,12 @@ ferrox_status ferrox_batch_tuning(const ferrox_batch* b, int* threads, int* rows
  * behind one grid barrier; more when contiguous instance ranges run on their
  * own CTAs behind their own barriers. */
 ferrox_status ferrox_batch_groups(const ferrox_batch* b, int* ngroups);
+/* Fix the launch shape instead of autotuning it: threads per CTA (256 or 512),
+ * rows per work unit (1, 2 or 4), CTAs per SM (1 .. what fits) and grouped (0:
+ * one grid barrier over every instance; 1: CTA groups with their own barriers).
+ * Every shape computes the same results; only the speed differs. */
+ferrox_status ferrox_batch_set_shape(ferrox_batch* b, int threads, int rows_per_unit,
+                                     int ctas_per_sm, int grouped);
 ferrox_status ferrox_batch_destroy(ferrox_batch* b);
 
 /* Failure-detection check of the bounded device waits: a two-block launch in

@@ -2026,6 +2026,30 @@ ferrox_status ferrox_batch_tuning(const ferrox_batch* B, int* threads, int* rows
   return B->tuned ? FERROX_OK : FERROX_ESTATE;
 }
 
+ferrox_status ferrox_batch_set_shape(ferrox_batch* B, int threads, int rows_per_unit,
+                                     int ctas_per_sm, int grouped) {
+  if (!B) return bfail(nullptr, FERROX_EINVAL, "null batch");
+  if ((threads != 256 && threads != 512) ||
+      (rows_per_unit != 1 && rows_per_unit != 2 && rows_per_unit != 4) || ctas_per_sm < 1 ||
+      (grouped != 0 && grouped != 1))
+    return bfail(B, FERROX_EINVAL, "bad launch shape");
+  int per_sm = 0;
+  FX_BCK(B->mixed ? batch_occupancy<float>(threads, B->smem, &per_sm)
+                  : batch_occupancy<double>(threads, B->smem, &per_sm));
+  if (ctas_per_sm > per_sm) return bfail(B, FERROX_EINVAL, "that many CTAs per SM do not fit");
+  FX_BCK(cudaStreamSynchronize(B->stream));
+  ferrox_status rc = batch_configure(B, threads, rows_per_unit, ctas_per_sm, grouped);
+  if (rc != FERROX_OK) return rc;
+  if (B->ge_step) { cudaGraphExecDestroy(B->ge_step); B->ge_step = nullptr; }
+  if (B->ge_solve) { cudaGraphExecDestroy(B->ge_solve); B->ge_solve = nullptr; }
+  if (B->gr_step) { cudaGraphDestroy(B->gr_step); B->gr_step = nullptr; }
+  if (B->gr_solve) { cudaGraphDestroy(B->gr_solve); B->gr_solve = nullptr; }
+  rc = batch_build_graphs(B);
+  if (rc != FERROX_OK) return rc;
+  B->tuned = true;
+  return FERROX_OK;
+}
+
 ferrox_status ferrox_batch_groups(const ferrox_batch* B, int* ngroups) {
   if (!B || !ngroups) return FERROX_EINVAL;
   *ngroups = B->ngroups;

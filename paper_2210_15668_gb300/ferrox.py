@@ -61,7 +61,7 @@ EXPORTS = ["ferrox_init_geometry", "ferrox_set_bias", "ferrox_solve_poisson", "f
            "ferrox_level_shape", "ferrox_profile_step", "ferrox_tdgl_update_static",
            "ferrox_init_batch", "ferrox_batch_set_bias", "ferrox_batch_solve_poisson",
            "ferrox_batch_step", "ferrox_batch_charge", "ferrox_batch_stats", "ferrox_batch_tuning",
-           "ferrox_batch_groups",
+           "ferrox_batch_groups", "ferrox_batch_set_shape",
            "ferrox_batch_destroy", "ferrox_batch_last_error", "ferrox_check_wait_timeout",
            "ferrox_carrier_exp",
            "ferrox_nn_create", "ferrox_nn_forward", "ferrox_nn_loss_grad", "ferrox_nn_params",
@@ -112,6 +112,7 @@ def load(path: str = LIB_PATH):
     lib.ferrox_batch_stats.argtypes = [vp, C.POINTER(Stats)]
     lib.ferrox_batch_tuning.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
     lib.ferrox_batch_groups.argtypes = [vp, C.POINTER(C.c_int)]
+    lib.ferrox_batch_set_shape.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int]
     lib.ferrox_batch_destroy.argtypes = [vp]
     lib.ferrox_batch_last_error.argtypes = [vp]
     lib.ferrox_batch_last_error.restype = C.c_char_p
@@ -368,6 +369,11 @@ class Batch:
         self.lib.ferrox_batch_groups(self.ctx, C.byref(g))
         return dict(threads=t.value, rows_per_unit=r.value, blocks=b.value, groups=g.value,
                     tuned=rc == FERROX_OK)
+
+    def set_shape(self, threads, rows_per_unit, ctas_per_sm, grouped):
+        """Fix the launch shape instead of autotuning it (same results, other speed)."""
+        self._ck(self.lib.ferrox_batch_set_shape(self.ctx, int(threads), int(rows_per_unit),
+                                                 int(ctas_per_sm), int(grouped)))
 
     def state(self, i):
         """(P, phi) of instance i as numpy arrays (synchronises)."""

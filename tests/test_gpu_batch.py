@@ -106,3 +106,28 @@ def test_bounded_wait_reports_timeout():
     d.solve_poisson()
     assert d.stats()["status"] == 0
     d.close()
+
+
+def test_launch_shapes_give_identical_results():
+    """Grouped and single-barrier launches, any thread count and work-unit size:
+    the same operations per instance in the same order, so bit-identical states
+    and equal cycle counts."""
+    from paper_2210_15668_gb300 import ferrox
+    geoms, P0s, biases = small_batch(n=6, seed=11)
+    num = ferrox.make_numerics(4e-13, tol=1e-10, precision=1)
+    outs = []
+    for shape in ((256, 1, 2, 1), (512, 4, 1, 0), (256, 2, 1, 1)):
+        B = ferrox.Batch(geoms, P0s, num)
+        B.set_shape(*shape)
+        B.set_bias(np.zeros(len(geoms)), biases)
+        B.solve_poisson()
+        B.step(5)
+        st = B.stats()
+        assert all(x["status"] == 0 for x in st)
+        assert B.tuning()["groups"] >= (2 if shape[3] else 1)
+        outs.append(([B.state(i) for i in range(len(geoms))], [x["cycles"] for x in st]))
+        B.close()
+    for states, cycles in outs[1:]:
+        assert cycles == outs[0][1]
+        for (P, phi), (P0, phi0) in zip(states, outs[0][0]):
+            assert np.array_equal(P, P0) and np.array_equal(phi, phi0)
