@@ -491,12 +491,19 @@ void launch_restrict_check(const MGArgs<double>& fa, double* rc, const LevelDesc
            black_residual_zero(F, nu1), ck);
 }
 
+// Latency-bound FP32 levels: the per-thread chains of the one-thread-per-coarse-
+// cell transfers dominate up to this size.  Measured on 256x256x32, 500 steps
+// (Mcell-steps/s, mixed / fast form): none 1781 / 2735, up to 4096 cells
+// 1799 / 2761, up to 32768 cells 1804 / 2775; larger FP32 levels lose.  FP64
+// levels use the split kernels at every size (+2.2% FP64).
+constexpr long long kSmallTransfer = 32768;
+
 template <typename T>
 void launch_restrict(const MGArgs<T>& a, const LevelDesc& F, const LevelDesc& C, int nu1,
                      cudaStream_t s) {
-  if (sizeof(T) == sizeof(double)) {
-    // FP64: four threads per coarse cell (FP64 latency bounds the small levels;
-    // measured +0.4% FP64, -2.6% in the FP32 form, which keeps one thread)
+  if (sizeof(T) == sizeof(double) || C.ncell <= kSmallTransfer) {
+    // four threads per coarse cell where latency bounds the restriction: FP64
+    // levels, and FP32 levels up to kSmallTransfer coarse cells
     const long long threads = 4 * C.ncell;
     launch_k(restrict4_kernel<T>, dim3((unsigned)((threads + 255) / 256)), dim3(256), 0, s, a, F, C,
              black_residual_zero(F, nu1));
@@ -515,10 +522,10 @@ void launch_prolong(const MGArgs<T>& a, const LevelDesc& F, const LevelDesc& C, 
     launch_k(prolong_tiled_kernel<T>, grid, dim3(kPX, kPY), 0, s, a, F, C, fine);
     return;
   }
-  if (sizeof(T) == sizeof(double)) {
-    // FP64: one thread per fine cell, a 15-operation chain instead of 84 per
-    // coarse cell (measured +1.8% FP64, -2.9% in the FP32 form, which keeps the
-    // per-coarse-cell kernel)
+  if (sizeof(T) == sizeof(double) || F.ncell <= kSmallTransfer) {
+    // one thread per fine cell, a 15-operation chain instead of 84 per coarse
+    // cell, where latency bounds the prolongation: FP64 levels, and FP32 levels
+    // up to kSmallTransfer fine cells
     dim3 block, grid;
     block_shape(F.nx, F.ny, block, grid, F.nz, spread_threads(F.ncell));
     launch_k(prolong_fine_kernel<T>, grid, block, 0, s, a, F, C, constant);
