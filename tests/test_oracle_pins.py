@@ -476,3 +476,127 @@ def test_workload_parameters_match_the_paper_table():
     assert I.de_layer(4)["eps_r"] == t["eps_sio2"] and I.de_layer(4, 10.0)["eps_r"] == t["eps_al2o3"]
     assert I.sc_layer(4)["eps_r"] == t["eps_sc"]
     assert I.H_DEFAULT == t["h"] and I.LAMBDA_DEFAULT == t["lambda"] and I.DT_DEFAULT == t["dt"]
+
+
+# ------------------------------------------- in-plane terms of the 3-component model ---
+#
+# A single lateral Fourier mode of P_x (or P_y) in a shorted all-ferroelectric stack
+# has a bound charge -dP_x/dx and a potential known in closed form, both for the
+# continuum problem and for the discrete finite-volume operator.  These pin the
+# in-plane bound charge of the right-hand side (sign, face average) and the in-plane
+# field that drives P_x (sign, face potentials), which laterally uniform cases leave
+# untouched.
+
+def _in_plane_stack(nx, ny, nz, h, eps_r=24.0):
+    fe = I.fe_layer(nz, g=0.0, alpha=0.0, beta=0.0, gamma=0.0,
+                    alpha_xy=0.0, beta_xy=0.0, gamma_xy=0.0, eps_r=eps_r)
+    return I.make_geometry(nx, ny, [fe], h=h, pbc=I.PBC_FREE, ncomp=3)
+
+
+def _mode_P(g, comp, A, m):
+    """P_comp = A sin(theta (i + 1/2)) along x (comp 0) or y (comp 1), theta = 2 pi m / n."""
+    nz = I.nz_of(g)
+    P = np.zeros((3, nz, g["ny"], g["nx"]))
+    n = g["nx"] if comp == 0 else g["ny"]
+    th = 2.0 * np.pi * m / n
+    wave = A * np.sin(th * (np.arange(n) + 0.5))
+    P[comp] = wave[None, None, :] if comp == 0 else wave[None, :, None]
+    return P, th
+
+
+@pytest.mark.parametrize("comp,m", [(0, 1), (0, 3), (1, 2)])
+def test_in_plane_mode_exact_discrete_potential(comp, m):
+    """P_x = A sin(theta (i+1/2)) gives the face-averaged bound charge
+    b_i = -A sin(theta) cos(theta (i+1/2))/h, and the discrete operator maps
+    cos(theta (i+1/2)) g_k onto itself with lateral eigenvalue eps (2-2cos theta)/h^2.
+    The z profile then solves a constant-coefficient recurrence, closed form:
+        g_k = G + C cosh(mu (k - (N-1)/2)),  cosh mu = 2 - cos theta,
+        G = s/(eps lambda),  s = -A sin(theta)/h,  lambda = (2 - 2cos theta)/h^2,
+    with C from the half-cell electrode face (coupling 2 eps/h^2, V = 0)."""
+    h, nz, A = 0.5e-9, 8, 0.07
+    nx, ny = (16, 2) if comp == 0 else (2, 12)
+    g = _in_plane_stack(nx, ny, nz, h)
+    pl = oracle.planes(g)
+    P, th = _mode_P(g, comp, A, m)
+    eps = pl["eps"][0]
+    # right-hand side: bound charge of the in-plane mode only
+    b = poisson.rhs(P, pl, h, 0.0, 0.0)
+    n = nx if comp == 0 else ny
+    c = np.cos(th * (np.arange(n) + 0.5))
+    lateral = c[None, None, :] if comp == 0 else c[None, :, None]
+    s = -A * np.sin(th) / h
+    assert np.abs(b - s * lateral * np.ones_like(b)).max() <= 1e-12 * abs(s)
+    # potential: exact discrete closed form
+    lam = (2.0 - 2.0 * np.cos(th)) / h ** 2
+    mu = np.arccosh(2.0 - np.cos(th))
+    G = s / (eps * lam)
+    mid = 0.5 * (nz - 1)
+    c0, c1 = np.cosh(mu * mid), np.cosh(mu * (mid - 1.0))
+    C = -(2.0 * eps / h ** 2) * G / (eps * lam * c0 + (2.0 * eps / h ** 2) * c0 + (eps / h ** 2) * (c0 - c1))
+    gk = G + C * np.cosh(mu * (np.arange(nz) - mid))
+    phi_exact = gk[:, None, None] * lateral
+    phi = poisson.solve_linear(P, pl, h, 0.0, 0.0)
+    assert np.abs(phi - phi_exact).max() <= 1e-11 * np.abs(phi_exact).max()
+
+
+@pytest.mark.parametrize("comp", [0, 1])
+def test_in_plane_depolarising_force_second_order(comp):
+    """Continuum: P_x = A sin(kx) in a shorted film of thickness Lz (eps uniform) gives
+    Phi = -(A/(eps k)) cos(kx) u(z), u = 1 - cosh(k(z - Lz/2))/cosh(k Lz/2), so with
+    the Landau and gradient terms off the TDGL force on P_x is
+        f_x = -Gamma dPhi/dx = -Gamma (A/eps) sin(kx) u(z)
+    (a depolarising force against P_x).  The oracle's force converges to it at second
+    order; a flipped sign of the bound charge or of the field coupling fails at once."""
+    A, L = 0.05, 8e-9
+    errs = []
+    for n in (32, 64, 128):
+        h = L / n
+        nz = n // 2
+        nx, ny = (n, 2) if comp == 0 else (2, n)
+        g = _in_plane_stack(nx, ny, nz, h)
+        pl = oracle.planes(g)
+        P, _ = _mode_P(g, comp, A, 1)
+        phi = poisson.solve_linear(P, pl, h, 0.0, 0.0)
+        f = tdgl.force(P, phi, pl, g, 0.0, 0.0)
+        eps, Gam = pl["eps"][0], pl["Gamma"][0]
+        k = 2.0 * np.pi / L
+        xc = (np.arange(n) + 0.5) * h
+        zc = (np.arange(nz) + 0.5) * h
+        Lz = nz * h
+        u = 1.0 - np.cosh(k * (zc - 0.5 * Lz)) / np.cosh(0.5 * k * Lz)
+        s = np.sin(k * xc)
+        lateral = s[None, None, :] if comp == 0 else s[None, :, None]
+        f_exact = -Gam * (A / eps) * u[:, None, None] * lateral
+        phi_exact = -(A / (eps * k)) * u[:, None, None] * (np.cos(k * xc)[None, None, :] if comp == 0
+                                                          else np.cos(k * xc)[None, :, None])
+        errs.append((np.abs(f[comp] - f_exact).max() / np.abs(f_exact).max(),
+                     np.abs(phi - phi_exact).max() / np.abs(phi_exact).max()))
+        # no field along the uniform lateral direction (P_z is driven by dPhi/dz, which
+        # the electrodes make nonzero)
+        assert np.all(f[1 - comp] == 0.0)
+    # the half-cell electrode closure leaves the coarsest grids slightly pre-asymptotic
+    for q in range(2):
+        assert errs[0][q] < 0.03
+        for a, b in zip(errs, errs[1:]):
+            assert 1.75 < math.log2(a[q] / b[q]) < 2.1, errs
+
+
+@pytest.mark.parametrize("comp", [0, 1])
+def test_in_plane_nyquist_mode_zero_displacement(comp):
+    """P_x = A (-1)^i: the face averages of P_x vanish, so there is no bound charge and
+    Phi = 0 at the cell centres.  With D_x = -eps dPhi/dx + P_x equal to the face flux
+    (zero) in every half-cell, the field inside each cell is E_x = -P_x/eps, and the
+    TDGL force (Landau and gradient off) is f_x = Gamma E_x = -Gamma P_x/eps."""
+    h, nz, A = 0.5e-9, 6, 0.03
+    nx, ny = (8, 2) if comp == 0 else (2, 10)
+    g = _in_plane_stack(nx, ny, nz, h)
+    pl = oracle.planes(g)
+    P, _ = _mode_P(g, comp, A, (nx if comp == 0 else ny) // 2)
+    # sin(pi (i + 1/2)) = (-1)^i
+    alt = (-1.0) ** np.arange(nx if comp == 0 else ny)
+    assert np.abs(P[comp] - A * (alt[None, None, :] if comp == 0 else alt[None, :, None])).max() < 1e-15
+    phi = poisson.solve_linear(P, pl, h, 0.0, 0.0)
+    assert np.abs(phi).max() <= 1e-25
+    f = tdgl.force(P, phi, pl, g, 0.0, 0.0)
+    eps, Gam = pl["eps"][0], pl["Gamma"][0]
+    assert np.abs(f[comp] + Gam * P[comp] / eps).max() <= 1e-13 * Gam * A / eps
