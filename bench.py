@@ -82,6 +82,17 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
+def measured_traffic(precision, kernel):
+    """DRAM bytes per launch from an ncu capture of the current source, else None."""
+    tpath = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(tpath):
+        return None
+    tj = json.load(open(tpath))
+    if tj.get("source_hash") != source_hash():
+        return None
+    return tj.get("per_launch_bytes", {}).get(f"{precision}:{kernel}")
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle sampling while the timed region runs."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -152,6 +163,27 @@ def kernel_work(kind, cells, fe_cells, dyn_cells, tsz):
     if kind == "copy":
         return fe_cells * 16, 0.0
     return None, None
+
+
+def class_rooflines(prof, hbm_peak, fp64_classes=()):
+    """Per kernel class of one eager, event-timed step: time, launches, algorithmic
+    bytes (from the library's own per-launch count), effective GB/s and fraction of
+    the measured HBM peak; plus the whole step (sum over classes)."""
+    out = {}
+    tb = tm = 0.0
+    for k, (ms, n, by) in prof.items():
+        if not n:
+            continue
+        gbs = by / (ms / 1e3) / 1e9 if ms > 0 else None
+        out[k] = {"ms": round(ms, 4), "launches": n, "bytes": by,
+                  "gbs": gbs, "hbm_frac": gbs / hbm_peak if gbs else None}
+        if k in fp64_classes:
+            out[k]["bound"] = "alu (FP64 pipe)"
+        tb += by
+        tm += ms
+    whole = {"bytes": tb, "eager_ms": tm, "gbs": tb / (tm / 1e3) / 1e9 if tm else None}
+    whole["hbm_frac"] = whole["gbs"] / hbm_peak if whole["gbs"] else None
+    return out, whole
 
 
 # -------------------------------------------------------------------- workloads -------
@@ -260,26 +292,30 @@ def run_ours(args, ws, rank, local):
     launches = st1["launches"] - st0["launches"]
 
     # per-kernel breakdown of one step (eager, event-timed) -> roofline of the dominant kernel
-    prof = dev.profile_step()
+    sp0 = dev.stats()
+    prof = dev.profile_step(with_bytes=True)
+    sp1 = dev.stats()
     tsz = 4 if prec_main == ferrox.MIXED else 8
-    modeled = [k for k in prof if prof[k][1] and kernel_work(k, 1, 1, 1, 8)[0] is not None]
+    modeled = [k for k in prof if prof[k][1] and prof[k][2] > 0]
     dom = max(modeled, key=lambda k: prof[k][0])
-    dom_ms, dom_n = prof[dom]
+    dom_ms, dom_n, dom_bytes = prof[dom]
     step_ms = sum(v[0] for v in prof.values())
     peaks, peak_src = measured_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
-    by, fl = kernel_work(dom, cells, fe_cells, dyn_cells, tsz)
+    by = dom_bytes / max(dom_n, 1)
+    _, fl = kernel_work(dom, cells, fe_cells, dyn_cells, tsz)
     avg_s = dom_ms / max(dom_n, 1) / 1e3
     gbs = by / avg_s / 1e9 if by else None
     tfl = fl / avg_s / 1e12 if fl else None
     fp64_kernel = prec_main != ferrox.MIXED or dom in ("resid", "tdgl", "update")
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "ncu_traffic.json")
-    if os.path.exists(tpath):
-        tj = json.load(open(tpath))
-        if tj.get("source_hash") == source_hash():
-            traffic = tj.get("per_launch_bytes", {}).get(f"{args.precision}:{dom}")
+    traffic = measured_traffic(args.precision, dom)
     share = dom_ms / step_ms if step_ms else None
+    fp64_classes = (("tdgl", "resid", "update") if prec_main == ferrox.MIXED else
+                    ("tdgl", "resid", "update", "smooth_fine", "smooth_coarse", "restrict", "prolong", "tail"))
+    classes, whole = class_rooflines(prof, hbm_peak, fp64_classes)
+    whole["graph_ms_per_step"] = t_max / K
+    whole["vcycles_profiled_step"] = sp1["vcycles"] - sp0["vcycles"]
+    whole["vcycles_per_timed_step"] = vcycles_per_step
     if fp64_kernel:
         units = {"smooth_fine": 0.5 * cells, "resid": cells, "tdgl": fe_cells, "restrict": cells,
                  "prolong": cells}.get(dom, cells)
@@ -289,12 +325,14 @@ def run_ours(args, ws, rank, local):
                 "kernel": dom, "peak_source": "derived: 152 SMs x 2 FP64 instr/clk x 2.07 GHz",
                 "work": f"{FP64_INSTR.get(dom, 0.0)} FP64 instructions per unit",
                 "flop_view": {"achieved_tflops": tfl, "peak_tflops": FP64_PEAK_TFLOPS},
-                "hbm_view": {"achieved_gbs": gbs, "peak_gbs": hbm_peak,
+                "hbm_view": {"achieved_gbs": gbs, "peak_gbs": hbm_peak, "algorithmic_bytes_per_launch": by,
                              "frac": gbs / hbm_peak if gbs else None, "peak_source": peak_src}}
     else:
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "share_of_step": share,
                 "frac": gbs / hbm_peak if gbs else None, "traffic": traffic, "kernel": dom,
-                "peak_source": peak_src}
+                "algorithmic_bytes_per_launch": by, "peak_source": peak_src}
+    roof["classes"] = classes
+    roof["whole_step"] = whole
     breakdown = {k: {"ms": round(v[0], 4), "launches": v[1]} for k, v in prof.items() if v[1]}
     dev.close()
 
@@ -306,11 +344,12 @@ def run_ours(args, ws, rank, local):
         t2, s20, s21, _ = timed_run(d2, K, args.warmup)
         t2 = reduce_max(t2, ws)
         v2 = ws * cells * K / (t2 / 1e3) / 1e6
-        prof2 = d2.profile_step()
+        prof2 = d2.profile_step(with_bytes=True)
+        cl2, wh2 = class_rooflines(prof2, hbm_peak, ("tdgl", "resid", "update"))
+        wh2["graph_ms_per_step"] = t2 / K
         other = {"precision": "fp64" if prec_o == ferrox.FP64 else "mixed", "value": v2,
                  "ms_per_step": t2 / K, "vcycles_per_step": (s21["vcycles"] - s20["vcycles"]) / K,
-                 "kernel_breakdown_ms_one_step": {k: {"ms": round(v[0], 4), "launches": v[1]}
-                                                  for k, v in prof2.items() if v[1]}}
+                 "roofline_classes": cl2, "whole_step": wh2}
         d2.close()
     # the GB300-native fast form: FP32 multigrid in FP64 defect correction, an
     # extrapolated initial guess and FAST_INNER V-cycles per FP64 residual (same
@@ -327,14 +366,19 @@ def run_ours(args, ws, rank, local):
         d4 = make_fast()
         t4, s40, s41, _ = timed_run(d4, K, args.warmup)
         t4 = reduce_max(t4, ws)
+        prof4 = d4.profile_step(with_bytes=True)
+        cl4, wh4 = class_rooflines(prof4, hbm_peak, ("tdgl", "resid", "update"))
+        wh4["graph_ms_per_step"] = t4 / K
         fast = {"precision": "mixed", "guess": "extrapolated", "inner": FAST_INNER,
                 "value": ws * cells * K / (t4 / 1e3) / 1e6, "ms_per_step": t4 / K,
                 "vcycles_per_step": (s41["vcycles"] - s40["vcycles"]) / K,
-                "outer_iterations_per_step": (s41["cycles"] - s40["cycles"]) / K}
+                "outer_iterations_per_step": (s41["cycles"] - s40["cycles"]) / K,
+                "roofline_classes": cl4, "whole_step": wh4}
         d4.close()
     learned = None if (args.no_compare or args.no_learned) else run_learned(args, ws, cfg, geom, P0, cells,
                                                                             sweep, timed_run)
     batch = None if args.no_batch else run_batch_qv(args, ws)
+    mfism = None if args.no_mfism else run_mfism(args, ws, hbm_peak)
     mixed_v = value if prec_main == ferrox.MIXED else (other or {}).get("value")
     fp64_v = value if prec_main != ferrox.MIXED else (other or {}).get("value")
 
@@ -371,10 +415,8 @@ def run_ours(args, ws, rank, local):
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if prec_main != ferrox.MIXED else "f32+f64",
             "data": "synthetic",
-            "config": {"workload": cfg["label"], "guess": args.guess, "nu1": args.nu1, "nu2": args.nu2, "inner": args.inner,
-                       "cells": cells, "tol": 1e-10, "order": 1,
-                       "precision": args.precision, "l2": "flushed between timed steps (256 MB write)",
-                       "parallelism": f"replicas x{ws}"},
+            "config": bench_config(ws, args) if args.workload == "mfim_256x256x32" else
+            dict(bench_config(ws, args), workload=cfg["label"], cells=cells),
             "vcycles_per_step": vcycles_per_step,
             "outer_iterations_per_step": cycles_per_step, "gpu_launches": launches,
             "learned_main": None if learned_main is None else
@@ -383,7 +425,8 @@ def run_ours(args, ws, rank, local):
             "vs_plain_fp64": (mixed_v / fp64_v) if (mixed_v and fp64_v) else None,
             "other_precision": other, "fast_form": fast,
             "vs_plain_fp64_fast_form": (fast["value"] / fp64_v) if (fast and fp64_v) else None,
-            "learned_form": learned, "batch_qv": batch, "e2e": e2e, "cpu_baseline": cpu, "clocks": ck}
+            "learned_form": learned, "batch_qv": batch, "mfism": mfism, "e2e": e2e, "cpu_baseline": cpu,
+            "clocks": ck}
     if rank == 0:
         print(json.dumps(line))
     if ws > 1:
@@ -435,11 +478,13 @@ def run_learned(args, ws, cfg, geom, P0, cells, sweep, timed_run):
     return out
 
 
-def train_network_on(args, ferrox, I):
+def train_network_on(args, ferrox, I, snapshots=None, epochs=None):
     """Collect snapshots on the --nn-train-on workloads (default: the 256x256x32 MFIM
     and 256x256x64 MFISM) and train one network on all of them (the weights carry
     over between grids: the network is fully convolutional)."""
     import torch
+    nsnap = args.nn_snapshots if snapshots is None else snapshots
+    nep = args.nn_epochs if epochs is None else epochs
     params, losses, t0 = None, [], time.perf_counter()
     for name in args.nn_train_on.split(","):
         cfg = workload_config(name)
@@ -447,25 +492,118 @@ def train_network_on(args, ferrox, I):
         num = ferrox.make_numerics(cfg["dt"], order=1, tol=1e-10, precision=ferrox.MIXED, guess=1)
         d = ferrox.Device(g, I.random_polarization(g, cfg["seed"]), numerics=num)
         lv = d.levels()[2]
-        net = ferrox.NN(lv[2], lv[1], lv[0], capacity=args.nn_snapshots,
+        net = ferrox.NN(lv[2], lv[1], lv[0], capacity=nsnap,
                         params=params if params is not None else ferrox.nn_init_params(7))
         sweep = cfg["sweep"]
         d.set_bias(0.0, sweep[0])
         d.solve_poisson()
         d.attach_nn(net, 1)
-        for k in range(args.nn_snapshots):
+        for k in range(nsnap):
             if len(sweep) > 1 and k % 25 == 0:
                 d.set_bias(0.0, sweep[(k // 25) % len(sweep)])
             d.step(1)
-        losses += [float(x) for x in net.train(epochs=args.nn_epochs, lr=3e-4, batch=8)]
+        losses += [float(x) for x in net.train(epochs=nep, lr=3e-4, batch=8)]
         w, b, _, _ = net.params()
         params = ([wi.reshape(27, ci, co) for wi, (ci, co) in zip(w, ferrox.NN_LAYERS)], b)
         d.close()
         net.close()
     torch.cuda.synchronize()
-    return {"params": params, "snapshots_per_workload": args.nn_snapshots, "epochs": args.nn_epochs,
+    return {"params": params, "snapshots_per_workload": nsnap, "epochs": nep,
+            "trained_on": args.nn_train_on,
             "train_loss_first_last": [losses[0], losses[-1]],
             "collect_and_train_s": time.perf_counter() - t0}
+
+
+# ------------------------------------------------------------- MFISM workloads -----
+
+MFISM_INNER = 4   # V-cycles per Newton (FP64) residual in the fast MFISM form
+
+
+def time_steps(d, K, W, flush):
+    """W untimed steps, then K steps each bracketed by CUDA events on the context's
+    stream, L2 flushed before every step.  Returns (total ms, stats before, after)."""
+    import torch
+    for _ in range(W):
+        flush.zero_()
+        d.step(1)
+    torch.cuda.synchronize()
+    st0 = d.stats()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for s in range(K):
+        flush.zero_()
+        ev[s][0].record(d.stream)
+        d.step(1)
+        ev[s][1].record(d.stream)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ev), st0, d.stats()
+
+
+def run_mfism(args, ws, hbm_peak):
+    """The two MFISM stacks (metal / p-Si / SiO2 / HZO / metal, damped Newton with
+    Boltzmann carriers, MG to 1e-10): 256x256x64 (seed 2) and 512x512x128 (seed 5),
+    at 0 V, each in plain FP64 multigrid (the defect-correction Newton form), the
+    fast mixed form (FP32 V-cycles in FP64 Newton defect correction, extrapolated
+    guess, MFISM_INNER V-cycles per Newton residual), and on 512x512x128 the same
+    with the learned warm start, the network trained on 256x256x32 MFIM and
+    256x256x64 MFISM snapshots."""
+    import torch
+    from paper_2210_15668_gb300 import ferrox, inputs as I
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    K, W = args.steps, args.warmup
+    net_params = None
+    out = {}
+    for name in ("mfism_256x256x64", "mfism_512x512x128"):
+        cfg = workload_config(name)
+        geom = cfg["geom"]
+        cells = geom["nx"] * geom["ny"] * I.nz_of(geom)
+        P0 = I.random_polarization(geom, cfg["seed"])
+        forms = [("fp64", dict(precision=ferrox.FP64)),
+                 ("mixed_fast", dict(precision=ferrox.MIXED, guess=1, inner=MFISM_INNER))]
+        if name == "mfism_512x512x128" and not args.no_learned:
+            forms.append(("mixed_fast_learned", dict(precision=ferrox.MIXED, guess=1, inner=MFISM_INNER)))
+        res = {"cells": cells, "steps": K, "warmup": W, "tol": 1e-10,
+               "l2": "flushed between timed steps (256 MB write)", "label": cfg["label"]}
+        for form, kw in forms:
+            num = ferrox.make_numerics(cfg["dt"], order=1, tol=1e-10, max_cycles=200, **kw)
+            d = ferrox.Device(geom, P0, numerics=num)
+            d.set_bias(0.0, cfg["v_top"])
+            d.solve_poisson()
+            net = None
+            extra = {}
+            if form.endswith("learned"):
+                if net_params is None:
+                    tr = train_network_on(args, ferrox, I, snapshots=args.mfism_nn_snapshots,
+                                          epochs=args.mfism_nn_epochs)
+                    net_params = tr["params"]
+                    extra = {k: v for k, v in tr.items() if k != "params"}
+                lv2 = d.levels()[2]
+                net = ferrox.NN(lv2[2], lv2[1], lv2[0], params=net_params)
+                d.attach_nn(net, 2)
+            t, s0, s1 = time_steps(d, K, W, flush)
+            t = reduce_max(t, ws)
+            r = {"value": ws * cells * K / (t / 1e3) / 1e6, "unit": UNIT, "ms_per_step": t / K,
+                 "vcycles_per_step": (s1["vcycles"] - s0["vcycles"]) / K,
+                 "newton_iterations_per_step": (s1["cycles"] - s0["cycles"]) / K}
+            r.update(extra)
+            if net is not None:
+                r["corrections_rejected"] = s1["nn_rejected"] - s0["nn_rejected"]
+            else:
+                prof = d.profile_step(with_bytes=True)
+                fp64c = ("tdgl", "resid", "update") + (() if kw["precision"] == ferrox.MIXED else
+                                                      ("smooth_fine", "smooth_coarse", "restrict",
+                                                       "prolong", "tail"))
+                cl, wh = class_rooflines(prof, hbm_peak, fp64c)
+                wh["graph_ms_per_step"] = t / K
+                r["roofline_classes"] = cl
+                r["whole_step"] = wh
+            res[form] = r
+            d.close()
+            if net is not None:
+                net.close()
+        if "fp64" in res and "mixed_fast" in res:
+            res["vs_plain_fp64"] = res["mixed_fast"]["value"] / res["fp64"]["value"]
+        out[name] = res
+    return out
 
 
 # ------------------------------------------------------- batched Q-V sweep workload -----
@@ -532,29 +670,109 @@ def _oracle_steps(budget_s, max_steps=None):
     return cells, n, el
 
 
+def cpu_model():
+    """CPU model name of this host (lscpu, else /proc/cpuinfo, else the machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def _oracle_replica(job):
+    """One spawned process: wait for the common start time, then run oracle steps for
+    the budget (or max_steps).  Returns (cells, steps, elapsed s)."""
+    budget_s, max_steps, warm, t_start = job
+    if warm:
+        _oracle_steps(1e9, max_steps=warm)
+    while time.time() < t_start:
+        time.sleep(0.001)
+    return _oracle_steps(budget_s, max_steps=max_steps)
+
+
+def oracle_all_cores(budget_s, max_steps=None, warm=0, cores=None):
+    """The oracle on every host core at once: one independent replica of the same
+    workload per core (spawned processes, one BLAS/OpenMP thread each), all started
+    together; throughput = all replicas' cell-steps over the slowest replica's time."""
+    import multiprocessing as mp
+    cores = cores or host_cores()
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        t_start = time.time() + 12.0 + 2.0 * warm       # after every replica's import and warm-up
+        res = pool.map(_oracle_replica, [(budget_s, max_steps, warm, t_start)] * cores)
+    cells = res[0][0]
+    n_tot = sum(r[1] for r in res)
+    el = max(r[2] for r in res)
+    return cells, n_tot, el, cores, min(r[1] for r in res)
+
+
+ORACLE_NOTE = ("numpy FP64 oracle, exact FFT/tridiagonal Poisson solve (a different algorithm "
+               "from the GPU multigrid)")
+
+
 def cpu_baseline(budget_s):
     cells, n, el = _oracle_steps(budget_s)
-    return {"value": cells * n / el / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n} oracle steps of mfim_256x256x32 at -2 V from Step 0 ({el:.1f} s; "
-                      "numpy FP64, exact FFT/tridiagonal Poisson solve, single thread)"}
+    one = {"value": cells * n / el / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{n} oracle steps of mfim_256x256x32 at -2 V from Step 0 ({el:.1f} s; "
+                     f"{ORACLE_NOTE}; one core)"}
+    cells, n_tot, el_all, cores, n_min = oracle_all_cores(budget_s)
+    return {"value": cells * n_tot / el_all / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{cores} replicas (one per host core, spawned processes) of oracle steps of "
+                      f"mfim_256x256x32 at -2 V from Step 0, {n_tot} steps in total (>= {n_min} each) "
+                      f"in {el_all:.1f} s; {ORACLE_NOTE}",
+            "cpu_model": cpu_model(), "nproc": os.cpu_count(), "single_core": one}
+
+
+def bench_config(ws, args=None):
+    """The workload record of the 256x256x32 line (the same for both arms)."""
+    from paper_2210_15668_gb300 import inputs as I
+    cfg = I.mfim_sweep()
+    g = cfg["geom"]
+    c = {"workload": "mfim_256x256x32 Q-V sweep (first steps at -2 V), seed 1",
+         "cells": g["nx"] * g["ny"] * I.nz_of(g), "tol": 1e-10, "order": 1, "precision": "fp64",
+         "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{ws}"}
+    if args is not None:
+        c.update(precision=args.precision, guess=args.guess, nu1=args.nu1, nu2=args.nu2, inner=args.inner)
+    return c
 
 
 def run_reference(args, ws, rank):
     if rank != 0:
         return
-    # warm-up steps, then the timed sample (bounded to keep the run within minutes)
-    _oracle_steps(1e9, max_steps=max(1, min(args.warmup, 3)))
-    budget = args.cpu_seconds
-    cells, n, el = _oracle_steps(budget, max_steps=args.steps)
-    value = cells * n / el / 1e6
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": n,
-            "warmup": args.warmup, "ms_per_step": el / n * 1e3, "higher_is_better": True,
+    # every host core runs one replica: W warm-up steps, then K timed steps each
+    # (bounded: K and W are capped so the run ends within a few minutes)
+    K = max(1, min(args.steps, 30))
+    W = max(1, min(args.warmup, 3))
+    cells, n_tot, el, cores, n_min = oracle_all_cores(1e9, max_steps=K, warm=W)
+    value = cells * n_tot / el / 1e6
+    cfg = bench_config(ws, args)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K,
+            "warmup": W, "ms_per_step": el / K * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "impl": "reference",
-            "config": {"workload": "mfim_256x256x32 Q-V sweep (first steps at -2 V), seed 1",
-                       "cells": cells, "tol": "exact solve", "order": 1, "precision": "fp64"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{n} oracle steps in {el:.1f} s (bounded sample of the workload)"},
+            "impl": "reference", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{cores} replicas x {K} oracle steps of the workload in {el:.1f} s "
+                                       f"(after {W} warm-up steps each); {ORACLE_NOTE}",
+                             "cpu_model": cpu_model(), "nproc": os.cpu_count()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -595,7 +813,7 @@ def main():
     ap.add_argument("--workload", default="mfim_256x256x32",
                     help="mfim_256x256x32 (the benchmark) or mfim_NXxNYxNZ (profiling copies)")
     ap.add_argument("--e2e-steps", type=int, default=200)
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -613,6 +831,10 @@ def main():
                     help="workloads whose snapshots train the --learned network (comma list)")
     ap.add_argument("--nn-epochs", type=int, default=20)
     ap.add_argument("--batch-steps", type=int, default=50)
+    ap.add_argument("--no-mfism", action="store_true", help="skip the 256x256x64 and 512x512x128 MFISM keys")
+    ap.add_argument("--mfism-nn-snapshots", type=int, default=1000,
+                    help="snapshots per training workload for the 512x512x128 learned form")
+    ap.add_argument("--mfism-nn-epochs", type=int, default=8)
     ap.add_argument("--nn-forward", action="store_true",
                     help="time only the network forward on the 64x64x8 level of the benchmark "
                          "stack (--steps forwards; for profiling the convolution kernels)")

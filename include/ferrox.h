@@ -221,6 +221,14 @@ enum {
  * The result of the step is the same as ferrox_step(ctx, 1).  Synchronises. */
 ferrox_status ferrox_profile_step(ferrox_ctx* ctx, double* ms, int* count);
 
+/* The same step, also reporting in bytes[k] (array of FERROX_K_COUNT, may be
+ * NULL) the algorithmic bytes of the class's launches: every array element the
+ * method needs read or written once per launch (multigrid arrays in the
+ * solve's precision, state and right-hand side in FP64; a dense bottom solve
+ * counts its inverse once).  bytes[k] / ms[k] is the class's effective
+ * bandwidth against the HBM roofline.  Synchronises. */
+ferrox_status ferrox_profile_step_bytes(ferrox_ctx* ctx, double* ms, int* count, double* bytes);
+
 /* Release everything the context allocated (the caller's arrays are untouched).
  * Synchronises the stream.  NULL is accepted. */
 ferrox_status ferrox_destroy(ferrox_ctx* ctx);
@@ -345,13 +353,16 @@ ferrox_status ferrox_attach_nn(ferrox_ctx* ctx, ferrox_nn* nn, int mode);
 #define FERROX_STATIC_MAX_CELLS 262144
 #define FERROX_STATIC_MAX_PLANES 512
 
-/* Step 1a (P <- P + dt f(P, phi)) without any allocation, for callers that
- * cannot allocate device memory: code running while a stream capture forbids
- * cudaMalloc, processes held to a fixed device-memory budget, or frameworks
- * whose own allocator must own every device byte.  The paper has no
+/* The explicit TDGL polarization update P <- P + dt f(P, phi) without any
+ * device allocation, for callers that cannot allocate device memory: processes
+ * held to a fixed device-memory budget, frameworks whose own allocator must own
+ * every device byte, and latency-bound loops that cannot afford the device-wide
+ * synchronisation that cudaMalloc and cudaFree may imply.  The paper has no
  * counterpart; this is a deployment variant of ferrox_tdgl_update.
  *   geom, dt, v_bottom, v_top: as for ferrox_init_geometry / ferrox_set_bias.
  *   P_dev (in/out) and phi_dev (in): caller-owned device arrays, layout above.
+ *   Only the ferroelectric planes of P_dev are written; every other plane keeps
+ *   the caller's values.
  * It runs the same fused TDGL kernel, with its scratch (plane table, staging
  * copy of the new P, right-hand side) in one file-scope device array of about
  * 8.1 MB that every GPU loading the library holds until the process exits.

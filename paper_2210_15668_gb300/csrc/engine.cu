@@ -386,8 +386,25 @@ double update_clamp(const ferrox_ctx* c) {
 
 struct NoWrap {
   template <typename F>
-  void operator()(int, F&& f) const { f(); }
+  void operator()(int, double, F&& f) const { f(); }
 };
+
+// Algorithmic bytes of one launch (each array element the method needs read or
+// written once), for the profiler's per-class bandwidth figures.  T-sized
+// multigrid arrays; FP64 state and right-hand side.
+template <typename T>
+double sweep_bytes(const ferrox_ctx* c, const LevelDesc& L) {
+  // one colour: the other colour's e (read), own r (read), own e (write), own s (SC)
+  return 0.5 * (double)L.ncell * sizeof(T) * (c->has_sc ? 4.0 : 3.0);
+}
+template <typename T>
+double restrict_bytes(const LevelDesc& F, const LevelDesc& Cc) {
+  return (double)F.ncell * 2.0 * sizeof(T) + (double)Cc.ncell * sizeof(T);
+}
+template <typename T>
+double prolong_bytes(const LevelDesc& F, const LevelDesc& Cc) {
+  return (double)Cc.ncell * sizeof(T) + (double)F.ncell * 2.0 * sizeof(T);
+}
 
 // One V-cycle on the correction equation; `wrap(kind, launch)` lets the profiler
 // bracket each launch with events (identity when capturing graphs).
@@ -410,33 +427,43 @@ void enqueue_levels(ferrox_ctx* c, cudaStream_t s, W wrap, int l0, bool first, b
     const int ks = l == 0 ? FERROX_K_SMOOTH0 : FERROX_K_SMOOTHC;
     for (int sw = 0; sw < nu1; ++sw) {
       const int zero = sw == 0 && (first || l > 0);
-      wrap(ks, [&] { launch_smooth<T>(a, c->lv[l], 0, zero, nullptr, s); });
-      wrap(ks, [&] { launch_smooth<T>(a, c->lv[l], 1, 0, nullptr, s); });
+      const double sb = sweep_bytes<T>(c, c->lv[l]);
+      wrap(ks, sb, [&] { launch_smooth<T>(a, c->lv[l], 0, zero, nullptr, s); });
+      wrap(ks, sb, [&] { launch_smooth<T>(a, c->lv[l], 1, 0, nullptr, s); });
     }
-    wrap(FERROX_K_RESTRICT, [&] { launch_restrict<T>(a, c->lv[l], c->lv[l + 1], nu1, s); });
+    wrap(FERROX_K_RESTRICT, restrict_bytes<T>(c->lv[l], c->lv[l + 1]),
+         [&] { launch_restrict<T>(a, c->lv[l], c->lv[l + 1], nu1, s); });
   }
   if (c->dense_wide_d) {
     // the whole tail as one exact solve of its first level, spread over the SMs
     const LevelDesc& B = c->lv[lt];
-    wrap(FERROX_K_TAIL, [&] {
+    // the inverse (n^2 elements) and the level's r in, e out
+    const double n = (double)B.ncell;
+    wrap(FERROX_K_TAIL, (n * n + 2.0 * n) * sizeof(T), [&] {
       launch_dense_solve<T>(static_cast<const T*>(c->dense_wide_d), (int)B.ncell, a.r + B.off,
                             a.e + B.off, s);
     });
   } else {
     TailArgs ta{c->lvt_d, L - lt + 1, c->tail_elems, c->lv[lt].off, nu1, nu2, c->num.bottom_sweeps,
                 constant, c->dense_d, c->dense_lev, 0};
-    wrap(FERROX_K_TAIL, [&] { launch_tail<T>(a, ta, c->tail_smem, s); });
+    double tb = 0.0;   // every tail level's r in and e out once (shared memory in between)
+    for (int l = lt; l <= L; ++l) tb += 2.0 * (double)c->lv[l].ncell * sizeof(T);
+    wrap(FERROX_K_TAIL, tb, [&] { launch_tail<T>(a, ta, c->tail_smem, s); });
   }
   const UpdateArgs upd{c->phi, c->stats_d, update_clamp(c)};
   for (int l = lt - 1; l >= l0; --l) {
     const int ks = l == 0 ? FERROX_K_SMOOTH0 : FERROX_K_SMOOTHC;
     // the tiled form where FP64 arithmetic bounds the launch: the fine level
     const bool tiled = sizeof(T) == sizeof(double) && l == 0;
-    wrap(FERROX_K_PROLONG, [&] { launch_prolong<T>(a, c->lv[l], c->lv[l + 1], constant, s, tiled); });
+    wrap(FERROX_K_PROLONG, prolong_bytes<T>(c->lv[l], c->lv[l + 1]),
+         [&] { launch_prolong<T>(a, c->lv[l], c->lv[l + 1], constant, s, tiled); });
+    const double sb = sweep_bytes<T>(c, c->lv[l]);
     for (int sw = 0; sw < nu2; ++sw) {
       const bool fuse = last && l == 0 && sw == nu2 - 1;   // phi += e folded into the last sweep
-      wrap(ks, [&] { launch_smooth<T>(a, c->lv[l], 0, 0, nullptr, s); });
-      wrap(ks, [&] { launch_smooth<T>(a, c->lv[l], 1, 0, fuse ? &upd : nullptr, s); });
+      // the fused update also reads and writes phi (FP64) on the swept colour
+      const double ub = fuse ? 0.5 * (double)c->lv[0].ncell * 16.0 : 0.0;
+      wrap(ks, sb, [&] { launch_smooth<T>(a, c->lv[l], 0, 0, nullptr, s); });
+      wrap(ks, sb + ub, [&] { launch_smooth<T>(a, c->lv[l], 1, 0, fuse ? &upd : nullptr, s); });
     }
   }
 }
@@ -474,8 +501,9 @@ template <typename W>
 void enqueue_fine_sweeps(ferrox_ctx* c, cudaStream_t s, W wrap, int nu, const DevStats* zst) {
   const MGArgs<double> fa = fine_args(c);
   for (int sw = 0; sw < nu; ++sw) {
-    wrap(FERROX_K_SMOOTH0, [&] { launch_smooth<double>(fa, c->lv[0], 0, 0, nullptr, s, zst); });
-    wrap(FERROX_K_SMOOTH0, [&] { launch_smooth<double>(fa, c->lv[0], 1, 0, nullptr, s, zst); });
+    const double sb = sweep_bytes<double>(c, c->lv[0]);
+    wrap(FERROX_K_SMOOTH0, sb, [&] { launch_smooth<double>(fa, c->lv[0], 0, 0, nullptr, s, zst); });
+    wrap(FERROX_K_SMOOTH0, sb, [&] { launch_smooth<double>(fa, c->lv[0], 1, 0, nullptr, s, zst); });
   }
 }
 
@@ -497,7 +525,9 @@ void enqueue_check(ferrox_ctx* c, cudaStream_t s, W wrap, int first, int set_con
   ck.first_launches = 2 * c->num.nu1 + 1;
   const MGArgs<double> fa = fine_args(c);
   double* rc = static_cast<double*>(c->r_arena);
-  wrap(FERROX_K_RESID, [&] { launch_restrict_check(fa, rc, c->lv[0], c->lv[1], c->num.nu1, ck, s); });
+  // phi and b of the fine level read, the coarse residual written
+  const double rb = (double)c->lv[0].ncell * 16.0 + (double)c->lv[1].ncell * 8.0;
+  wrap(FERROX_K_RESID, rb, [&] { launch_restrict_check(fa, rc, c->lv[0], c->lv[1], c->num.nu1, ck, s); });
 }
 
 // prologue of a solve: pre-smoothing and the first check
@@ -515,7 +545,8 @@ void enqueue_direct_cycle(ferrox_ctx* c, cudaStream_t s, W wrap, int set_cond,
                           unsigned long long handle) {
   enqueue_levels<double>(c, s, wrap, 1, true, false);
   MGArgs<double> a = mg_args<double>(c);
-  wrap(FERROX_K_PROLONG, [&] { launch_prolong<double>(a, c->lv[0], c->lv[1], 0, s, true, c->phi); });
+  wrap(FERROX_K_PROLONG, prolong_bytes<double>(c->lv[0], c->lv[1]),
+       [&] { launch_prolong<double>(a, c->lv[0], c->lv[1], 0, s, true, c->phi); });
   enqueue_fine_sweeps(c, s, wrap, c->num.nu2, c->stats_d);
   enqueue_fine_sweeps(c, s, wrap, c->num.nu1, c->stats_d);
   enqueue_check(c, s, wrap, 0, set_cond, handle);
@@ -845,23 +876,54 @@ ferrox_status collect_step_t(ferrox_ctx* ctx) {
 // ---- eager, event-timed step (per-kernel breakdown) -------------------------------------
 struct EventTimer {
   cudaStream_t s;
-  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> rec;
+  struct Rec {
+    int kind;
+    double bytes;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> rec;
   template <typename F>
-  void operator()(int kind, F&& f) {
+  void operator()(int kind, double bytes, F&& f) {
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
     cudaEventRecord(a, s);
     f();
     cudaEventRecord(b, s);
-    rec.push_back({kind, {a, b}});
+    rec.push_back({kind, bytes, a, b});
   }
 };
 
+// algorithmic bytes of the step-level launches (FP64 state; T-sized residual)
+struct StepBytes {
+  double resid, tdgl, copy_back, extrap, update;
+};
+
 template <typename T>
-ferrox_status profile_step_t(ferrox_ctx* ctx, double* ms, int* count) {
+StepBytes step_bytes(const ferrox_ctx* c) {
+  const double plane = (double)c->nx * c->ny, N = plane * c->nz;
+  double dyn = 0.0, fe = 0.0, sc = 0.0;
+  for (const auto& p : c->planes) {
+    dyn += p.b_dyn ? plane : 0.0;
+    fe += p.fe ? plane : 0.0;
+  }
+  for (const auto& L : c->layers) sc += L.kind == FERROX_SC ? plane * L.ncells : 0.0;
+  StepBytes b;
+  // phi read, b read on the planes the TDGL update writes, r written, s written (SC)
+  b.resid = N * (8.0 + sizeof(T)) + dyn * 8.0 + sc * sizeof(T);
+  // P (all components) and phi read, new P written; b written on the dynamic planes
+  b.tdgl = fe * c->ncomp * 16.0 + fe * 8.0 + dyn * 8.0;
+  b.copy_back = fe * c->ncomp * 16.0;
+  b.extrap = N * 24.0;
+  b.update = N * (sizeof(T) + 16.0);
+  return b;
+}
+
+template <typename T>
+ferrox_status profile_step_t(ferrox_ctx* ctx, double* ms, int* count, double* bytes) {
   cudaStream_t s = ctx->stream;
   EventTimer tm{s, {}};
+  const StepBytes sb = step_bytes<T>(ctx);
   auto solve = [&]() -> ferrox_status {
     if (ctx->direct) {
       enqueue_direct_prologue(ctx, s, std::ref(tm), 0, 0ULL);
@@ -877,7 +939,7 @@ ferrox_status profile_step_t(ferrox_ctx* ctx, double* ms, int* count) {
       }
       return FERROX_OK;
     }
-    tm(FERROX_K_RESID, [&] { enqueue_resid<T>(ctx, s, 1, 0, 0ULL); });
+    tm(FERROX_K_RESID, sb.resid, [&] { enqueue_resid<T>(ctx, s, 1, 0, 0ULL); });
     for (int guard = 0; guard <= ctx->num.max_cycles + 1; ++guard) {
       FX_CK(cudaMemcpyAsync(ctx->host_pinned, reinterpret_cast<char*>(ctx->stats_d) +
                                                   offsetof(DevStats, last_cond),
@@ -897,37 +959,46 @@ ferrox_status profile_step_t(ferrox_ctx* ctx, double* ms, int* count) {
       } else {
         enqueue_cycles<T>(ctx, s, std::ref(tm));
       }
-      if (separate_update(ctx)) tm(FERROX_K_UPDATE, [&] { enqueue_update<T>(ctx, s); });
-      tm(FERROX_K_RESID, [&] { enqueue_resid<T>(ctx, s, 0, 0, 0ULL); });
+      if (separate_update(ctx)) tm(FERROX_K_UPDATE, sb.update, [&] { enqueue_update<T>(ctx, s); });
+      tm(FERROX_K_RESID, sb.resid, [&] { enqueue_resid<T>(ctx, s, 0, 0, 0ULL); });
     }
     return FERROX_OK;
   };
   ferrox_status rc;
   const long long N = (long long)ctx->nx * ctx->ny * ctx->nz;
   if (ctx->num.order == 1) {
-    tm(FERROX_K_TDGL, [&] { launch_tdgl(tdgl_args(ctx, 0), s); });
-    tm(FERROX_K_COPY, [&] { enqueue_copy_back(ctx, s); });
-    if (ctx->num.guess == 1) tm(FERROX_K_COPY, [&] { launch_extrapolate(ctx->phi, ctx->phi_prev, N, s); });
+    tm(FERROX_K_TDGL, sb.tdgl, [&] { launch_tdgl(tdgl_args(ctx, 0), s); });
+    tm(FERROX_K_COPY, sb.copy_back, [&] { enqueue_copy_back(ctx, s); });
+    if (ctx->num.guess == 1)
+      tm(FERROX_K_COPY, sb.extrap, [&] { launch_extrapolate(ctx->phi, ctx->phi_prev, N, s); });
     if ((rc = solve()) != FERROX_OK) return rc;
   } else {
-    tm(FERROX_K_TDGL, [&] { launch_tdgl(tdgl_args(ctx, 1), s); });
-    if (ctx->num.guess == 1) tm(FERROX_K_COPY, [&] { launch_extrapolate(ctx->phi, ctx->phi_prev, N, s); });
+    // order 2: the predictor also stores f (8 B per FE cell and component); the
+    // corrector reads it and the base P
+    tm(FERROX_K_TDGL, sb.tdgl + sb.copy_back * 0.5, [&] { launch_tdgl(tdgl_args(ctx, 1), s); });
+    if (ctx->num.guess == 1)
+      tm(FERROX_K_COPY, sb.extrap, [&] { launch_extrapolate(ctx->phi, ctx->phi_prev, N, s); });
     if ((rc = solve()) != FERROX_OK) return rc;
-    tm(FERROX_K_TDGL, [&] { launch_tdgl(tdgl_args(ctx, 2), s); });
+    tm(FERROX_K_TDGL, sb.tdgl + sb.copy_back, [&] { launch_tdgl(tdgl_args(ctx, 2), s); });
     if ((rc = solve()) != FERROX_OK) return rc;
   }
   launch_stats_step(ctx->stats_d, 1,
                     tdgl_launches(ctx) * ctx->num.order + 1 + (ctx->num.guess == 1 ? 1 : 0), s);
   FX_CK(cudaGetLastError());
   FX_CK(cudaStreamSynchronize(s));
-  for (int k = 0; k < FERROX_K_COUNT; ++k) { ms[k] = 0.0; count[k] = 0; }
+  for (int k = 0; k < FERROX_K_COUNT; ++k) {
+    ms[k] = 0.0;
+    count[k] = 0;
+    if (bytes) bytes[k] = 0.0;
+  }
   for (auto& r : tm.rec) {
     float t = 0.f;
-    cudaEventElapsedTime(&t, r.second.first, r.second.second);
-    ms[r.first] += t;
-    count[r.first] += 1;
-    cudaEventDestroy(r.second.first);
-    cudaEventDestroy(r.second.second);
+    cudaEventElapsedTime(&t, r.a, r.b);
+    ms[r.kind] += t;
+    count[r.kind] += 1;
+    if (bytes) bytes[r.kind] += r.bytes;
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
   }
   return FERROX_OK;
 }
@@ -1247,9 +1318,13 @@ ferrox_status ferrox_attach_nn(ferrox_ctx* ctx, ferrox_nn* nn, int mode) {
 }
 
 ferrox_status ferrox_profile_step(ferrox_ctx* ctx, double* ms, int* count) {
+  return ferrox_profile_step_bytes(ctx, ms, count, nullptr);
+}
+
+ferrox_status ferrox_profile_step_bytes(ferrox_ctx* ctx, double* ms, int* count, double* bytes) {
   if (!ctx || !ms || !count) return fail(ctx, FERROX_EINVAL, "null argument");
-  return ctx->num.precision == FERROX_MIXED ? profile_step_t<float>(ctx, ms, count)
-                                            : profile_step_t<double>(ctx, ms, count);
+  return ctx->num.precision == FERROX_MIXED ? profile_step_t<float>(ctx, ms, count, bytes)
+                                            : profile_step_t<double>(ctx, ms, count, bytes);
 }
 
 ferrox_status ferrox_sync_stats(ferrox_ctx* ctx, ferrox_stats* out) {
@@ -2106,9 +2181,10 @@ const char* ferrox_batch_last_error(const ferrox_batch* B) {
 
 // ---- entry point without allocation -----------------------------------------------------
 //
-// Callers that cannot allocate device memory (code that runs while a CUDA stream
-// capture forbids cudaMalloc, processes under a fixed device-memory budget, or
-// frameworks whose own allocator must own every byte) still need the TDGL
+// Callers that cannot allocate device memory (processes held to a fixed
+// device-memory budget, frameworks whose own allocator must own every device
+// byte, or latency-bound loops that cannot afford the device-wide
+// synchronisation cudaMalloc and cudaFree may imply) still need the TDGL
 // update.  ferrox_tdgl_update_static runs the same fused TDGL kernel as
 // ferrox_tdgl_update, with its three scratch areas (plane table, staging copy
 // of the new polarization, right-hand side) carved from the file-scope array
@@ -2250,12 +2326,23 @@ extern "C" ferrox_status ferrox_tdgl_update_static(const ferrox_geometry* geom, 
   a.b_scale = geom->h / kEps0;
   a.mode = 0;
   launch_tdgl(a, s);
+  // The kernel writes the new polarization on ferroelectric planes only, so copy
+  // back each contiguous run of them on its own: the staging area keeps whatever
+  // an earlier call left on the other planes, and the caller's planes between two
+  // ferroelectric layers must not receive it.
   const long long plane = (long long)geom->nx * geom->ny;
-  const size_t off = (size_t)fe_lo * plane, cnt = (size_t)(fe_hi - fe_lo + 1) * plane;
-  for (int q = 0; q < geom->ncomp; ++q) {
-    e = cudaMemcpyAsync(P_dev + q * N + off, Pout + q * N + off, cnt * sizeof(double),
-                        cudaMemcpyDeviceToDevice, s);
-    if (e != cudaSuccess) return fail(nullptr, FERROX_ECUDA, std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e));
+  for (int z0 = fe_lo; z0 <= fe_hi;) {
+    if (!planes[z0].fe) { ++z0; continue; }
+    int z1 = z0;
+    while (z1 + 1 <= fe_hi && planes[z1 + 1].fe) ++z1;
+    const size_t off = (size_t)z0 * plane, cnt = (size_t)(z1 - z0 + 1) * plane;
+    for (int q = 0; q < geom->ncomp; ++q) {
+      e = cudaMemcpyAsync(P_dev + q * N + off, Pout + q * N + off, cnt * sizeof(double),
+                          cudaMemcpyDeviceToDevice, s);
+      if (e != cudaSuccess)
+        return fail(nullptr, FERROX_ECUDA, std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e));
+    }
+    z0 = z1 + 1;
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail(nullptr, FERROX_ECUDA, std::string("launch: ") + cudaGetErrorString(e));

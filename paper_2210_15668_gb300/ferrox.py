@@ -58,7 +58,8 @@ EXPORTS = ["ferrox_init_geometry", "ferrox_set_bias", "ferrox_solve_poisson", "f
            "ferrox_step", "ferrox_charge", "ferrox_sync_stats", "ferrox_clear_status",
            "ferrox_get_state", "ferrox_set_state", "ferrox_fe_planes", "ferrox_get_state_fe",
            "ferrox_set_state_fe", "ferrox_destroy", "ferrox_last_error",
-           "ferrox_level_shape", "ferrox_profile_step", "ferrox_tdgl_update_static",
+           "ferrox_level_shape", "ferrox_profile_step", "ferrox_profile_step_bytes",
+           "ferrox_tdgl_update_static",
            "ferrox_init_batch", "ferrox_batch_set_bias", "ferrox_batch_solve_poisson",
            "ferrox_batch_step", "ferrox_batch_charge", "ferrox_batch_stats", "ferrox_batch_tuning",
            "ferrox_batch_groups", "ferrox_batch_set_shape",
@@ -101,6 +102,8 @@ def load(path: str = LIB_PATH):
     lib.ferrox_level_shape.argtypes = [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                        C.POINTER(C.c_int), C.POINTER(C.c_int)]
     lib.ferrox_profile_step.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int)]
+    lib.ferrox_profile_step_bytes.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int),
+                                              C.POINTER(C.c_double)]
     lib.ferrox_tdgl_update_static.argtypes = [C.POINTER(Geometry), C.c_double, C.c_double,
                                               C.c_double, vp, vp, vp]
     lib.ferrox_init_batch.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(Geometry),
@@ -267,12 +270,16 @@ class Device:
         fp = C.c_void_p(phi_host.ctypes.data) if phi_host is not None else None
         self._ck(self.lib.ferrox_set_state_fe(self.ctx, pp, fp))
 
-    def profile_step(self):
-        """One event-timed eager step: {kernel class: (total ms, launches)}."""
+    def profile_step(self, with_bytes=False):
+        """One event-timed eager step: {kernel class: (total ms, launches)}, or with
+        with_bytes {kernel class: (total ms, launches, algorithmic bytes)}."""
         n = len(KERNEL_CLASSES)
         ms = (C.c_double * n)()
         cnt = (C.c_int * n)()
-        self._ck(self.lib.ferrox_profile_step(self.ctx, ms, cnt))
+        by = (C.c_double * n)()
+        self._ck(self.lib.ferrox_profile_step_bytes(self.ctx, ms, cnt, by))
+        if with_bytes:
+            return {KERNEL_CLASSES[k]: (ms[k], cnt[k], by[k]) for k in range(n)}
         return {KERNEL_CLASSES[k]: (ms[k], cnt[k]) for k in range(n)}
 
     def attach_nn(self, net, mode):

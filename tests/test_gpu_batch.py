@@ -53,6 +53,33 @@ def test_batch_matches_oracle_per_instance(precision, tol, bound):
     B.close()
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_large_instances_match_oracle(precision):
+    """The two largest lateral sizes of the 64-instance sweep (96^2 and 128^2 x 16),
+    batched with a small one, each against its own oracle run."""
+    from paper_2210_15668_gb300 import ferrox
+    sizes, biases = [128, 32, 96], [1.7, -0.4, -1.9]
+    geoms = [I.make_geometry(s, s, I.mfim_stack(16)) for s in sizes]
+    P0s = [I.random_polarization(g, seed=300 + i) for i, g in enumerate(geoms)]
+    num = ferrox.make_numerics(4e-13, tol=1e-12, precision=precision)
+    B = ferrox.Batch(geoms, P0s, num)
+    B.set_bias(np.zeros(len(geoms)), biases)
+    B.solve_poisson()
+    steps = 12
+    B.step(steps)
+    st = B.stats()
+    charges = B.charge()
+    for i, g in enumerate(geoms):
+        pl = oracle.planes(g)
+        Po, phio = tdgl.run(P0s[i], pl, g, 4e-13, 0.0, biases[i], steps)
+        Pg, phig = B.state(i)
+        assert st[i]["status"] == 0 and st[i]["steps"] == steps
+        assert rel_l2(Pg, Po) <= 1e-9 and rel_l2(phig, phio) <= 1e-9, (sizes[i], rel_l2(Pg, Po))
+        qo = diagnostics.charges(phio, Po, pl, g, 0.0, biases[i])
+        assert abs(charges[i]["Q_int"] - qo["Q_int"]) <= 1e-8 * abs(qo["Q_int"])
+    B.close()
+
+
 def test_batch_matches_single_instance_gpu_path():
     """The batched and the single-instance engines stop on the same residual test
     but solve the coarsest levels differently (a shared-memory V-cycle against an

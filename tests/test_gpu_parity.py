@@ -136,6 +136,87 @@ def test_bench_workload_256x256x32_steps(precision, tol, bound):
     d.close()
 
 
+_BENCH_ORACLE = {}
+
+
+def _bench_oracle(steps=5):
+    """Oracle run of the 256x256x32 bench workload: Step 0 and `steps` steps at -2 V."""
+    if steps not in _BENCH_ORACLE:
+        cfg = I.mfim_sweep()
+        geom = cfg["geom"]
+        pl = oracle.planes(geom)
+        P0 = I.random_polarization(geom, cfg["seed"])
+        Po, phio = tdgl.run(P0, pl, geom, cfg["dt"], 0.0, -2.0, steps)
+        _BENCH_ORACLE[steps] = (cfg, geom, pl, P0, Po, phio)
+    return _BENCH_ORACLE[steps]
+
+
+def _trained_net(geom, P0, num, snapshots=48, epochs=12):
+    """A warm-start network trained on snapshots of the workload itself (the bench's
+    learned form trains the same way, on more snapshots)."""
+    from paper_2210_15668_gb300 import ferrox
+    d = ferrox.Device(geom, P0, numerics=num)
+    lv = d.levels()[2]
+    net = ferrox.NN(lv[2], lv[1], lv[0], capacity=snapshots, seed=7)
+    d.set_bias(0.0, -2.0)
+    d.solve_poisson()
+    d.attach_nn(net, 1)
+    for k in range(snapshots):
+        if k % 12 == 0:
+            d.set_bias(0.0, [-2.0, -1.0, 0.0, 1.0][(k // 12) % 4])
+        d.step(1)
+    d.close()
+    net.train(epochs=epochs, lr=3e-4, batch=8)
+    return net
+
+
+@pytest.mark.parametrize("form", ["mixed", "fast", "learned"])
+@pytest.mark.parametrize("tol", [1e-10, 1e-12])
+def test_bench_workload_256x256x32_fast_forms(form, tol):
+    """The bench's other forms on the 256x256x32 workload at full size, every element
+    against the oracle after Step 0 and 5 steps at -2 V:
+      mixed   FP32 V-cycles inside FP64 defect correction (one V-cycle per FP64 residual);
+      fast    mixed + extrapolated initial guess + up to 8 V-cycles per FP64 residual;
+      learned fast + the trained warm-start network (corrections kept only when they
+              lower ||r||).
+    These switch on the kernel variants that only large grids use (two planes per
+    thread in the FP32 sweeps, the FP32 dense solve of the 16x16x2 level, the split
+    transfer kernels at the 128x128x16 boundary).  Bounds: the mixed-form bounds
+    (max|dP|/max|P| <= 1e-6, Q within 1e-8) and, as for the FP64 forms, relative L2
+    <= 2e-8 at tol 1e-10 and <= 1e-9 at tol 1e-12."""
+    from paper_2210_15668_gb300 import ferrox
+    cfg, geom, pl, P0, Po, phio = _bench_oracle()
+    kw = dict(tol=tol, precision=ferrox.MIXED, v=(0.0, -2.0))
+    if form in ("fast", "learned"):
+        kw.update(guess=1, inner=-8)
+    net = None
+    if form == "learned":
+        num = ferrox.make_numerics(cfg["dt"], tol=tol, precision=ferrox.MIXED, guess=1, inner=-8)
+        net = _trained_net(geom, P0, num)
+    d = _dev(geom, P0, **kw)
+    d.solve_poisson()
+    if net is not None:
+        d.attach_nn(net, 2)
+    d.step(5)
+    Pg, phig = d.get_state()
+    st = d.stats()
+    assert st["status"] == 0 and st["last_rel_res"] <= tol and st["steps"] == 5
+    bound = 2e-8 if tol == 1e-10 else 1e-9
+    eP = np.abs(Pg - Po).max() / np.abs(Po).max()
+    print(f"{form} tol {tol}: max rel P {eP:.2e}, rel L2 P {rel_l2(Pg, Po):.2e} phi {rel_l2(phig, phio):.2e}, "
+          f"V-cycles {st['vcycles']}, rejected {st['nn_rejected']}")
+    assert eP <= 1e-6
+    assert rel_l2(Pg, Po) <= bound and rel_l2(phig, phio) <= bound, (rel_l2(Pg, Po), rel_l2(phig, phio))
+    q = d.charge()
+    qo = diagnostics.charges(phio, Po, pl, geom, 0.0, -2.0)
+    for k in ("Q_int", "sigma_top", "sigma_bot"):
+        assert abs(q[k] - qo[k]) <= 1e-8 * abs(qo[k]), (k, q[k], qo[k])
+    if net is not None:
+        assert st["nn_rejected"] < 5
+        net.close()
+    d.close()
+
+
 def test_zero_rhs_needs_no_cycle():
     geom = I.make_geometry(16, 16, I.mfim_stack(8, n_fe=4))
     P = np.zeros((1, 8, 16, 16))
