@@ -17,6 +17,7 @@
 #include <cmath>
 #include <cstddef>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <functional>
 #include <mutex>
@@ -76,6 +77,7 @@ struct ferrox_ctx {
   double* Fbuf = nullptr;
   double* phi_prev = nullptr;         // previous step's potential (guess = 1)
   void* e_arena = nullptr;
+  void* e_alt = nullptr;              // second error array of the fused sweeps (largest such level)
   void* r_arena = nullptr;
   void* s_arena = nullptr;
   void* coef = nullptr;               // PlaneCoef<T> of all levels
@@ -414,6 +416,22 @@ int inner_cycles(const ferrox_ctx* c) { return c->num.inner > 1 ? c->num.inner :
 // chosen on the device after every FP64 residual (0: fixed count)
 int adapt_max(const ferrox_ctx* c) { return c->num.inner < 0 ? -c->num.inner : 0; }
 
+// Levels whose smoothing runs as fused red-black sweeps (one launch per full
+// sweep, alternating between the level's array and e_alt): the level must take
+// the fused kernel's tile, and the sweep count must be even so that the last
+// sweep lands in the level's own array.
+template <typename T>
+bool rb_sweeps(const ferrox_ctx* c, int l, int nu) {
+  return c->e_alt && nu % 2 == 0 && smooth_rb_tile<T>(c->lv[l]) > 0;
+}
+
+// kernels of one smoothing of level l with nu sweeps
+int smoothing_launches(const ferrox_ctx* c, int l, int nu) {
+  const bool rb = c->num.precision == FERROX_MIXED ? rb_sweeps<float>(c, l, nu)
+                                                   : rb_sweeps<double>(c, l, nu);
+  return rb ? nu : 2 * nu;
+}
+
 // first: the fine level starts from a zero correction; last: phi += e rides on
 // the last fine-level sweep
 // levels l0 .. L of one V-cycle (l0 = 1: the coarse part of the direct form)
@@ -423,13 +441,24 @@ void enqueue_levels(ferrox_ctx* c, cudaStream_t s, W wrap, int l0, bool first, b
   const int nu1 = c->num.nu1, nu2 = c->num.nu2;
   const int constant = 0;
   const int lt = c->tail_first, L = (int)c->lv.size() - 1;
+  T* alt = static_cast<T*>(c->e_alt);
   for (int l = l0; l < lt; ++l) {
     const int ks = l == 0 ? FERROX_K_SMOOTH0 : FERROX_K_SMOOTHC;
-    for (int sw = 0; sw < nu1; ++sw) {
-      const int zero = sw == 0 && (first || l > 0);
-      const double sb = sweep_bytes<T>(c, c->lv[l]);
-      wrap(ks, sb, [&] { launch_smooth<T>(a, c->lv[l], 0, zero, nullptr, s); });
-      wrap(ks, sb, [&] { launch_smooth<T>(a, c->lv[l], 1, 0, nullptr, s); });
+    const double sb = sweep_bytes<T>(c, c->lv[l]);
+    if (rb_sweeps<T>(c, l, nu1)) {
+      T* own = a.e + c->lv[l].off;
+      for (int sw = 0; sw < nu1; ++sw) {
+        const int zero = sw == 0 && (first || l > 0);
+        T* src = sw % 2 ? alt : own;
+        T* dst = sw % 2 ? own : alt;
+        wrap(ks, 2.0 * sb, [&] { launch_smooth_rb<T>(a, c->lv[l], src, dst, zero, nullptr, s); });
+      }
+    } else {
+      for (int sw = 0; sw < nu1; ++sw) {
+        const int zero = sw == 0 && (first || l > 0);
+        wrap(ks, sb, [&] { launch_smooth<T>(a, c->lv[l], 0, zero, nullptr, s); });
+        wrap(ks, sb, [&] { launch_smooth<T>(a, c->lv[l], 1, 0, nullptr, s); });
+      }
     }
     wrap(FERROX_K_RESTRICT, restrict_bytes<T>(c->lv[l], c->lv[l + 1]),
          [&] { launch_restrict<T>(a, c->lv[l], c->lv[l + 1], nu1, s); });
@@ -458,12 +487,22 @@ void enqueue_levels(ferrox_ctx* c, cudaStream_t s, W wrap, int l0, bool first, b
     wrap(FERROX_K_PROLONG, prolong_bytes<T>(c->lv[l], c->lv[l + 1]),
          [&] { launch_prolong<T>(a, c->lv[l], c->lv[l + 1], constant, s, tiled); });
     const double sb = sweep_bytes<T>(c, c->lv[l]);
+    const bool rb = rb_sweeps<T>(c, l, nu2);
+    T* own = a.e + c->lv[l].off;
     for (int sw = 0; sw < nu2; ++sw) {
       const bool fuse = last && l == 0 && sw == nu2 - 1;   // phi += e folded into the last sweep
-      // the fused update also reads and writes phi (FP64) on the swept colour
-      const double ub = fuse ? 0.5 * (double)c->lv[0].ncell * 16.0 : 0.0;
-      wrap(ks, sb, [&] { launch_smooth<T>(a, c->lv[l], 0, 0, nullptr, s); });
-      wrap(ks, sb + ub, [&] { launch_smooth<T>(a, c->lv[l], 1, 0, fuse ? &upd : nullptr, s); });
+      // the fused update also reads and writes phi (FP64) of the swept cells
+      if (rb) {
+        const double ub = fuse ? (double)c->lv[0].ncell * 16.0 : 0.0;
+        T* src = sw % 2 ? alt : own;
+        T* dst = sw % 2 ? own : alt;
+        wrap(ks, 2.0 * sb + ub,
+             [&] { launch_smooth_rb<T>(a, c->lv[l], src, dst, 0, fuse ? &upd : nullptr, s); });
+      } else {
+        const double ub = fuse ? 0.5 * (double)c->lv[0].ncell * 16.0 : 0.0;
+        wrap(ks, sb, [&] { launch_smooth<T>(a, c->lv[l], 0, 0, nullptr, s); });
+        wrap(ks, sb + ub, [&] { launch_smooth<T>(a, c->lv[l], 1, 0, fuse ? &upd : nullptr, s); });
+      }
     }
   }
 }
@@ -566,7 +605,10 @@ bool separate_update(const ferrox_ctx* c) {
 
 // kernels launched by one outer iteration: V-cycle, (update), residual
 int vcycle_launches(const ferrox_ctx* c) {
-  return c->tail_first * (2 * c->num.nu1 + 1 + 1 + 2 * c->num.nu2) + 1;
+  int n = 1;   // the tail or the dense bottom solve
+  for (int l = 0; l < c->tail_first; ++l)
+    n += smoothing_launches(c, l, c->num.nu1) + 1 + 1 + smoothing_launches(c, l, c->num.nu2);
+  return n;
 }
 
 int launches_per_cycle(const ferrox_ctx* c) {
@@ -1010,7 +1052,7 @@ void release(ferrox_ctx* c) {
   cudaGraph_t gr[4] = {c->gr_step, c->gr_solve, c->gr_tdgl, c->gr_step_nn};
   for (auto g : ge) if (g) cudaGraphExecDestroy(g);
   for (auto g : gr) if (g) cudaGraphDestroy(g);
-  void* ptrs[] = {c->b, c->Pbuf, c->Fbuf, c->phi_prev, c->e_arena, c->r_arena, c->s_arena, c->coef, c->coef0,
+  void* ptrs[] = {c->b, c->Pbuf, c->Fbuf, c->phi_prev, c->e_arena, c->e_alt, c->r_arena, c->s_arena, c->coef, c->coef0,
                   c->planes_d, c->lv_d, c->lvt_d, c->nn_scale, c->phi_guess, c->nn_pf, c->nn_stats, c->params_d, c->stats_d, c->partials_d, c->charge_d,
                   c->charge_part_d, c->dense_d, c->dense_wide_d};
   for (void* p : ptrs) if (p) cudaFree(p);
@@ -1128,6 +1170,19 @@ ferrox_status ferrox_init_geometry(ferrox_ctx** out, const ferrox_geometry* geom
     FX_INIT_CK(cudaMemset(ctx->phi_prev, 0, N * sizeof(double)));
   }
   FX_INIT_CK(cudaMalloc(&ctx->e_arena, ctx->arena * tsz));
+  // FERROX_RB_SWEEPS=0 in the environment keeps the colour-by-colour sweeps
+  // (same results; for comparing the two paths)
+  const char* rb_env = std::getenv("FERROX_RB_SWEEPS");
+  if (mixed && !(rb_env && rb_env[0] == '0')) {
+    // the fused red-black sweeps alternate between a level's array and e_alt
+    long long alt = 0;
+    for (int l = 0; l < ctx->tail_first; ++l)
+      if (smooth_rb_tile<float>(ctx->lv[l]) > 0) alt = std::max(alt, ctx->lv[l].ncell);
+    if (alt > 0) {
+      FX_INIT_CK(cudaMalloc(&ctx->e_alt, alt * tsz));
+      FX_INIT_CK(smooth_rb_prepare<float>());
+    }
+  }
   FX_INIT_CK(cudaMalloc(&ctx->r_arena, ctx->arena * tsz));
   if (ctx->has_sc) FX_INIT_CK(cudaMalloc(&ctx->s_arena, ctx->arena * tsz));
   FX_INIT_CK(cudaMalloc(&ctx->planes_d, ctx->nz * sizeof(PlaneTDGL)));

@@ -208,6 +208,15 @@ struct CheckArgs {
 template <typename T>
 void launch_smooth(const MGArgs<T>& a, const LevelDesc& L, int color, int zero_init,
                    const UpdateArgs* upd, cudaStream_t s, const DevStats* zero_stats = nullptr);
+// fused red-black sweep (both colours in one launch, e_in -> e_out, level-relative
+// arrays): smooth_rb_tile is 0 where the level cannot take it
+template <typename T>
+int smooth_rb_tile(const LevelDesc& L);
+template <typename T>
+cudaError_t smooth_rb_prepare();
+template <typename T>
+void launch_smooth_rb(const MGArgs<T>& a, const LevelDesc& L, const T* e_in, T* e_out,
+                      int zero_init, const UpdateArgs* upd, cudaStream_t s);
 dim3 check_grid(const LevelDesc& C);
 void launch_restrict_check(const MGArgs<double>& fa, double* rc, const LevelDesc& F,
                            const LevelDesc& C, int nu1, const CheckArgs& ck, cudaStream_t s);

@@ -104,6 +104,125 @@ __global__ void __launch_bounds__(256) smooth_kz_kernel(MGArgs<T> a, LevelDesc L
   }
 }
 
+// ---- fused red-black sweep (one launch per full sweep, out of place) -------------------
+// One red-black Gauss-Seidel sweep of a level (red cells, then black cells) in
+// one launch, reading e_in and writing e_out.  A block owns a TX x TY x TZ tile.
+// It stages e_in on the tile plus a two-cell halo and r on the tile plus a
+// one-cell halo in shared memory, relaxes the red cells of the tile and of its
+// one-cell halo (the halo's red values are recomputed from the same inputs and
+// operations as in the block that owns those cells, so they are identical),
+// relaxes the black cells of the tile against them, and writes both colours of
+// the tile.  Red cells are (i + j + k) even, as in the colour sweeps.  Every
+// cell sees the operations of smooth_pair in the same order, so one launch
+// equals the red sweep followed by the black sweep bit for bit, while each
+// array element is read and written once per full sweep instead of once per
+// colour.  Lateral sizes must be even and at least the tile's (one periodic
+// wrap covers the halo); z beyond the level is the zero of the correction
+// equation's Dirichlet faces.  With zero_init the sweep starts from e = 0
+// (e_in unused).  With u.phi set, phi += e of both colours (clamped) follows.
+template <typename T>
+struct RBArgs {
+  const T* e_in;            // level-relative
+  T* e_out;                 // level-relative
+  const T* r;               // level-relative
+  const T* s;               // level-relative Newton shift (null without SC)
+  const PlaneCoef<T>* coef; // the level's planes
+  int nx, ny, nz;
+  int zero_init;
+  Upd u;
+  const DevStats* st;       // zero_phi flag for the fused update
+};
+
+template <typename T, int TX, int TY, int TZ>
+__global__ void __launch_bounds__(256) smooth_rb_kernel(RBArgs<T> a) {
+  pdl_enter();
+  constexpr int EX = TX + 4, EY = TY + 4, EZ = TZ + 4, EN = EX * EY * EZ;
+  constexpr int RX = TX + 2, RY = TY + 2, RZ = TZ + 2, RN = RX * RY * RZ;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  PlaneCoef<T>* Cs = reinterpret_cast<PlaneCoef<T>*>(smem_raw);
+  T* Es = reinterpret_cast<T*>(smem_raw + ((RZ * sizeof(PlaneCoef<T>) + 15) / 16) * 16);
+  T* Rs = Es + (a.zero_init ? 0 : EN);
+  const int tid = threadIdx.x;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
+  const int nx = a.nx, ny = a.ny, nz = a.nz;
+  const int plane = nx * ny;
+  // stage: e_in with a two-cell halo (zero outside 0..nz-1), r with a one-cell halo
+  if (!a.zero_init) {
+    for (int q = tid; q < EN; q += 256) {
+      const int xx = q % EX, t = q / EX, yy = t % EY, zz = t / EY;
+      int x = x0 - 2 + xx, y = y0 - 2 + yy;
+      const int z = z0 - 2 + zz;
+      x += x < 0 ? nx : 0; x -= x >= nx ? nx : 0;
+      y += y < 0 ? ny : 0; y -= y >= ny ? ny : 0;
+      Es[q] = (z >= 0 && z < nz) ? a.e_in[z * plane + y * nx + x] : T(0);
+    }
+  }
+  for (int q = tid; q < RN; q += 256) {
+    const int xx = q % RX, t = q / RX, yy = t % RY, zz = t / RY;
+    int x = x0 - 1 + xx, y = y0 - 1 + yy;
+    const int z = z0 - 1 + zz;
+    x += x < 0 ? nx : 0; x -= x >= nx ? nx : 0;
+    y += y < 0 ? ny : 0; y -= y >= ny ? ny : 0;
+    Rs[q] = (z >= 0 && z < nz) ? a.r[z * plane + y * nx + x] : T(0);
+  }
+  if (tid < RZ) {
+    const int z = z0 - 1 + tid;
+    if (z >= 0 && z < nz) Cs[tid] = ldg_struct(a.coef + z);
+  }
+  __syncthreads();
+  // red cells of the tile and its one-cell halo; Rs then holds the new red values
+  for (int q = tid; q < RN; q += 256) {
+    const int xx = q % RX, t = q / RX, yy = t % RY, zz = t / RY;
+    int x = x0 - 1 + xx, y = y0 - 1 + yy;
+    const int z = z0 - 1 + zz;
+    if (z < 0 || z >= nz) continue;
+    x += x < 0 ? nx : 0; x -= x >= nx ? nx : 0;
+    y += y < 0 ? ny : 0; y -= y >= ny ? ny : 0;
+    if ((x + y + z) & 1) continue;
+    const PlaneCoef<T> c = Cs[zz];
+    const int id = z * plane + y * nx + x;
+    T ev;
+    if (a.zero_init) {
+      const T d = c.has_s ? T(1) / (c.diag + a.s[id]) : c.invdiag;
+      ev = Rs[q] * d;
+    } else {
+      const int e = ((zz + 1) * EY + (yy + 1)) * EX + (xx + 1);
+      T acc = Rs[q];
+      acc = fma(c.cx, Es[e - 1] + Es[e + 1], acc);
+      acc = fma(c.cy, Es[e - EX] + Es[e + EX], acc);
+      acc = fma(c.czlo, Es[e - EX * EY], acc);
+      acc = fma(c.czhi, Es[e + EX * EY], acc);
+      ev = c.has_s ? acc / (c.diag + a.s[id]) : acc * c.invdiag;
+    }
+    Rs[q] = ev;
+  }
+  __syncthreads();
+  // black cells of the tile against the new red values; both colours written out
+  Upd u = a.u;
+  if (u.phi) u.zero = a.st->zero_phi;
+  for (int q = tid; q < TX * TY * TZ; q += 256) {
+    const int xx = q % TX, t = q / TX, yy = t % TY, zz = t / TY;
+    const int x = x0 + xx, y = y0 + yy, z = z0 + zz;
+    if (x >= nx || y >= ny || z >= nz) continue;
+    const int id = z * plane + y * nx + x;
+    const int rq = ((zz + 1) * RY + (yy + 1)) * RX + (xx + 1);
+    T ev;
+    if ((x + y + z) & 1) {
+      const PlaneCoef<T> c = Cs[zz + 1];
+      T acc = Rs[rq];
+      acc = fma(c.cx, Rs[rq - 1] + Rs[rq + 1], acc);
+      acc = fma(c.cy, Rs[rq - RX] + Rs[rq + RX], acc);
+      acc = fma(c.czlo, Rs[rq - RX * RY], acc);
+      acc = fma(c.czhi, Rs[rq + RX * RY], acc);
+      ev = c.has_s ? acc / (c.diag + a.s[id]) : acc * c.invdiag;
+    } else {
+      ev = Rs[rq];
+    }
+    a.e_out[id] = ev;
+    if (u.phi) apply_update(u, id, ev);
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) restrict_kernel(MGArgs<T> a, LevelDesc F, LevelDesc C,
                                                        int skip_black) {
@@ -477,6 +596,67 @@ void launch_smooth(const MGArgs<T>& a, const LevelDesc& L, int color, int zero_i
   launch_k(smooth_kernel<T>, grid, block, 0, s, a, L, color, zero_init, u, st, zero_stats);
 }
 
+namespace {
+template <typename T, int TX, int TY, int TZ>
+size_t rb_smem_bytes(int zero_init) {
+  constexpr int RZ = TZ + 2;
+  const size_t head = ((RZ * sizeof(PlaneCoef<T>) + 15) / 16) * 16;
+  const size_t en = zero_init ? 0 : (size_t)(TX + 4) * (TY + 4) * (TZ + 4);
+  return head + (en + (size_t)(TX + 2) * (TY + 2) * RZ) * sizeof(T);
+}
+
+template <typename T, int TX, int TY, int TZ>
+void launch_rb(const RBArgs<T>& a, cudaStream_t s) {
+  const size_t smem = rb_smem_bytes<T, TX, TY, TZ>(a.zero_init);
+  const dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, (a.nz + TZ - 1) / TZ);
+  launch_k(smooth_rb_kernel<T, TX, TY, TZ>, grid, dim3(256), smem, s, a);
+}
+
+template <typename T, int TX, int TY, int TZ>
+cudaError_t rb_prepare_one() {
+  return cudaFuncSetAttribute(smooth_rb_kernel<T, TX, TY, TZ>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)rb_smem_bytes<T, TX, TY, TZ>(0));
+}
+}  // namespace
+
+// shared-memory opt-in of the fused sweep kernels on the current device
+template <typename T>
+cudaError_t smooth_rb_prepare() {
+  cudaError_t e = rb_prepare_one<T, 32, 16, 8>();
+  return e != cudaSuccess ? e : rb_prepare_one<T, 16, 8, 4>();
+}
+
+// tile of the fused sweep for a level: the large tile where it still gives
+// enough blocks, a small one otherwise (0: not eligible)
+template <typename T>
+int smooth_rb_tile(const LevelDesc& L) {
+  if (sizeof(T) != sizeof(float)) return 0;
+  if ((L.nx & 1) || (L.ny & 1)) return 0;
+  if (L.nx >= 32 && L.ny >= 16 && L.ncell >= (1LL << 20)) return 2;   // 32 x 16 x 8
+  if (L.nx >= 16 && L.ny >= 8 && L.ncell >= (1LL << 14)) return 1;    // 16 x 8 x 4
+  return 0;
+}
+
+template <typename T>
+void launch_smooth_rb(const MGArgs<T>& a, const LevelDesc& L, const T* e_in, T* e_out,
+                      int zero_init, const UpdateArgs* upd, cudaStream_t s) {
+  RBArgs<T> r{};
+  r.e_in = e_in;
+  r.e_out = e_out;
+  r.r = a.r + L.off;
+  r.s = a.s ? a.s + L.off : nullptr;
+  r.coef = a.coef + L.coef_off;
+  r.nx = L.nx; r.ny = L.ny; r.nz = L.nz;
+  r.zero_init = zero_init;
+  r.u = Upd{nullptr, 0.0, 0};
+  if (upd) { r.u.phi = upd->phi; r.u.clamp = upd->clamp; r.st = upd->stats; }
+  if (smooth_rb_tile<T>(L) == 2)
+    launch_rb<T, 32, 16, 8>(r, s);
+  else
+    launch_rb<T, 16, 8, 4>(r, s);
+}
+
 dim3 check_grid(const LevelDesc& C) {
   dim3 block, grid;
   block_shape(C.nx, C.ny, block, grid, C.nz);
@@ -608,6 +788,10 @@ cudaError_t launch_carrier_exp(const double* u, double* ep, double* em, long lon
 #define FX_INST(T)                                                                              \
   template void launch_smooth<T>(const MGArgs<T>&, const LevelDesc&, int, int,                  \
                                  const UpdateArgs*, cudaStream_t, const DevStats*);             \
+  template int smooth_rb_tile<T>(const LevelDesc&);                                             \
+  template cudaError_t smooth_rb_prepare<T>();                                                  \
+  template void launch_smooth_rb<T>(const MGArgs<T>&, const LevelDesc&, const T*, T*, int,      \
+                                    const UpdateArgs*, cudaStream_t);                           \
   template void launch_restrict<T>(const MGArgs<T>&, const LevelDesc&, const LevelDesc&, int,   \
                                    cudaStream_t);                                               \
   template void launch_prolong<T>(const MGArgs<T>&, const LevelDesc&, const LevelDesc&, int,    \
