@@ -422,7 +422,7 @@ int adapt_max(const ferrox_ctx* c) { return c->num.inner < 0 ? -c->num.inner : 0
 // sweep lands in the level's own array.
 template <typename T>
 bool rb_sweeps(const ferrox_ctx* c, int l, int nu) {
-  return c->e_alt && nu % 2 == 0 && smooth_rb_tile<T>(c->lv[l]) > 0;
+  return c->e_alt && nu % 2 == 0 && smooth_rb_tile<T>(c->lv[l], c->has_sc) > 0;
 }
 
 // kernels of one smoothing of level l with nu sweeps
@@ -1177,7 +1177,7 @@ ferrox_status ferrox_init_geometry(ferrox_ctx** out, const ferrox_geometry* geom
     // the fused red-black sweeps alternate between a level's array and e_alt
     long long alt = 0;
     for (int l = 0; l < ctx->tail_first; ++l)
-      if (smooth_rb_tile<float>(ctx->lv[l]) > 0) alt = std::max(alt, ctx->lv[l].ncell);
+      if (smooth_rb_tile<float>(ctx->lv[l], ctx->has_sc) > 0) alt = std::max(alt, ctx->lv[l].ncell);
     if (alt > 0) {
       FX_INIT_CK(cudaMalloc(&ctx->e_alt, alt * tsz));
       FX_INIT_CK(smooth_rb_prepare<float>());

@@ -211,7 +211,7 @@ void launch_smooth(const MGArgs<T>& a, const LevelDesc& L, int color, int zero_i
 // fused red-black sweep (both colours in one launch, e_in -> e_out, level-relative
 // arrays): smooth_rb_tile is 0 where the level cannot take it
 template <typename T>
-int smooth_rb_tile(const LevelDesc& L);
+int smooth_rb_tile(const LevelDesc& L, bool has_s);
 template <typename T>
 cudaError_t smooth_rb_prepare();
 template <typename T>

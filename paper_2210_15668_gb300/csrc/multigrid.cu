@@ -20,6 +20,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <algorithm>
+
 #include "ferrox_internal.cuh"
 #include "mg_device.cuh"
 
@@ -106,20 +108,22 @@ __global__ void __launch_bounds__(256) smooth_kz_kernel(MGArgs<T> a, LevelDesc L
 
 // ---- fused red-black sweep (one launch per full sweep, out of place) -------------------
 // One red-black Gauss-Seidel sweep of a level (red cells, then black cells) in
-// one launch, reading e_in and writing e_out.  A block owns a TX x TY x TZ tile.
-// It stages e_in on the tile plus a two-cell halo and r on the tile plus a
-// one-cell halo in shared memory, relaxes the red cells of the tile and of its
-// one-cell halo (the halo's red values are recomputed from the same inputs and
-// operations as in the block that owns those cells, so they are identical),
-// relaxes the black cells of the tile against them, and writes both colours of
-// the tile.  Red cells are (i + j + k) even, as in the colour sweeps.  Every
-// cell sees the operations of smooth_pair in the same order, so one launch
-// equals the red sweep followed by the black sweep bit for bit, while each
-// array element is read and written once per full sweep instead of once per
-// colour.  Lateral sizes must be even and at least the tile's (one periodic
-// wrap covers the halo); z beyond the level is the zero of the correction
-// equation's Dirichlet faces.  With zero_init the sweep starts from e = 0
-// (e_in unused).  With u.phi set, phi += e of both colours (clamped) follows.
+// one launch, reading e_in and writing e_out.  A block owns a 32 x 16 lateral
+// tile and marches up a chunk of planes.  Each plane of e_in (with a two-cell
+// lateral halo) and of r (one-cell halo) is copied into a shared-memory ring a
+// few planes ahead of its use (cp.async).  At each step the block relaxes the
+// red cells of one plane, tile plus one-cell halo (the halo's red values are
+// recomputed from the same inputs and operations as in the block that owns those
+// cells, so they are identical), then the black cells of the plane below against
+// the new red values of its three planes, and writes both colours of that plane.
+// Red cells are (i + j + k) even, as in the colour sweeps.  Every cell sees the
+// operations of smooth_pair in the same order, so one launch equals the red
+// sweep followed by the black sweep bit for bit, while each array element is read
+// from memory and written once per full sweep instead of once per colour.
+// Lateral sizes must be even and at least the tile's (one periodic wrap covers
+// the halo); planes beyond the level are the zero of the correction equation's
+// Dirichlet faces.  With zero_init the sweep starts from e = 0 (e_in unused).
+// With u.phi set, phi += e of both colours (clamped) follows.
 template <typename T>
 struct RBArgs {
   const T* e_in;            // level-relative
@@ -128,99 +132,167 @@ struct RBArgs {
   const T* s;               // level-relative Newton shift (null without SC)
   const PlaneCoef<T>* coef; // the level's planes
   int nx, ny, nz;
+  int kz;                   // planes per block (z chunk)
   int zero_init;
   Upd u;
   const DevStats* st;       // zero_phi flag for the fused update
 };
 
-template <typename T, int TX, int TY, int TZ>
-__global__ void __launch_bounds__(256) smooth_rb_kernel(RBArgs<T> a) {
+// asynchronous 16-byte global -> shared copy (zero-filled when !valid)
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src),
+               "r"(valid ? 16 : 0)
+               : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Shared-memory planes are 40 floats wide: global x0 - 4 .. x0 + 35 (local lx =
+// x - x0 + 4), staged as ten 16-byte chunks per row.  The e planes hold rows
+// y0 - 2 .. y0 + 17 (two-cell halo), the r (s) planes rows y0 - 1 .. y0 + 16.
+constexpr int kRbTX = 32, kRbTY = 16;          // lateral tile, 256 threads
+constexpr int kRbD = 1;                        // planes staged ahead of use
+constexpr int kRbW = 40, kRbCH = 10;           // row width (floats) and 16-byte chunks per row
+constexpr int kRbEY = kRbTY + 4, kRbEP = kRbEY * kRbW;
+constexpr int kRbRY = kRbTY + 2, kRbRP = kRbRY * kRbW;
+constexpr int kRbNE = kRbD + 3, kRbNR = kRbD + 5;   // ring slots (see the step loop)
+constexpr int kRbKZ = 128;                          // planes per block at most
+constexpr long long kRbMinCells = 1LL << 23;        // smaller levels keep the colour sweeps
+constexpr int kRbCoefBytes = (kRbKZ + 2) * (int)sizeof(PlaneCoef<float>);
+
+__global__ void __launch_bounds__(256) smooth_rb_kernel(RBArgs<float> a) {
   pdl_enter();
-  constexpr int EX = TX + 4, EY = TY + 4, EZ = TZ + 4, EN = EX * EY * EZ;
-  constexpr int RX = TX + 2, RY = TY + 2, RZ = TZ + 2, RN = RX * RY * RZ;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  PlaneCoef<T>* Cs = reinterpret_cast<PlaneCoef<T>*>(smem_raw);
-  T* Es = reinterpret_cast<T*>(smem_raw + ((RZ * sizeof(PlaneCoef<T>) + 15) / 16) * 16);
-  T* Rs = Es + (a.zero_init ? 0 : EN);
-  const int tid = threadIdx.x;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
+  PlaneCoef<float>* Cs = reinterpret_cast<PlaneCoef<float>*>(smem_raw);   // planes z0-1 .. z1
+  float* Es = reinterpret_cast<float*>(smem_raw + kRbCoefBytes);  // kRbNE e planes (not with zero_init)
+  float* Rs = Es + (a.zero_init ? 0 : kRbNE * kRbEP);        // kRbNR planes: r, then new red values
+  float* Ss = Rs + kRbNR * kRbRP;                            // kRbNR planes of s (semiconductor)
+  const int t = threadIdx.x;
   const int nx = a.nx, ny = a.ny, nz = a.nz;
   const int plane = nx * ny;
-  // stage: e_in with a two-cell halo (zero outside 0..nz-1), r with a one-cell halo
-  if (!a.zero_init) {
-    for (int q = tid; q < EN; q += 256) {
-      const int xx = q % EX, t = q / EX, yy = t % EY, zz = t / EY;
-      int x = x0 - 2 + xx, y = y0 - 2 + yy;
-      const int z = z0 - 2 + zz;
-      x += x < 0 ? nx : 0; x -= x >= nx ? nx : 0;
-      y += y < 0 ? ny : 0; y -= y >= ny ? ny : 0;
-      Es[q] = (z >= 0 && z < nz) ? a.e_in[z * plane + y * nx + x] : T(0);
+  const int x0 = blockIdx.x * kRbTX, y0 = blockIdx.y * kRbTY;
+  const int z0 = blockIdx.z * a.kz, z1 = min(z0 + a.kz, nz);
+  auto wrapx = [&](int x) { return x < 0 ? x + nx : (x >= nx ? x - nx : x); };
+  auto wrapy = [&](int y) { return y < 0 ? y + ny : (y >= ny ? y - ny : y); };
+  // staging items of this thread (fixed across planes): e chunk t (< 200), r/s chunk t (< 180)
+  const bool has_e = !a.zero_init && t < kRbEY * kRbCH;
+  const bool has_r = t < kRbRY * kRbCH;
+  const int ch = t % kRbCH;
+  const int e_soff = (t / kRbCH) * kRbW + ch * 4;
+  const int e_goff = wrapy(y0 - 2 + t / kRbCH) * nx + wrapx(x0 - 4 + ch * 4);
+  const int r_soff = e_soff;                                   // same row/chunk layout
+  const int r_goff = wrapy(y0 - 1 + t / kRbCH) * nx + wrapx(x0 - 4 + ch * 4);
+  const int nunits = z1 - z0 + 4;                               // e planes z0-2 .. z1+1
+  auto stage = [&](int j) {
+    if (j < nunits) {
+      const int z = z0 - 2 + j;
+      const bool zin = z >= 0 && z < nz;
+      const int zoff = zin ? z * plane : 0;
+      if (has_e) cp_async16(Es + (j % kRbNE) * kRbEP + e_soff, a.e_in + zoff + e_goff, zin);
+      if (has_r && z >= z0 - 1 && z <= z1) {
+        cp_async16(Rs + (j % kRbNR) * kRbRP + r_soff, a.r + zoff + r_goff, zin);
+        if (a.s) cp_async16(Ss + (j % kRbNR) * kRbRP + r_soff, a.s + zoff + r_goff, zin);
+      }
     }
-  }
-  for (int q = tid; q < RN; q += 256) {
-    const int xx = q % RX, t = q / RX, yy = t % RY, zz = t / RY;
-    int x = x0 - 1 + xx, y = y0 - 1 + yy;
-    const int z = z0 - 1 + zz;
-    x += x < 0 ? nx : 0; x -= x >= nx ? nx : 0;
-    y += y < 0 ? ny : 0; y -= y >= ny ? ny : 0;
-    Rs[q] = (z >= 0 && z < nz) ? a.r[z * plane + y * nx + x] : T(0);
-  }
-  if (tid < RZ) {
-    const int z = z0 - 1 + tid;
-    if (z >= 0 && z < nz) Cs[tid] = ldg_struct(a.coef + z);
-  }
-  __syncthreads();
-  // red cells of the tile and its one-cell halo; Rs then holds the new red values
-  for (int q = tid; q < RN; q += 256) {
-    const int xx = q % RX, t = q / RX, yy = t % RY, zz = t / RY;
-    int x = x0 - 1 + xx, y = y0 - 1 + yy;
-    const int z = z0 - 1 + zz;
-    if (z < 0 || z >= nz) continue;
-    x += x < 0 ? nx : 0; x -= x >= nx ? nx : 0;
-    y += y < 0 ? ny : 0; y -= y >= ny ? ny : 0;
-    if ((x + y + z) & 1) continue;
-    const PlaneCoef<T> c = Cs[zz];
-    const int id = z * plane + y * nx + x;
-    T ev;
-    if (a.zero_init) {
-      const T d = c.has_s ? T(1) / (c.diag + a.s[id]) : c.invdiag;
-      ev = Rs[q] * d;
-    } else {
-      const int e = ((zz + 1) * EY + (yy + 1)) * EX + (xx + 1);
-      T acc = Rs[q];
-      acc = fma(c.cx, Es[e - 1] + Es[e + 1], acc);
-      acc = fma(c.cy, Es[e - EX] + Es[e + EX], acc);
-      acc = fma(c.czlo, Es[e - EX * EY], acc);
-      acc = fma(c.czhi, Es[e + EX * EY], acc);
-      ev = c.has_s ? acc / (c.diag + a.s[id]) : acc * c.invdiag;
-    }
-    Rs[q] = ev;
-  }
-  __syncthreads();
-  // black cells of the tile against the new red values; both colours written out
+    cp_async_commit();   // one group per unit, empty past the end
+  };
+  // red items of this thread: item t and t + 256 of the 18 rows x 17 red cells of the
+  // r region (x0 - 1 .. x0 + 32); black item: row t / 16, pair t % 16 of the tile
+  const int it0 = t, it1 = t + 256;
+  const int ry0 = it0 / 17, rk0 = it0 % 17;
+  const int ry1 = it1 / 17, rk1 = it1 % 17;
+  const bool red1 = it1 < kRbRY * 17;
+  const int by = t >> 4, bk = t & 15;
+  const int gy_b = y0 + by;
+  const bool bout = (x0 + 2 * bk) < nx && gy_b < ny;
   Upd u = a.u;
   if (u.phi) u.zero = a.st->zero_phi;
-  for (int q = tid; q < TX * TY * TZ; q += 256) {
-    const int xx = q % TX, t = q / TX, yy = t % TY, zz = t / TY;
-    const int x = x0 + xx, y = y0 + yy, z = z0 + zz;
-    if (x >= nx || y >= ny || z >= nz) continue;
-    const int id = z * plane + y * nx + x;
-    const int rq = ((zz + 1) * RY + (yy + 1)) * RX + (xx + 1);
-    T ev;
-    if ((x + y + z) & 1) {
-      const PlaneCoef<T> c = Cs[zz + 1];
-      T acc = Rs[rq];
-      acc = fma(c.cx, Rs[rq - 1] + Rs[rq + 1], acc);
-      acc = fma(c.cy, Rs[rq - RX] + Rs[rq + RX], acc);
-      acc = fma(c.czlo, Rs[rq - RX * RY], acc);
-      acc = fma(c.czhi, Rs[rq + RX * RY], acc);
-      ev = c.has_s ? acc / (c.diag + a.s[id]) : acc * c.invdiag;
-    } else {
-      ev = Rs[rq];
-    }
-    a.e_out[id] = ev;
-    if (u.phi) apply_update(u, id, ev);
+
+  for (int j = 0; j < kRbD + 2; ++j) stage(j);
+  // coefficients of every plane the block relaxes (the first barrier publishes them)
+  for (int q = t; q < z1 - z0 + 2; q += 256) {
+    const int z = z0 - 1 + q;
+    if (z >= 0 && z < nz) Cs[q] = ldg_struct(a.coef + z);
   }
+  // step i: red cells of plane p = z0 - 1 + i (units i .. i + 2 staged), then the
+  // black cells of plane p - 1 and both colours of it written out
+  int se = 0, sr = 0;   // ring slot of unit i in the e and r rings
+  for (int i = 0; i < z1 - z0 + 2; ++i) {
+    stage(i + kRbD + 2);
+    cp_async_wait<kRbD>();
+    __syncthreads();
+    const int p = z0 - 1 + i;
+    const int se1 = se + 1 == kRbNE ? 0 : se + 1, se2 = se1 + 1 == kRbNE ? 0 : se1 + 1;
+    const int sr1 = sr + 1 == kRbNR ? 0 : sr + 1, srm = sr == 0 ? kRbNR - 1 : sr - 1;
+    if (p >= 0 && p < nz) {
+      const PlaneCoef<float> c = Cs[i];
+      float* R = Rs + sr1 * kRbRP;
+      const float* S = Ss + sr1 * kRbRP;
+      const float* Ec = Es + se1 * kRbEP;   // plane p
+      const float* Ed = Es + se * kRbEP;    // plane p - 1
+      const float* Eu = Es + se2 * kRbEP;   // plane p + 1
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (h == 1 && !red1) break;
+        const int ry = h ? ry1 : ry0, k = h ? rk1 : rk0;
+        // red cells of the row: local lx = 3 or 4, then every second one
+        const int lx = 3 + ((3 + y0 - 1 + ry + p) & 1) + 2 * k;
+        const int q = ry * kRbW + lx;
+        float ev;
+        if (a.zero_init) {
+          const float d = c.has_s ? 1.0f / (c.diag + S[q]) : c.invdiag;
+          ev = R[q] * d;
+        } else {
+          const int e = q + kRbW;             // the e planes start one row lower
+          float acc = R[q];
+          acc = fmaf(c.cx, Ec[e - 1] + Ec[e + 1], acc);
+          acc = fmaf(c.cy, Ec[e - kRbW] + Ec[e + kRbW], acc);
+          acc = fmaf(c.czlo, Ed[e], acc);
+          acc = fmaf(c.czhi, Eu[e], acc);
+          ev = c.has_s ? acc / (c.diag + S[q]) : acc * c.invdiag;
+        }
+        R[q] = ev;
+      }
+    }
+    __syncthreads();
+    const int pb = p - 1;
+    if (pb >= z0 && pb < z1 && bout) {
+      const PlaneCoef<float> c = Cs[i - 1];
+      const float* Rc = Rs + sr * kRbRP;    // plane pb
+      const float* Rd = Rs + srm * kRbRP;   // plane pb - 1
+      const float* Ru = Rs + sr1 * kRbRP;   // plane pb + 1 (red values of this step)
+      const float* S = Ss + sr * kRbRP;
+      // the pair (x0 + 2 bk, x0 + 2 bk + 1): its black cell is the second when x0 + 2 bk is red
+      const int second = ((gy_b + pb) & 1) == 0;
+      const int q0 = (by + 1) * kRbW + 4 + 2 * bk;
+      const int qb = q0 + second;
+      float acc = Rc[qb];
+      acc = fmaf(c.cx, Rc[qb - 1] + Rc[qb + 1], acc);
+      acc = fmaf(c.cy, Rc[qb - kRbW] + Rc[qb + kRbW], acc);
+      acc = fmaf(c.czlo, Rd[qb], acc);
+      acc = fmaf(c.czhi, Ru[qb], acc);
+      const float eb = c.has_s ? acc / (c.diag + S[qb]) : acc * c.invdiag;
+      const float er = Rc[q0 + 1 - second];
+      const int id = pb * plane + gy_b * nx + x0 + 2 * bk;
+      const float2 v = second ? make_float2(er, eb) : make_float2(eb, er);
+      *reinterpret_cast<float2*>(a.e_out + id) = v;
+      if (u.phi) {
+        apply_update(u, id, v.x);
+        apply_update(u, id + 1, v.y);
+      }
+    }
+    se = se1;
+    sr = sr1;
+  }
+  cp_async_wait<0>();
 }
 
 template <typename T>
@@ -597,64 +669,64 @@ void launch_smooth(const MGArgs<T>& a, const LevelDesc& L, int color, int zero_i
 }
 
 namespace {
-template <typename T, int TX, int TY, int TZ>
-size_t rb_smem_bytes(int zero_init) {
-  constexpr int RZ = TZ + 2;
-  const size_t head = ((RZ * sizeof(PlaneCoef<T>) + 15) / 16) * 16;
-  const size_t en = zero_init ? 0 : (size_t)(TX + 4) * (TY + 4) * (TZ + 4);
-  return head + (en + (size_t)(TX + 2) * (TY + 2) * RZ) * sizeof(T);
+size_t rb_smem_bytes(int zero_init, bool has_s) {
+  return kRbCoefBytes +
+         ((zero_init ? 0 : (size_t)kRbNE * kRbEP) + (size_t)kRbNR * kRbRP * (has_s ? 2 : 1)) *
+             sizeof(float);
 }
 
-template <typename T, int TX, int TY, int TZ>
-void launch_rb(const RBArgs<T>& a, cudaStream_t s) {
-  const size_t smem = rb_smem_bytes<T, TX, TY, TZ>(a.zero_init);
-  const dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, (a.nz + TZ - 1) / TZ);
-  launch_k(smooth_rb_kernel<T, TX, TY, TZ>, grid, dim3(256), smem, s, a);
-}
-
-template <typename T, int TX, int TY, int TZ>
-cudaError_t rb_prepare_one() {
-  return cudaFuncSetAttribute(smooth_rb_kernel<T, TX, TY, TZ>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)rb_smem_bytes<T, TX, TY, TZ>(0));
+// planes per block: the largest power of two (4 .. kRbKZ) that still gives six
+// blocks per SM
+int rb_kz(const LevelDesc& L) {
+  const long long tiles = (long long)((L.nx + kRbTX - 1) / kRbTX) * ((L.ny + kRbTY - 1) / kRbTY);
+  int kz = 1;
+  while (kz < L.nz && kz < kRbKZ) kz <<= 1;
+  while (kz > 4 && tiles * ((L.nz + kz - 1) / kz) < 6LL * 152) kz >>= 1;
+  return kz;
 }
 }  // namespace
 
-// shared-memory opt-in of the fused sweep kernels on the current device
+// shared-memory opt-in of the fused sweep kernel on the current device
 template <typename T>
 cudaError_t smooth_rb_prepare() {
-  cudaError_t e = rb_prepare_one<T, 32, 16, 8>();
-  return e != cudaSuccess ? e : rb_prepare_one<T, 16, 8, 4>();
+  return cudaFuncSetAttribute(smooth_rb_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)rb_smem_bytes(0, true));
 }
 
-// tile of the fused sweep for a level: the large tile where it still gives
-// enough blocks, a small one otherwise (0: not eligible)
+// 1 where the level takes the fused sweep, 0 where it keeps the colour sweeps.
+// FP32 levels whose lateral sizes are multiples of 4 and at least 36 x 16 (one
+// periodic wrap covers the staged window; the 16-byte chunks never straddle it)
+// and that hold at least kRbMinCells cells.  Measured on GB300 inside the CUDA
+// graph of a step: on DRAM-bound levels (512 x 512 x 128) the fused sweep wins
+// (mixed Newton form 2110 -> 2264 Mcell-steps/s); on L2-resident levels of
+// 2-4 M cells the colour sweeps overlap better under programmatic launch and
+// win (256 x 256 x 32: 1578 vs 1494; 256 x 256 x 64: 1749 vs 1635).
 template <typename T>
-int smooth_rb_tile(const LevelDesc& L) {
+int smooth_rb_tile(const LevelDesc& L, bool) {
   if (sizeof(T) != sizeof(float)) return 0;
-  if ((L.nx & 1) || (L.ny & 1)) return 0;
-  if (L.nx >= 32 && L.ny >= 16 && L.ncell >= (1LL << 20)) return 2;   // 32 x 16 x 8
-  if (L.nx >= 16 && L.ny >= 8 && L.ncell >= (1LL << 14)) return 1;    // 16 x 8 x 4
-  return 0;
+  if ((L.nx & 3) || (L.ny & 1) || L.nx < 36 || L.ny < kRbTY || L.ncell < kRbMinCells) return 0;
+  return 1;
 }
 
 template <typename T>
 void launch_smooth_rb(const MGArgs<T>& a, const LevelDesc& L, const T* e_in, T* e_out,
                       int zero_init, const UpdateArgs* upd, cudaStream_t s) {
-  RBArgs<T> r{};
-  r.e_in = e_in;
-  r.e_out = e_out;
-  r.r = a.r + L.off;
-  r.s = a.s ? a.s + L.off : nullptr;
-  r.coef = a.coef + L.coef_off;
-  r.nx = L.nx; r.ny = L.ny; r.nz = L.nz;
-  r.zero_init = zero_init;
-  r.u = Upd{nullptr, 0.0, 0};
-  if (upd) { r.u.phi = upd->phi; r.u.clamp = upd->clamp; r.st = upd->stats; }
-  if (smooth_rb_tile<T>(L) == 2)
-    launch_rb<T, 32, 16, 8>(r, s);
-  else
-    launch_rb<T, 16, 8, 4>(r, s);
+  if constexpr (sizeof(T) == sizeof(float)) {
+    RBArgs<float> r{};
+    r.e_in = e_in;
+    r.e_out = e_out;
+    r.r = a.r + L.off;
+    r.s = a.s ? a.s + L.off : nullptr;
+    r.coef = a.coef + L.coef_off;
+    r.nx = L.nx; r.ny = L.ny; r.nz = L.nz;
+    r.kz = rb_kz(L);
+    r.zero_init = zero_init;
+    r.u = Upd{nullptr, 0.0, 0};
+    if (upd) { r.u.phi = upd->phi; r.u.clamp = upd->clamp; r.st = upd->stats; }
+    const dim3 grid((L.nx + kRbTX - 1) / kRbTX, (L.ny + kRbTY - 1) / kRbTY,
+                    (L.nz + r.kz - 1) / r.kz);
+    launch_k(smooth_rb_kernel, grid, dim3(256), rb_smem_bytes(zero_init, r.s != nullptr), s, r);
+  }
 }
 
 dim3 check_grid(const LevelDesc& C) {
@@ -788,7 +860,7 @@ cudaError_t launch_carrier_exp(const double* u, double* ep, double* em, long lon
 #define FX_INST(T)                                                                              \
   template void launch_smooth<T>(const MGArgs<T>&, const LevelDesc&, int, int,                  \
                                  const UpdateArgs*, cudaStream_t, const DevStats*);             \
-  template int smooth_rb_tile<T>(const LevelDesc&);                                             \
+  template int smooth_rb_tile<T>(const LevelDesc&, bool);                                       \
   template cudaError_t smooth_rb_prepare<T>();                                                  \
   template void launch_smooth_rb<T>(const MGArgs<T>&, const LevelDesc&, const T*, T*, int,      \
                                     const UpdateArgs*, cudaStream_t);                           \

@@ -15,16 +15,16 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 CASES = {
-    # fine level 32 x 16 x 8 tiles, levels 1 and 2 16 x 8 x 4 tiles
-    "mfim_256x256x32": (lambda: I.make_geometry(256, 256, I.mfim_stack(32)), dict(), (0.0, -2.0)),
+    # the fused sweep serves levels of at least 2^23 cells: 512 x 512 x 32 fine level
+    "mfim_512x512x32": (lambda: I.make_geometry(512, 512, I.mfim_stack(32)), dict(), (0.0, -2.0)),
     # several V-cycles per residual: the fine level's first sweep starts from e != 0
-    "mfim_128x64x16_inner3": (lambda: I.make_geometry(128, 64, I.mfim_stack(16)), dict(inner=3, guess=1),
-                              (0.0, 1.1)),
-    # sizes that are not multiples of the 16 x 8 x 4 tile (partial tiles in x and z)
-    "mfim_40x40x18": (lambda: I.make_geometry(40, 40, I.mfim_stack(18)), dict(), (0.0, 0.7)),
+    "mfim_512x512x32_inner3": (lambda: I.make_geometry(512, 512, I.mfim_stack(32)), dict(inner=3, guess=1),
+                               (0.0, 1.1)),
+    # a lateral size that is not a multiple of the 32 x 16 tile (528 = 16.5 x 32)
+    "mfim_528x528x32": (lambda: I.make_geometry(528, 528, I.mfim_stack(32)), dict(), (0.0, 0.7)),
     # semiconductor: Newton shift s in the sweep (division by diag + s)
-    "mfism_64x64x32": (lambda: I.make_geometry(64, 64, I.mfism_stack(32)), dict(inner=4, guess=1),
-                       (0.0, 0.3)),
+    "mfism_512x512x40": (lambda: I.make_geometry(512, 512, I.mfism_stack(40)), dict(inner=4, guess=1),
+                         (0.0, 0.3)),
 }
 
 
