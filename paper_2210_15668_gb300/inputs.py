@@ -48,10 +48,19 @@ def de_layer(ncells, eps_r=EPS_SIO2):
                 gamma=0.0, g11=0.0, g44=0.0, Gamma=0.0, N_A=0.0, N_D=0.0, n_i=0.0, T=300.0)
 
 
-def sc_layer(ncells, N_A=1e24, N_D=0.0, n_i=1e16, T=300.0, eps_r=EPS_SI):
+# Carrier statistics of a semiconductor layer, and Si data for the Fermi-Dirac model:
+# effective masses from the paper's Table 1; the band gap (not in the paper) is the
+# usual 300 K value for Si.
+STATS_BOLTZMANN, STATS_FERMI_DIRAC = 0, 1
+SI_ME, SI_MP, SI_EG = 1.08, 0.81, 1.12
+
+
+def sc_layer(ncells, N_A=1e24, N_D=0.0, n_i=1e16, T=300.0, eps_r=EPS_SI, stats=STATS_BOLTZMANN,
+             m_e=SI_ME, m_p=SI_MP, E_g=SI_EG):
     return dict(kind=SC, ncells=int(ncells), eps_r=float(eps_r), alpha=0.0, beta=0.0,
                 gamma=0.0, g11=0.0, g44=0.0, Gamma=0.0, N_A=float(N_A), N_D=float(N_D),
-                n_i=float(n_i), T=float(T))
+                n_i=float(n_i), T=float(T), stats=int(stats), m_e=float(m_e), m_p=float(m_p),
+                E_g=float(E_g))
 
 
 def make_geometry(nx, ny, layers, h=H_DEFAULT, pbc=PBC_LAMBDA, lam=LAMBDA_DEFAULT, ncomp=1):

@@ -600,3 +600,128 @@ def test_in_plane_nyquist_mode_zero_displacement(comp):
     f = tdgl.force(P, phi, pl, g, 0.0, 0.0)
     eps, Gam = pl["eps"][0], pl["Gamma"][0]
     assert np.abs(f[comp] + Gam * P[comp] / eps).max() <= 1e-13 * Gam * A / eps
+
+
+# ------------------------------------------- Fermi-Dirac carriers (the paper's model) ---
+
+def _fd_quad(eta, order=0.5):
+    """(1/Gamma(order+1)) int_0^inf x^order/(1+e^(x-eta)) dx by adaptive quadrature (order
+    1/2: F_1/2 normalised to e^eta for eta -> -inf; order -1/2: its exact derivative)."""
+    from scipy import integrate, special
+    f = lambda x: x ** order / (1.0 + math.exp(x - eta)) if x - eta < 700 else 0.0  # noqa: E731
+    v, _ = integrate.quad(f, 0.0, max(eta, 0.0) + 60.0, limit=400, epsabs=0.0, epsrel=1e-12)
+    return v / special.gamma(order + 1.0)
+
+
+def test_fd_half_approximation_against_quadrature():
+    """The Fermi-Dirac integral of order 1/2 of the paper's carrier model, by the
+    approximation the paper cites, agrees with the integral itself (quadrature of
+    Eq. ne's integrand) within the approximation's accuracy (0.4%), and has the
+    right limits: e^eta (non-degenerate, Boltzmann) and (4/(3 sqrt pi)) eta^(3/2)
+    (fully degenerate)."""
+    etas = np.linspace(-20.0, 40.0, 241)
+    rel = [abs(float(carriers.fd_half(e)) / _fd_quad(e) - 1.0) for e in etas]
+    assert max(rel) <= 4e-3, max(rel)
+    assert abs(float(carriers.fd_half(-30.0)) / math.exp(-30.0) - 1.0) < 1e-9
+    big = 1e4
+    assert abs(float(carriers.fd_half(big)) / (4.0 / (3.0 * math.sqrt(math.pi)) * big ** 1.5) - 1.0) < 1e-6
+
+
+def test_fd_half_derivative():
+    """The Newton Jacobian uses the derivative of the approximation: it matches a
+    central difference of the approximation, and the exact derivative of F_1/2
+    (which is F_-1/2) within a few per cent."""
+    for e in (-15.0, -3.0, -1.0, 0.0, 0.7, 2.5, 8.0, 25.0):
+        d = float(carriers.fd_half_deriv(e))
+        h = 1e-5 * max(1.0, abs(e))
+        fd = (float(carriers.fd_half(e + h)) - float(carriers.fd_half(e - h))) / (2 * h)
+        assert abs(d / fd - 1.0) < 1e-6, (e, d, fd)
+        assert abs(d / _fd_quad(e, -0.5) - 1.0) < 0.03, (e, d)
+
+
+def test_effective_density_of_states_silicon():
+    """N = 2 (2 pi m* k_B T / h^2)^(3/2) with the paper's effective masses (Table 1:
+    1.08 and 0.81 m_e) gives the textbook 300 K silicon values 2.8e19 and 1.83e19 cm^-3."""
+    assert abs(carriers.effective_dos(1.08, 300.0) / 2.8e25 - 1.0) < 0.01
+    assert abs(carriers.effective_dos(0.81, 300.0) / 1.83e25 - 1.0) < 0.01
+    # T^(3/2) and m^(3/2)
+    assert abs(carriers.effective_dos(1.08, 600.0) / carriers.effective_dos(1.08, 300.0) - 2 ** 1.5) < 1e-12
+
+
+def _fd_stack(N_A=0.0, N_D=0.0, nsc=12, nx=4, ny=4):
+    return I.make_geometry(nx, ny, [I.sc_layer(nsc, N_A=N_A, N_D=N_D, stats=I.STATS_FERMI_DIRAC),
+                                    I.de_layer(2), I.fe_layer(6)], pbc=I.PBC_FREE)
+
+
+@pytest.mark.parametrize("N_A,N_D", [(0.0, 0.0), (1e24, 0.0), (0.0, 3e23), (1e26, 0.0)])
+def test_fd_bulk_neutral_at_zero_potential(N_A, N_D):
+    """The band edges are placed so that the semiconductor bulk is neutral at Phi = 0
+    (ohmic contact at V0 = 0), for undoped, p-, n- and degenerately doped Si; the
+    carrier densities obey the mass-action law n p = N_c N_v F(eta_e)F(eta_p) and, for
+    undoped Si, n = p = n_i = sqrt(N_c N_v) exp(-E_g/2k_BT) to the Boltzmann limit."""
+    g = _fd_stack(N_A, N_D)
+    pl = oracle.planes(g)
+    phi = np.zeros((I.nz_of(g), 4, 4))
+    rho, s = carriers.charge(phi, pl)
+    scale = Q_E * max(N_A, N_D, 1e16)
+    assert np.abs(rho).max() <= 1e-12 * scale
+    assert np.all(s[pl["sc"]] > 0.0)
+    if N_A == 0.0 and N_D == 0.0:
+        Nc, Nv = carriers.effective_dos(1.08, 300.0), carriers.effective_dos(0.81, 300.0)
+        ee, ep = carriers.fd_reference(Nc, Nv, 1.12, 300.0, 0.0, 0.0)
+        n_i = math.sqrt(Nc * Nv) * math.exp(-1.12 * Q_E / (2 * K_B * 300.0))
+        assert abs(Nc * float(carriers.fd_half(ee)) / n_i - 1.0) < 1e-6
+        assert abs(Nv * float(carriers.fd_half(ep)) / n_i - 1.0) < 1e-6
+
+
+def test_fd_reduces_to_boltzmann_when_non_degenerate():
+    """Undoped Si at moderate potentials is non-degenerate, so the Fermi-Dirac charge
+    and its derivative equal the Maxwell-Boltzmann ones (Eq. MaxBolt_ne_np) with the
+    same intrinsic density, to the size of e^eta."""
+    g_fd = _fd_stack()
+    pl_fd = oracle.planes(g_fd)
+    Nc, Nv = carriers.effective_dos(1.08, 300.0), carriers.effective_dos(0.81, 300.0)
+    n_i = math.sqrt(Nc * Nv) * math.exp(-1.12 * Q_E / (2 * K_B * 300.0))
+    g_mb = I.make_geometry(4, 4, [I.sc_layer(12, N_A=0.0, n_i=n_i), I.de_layer(2), I.fe_layer(6)],
+                           pbc=I.PBC_FREE)
+    pl_mb = oracle.planes(g_mb)
+    phi = np.random.default_rng(3).uniform(-0.25, 0.25, (20, 4, 4))
+    r_fd, s_fd = carriers.charge(phi, pl_fd)
+    r_mb, s_mb = carriers.charge(phi, pl_mb)
+    sc = pl_fd["sc"]
+    assert np.abs(r_fd[sc] - r_mb[sc]).max() <= 1e-4 * np.abs(r_mb[sc]).max()
+    assert np.abs(s_fd[sc] / s_mb[sc] - 1.0).max() <= 1e-4
+
+
+def test_fd_degenerate_density():
+    """Deep in the conduction band the electron density is the degenerate limit
+    N_c (4/(3 sqrt pi)) eta^(3/2), far below the Boltzmann exponential."""
+    g = _fd_stack(N_D=1e24)
+    pl = oracle.planes(g)
+    Nc, Nv = carriers.effective_dos(1.08, 300.0), carriers.effective_dos(0.81, 300.0)
+    ee, _ = carriers.fd_reference(Nc, Nv, 1.12, 300.0, 0.0, 1e24)
+    vt = K_B * 300.0 / Q_E
+    phi = np.zeros((20, 4, 4))
+    phi[:12] = 3.0                                      # eta_e ~ 110
+    rho, _ = carriers.charge(phi, pl)
+    eta = ee + 3.0 / vt
+    n_deg = Nc * 4.0 / (3.0 * math.sqrt(math.pi)) * eta ** 1.5
+    n = -(rho[0, 0, 0] / Q_E - 1e24)                    # p is negligible here
+    assert abs(n / n_deg - 1.0) < 1e-3
+    assert n < 1e-30 * Nc * math.exp(eta)
+
+
+def test_fd_newton_matches_lagged_fixed_point_undoped():
+    """The paper's MFISM with undoped Si and Fermi-Dirac carriers: the damped Newton
+    solve and the paper's lagged fixed point (Methods, "Numerical Approach") reach the
+    same potential (the problem has one solution)."""
+    g = I.make_geometry(8, 6, [I.sc_layer(10, N_A=0.0, stats=I.STATS_FERMI_DIRAC), I.de_layer(4),
+                               I.fe_layer(8)], pbc=I.PBC_LAMBDA)
+    pl = oracle.planes(g)
+    P = I.random_polarization(g, seed=4, amp=0.15)
+    b = poisson.rhs(P, pl, g["h"], 0.0, 0.8)
+    phi_n, _ = carriers.newton_solve(b, np.zeros(P.shape[1:]), pl, g["h"], tol=1e-14)
+    phi_f, _ = carriers.fixed_point_solve(b, np.zeros(P.shape[1:]), pl, g["h"], tol=1e-15)
+    assert np.abs(phi_n - phi_f).max() <= 1e-12 * np.abs(phi_f).max()
+    rho, _ = carriers.charge(phi_n, pl)
+    assert np.abs(rho).max() > 0.0
