@@ -4,8 +4,9 @@
  * The library advances the self-consistent ferroelectric device model of
  * FerroX (arXiv 2210.15668): the time-dependent Ginzburg-Landau equation for
  * the polarization (Eq. TDGL2) coupled to the variable-permittivity Poisson
- * equation div(eps grad Phi) = div P - rho (Eq. Poisson), with Boltzmann carrier
- * charge in semiconductor layers (Eq. rho, Eq. MaxBolt_ne_np), periodic x/y
+ * equation div(eps grad Phi) = div P - rho (Eq. Poisson), with the carrier
+ * charge of semiconductor layers (Eq. rho; Boltzmann, Eq. MaxBolt_ne_np, or
+ * Fermi-Dirac, Eqs. ne and np), periodic x/y
  * boundaries and Dirichlet electrodes (Methods, "Electrical boundary
  * conditions").  One context holds one device stack on one GPU.
  *
@@ -73,6 +74,17 @@ enum { FERROX_PBC_FREE = 0, FERROX_PBC_ZERO = 1, FERROX_PBC_LAMBDA = 2 };
  * The batched engine runs the defect-correction form for FERROX_FP64. */
 enum { FERROX_FP64 = 0, FERROX_MIXED = 1, FERROX_FP64_DEFECT = 2 };
 
+/* Carrier statistics of a semiconductor layer.
+ *   FERROX_BOLTZMANN: the Maxwell-Boltzmann limit (Eq. MaxBolt_ne_np) with the
+ *     intrinsic density n_i: n = n0 e^{Phi/V_T}, p = p0 e^{-Phi/V_T}, n0 p0 = n_i^2.
+ *   FERROX_FERMI_DIRAC: the paper's Fermi-Dirac model (Eqs. ne, np), n = N_c
+ *     F_1/2(eta_e), p = N_v F_1/2(eta_p), with N_c, N_v = 2 (2 pi m* k_B T/h^2)^{3/2}
+ *     from the effective masses m_e, m_p and F_1/2 by the Bednarczyk approximation
+ *     the paper uses (Methods, "Numerical Approach"); the band edges, E_g apart, are
+ *     placed so that the bulk is neutral at Phi = 0.
+ * Either way the bulk is neutral at Phi = 0 (ohmic contact at V0 = 0). */
+enum { FERROX_BOLTZMANN = 0, FERROX_FERMI_DIRAC = 1 };
+
 /* One planar layer (Table 1 lists the parameters).  Only the fields of its
  * kind are read: Landau/gradient/kinetic data for FE, carrier data for SC. */
 typedef struct {
@@ -84,8 +96,13 @@ typedef struct {
   double g11, g44;                    /* gradient coefficients (Eq. grad): z, and x/y */
   double Gamma;                       /* kinetic coefficient (Eq. TDGL1) */
   double N_A, N_D;                    /* acceptor / donor density, m^-3 (SC) */
-  double n_i;                         /* intrinsic carrier density, m^-3 (SC) */
+  double n_i;                         /* intrinsic carrier density, m^-3 (SC, Boltzmann) */
   double T;                           /* temperature, K (SC) */
+  int stats;                          /* SC carrier statistics: FERROX_BOLTZMANN or
+                                         FERROX_FERMI_DIRAC */
+  int pad;
+  double m_e, m_p;                    /* effective masses / m_e (SC, Fermi-Dirac; Table 1) */
+  double E_g;                         /* band gap, eV (SC, Fermi-Dirac) */
 } ferrox_layer;
 
 typedef struct {

@@ -293,6 +293,38 @@ std::vector<PlaneCoef<T>> level_coefficients(const ferrox_ctx* c) {
   return out;
 }
 
+// Fermi-Dirac integral of order 1/2, normalised to e^eta for eta -> -inf, by the
+// approximation of Bednarczyk & Bednarczyk (Phys. Lett. A 64, 409 (1978)) that the
+// paper uses: F = 1/(e^-eta + xi), xi = (3 sqrt(pi)/4) v^(-3/8),
+// v = eta^4 + 50 + 33.6 eta (1 - 0.68 e^(-0.17 (eta + 1)^2)).
+double fd_half_host(double eta) {
+  const double w = 1.0 - 0.68 * std::exp(-0.17 * (eta + 1.0) * (eta + 1.0));
+  const double v = eta * eta * eta * eta + 50.0 + 33.6 * eta * w;
+  const double xi = 0.75 * std::sqrt(M_PI) * std::pow(v, -0.375);
+  return 1.0 / (std::exp(-eta) + xi);
+}
+
+// effective density of states 2 (2 pi m* k_B T / h^2)^(3/2), m* = m_rel m_e
+double effective_dos(double m_rel, double T) {
+  constexpr double kH = 6.62607015e-34, kME = 9.1093837015e-31;
+  return 2.0 * std::pow(2.0 * M_PI * m_rel * kME * kKB * T / (kH * kH), 1.5);
+}
+
+// reduced band-edge distances at Phi = 0 that make the bulk neutral:
+// Nv F(eta_p0) - Nc F(eta_e0) + N_D - N_A = 0 with eta_e0 + eta_p0 = -E_g/(k_B T)
+void fd_reference(double Nc, double Nv, double Eg_eV, double T, double N_A, double N_D,
+                  double* eta_e0, double* eta_p0) {
+  const double gap = Eg_eV * kQ / (kKB * T);
+  double lo = -gap - 60.0, hi = 60.0;   // the net charge falls with eta_e0
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    const double net = Nv * fd_half_host(-gap - mid) - Nc * fd_half_host(mid) + N_D - N_A;
+    if (net > 0.0) lo = mid; else hi = mid;
+  }
+  *eta_e0 = 0.5 * (lo + hi);
+  *eta_p0 = -gap - *eta_e0;
+}
+
 ferrox_status build_planes(ferrox_ctx* c) {
   const int nz = c->nz;
   c->planes.assign(nz, PlaneTDGL{});
@@ -330,6 +362,12 @@ ferrox_status build_planes(ferrox_ctx* c) {
       p.n0 = n0; p.p0 = p0; p.Nnet = N;
       p.kq = kQ * h * h / kEps0;
       p.inv_vt = kQ / (kKB * L.T);
+      p.fd = L.stats == FERROX_FERMI_DIRAC;
+      if (p.fd) {
+        p.Nc = effective_dos(L.m_e, L.T);
+        p.Nv = effective_dos(L.m_p, L.T);
+        fd_reference(p.Nc, p.Nv, L.E_g, L.T, L.N_A, L.N_D, &p.eta_e0, &p.eta_p0);
+      }
       c->has_sc = true;
     }
   }
@@ -1086,6 +1124,11 @@ ferrox_status validate(const ferrox_geometry* g, const ferrox_numerics* n, const
     if (L.kind == FERROX_FE) nfe++;
     if (L.kind == FERROX_SC && !(L.T > 0.0)) return bad("semiconductor temperature must be > 0");
     if (L.kind == FERROX_SC && (L.N_A < 0 || L.N_D < 0 || L.n_i < 0)) return bad("negative density");
+    if (L.kind == FERROX_SC && L.stats != FERROX_BOLTZMANN && L.stats != FERROX_FERMI_DIRAC)
+      return bad("unknown carrier statistics");
+    if (L.kind == FERROX_SC && L.stats == FERROX_FERMI_DIRAC &&
+        !(L.m_e > 0.0 && L.m_p > 0.0 && L.E_g > 0.0))
+      return bad("Fermi-Dirac carriers need m_e, m_p, E_g > 0");
     nz += L.ncells;
   }
   if (nz < 2) return bad("Nz must be >= 2");

@@ -74,7 +74,7 @@ struct PlaneTDGL {
   int fe;          // ferroelectric plane
   int b_dyn;       // b may be nonzero from P on this plane (FE or FE-adjacent)
   int sc;          // semiconductor plane
-  int pad;
+  int fd;          // Fermi-Dirac carriers (else Boltzmann)
   double alpha, beta, gamma;          // z component
   double alpha_xy, beta_xy, gamma_xy; // in-plane components
   double g11, g44, Gamma;
@@ -85,6 +85,8 @@ struct PlaneTDGL {
   double eps_r;
   // carriers (scaled): rho' = kq (p0 e^{-phi/VT} - n0 e^{phi/VT} + Nnet), s' = kq (n + p)/VT
   double kq, n0, p0, Nnet, inv_vt;
+  // Fermi-Dirac: n = Nc F(eta_e0 + phi/VT), p = Nv F(eta_p0 - phi/VT)
+  double Nc, Nv, eta_e0, eta_p0;
 };
 
 // ---- per-plane multigrid coefficients of one level ----------------------------------

@@ -400,6 +400,29 @@ __device__ __forceinline__ T narrow_resid(double x) {
   return (T)x;
 }
 
+// Fermi-Dirac integral of order 1/2 (normalised to e^eta for eta -> -inf) and its
+// derivative, by the approximation of Bednarczyk & Bednarczyk (1978) that the paper
+// uses for the carrier integrals: F = 1/(e^-eta + xi), xi = (3 sqrt(pi)/4) v^(-3/8),
+// v = eta^4 + 50 + 33.6 eta (1 - 0.68 e^(-0.17 (eta + 1)^2)).  Far below the band
+// edge (eta < -700, where e^-eta overflows) F = e^eta to double precision.
+__device__ __forceinline__ double fd_half(double eta, double& dF) {
+  if (eta < -700.0) {
+    dF = exp(eta);
+    return dF;
+  }
+  const double g = exp(-0.17 * (eta + 1.0) * (eta + 1.0));
+  const double w = fma(-0.68, g, 1.0);
+  const double e2 = eta * eta;
+  const double v = fma(e2, e2, fma(33.6 * eta, w, 50.0));
+  const double dv = fma(4.0 * e2, eta, 33.6 * fma(eta * 0.2312 * g, eta + 1.0, w));
+  const double xi = 1.3293403881791355 * exp(-0.375 * log(v));   // (3 sqrt(pi)/4) v^(-3/8)
+  const double dxi = -0.375 * xi * dv / v;
+  const double em = exp(-eta);
+  const double F = 1.0 / (em + xi);
+  dF = (em - dxi) * F * F;
+  return F;
+}
+
 // FP64 residual of planes [k0, k1) of one (x, y) column, marching up with a
 // register window; accumulates r^2, b^2 (first residual of a solve only) and
 // rho^2.  SC = false compiles out the carrier term (stacks without a
@@ -437,12 +460,22 @@ __device__ __forceinline__ void resid_column(const ResidArgs& a, int i, int j, i
     }
     double rho = 0.0;
     if (SC && pt.sc) {
-      double ep, em;
-      exp_pm(pc * pt.inv_vt, ep, em);
-      const double n = pt.n0 * ep;
-      const double p = pt.p0 * em;
-      rho = pt.kq * (p - n + pt.Nnet);
-      if (s_out) s_out[t] = (T)(pt.kq * (n + p) * pt.inv_vt);
+      if (pt.fd) {
+        // n = Nc F(eta_e0 + u), p = Nv F(eta_p0 - u); -d rho/d phi = kq (dn + dp)/VT
+        const double u = pc * pt.inv_vt;
+        double dn, dp;
+        const double n = pt.Nc * fd_half(pt.eta_e0 + u, dn);
+        const double p = pt.Nv * fd_half(pt.eta_p0 - u, dp);
+        rho = pt.kq * (p - n + pt.Nnet);
+        if (s_out) s_out[t] = (T)(pt.kq * fma(pt.Nc, dn, pt.Nv * dp) * pt.inv_vt);
+      } else {
+        double ep, em;
+        exp_pm(pc * pt.inv_vt, ep, em);
+        const double n = pt.n0 * ep;
+        const double p = pt.p0 * em;
+        rho = pt.kq * (p - n + pt.Nnet);
+        if (s_out) s_out[t] = (T)(pt.kq * (n + p) * pt.inv_vt);
+      }
       acc_rho = fma(rho, rho, acc_rho);
     }
     // r = b + rho - A phi = (b + rho) - diag phi + couplings * neighbours

@@ -27,7 +27,9 @@ class Layer(C.Structure):
                 ("alpha", C.c_double), ("beta", C.c_double), ("gamma", C.c_double),
                 ("alpha_xy", C.c_double), ("beta_xy", C.c_double), ("gamma_xy", C.c_double),
                 ("g11", C.c_double), ("g44", C.c_double), ("Gamma", C.c_double),
-                ("N_A", C.c_double), ("N_D", C.c_double), ("n_i", C.c_double), ("T", C.c_double)]
+                ("N_A", C.c_double), ("N_D", C.c_double), ("n_i", C.c_double), ("T", C.c_double),
+                ("stats", C.c_int), ("pad", C.c_int), ("m_e", C.c_double), ("m_p", C.c_double),
+                ("E_g", C.c_double)]
 
 
 class Geometry(C.Structure):
@@ -140,8 +142,10 @@ def make_layers(layers):
     for q, l in enumerate(layers):
         L = arr[q]
         L.kind, L.ncells, L.eps_r = int(l["kind"]), int(l["ncells"]), float(l["eps_r"])
-        for k in ("alpha", "beta", "gamma", "g11", "g44", "Gamma", "N_A", "N_D", "n_i", "T"):
+        for k in ("alpha", "beta", "gamma", "g11", "g44", "Gamma", "N_A", "N_D", "n_i", "T", "m_e",
+                  "m_p", "E_g"):
             setattr(L, k, float(l.get(k, 0.0)))
+        L.stats = int(l.get("stats", 0))
         for k in ("alpha", "beta", "gamma"):
             setattr(L, k + "_xy", float(l.get(k + "_xy", l.get(k, 0.0))))
     return arr

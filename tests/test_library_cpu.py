@@ -45,12 +45,36 @@ def test_binding_covers_every_declared_symbol():
     assert declared_symbols() <= set(ferrox.EXPORTS) | {"ferrox_status"}
 
 
-def test_struct_layouts_match_header(lib):
-    """The ctypes mirrors have the sizes the C compiler gives the structs."""
+def test_struct_layouts_match_header(lib, tmp_path):
+    """The ctypes mirrors have the sizes and field offsets the C compiler gives the
+    structs of include/ferrox.h (a small C program built against the header)."""
+    import shutil
+    import subprocess
     from paper_2210_15668_gb300 import ferrox
-    assert ctypes.sizeof(ferrox.Layer) == 8 + 14 * 8
-    assert ctypes.sizeof(ferrox.Numerics) == 8 + 4 + 4 + 8 + 5 * 4 + 4 + 4 + 4
-    assert ctypes.sizeof(ferrox.Stats) == 4 * 8 + 8 + 8 + 8 + 8 + 8
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    mirrors = {"ferrox_layer": ferrox.Layer, "ferrox_geometry": ferrox.Geometry,
+               "ferrox_numerics": ferrox.Numerics, "ferrox_charge_t": ferrox.Charge,
+               "ferrox_stats": ferrox.Stats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ferrox.h"', "int main(void) {"]
+    for cname, py in mirrors.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            cf = "lambda" if fname == "lambda_" else fname
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {cf}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(ROOT, "include")
+    subprocess.run([cc, "-std=c99", "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in mirrors.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
 
 
 def test_init_rejects_bad_arguments_without_gpu(lib):
