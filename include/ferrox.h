@@ -137,7 +137,19 @@ typedef struct {
                        over the previous outer iteration (kept across solves) and the
                        distance to the tolerance.  The stopping test is unchanged.
                        The batched engine takes 0 or 1 only. */
+  int nonlinear;    /* iteration for the carrier charge rho(Phi) of semiconductor layers:
+                       FERROX_NEWTON (damped Newton: the Jacobian's diagonal shift
+                       q^2 (n + p)/kT in the multigrid operator) or FERROX_FIXED_POINT
+                       (the paper's lagged fixed point, Methods "Numerical Approach":
+                       each outer iteration relaxes A Phi = b + rho(Phi_k) with rho
+                       frozen at the current Phi, no shift).  Both stop on the same
+                       residual test and reach the same solution where they converge;
+                       the fixed point converges only while the carrier response is
+                       weak (undoped Si) and reports FERROX_ENOCONV otherwise.  The
+                       batched engine takes FERROX_NEWTON only. */
 } ferrox_numerics;
+
+enum { FERROX_NEWTON = 0, FERROX_FIXED_POINT = 1 };
 
 typedef struct {
   double Q_int;        /* -<D_z> on the bottom face of the lowest FE plane (C/m^2) */
@@ -192,6 +204,19 @@ ferrox_status ferrox_step(ferrox_ctx* ctx, int nsteps);
 /* Interface and electrode charges of the current state (Results, MFIM: Q and
  * V_fe).  Synchronises the stream; returns the sticky device status. */
 ferrox_status ferrox_charge(ferrox_ctx* ctx, ferrox_charge_t* out);
+
+/* A Q-V sweep (Results, MFIM: the triangular-wave voltage protocol of the Q-V
+ * and Q-V_fe characteristics): for each point q < npoints, set the electrodes to
+ * v_bottom = 0, v_top = v_app[q] (host array), advance steps_per_point time steps
+ * and record the charges of the resulting state in out[q] (host array of
+ * npoints).  The state carries over from point to point (the hysteresis depends
+ * on the path).  Equivalent to the calls ferrox_set_bias / ferrox_step /
+ * ferrox_charge in that order.  Synchronises once per point; EINVAL for npoints
+ * < 1, steps_per_point < 0 or null arrays; stops at the first point whose
+ * status is not FERROX_OK and returns that status (out[q] of later points
+ * untouched). */
+ferrox_status ferrox_qv_sweep(ferrox_ctx* ctx, const double* v_app, int npoints, int steps_per_point,
+                              ferrox_charge_t* out);
 
 /* Counters and the sticky status.  Synchronises the stream. */
 ferrox_status ferrox_sync_stats(ferrox_ctx* ctx, ferrox_stats* out);

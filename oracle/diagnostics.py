@@ -35,3 +35,18 @@ def charges(phi, P, pl, geom, v_bottom, v_top):
     phi_int = float(np.mean(phi_f))
     return dict(Q_int=-float(np.mean(F)), phi_int_avg=phi_int, V_fe=v_top - phi_int,
                 sigma_top=-float(np.mean(F_top)), sigma_bot=float(np.mean(F_bot)))
+
+
+def qv_sweep(P0, phi0, pl, geom, dt, v_app, steps_per_point, order=1):
+    """Q-V protocol (Results, MFIM: the voltage follows a triangular wave and Q, V_fe
+    are recorded along it): for each bias point, V0 = 0 and V1 = v_app[q], advance
+    steps_per_point time steps from the previous point's state, record the charges.
+    Returns (records, P, phi)."""
+    from . import tdgl
+    P, phi = P0.copy(), phi0.copy()
+    out = []
+    for v in v_app:
+        for _ in range(steps_per_point):
+            P, phi = tdgl.step(P, phi, pl, geom, dt, 0.0, v, order)
+        out.append(charges(phi, P, pl, geom, 0.0, v))
+    return out, P, phi

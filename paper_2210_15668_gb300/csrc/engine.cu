@@ -50,6 +50,7 @@ struct ferrox_ctx {
   std::vector<ferrox_layer> layers;
   ferrox_numerics num{};
   bool has_sc = false;
+  bool shift = false;   // Newton shift in the multigrid operator (carriers, damped Newton)
   int kd_lo = 0, kd_hi = 0, fe_lo = 0, fe_hi = 0, k_int = 0;
   std::vector<double> epsr;  // per fine plane
   std::vector<PlaneTDGL> planes;
@@ -172,11 +173,11 @@ void build_levels(ferrox_ctx* c) {
 // inverse across the SMs (no carriers), so its tail may start there
 void plan_tail(ferrox_ctx* c, size_t elem_size, bool wide = false) {
   const int L = (int)c->lv.size() - 1;
-  const int narr = c->has_sc ? 3 : 2;
+  const int narr = c->shift ? 3 : 2;
   c->tail_first = L;
   // one SM runs FP64 at 2 DFMA/clk, so in FP64 the tail starts at a smaller level;
   // with the wide dense solve the FP32 form starts there too
-  const long long max_cells = (elem_size == sizeof(double) || (wide && !c->has_sc))
+  const long long max_cells = (elem_size == sizeof(double) || (wide && !c->shift))
                                   ? kTailMaxCellsFP64 : kTailMaxCells;
   for (int l = 0; l <= L; ++l) {
     const long long elems = c->arena - c->lv[l].off;
@@ -201,7 +202,7 @@ void plan_tail(ferrox_ctx* c, size_t elem_size, bool wide = false) {
 // exactly by its inverse in stacks without carriers (no Newton shift on the
 // diagonal, so the operator is fixed for the context's lifetime).
 int dense_level(const ferrox_ctx* c) {
-  if (c->has_sc) return -1;
+  if (c->shift) return -1;
   for (size_t l = 0; l < c->lv_tail.size(); ++l)
     if (c->lv_tail[l].ncell <= kDenseMax) return c->lv_tail[l].ncell > 1 ? (int)l : -1;
   return -1;
@@ -269,7 +270,7 @@ std::vector<PlaneCoef<T>> level_coefficients(const ferrox_ctx* c) {
       int has_s = 0;
       for (int i = K * fz; i < (K + 1) * fz; ++i) {
         lat += c->epsr[i];
-        if (c->planes[i].sc) has_s = 1;
+        if (c->shift && c->planes[i].sc) has_s = 1;
       }
       lat /= fz;
       const double cx = L.nx > 1 ? lat / (double(fx) * fx) : 0.0;
@@ -435,7 +436,7 @@ struct NoWrap {
 template <typename T>
 double sweep_bytes(const ferrox_ctx* c, const LevelDesc& L) {
   // one colour: the other colour's e (read), own r (read), own e (write), own s (SC)
-  return 0.5 * (double)L.ncell * sizeof(T) * (c->has_sc ? 4.0 : 3.0);
+  return 0.5 * (double)L.ncell * sizeof(T) * (c->shift ? 4.0 : 3.0);
 }
 template <typename T>
 double restrict_bytes(const LevelDesc& F, const LevelDesc& Cc) {
@@ -460,7 +461,7 @@ int adapt_max(const ferrox_ctx* c) { return c->num.inner < 0 ? -c->num.inner : 0
 // sweep lands in the level's own array.
 template <typename T>
 bool rb_sweeps(const ferrox_ctx* c, int l, int nu) {
-  return c->e_alt && nu % 2 == 0 && smooth_rb_tile<T>(c->lv[l], c->has_sc) > 0;
+  return c->e_alt && nu % 2 == 0 && smooth_rb_tile<T>(c->lv[l], c->shift) > 0;
 }
 
 // kernels of one smoothing of level l with nu sweeps
@@ -667,7 +668,8 @@ void enqueue_resid(ferrox_ctx* c, cudaStream_t s, int first, int set_cond,
   a.phi = c->phi; a.b = c->b; a.planes = c->planes_d; a.coef0 = c->coef0; a.params = c->params_d;
   a.nx = c->nx; a.ny = c->ny; a.nz = c->nz;
   a.r_out = c->r_arena;
-  a.s_out = c->has_sc ? c->s_arena : nullptr;
+  a.s_out = c->shift ? c->s_arena : nullptr;
+  a.carriers = c->has_sc;
   a.partials = c->partials_d;
   a.kchunk = c->resid_kchunk;
   a.stats = c->stats_d;
@@ -860,7 +862,8 @@ void enqueue_nn_features(ferrox_ctx* c, cudaStream_t s, __nv_bfloat16* x) {
   a.phi = c->phi; a.b = c->b; a.planes = c->planes_d; a.coef0 = c->coef0; a.params = c->params_d;
   a.nx = c->nx; a.ny = c->ny; a.nz = c->nz;
   a.r_out = c->r_arena;
-  a.s_out = c->has_sc ? c->s_arena : nullptr;
+  a.s_out = c->shift ? c->s_arena : nullptr;
+  a.carriers = c->has_sc;
   a.stats = c->stats_d;
   a.partials = c->partials_d;
   a.norm_out = c->nn_scale + 1;   // ||r|| of the guess, for the check of the correction
@@ -1138,6 +1141,8 @@ ferrox_status validate(const ferrox_geometry* g, const ferrox_numerics* n, const
   if (!(n->tol > 0.0)) return bad("tol must be > 0");
   if (n->nu1 < 1 || n->nu2 < 0) return bad("need nu1 >= 1 and nu2 >= 0");
   if (n->max_cycles < 1) return bad("max_cycles must be >= 1");
+  if (n->nonlinear != FERROX_NEWTON && n->nonlinear != FERROX_FIXED_POINT)
+    return bad("nonlinear must be FERROX_NEWTON or FERROX_FIXED_POINT");
   if (n->precision != FERROX_FP64 && n->precision != FERROX_MIXED &&
       n->precision != FERROX_FP64_DEFECT)
     return bad("unknown precision");
@@ -1169,6 +1174,7 @@ ferrox_status ferrox_init_geometry(ferrox_ctx** out, const ferrox_geometry* geom
   ctx->P = P_dev;
   ctx->phi = phi_dev;
   if ((rc = build_planes(ctx)) != FERROX_OK) { ctx->err = g_init_error; release(ctx); return rc; }
+  ctx->shift = ctx->has_sc && ctx->num.nonlinear == FERROX_NEWTON;
   build_levels(ctx);
   if (ctx->arena >= (1LL << 31)) {   // the multigrid kernels index the arenas with 32-bit integers
     release(ctx);
@@ -1220,14 +1226,14 @@ ferrox_status ferrox_init_geometry(ferrox_ctx** out, const ferrox_geometry* geom
     // the fused red-black sweeps alternate between a level's array and e_alt
     long long alt = 0;
     for (int l = 0; l < ctx->tail_first; ++l)
-      if (smooth_rb_tile<float>(ctx->lv[l], ctx->has_sc) > 0) alt = std::max(alt, ctx->lv[l].ncell);
+      if (smooth_rb_tile<float>(ctx->lv[l], ctx->shift) > 0) alt = std::max(alt, ctx->lv[l].ncell);
     if (alt > 0) {
       FX_INIT_CK(cudaMalloc(&ctx->e_alt, alt * tsz));
       FX_INIT_CK(smooth_rb_prepare<float>());
     }
   }
   FX_INIT_CK(cudaMalloc(&ctx->r_arena, ctx->arena * tsz));
-  if (ctx->has_sc) FX_INIT_CK(cudaMalloc(&ctx->s_arena, ctx->arena * tsz));
+  if (ctx->shift) FX_INIT_CK(cudaMalloc(&ctx->s_arena, ctx->arena * tsz));
   FX_INIT_CK(cudaMalloc(&ctx->planes_d, ctx->nz * sizeof(PlaneTDGL)));
   FX_INIT_CK(cudaMalloc(&ctx->lv_d, ctx->lv.size() * sizeof(LevelDesc)));
   FX_INIT_CK(cudaMalloc(&ctx->params_d, sizeof(DevParams)));
@@ -1259,7 +1265,7 @@ ferrox_status ferrox_init_geometry(ferrox_ctx** out, const ferrox_geometry* geom
                             cudaMemcpyHostToDevice));
     }
     const LevelDesc& T0 = ctx->lv_tail[0];
-    if (!ctx->has_sc && T0.ncell > kDenseMax && T0.ncell <= kDenseWide) {
+    if (!ctx->shift && T0.ncell > kDenseMax && T0.ncell <= kDenseWide) {
       const auto inv = dense_inverse<float>(c32, T0);
       FX_INIT_CK(cudaMalloc(&ctx->dense_wide_d, inv.size() * sizeof(float)));
       FX_INIT_CK(cudaMemcpy(ctx->dense_wide_d, inv.data(), inv.size() * sizeof(float),
@@ -1270,7 +1276,7 @@ ferrox_status ferrox_init_geometry(ferrox_ctx** out, const ferrox_geometry* geom
     FX_INIT_CK(cudaMemcpy(ctx->coef, c64.data(), c64.size() * sizeof(PlaneCoef<double>),
                           cudaMemcpyHostToDevice));
     const LevelDesc& T0 = ctx->lv_tail[0];
-    if (!ctx->has_sc && T0.ncell > kDenseMax && T0.ncell <= kDenseWide) {
+    if (!ctx->shift && T0.ncell > kDenseMax && T0.ncell <= kDenseWide) {
       const auto inv = dense_inverse<double>(c64, T0);
       FX_INIT_CK(cudaMalloc(&ctx->dense_wide_d, inv.size() * sizeof(double)));
       FX_INIT_CK(cudaMemcpy(ctx->dense_wide_d, inv.data(), inv.size() * sizeof(double),
@@ -1490,6 +1496,21 @@ ferrox_status ferrox_charge(ferrox_ctx* ctx, ferrox_charge_t* out) {
   out->sigma_bot = s[3] * inv;
   ferrox_stats st;
   return ferrox_sync_stats(ctx, &st);
+}
+
+ferrox_status ferrox_qv_sweep(ferrox_ctx* ctx, const double* v_app, int npoints, int steps_per_point,
+                              ferrox_charge_t* out) {
+  if (!ctx) return fail(nullptr, FERROX_EINVAL, "null context");
+  if (!v_app || !out || npoints < 1 || steps_per_point < 0)
+    return fail(ctx, FERROX_EINVAL, "ferrox_qv_sweep: need bias and output arrays, npoints >= 1, "
+                                    "steps_per_point >= 0");
+  for (int q = 0; q < npoints; ++q) {
+    ferrox_status rc = ferrox_set_bias(ctx, 0.0, v_app[q]);
+    if (rc == FERROX_OK && steps_per_point > 0) rc = ferrox_step(ctx, steps_per_point);
+    if (rc == FERROX_OK) rc = ferrox_charge(ctx, &out[q]);
+    if (rc != FERROX_OK) return rc;
+  }
+  return FERROX_OK;
 }
 
 ferrox_status ferrox_get_state(ferrox_ctx* ctx, double* P_host, double* phi_host) {
@@ -1903,6 +1924,8 @@ ferrox_status ferrox_init_batch(ferrox_batch** out, int n, const ferrox_geometry
     if (geoms[i].ncomp != 1) return bfail(nullptr, FERROX_EINVAL, "batched instances are uniaxial (ncomp = 1)");
   }
   if (num->order != 1) return bfail(nullptr, FERROX_EINVAL, "the batched engine runs order-1 steps");
+  if (num->nonlinear != FERROX_NEWTON)
+    return bfail(nullptr, FERROX_EINVAL, "the batched engine iterates the carrier charge by Newton");
   if (num->inner > 1 || num->inner < 0)
     return bfail(nullptr, FERROX_EINVAL, "the batched engine runs one V-cycle per outer iteration");
   ferrox_batch* B = new ferrox_batch();
@@ -1932,6 +1955,7 @@ ferrox_status ferrox_init_batch(ferrox_batch** out, int n, const ferrox_geometry
       batch_release(B);
       return bfail(nullptr, FERROX_EINVAL, m);
     }
+    c.shift = c.has_sc;   // the batched engine iterates by damped Newton
     build_levels(&c);
     plan_tail(&c, B->tsz);
     p.cell_off = cells;
@@ -2057,6 +2081,7 @@ ferrox_status ferrox_init_batch(ferrox_batch** out, int n, const ferrox_geometry
     ra.nx = c.nx; ra.ny = c.ny; ra.nz = c.nz;
     ra.r_out = static_cast<char*>(B->r) + (size_t)p.arena_off * tsz;
     ra.s_out = has_sc && c.has_sc ? static_cast<char*>(B->s) + (size_t)p.arena_off * tsz : nullptr;
+    ra.carriers = c.has_sc;
     ra.partials = nullptr;
     ra.stats = B->stats + i;
     ra.tol = num->tol; ra.max_cycles = num->max_cycles; ra.first = 1; ra.set_cond = 0;

@@ -161,6 +161,7 @@ struct ResidArgs {
   const double* reject_ref;          // ||r|| of the guess before a learned correction: the
   unsigned long long reject_handle;  // first residual sets this IF condition to 1 when
                                      // the corrected guess is no better (reject it)
+  int carriers;                      // the stack has semiconductor planes (carrier charge)
 };
 
 // ---- launchers (kernels.cu / tdgl.cu) ------------------------------------------------

@@ -813,7 +813,7 @@ void launch_resid(const ResidArgs& a, cudaStream_t s) {
   dim3 block(kResidBX, kResidBY);
   dim3 grid((a.nx + kResidBX - 1) / kResidBX, (a.ny + kResidBY - 1) / kResidBY,
             (a.nz + a.kchunk - 1) / a.kchunk);
-  if (a.s_out)
+  if (a.carriers)
     launch_k(resid_kernel<T, true>, grid, block, 0, s, a);
   else
     launch_k(resid_kernel<T, false>, grid, block, 0, s, a);

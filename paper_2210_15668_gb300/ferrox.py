@@ -41,7 +41,8 @@ class Geometry(C.Structure):
 class Numerics(C.Structure):
     _fields_ = [("dt", C.c_double), ("order", C.c_int), ("tol", C.c_double), ("nu1", C.c_int),
                 ("nu2", C.c_int), ("max_cycles", C.c_int), ("precision", C.c_int),
-                ("bottom_sweeps", C.c_int), ("guess", C.c_int), ("inner", C.c_int)]
+                ("bottom_sweeps", C.c_int), ("guess", C.c_int), ("inner", C.c_int),
+                ("nonlinear", C.c_int)]
 
 
 class Charge(C.Structure):
@@ -60,7 +61,7 @@ EXPORTS = ["ferrox_init_geometry", "ferrox_set_bias", "ferrox_solve_poisson", "f
            "ferrox_step", "ferrox_charge", "ferrox_sync_stats", "ferrox_clear_status",
            "ferrox_get_state", "ferrox_set_state", "ferrox_fe_planes", "ferrox_get_state_fe",
            "ferrox_set_state_fe", "ferrox_destroy", "ferrox_last_error",
-           "ferrox_level_shape", "ferrox_profile_step", "ferrox_profile_step_bytes",
+           "ferrox_level_shape", "ferrox_profile_step", "ferrox_profile_step_bytes", "ferrox_qv_sweep",
            "ferrox_tdgl_update_static",
            "ferrox_init_batch", "ferrox_batch_set_bias", "ferrox_batch_solve_poisson",
            "ferrox_batch_step", "ferrox_batch_charge", "ferrox_batch_stats", "ferrox_batch_tuning",
@@ -104,6 +105,7 @@ def load(path: str = LIB_PATH):
     lib.ferrox_level_shape.argtypes = [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                        C.POINTER(C.c_int), C.POINTER(C.c_int)]
     lib.ferrox_profile_step.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int)]
+    lib.ferrox_qv_sweep.argtypes = [vp, C.POINTER(C.c_double), C.c_int, C.c_int, C.POINTER(Charge)]
     lib.ferrox_profile_step_bytes.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int),
                                               C.POINTER(C.c_double)]
     lib.ferrox_tdgl_update_static.argtypes = [C.POINTER(Geometry), C.c_double, C.c_double,
@@ -151,10 +153,13 @@ def make_layers(layers):
     return arr
 
 
+NEWTON, FIXED_POINT = 0, 1
+
+
 def make_numerics(dt, order=1, tol=1e-10, nu1=2, nu2=2, max_cycles=200, precision=FP64,
-                  bottom_sweeps=0, guess=0, inner=1):
+                  bottom_sweeps=0, guess=0, inner=1, nonlinear=NEWTON):
     return Numerics(float(dt), int(order), float(tol), int(nu1), int(nu2), int(max_cycles),
-                    int(precision), int(bottom_sweeps), int(guess), int(inner))
+                    int(precision), int(bottom_sweeps), int(guess), int(inner), int(nonlinear))
 
 
 def tdgl_update_static(geom, dt, v_bottom, v_top, P, phi, stream=None):
@@ -273,6 +278,14 @@ class Device:
         pp = C.c_void_p(P_fe_host.ctypes.data) if P_fe_host is not None else None
         fp = C.c_void_p(phi_host.ctypes.data) if phi_host is not None else None
         self._ck(self.lib.ferrox_set_state_fe(self.ctx, pp, fp))
+
+    def qv_sweep(self, v_app, steps_per_point):
+        """Triangular-wave (or any) Q-V protocol run natively: a list of charge
+        records {Q_int, phi_int_avg, V_fe, sigma_top, sigma_bot}, one per bias point."""
+        v = (C.c_double * len(v_app))(*[float(x) for x in v_app])
+        out = (Charge * len(v_app))()
+        self._ck(self.lib.ferrox_qv_sweep(self.ctx, v, len(v_app), int(steps_per_point), out))
+        return [{k: getattr(o, k) for k, _ in Charge._fields_} for o in out]
 
     def profile_step(self, with_bytes=False):
         """One event-timed eager step: {kernel class: (total ms, launches)}, or with

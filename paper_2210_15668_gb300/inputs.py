@@ -91,6 +91,28 @@ def random_polarization(geom, seed, amp=1e-3, ncomp=None):
     return np.ascontiguousarray(P)
 
 
+def random_polarization_y_uniform(geom, seed, amp=1e-3, ncomp=None):
+    """The paper's 2-D setting (Results, MFIM): P uniform along y, U[-amp, amp] in the
+    x-z plane of ferroelectric cells, zero elsewhere; P[c][z][y][x] float64."""
+    ncomp = geom["ncomp"] if ncomp is None else ncomp
+    nz = nz_of(geom)
+    rng = np.random.default_rng(seed)
+    xz = rng.uniform(-amp, amp, size=(ncomp, nz, 1, geom["nx"]))
+    P = np.repeat(xz, geom["ny"], axis=2)
+    P[:, ~fe_plane_mask(geom)] = 0.0
+    return np.ascontiguousarray(P)
+
+
+def triangle_wave(v_max, points_per_quarter, sweeps=1):
+    """Bias points of the triangular voltage protocol of the Q-V characteristics
+    (Results, MFIM): 0 -> +v_max -> 0 -> -v_max -> 0, repeated `sweeps` times, in
+    steps of v_max / points_per_quarter (each turning point visited once)."""
+    q = int(points_per_quarter)
+    up = np.arange(1, q + 1) / q
+    period = np.concatenate([up, 1.0 - up, -up, -1.0 + up]) * float(v_max)
+    return list(np.tile(period, int(sweeps)))
+
+
 # --- the device workloads -------------------------------------------------------------
 
 def mfim_stack(nz, n_fe=10, eps_de=EPS_SIO2, g=1e-10):

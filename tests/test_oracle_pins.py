@@ -725,3 +725,33 @@ def test_fd_newton_matches_lagged_fixed_point_undoped():
     assert np.abs(phi_n - phi_f).max() <= 1e-12 * np.abs(phi_f).max()
     rho, _ = carriers.charge(phi_n, pl)
     assert np.abs(rho).max() > 0.0
+
+
+# ------------------------------------------------------------ Q-V sweep protocol -------
+
+def test_triangle_wave_protocol():
+    """0 -> +Vmax -> 0 -> -Vmax -> 0 in equal steps, repeated per sweep."""
+    v = I.triangle_wave(2.0, 4, sweeps=2)
+    assert len(v) == 32
+    assert v[:4] == [0.5, 1.0, 1.5, 2.0] and v[4:8] == [1.5, 1.0, 0.5, 0.0]
+    assert v[8:12] == [-0.5, -1.0, -1.5, -2.0] and v[12:16] == [-1.5, -1.0, -0.5, 0.0]
+    assert v[16:] == v[:16]
+
+
+def test_qv_sweep_linear_capacitor():
+    """With the ferroelectric frozen at P = 0 (Gamma = 0) the stack is two dielectrics
+    in series: every recorded point has Q = V_app / (t_de/eps_de + t_fe/eps_fe) and
+    V_fe = Q t_fe/eps_fe, whatever the path, so the protocol's bookkeeping (bias order,
+    signs, which state is recorded) is pinned by the series-capacitor closed form."""
+    h = 0.5e-9
+    g = I.make_geometry(4, 4, [I.de_layer(8, 10.0), I.fe_layer(10, Gamma=0.0)], h=h, pbc=I.PBC_FREE)
+    pl = oracle.planes(g)
+    P0 = np.zeros((1, 18, 4, 4))
+    v = I.triangle_wave(3.0, 3)
+    rec, P, _ = diagnostics.qv_sweep(P0, np.zeros((18, 4, 4)), pl, g, 4e-13, v, 2)
+    t_de, t_fe = 8 * h, 10 * h
+    c_series = 1.0 / (t_de / (10.0 * EPS0) + t_fe / (24.0 * EPS0))
+    for vq, r in zip(v, rec):
+        assert abs(r["Q_int"] - c_series * vq) <= 1e-12 * c_series * 3.0
+        assert abs(r["V_fe"] - r["Q_int"] * t_fe / (24.0 * EPS0)) <= 1e-12 * 3.0
+    assert np.all(P == 0.0)
