@@ -161,3 +161,27 @@ def mfism_large():
     """512x512x128 MFISM, seed 5, V = 0, 100 steps."""
     return dict(name="mfism_512x512x128", geom=make_geometry(512, 512, mfism_stack(128)), seed=5,
                 v_bottom=0.0, v_top=0.0, steps=100, dt=DT_DEFAULT, order=1, precision=1)
+
+
+def convergence_cube(n, stats=STATS_FERMI_DIRAC, eps_de=EPS_SIO2):
+    """The convergence-study problem of the Numerical Validation section: a 32 nm cube
+    of n^3 cells, bottom 25% undoped Si (Fermi-Dirac carriers, the paper's model), 25%
+    dielectric (SiO2), top 50% ferroelectric with the parameter table's g = 1e-9,
+    lambda = 3 nm; Phi = 0 on both faces is the caller's bias."""
+    q = n // 4
+    layers = [sc_layer(q, N_A=0.0, stats=stats), de_layer(q, eps_de), fe_layer(2 * q, g=1e-9)]
+    return make_geometry(n, n, layers, h=32e-9 / n, pbc=PBC_LAMBDA, lam=3e-9)
+
+
+def gaussian_bump(geom, amp=0.002, s1=5e-9, s2=2e-9, z0=24e-9):
+    """P = amp exp(-(x^2 + y^2)/(2 s1^2) - (z - z0)^2/(2 s2^2)) on ferroelectric cells,
+    x, y measured from the centre of the periodic cross-section, z from the bottom."""
+    n, h = geom["nx"], geom["h"]
+    nz = nz_of(geom)
+    c = (np.arange(n) + 0.5) * h - n * h / 2
+    cy = (np.arange(geom["ny"]) + 0.5) * h - geom["ny"] * h / 2
+    z = (np.arange(nz) + 0.5) * h
+    Z, Y, X = np.meshgrid(z, cy, c, indexing="ij")
+    P = amp * np.exp(-(X ** 2 + Y ** 2) / (2 * s1 ** 2) - (Z - z0) ** 2 / (2 * s2 ** 2))
+    P[~fe_plane_mask(geom)] = 0.0
+    return np.ascontiguousarray(P[None])
