@@ -140,7 +140,12 @@ class ClockSampler:
 # FP64 pipe instructions per unit of work (the FP64 forms are bound by this pipe)
 FAST_INNER = -8  # fast and learned forms: V-cycles per FP64 residual chosen on the device (<= 8)
 
-FP64_INSTR = {"smooth_fine": 7.0, "resid": 10.0, "tdgl": 30.0, "restrict": 8.0, "prolong": 4.5}
+FP64_INSTR = {"smooth_fine": 7.0, "smooth_coarse": 7.0, "resid": 10.0, "tdgl": 30.0, "restrict": 8.0,
+              "prolong": 4.5}
+# algorithmic bytes per unit of FP64 work (the same counts as the library's): a colour
+# sweep moves 24 B per updated cell, residual + restriction and prolongation 17 B per
+# fine cell
+FP64_BYTES_PER_UNIT = {"smooth_fine": 24.0, "smooth_coarse": 24.0, "restrict": 17.0, "prolong": 17.0}
 
 
 def kernel_work(kind, cells, fe_cells, dyn_cells, tsz):
@@ -317,8 +322,10 @@ def run_ours(args, ws, rank, local):
     whole["vcycles_profiled_step"] = sp1["vcycles"] - sp0["vcycles"]
     whole["vcycles_per_timed_step"] = vcycles_per_step
     if fp64_kernel:
-        units = {"smooth_fine": 0.5 * cells, "resid": cells, "tdgl": fe_cells, "restrict": cells,
-                 "prolong": cells}.get(dom, cells)
+        if dom in FP64_BYTES_PER_UNIT:
+            units = by / FP64_BYTES_PER_UNIT[dom]
+        else:
+            units = {"resid": cells, "tdgl": fe_cells}.get(dom, cells)
         gi = FP64_INSTR.get(dom, 0.0) * units / avg_s / 1e9
         roof = {"bound": "alu", "achieved": gi, "peak": FP64_PEAK_GINSTR, "unit": "G FP64-instr/s",
                 "share_of_step": share, "frac": gi / FP64_PEAK_GINSTR, "traffic": traffic,

@@ -205,6 +205,18 @@ ferrox_status ferrox_step(ferrox_ctx* ctx, int nsteps);
  * V_fe).  Synchronises the stream; returns the sticky device status. */
 ferrox_status ferrox_charge(ferrox_ctx* ctx, ferrox_charge_t* out);
 
+/* The residual r = b + rho(Phi) - A Phi of the Poisson problem (Eq. Poisson in
+ * the finite-volume form, scaled by h^2/eps0) for the current state: b is formed
+ * from the current P and bias, rho from the current Phi.  r_host is a host array
+ * of Nz*Ny*Nx doubles.  arithmetic selects how the stencil is evaluated:
+ * FERROX_RESID_FP64 (the FP64 forms' outer residual) or
+ * FERROX_RESID_DOUBLE_FLOAT (the mixed form's outer residual: double-float pairs
+ * on the FP32 pipe, about 48 significant bits; r = h + l).  A diagnostic: it
+ * allocates a device buffer, synchronises, and leaves the state unchanged (b is
+ * recomputed from P, as every step does). */
+enum { FERROX_RESID_FP64 = 0, FERROX_RESID_DOUBLE_FLOAT = 1 };
+ferrox_status ferrox_residual(ferrox_ctx* ctx, int arithmetic, double* r_host);
+
 /* A Q-V sweep (Results, MFIM: the triangular-wave voltage protocol of the Q-V
  * and Q-V_fe characteristics): for each point q < npoints, set the electrodes to
  * v_bottom = 0, v_top = v_app[q] (host array), advance steps_per_point time steps

@@ -63,6 +63,7 @@ struct ferrox_ctx {
   size_t tail_smem = 0;
   int resid_blocks = 0;
   int resid_kchunk = 0;   // planes per z chunk of the residual kernel
+  int resid_kchunk_df = 0;  // the same for its double-float form (longer columns per thread)
   bool direct = false;    // FP64 V-cycles on phi itself (see direct_form)
   int dense_lev = -1;     // tail level solved by its inverse (-1: none)
   void* dense_d = nullptr;
@@ -83,6 +84,8 @@ struct ferrox_ctx {
   void* s_arena = nullptr;
   void* coef = nullptr;               // PlaneCoef<T> of all levels
   PlaneCoef<double>* coef0 = nullptr; // level 0 in FP64 (outer residual)
+  PlaneCoefDF* coef_df = nullptr;     // level 0 as double-float pairs (double-float residual)
+  bool df_resid = false;              // the mixed form's outer residual in double-float
   PlaneTDGL* planes_d = nullptr;
   LevelDesc* lv_d = nullptr;
   LevelDesc* lvt_d = nullptr;
@@ -425,6 +428,15 @@ double update_clamp(const ferrox_ctx* c) {
   return 10.0 * kKB * tmax / kQ;
 }
 
+// residual instantiation for the stack's carriers: 0 none, 1 Boltzmann only, 2 with
+// Fermi-Dirac planes
+int carrier_kind(const ferrox_ctx* c) {
+  if (!c->has_sc) return 0;
+  for (const auto& p : c->planes)
+    if (p.sc && p.fd) return 2;
+  return 1;
+}
+
 struct NoWrap {
   template <typename F>
   void operator()(int, double, F&& f) const { f(); }
@@ -669,9 +681,10 @@ void enqueue_resid(ferrox_ctx* c, cudaStream_t s, int first, int set_cond,
   a.nx = c->nx; a.ny = c->ny; a.nz = c->nz;
   a.r_out = c->r_arena;
   a.s_out = c->shift ? c->s_arena : nullptr;
-  a.carriers = c->has_sc;
+  a.carriers = carrier_kind(c);
+  a.coef_df = c->df_resid ? c->coef_df : nullptr;
   a.partials = c->partials_d;
-  a.kchunk = c->resid_kchunk;
+  a.kchunk = c->df_resid ? c->resid_kchunk_df : c->resid_kchunk;
   a.stats = c->stats_d;
   a.tol = c->num.tol;
   a.max_cycles = c->num.max_cycles;
@@ -863,11 +876,12 @@ void enqueue_nn_features(ferrox_ctx* c, cudaStream_t s, __nv_bfloat16* x) {
   a.nx = c->nx; a.ny = c->ny; a.nz = c->nz;
   a.r_out = c->r_arena;
   a.s_out = c->shift ? c->s_arena : nullptr;
-  a.carriers = c->has_sc;
+  a.carriers = carrier_kind(c);
+  a.coef_df = c->df_resid ? c->coef_df : nullptr;
   a.stats = c->stats_d;
   a.partials = c->partials_d;
   a.norm_out = c->nn_scale + 1;   // ||r|| of the guess, for the check of the correction
-  a.kchunk = c->resid_kchunk;
+  a.kchunk = c->df_resid ? c->resid_kchunk_df : c->resid_kchunk;
   launch_resid<T>(a, s);
   T* r = static_cast<T*>(c->r_arena);
   nn_bridge_restrict<T>(r, c->lv, c->nn_level, s);
@@ -1093,7 +1107,7 @@ void release(ferrox_ctx* c) {
   cudaGraph_t gr[4] = {c->gr_step, c->gr_solve, c->gr_tdgl, c->gr_step_nn};
   for (auto g : ge) if (g) cudaGraphExecDestroy(g);
   for (auto g : gr) if (g) cudaGraphDestroy(g);
-  void* ptrs[] = {c->b, c->Pbuf, c->Fbuf, c->phi_prev, c->e_arena, c->e_alt, c->r_arena, c->s_arena, c->coef, c->coef0,
+  void* ptrs[] = {c->b, c->Pbuf, c->Fbuf, c->phi_prev, c->e_arena, c->e_alt, c->r_arena, c->s_arena, c->coef, c->coef0, c->coef_df,
                   c->planes_d, c->lv_d, c->lvt_d, c->nn_scale, c->phi_guess, c->nn_pf, c->nn_stats, c->params_d, c->stats_d, c->partials_d, c->charge_d,
                   c->charge_part_d, c->dense_d, c->dense_wide_d};
   for (void* p : ptrs) if (p) cudaFree(p);
@@ -1192,6 +1206,11 @@ ferrox_status ferrox_init_geometry(ferrox_ctx** out, const ferrox_geometry* geom
     while ((long long)bxy * zc < 4LL * 152 * 3 && ctx->nz / (2 * zc) >= 4) zc *= 2;
     ctx->resid_kchunk = (ctx->nz + zc - 1) / zc;
     ctx->resid_blocks = bxy * ((ctx->nz + ctx->resid_kchunk - 1) / ctx->resid_kchunk);
+    // the double-float form: at least 8 planes per thread (its block reduction and
+    // per-column set-up cost more than the FP64 form's), about two waves
+    int zd = 1;
+    while ((long long)bxy * zd < 2LL * 152 * 4 && ctx->nz / (2 * zd) >= 8) zd *= 2;
+    ctx->resid_kchunk_df = (ctx->nz + zd - 1) / zd;
   }
   ctx->direct = direct_form(ctx);
   if (ctx->direct) {
@@ -1252,6 +1271,29 @@ ferrox_status ferrox_init_geometry(ferrox_ctx** out, const ferrox_geometry* geom
   FX_INIT_CK(cudaMalloc(&ctx->coef0, ctx->nz * sizeof(PlaneCoef<double>)));
   FX_INIT_CK(cudaMemcpy(ctx->coef0, c64.data(), ctx->nz * sizeof(PlaneCoef<double>),
                         cudaMemcpyHostToDevice));
+  {
+    // the same coefficients as double-float pairs: h = the nearest float, l = the
+    // nearest float to the remainder
+    std::vector<PlaneCoefDF> cdf(ctx->nz);
+    auto split = [](double x, float& h, float& l) {
+      h = (float)x;
+      l = (float)(x - (double)h);
+    };
+    for (int k = 0; k < ctx->nz; ++k) {
+      const PlaneCoef<double>& q = c64[k];
+      split(q.cx, cdf[k].cx_h, cdf[k].cx_l);
+      split(q.cy, cdf[k].cy_h, cdf[k].cy_l);
+      split(q.czlo, cdf[k].czlo_h, cdf[k].czlo_l);
+      split(q.czhi, cdf[k].czhi_h, cdf[k].czhi_l);
+      split(q.diag, cdf[k].diag_h, cdf[k].diag_l);
+    }
+    FX_INIT_CK(cudaMalloc(&ctx->coef_df, ctx->nz * sizeof(PlaneCoefDF)));
+    FX_INIT_CK(cudaMemcpy(ctx->coef_df, cdf.data(), ctx->nz * sizeof(PlaneCoefDF),
+                          cudaMemcpyHostToDevice));
+    // FERROX_DF_RESID=0 in the environment keeps the FP64 residual in the mixed form
+    const char* df_env = std::getenv("FERROX_DF_RESID");
+    ctx->df_resid = mixed && !(df_env && df_env[0] == '0');
+  }
   ctx->dense_lev = dense_level(ctx);
   if (mixed) {
     auto c32 = level_coefficients<float>(ctx);
@@ -1496,6 +1538,38 @@ ferrox_status ferrox_charge(ferrox_ctx* ctx, ferrox_charge_t* out) {
   out->sigma_bot = s[3] * inv;
   ferrox_stats st;
   return ferrox_sync_stats(ctx, &st);
+}
+
+ferrox_status ferrox_residual(ferrox_ctx* ctx, int arithmetic, double* r_host) {
+  if (!ctx) return fail(nullptr, FERROX_EINVAL, "null context");
+  if (!r_host) return fail(ctx, FERROX_EINVAL, "null output array");
+  if (arithmetic != FERROX_RESID_FP64 && arithmetic != FERROX_RESID_DOUBLE_FLOAT)
+    return fail(ctx, FERROX_EINVAL, "arithmetic must be FERROX_RESID_FP64 or FERROX_RESID_DOUBLE_FLOAT");
+  cudaStream_t s = ctx->stream;
+  const long long N = (long long)ctx->nx * ctx->ny * ctx->nz;
+  double* r_d = nullptr;
+  FX_CK(cudaMalloc(&r_d, N * sizeof(double)));
+  // the right-hand side of the current polarization, then r = b + rho(phi) - A phi
+  launch_tdgl(tdgl_args(ctx, 3), s);
+  ResidArgs a{};
+  a.phi = ctx->phi; a.b = ctx->b; a.planes = ctx->planes_d; a.coef0 = ctx->coef0;
+  a.params = ctx->params_d;
+  a.nx = ctx->nx; a.ny = ctx->ny; a.nz = ctx->nz;
+  a.r_out = r_d;
+  a.s_out = nullptr;
+  a.carriers = carrier_kind(ctx);
+  a.coef_df = arithmetic == FERROX_RESID_DOUBLE_FLOAT ? ctx->coef_df : nullptr;
+  a.kchunk = arithmetic == FERROX_RESID_DOUBLE_FLOAT ? ctx->resid_kchunk_df : ctx->resid_kchunk;
+  a.no_stats = 1;
+  a.stats = ctx->stats_d;
+  a.partials = ctx->partials_d;
+  launch_resid<double>(a, s);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(r_host, r_d, N * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(r_d);
+  if (e != cudaSuccess) return fail(ctx, FERROX_ECUDA, std::string("ferrox_residual: ") + cudaGetErrorString(e));
+  return FERROX_OK;
 }
 
 ferrox_status ferrox_qv_sweep(ferrox_ctx* ctx, const double* v_app, int npoints, int steps_per_point,
@@ -2081,7 +2155,7 @@ ferrox_status ferrox_init_batch(ferrox_batch** out, int n, const ferrox_geometry
     ra.nx = c.nx; ra.ny = c.ny; ra.nz = c.nz;
     ra.r_out = static_cast<char*>(B->r) + (size_t)p.arena_off * tsz;
     ra.s_out = has_sc && c.has_sc ? static_cast<char*>(B->s) + (size_t)p.arena_off * tsz : nullptr;
-    ra.carriers = c.has_sc;
+    ra.carriers = carrier_kind(&c);
     ra.partials = nullptr;
     ra.stats = B->stats + i;
     ra.tol = num->tol; ra.max_cycles = num->max_cycles; ra.first = 1; ra.set_cond = 0;

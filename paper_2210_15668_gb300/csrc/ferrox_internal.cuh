@@ -100,6 +100,12 @@ struct PlaneCoef {
   int pad;
 };
 
+// fine-level coefficients as double-float pairs (h + l = the FP64 value to 2^-48),
+// for the double-float outer residual of the mixed form
+struct PlaneCoefDF {
+  float cx_h, cx_l, cy_h, cy_l, czlo_h, czlo_l, czhi_h, czhi_l, diag_h, diag_l;
+};
+
 struct LevelDesc {
   int nx, ny, nz;
   int crx, cry, crz;  // this level is coarsened in x / y / z to form the next one
@@ -161,7 +167,10 @@ struct ResidArgs {
   const double* reject_ref;          // ||r|| of the guess before a learned correction: the
   unsigned long long reject_handle;  // first residual sets this IF condition to 1 when
                                      // the corrected guess is no better (reject it)
-  int carriers;                      // the stack has semiconductor planes (carrier charge)
+  int carriers;                      // carrier charge: 0 none, 1 Boltzmann planes only, 2 with
+                                     // Fermi-Dirac planes
+  const PlaneCoefDF* coef_df;        // non-null: stencil in double-float arithmetic (FP32 pipe)
+  int warp_rows;                     // nx is a multiple of 32: each warp holds 32 cells of a row
 };
 
 // ---- launchers (kernels.cu / tdgl.cu) ------------------------------------------------

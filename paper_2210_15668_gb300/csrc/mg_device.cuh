@@ -6,6 +6,7 @@
 #include <math.h>
 
 #include "carrier_exp.cuh"
+#include "df_arith.cuh"
 #include "ferrox_internal.cuh"
 
 namespace fx {
@@ -363,6 +364,31 @@ __device__ __forceinline__ void block_sum1(double& x) {
 }
 
 // Block sum of three values; result valid in thread 0.
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// FP32 block sums of two per-thread values (the double-float residual's norms, which
+// decide a tolerance: FP32 sums within a block are ample); valid in thread 0
+__device__ __forceinline__ void block_sum2f(float& x, float& y) {
+  __shared__ float shf[2][32];
+  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+  const int nthr = blockDim.x * blockDim.y;
+  x = warp_sum_f(x); y = warp_sum_f(y);
+  const int w = tid >> 5, l = tid & 31;
+  if (l == 0) { shf[0][w] = x; shf[1][w] = y; }
+  __syncthreads();
+  const int nw = (nthr + 31) >> 5;
+  if (w == 0) {
+    x = l < nw ? shf[0][l] : 0.0f;
+    y = l < nw ? shf[1][l] : 0.0f;
+    x = warp_sum_f(x); y = warp_sum_f(y);
+  }
+  __syncthreads();
+}
+
 __device__ __forceinline__ void block_sum3(double& x, double& y, double& z) {
   __shared__ double sh[3][32];
   const int tid = threadIdx.x + threadIdx.y * blockDim.x;
@@ -425,9 +451,9 @@ __device__ __forceinline__ double fd_half(double eta, double& dF) {
 
 // FP64 residual of planes [k0, k1) of one (x, y) column, marching up with a
 // register window; accumulates r^2, b^2 (first residual of a solve only) and
-// rho^2.  SC = false compiles out the carrier term (stacks without a
-// semiconductor layer).
-template <typename T, bool SC = true>
+// rho^2.  SC = 0 compiles out the carrier term (stacks without a semiconductor
+// layer), SC = 1 keeps Boltzmann statistics only, SC = 2 also Fermi-Dirac.
+template <typename T, int SC = 2>
 __device__ __forceinline__ void resid_column(const ResidArgs& a, int i, int j, int k0, int k1,
                                              double& acc_r, double& acc_b, double& acc_rho) {
   const int nx = a.nx, ny = a.ny, nz = a.nz;
@@ -460,7 +486,7 @@ __device__ __forceinline__ void resid_column(const ResidArgs& a, int i, int j, i
     }
     double rho = 0.0;
     if (SC && pt.sc) {
-      if (pt.fd) {
+      if (SC == 2 && pt.fd) {
         // n = Nc F(eta_e0 + u), p = Nv F(eta_p0 - u); -d rho/d phi = kq (dn + dp)/VT
         const double u = pc * pt.inv_vt;
         double dn, dp;
@@ -489,6 +515,105 @@ __device__ __forceinline__ void resid_column(const ResidArgs& a, int i, int j, i
     if (a.first) acc_b = fma(bb, bb, acc_b);
     pd = pc;
     pc = pu;
+  }
+}
+
+// The same residual with the stencil in double-float arithmetic (df_arith.cuh):
+// the potentials, the right-hand side b + rho and the coefficients enter as h + l
+// pairs, the products and sums keep about 48 bits, so r agrees with the FP64
+// residual to a few 2^-48 of the largest term while the FP64 pipe is left to the
+// carrier exponentials.  The output is the high part (T = float, the mixed form's
+// FP32 correction equation) or h + l (T = double); the squared norms accumulate
+// per thread in FP32 (they decide a tolerance, 1e-7 relative is ample) and enter
+// the block sums in FP64.
+template <typename T, int SC>
+__device__ __forceinline__ void resid_column_df(const ResidArgs& a, int i, int j, int k0, int k1,
+                                                float& acc_r, float& acc_b, double& acc_rho) {
+  const int nx = a.nx, ny = a.ny, nz = a.nz;
+  const long long plane = (long long)nx * ny;
+  T* r_out = static_cast<T*>(a.r_out);
+  T* s_out = static_cast<T*>(a.s_out);
+  const double v_bot = a.params->v_bot, v_top = a.params->v_top;
+  const int im = (i == 0) ? nx - 1 : i - 1, ip = (i == nx - 1) ? 0 : i + 1;
+  const long long dxm = im - i, dxp = ip - i;
+  const long long dym = (long long)((j == 0) ? ny - 1 : j - 1) * nx - (long long)j * nx;
+  const long long dyp = (long long)((j == ny - 1) ? 0 : j + 1) * nx - (long long)j * nx;
+  const double* phi = a.phi;
+  const long long col = (long long)j * nx + i;
+  double pc_d = phi[(long long)k0 * plane + col];
+  df pd = k0 > 0 ? df_from_double(phi[(long long)(k0 - 1) * plane + col]) : df{0.0f, 0.0f};
+  df pc = df_from_double(pc_d);
+  for (int k = k0; k < k1; ++k) {
+    const long long t = k * plane + col;
+    const double pu_d = (k < nz - 1) ? phi[t + plane] : 0.0;
+    const df pu = df_from_double(pu_d);
+    const PlaneCoefDF c = ldg_struct(a.coef_df + k);
+    // only the plane fields this cell needs (the whole record is 28 words)
+    const PlaneTDGL* pk = a.planes + k;
+    const int b_dyn = __ldg(&pk->b_dyn);
+    // x neighbours: the centre pairs of the neighbouring lanes when a warp holds 32
+    // cells of one row (the row's ends convert their own)
+    df xm, xp;
+    if (a.warp_rows) {
+      const int lane = threadIdx.x & 31;
+      xm.h = __shfl_up_sync(0xffffffffu, pc.h, 1);
+      xm.l = __shfl_up_sync(0xffffffffu, pc.l, 1);
+      xp.h = __shfl_down_sync(0xffffffffu, pc.h, 1);
+      xp.l = __shfl_down_sync(0xffffffffu, pc.l, 1);
+      if (lane == 0) xm = df_from_double(phi[t + dxm]);
+      if (lane == 31) xp = df_from_double(phi[t + dxp]);
+    } else {
+      xm = df_from_double(phi[t + dxm]);
+      xp = df_from_double(phi[t + dxp]);
+    }
+    const df sx = df_add_fast(xm, xp);
+    const df sy = df_add_fast(df_from_double(phi[t + dym]), df_from_double(phi[t + dyp]));
+    double bb;
+    if (b_dyn) {
+      bb = a.b[t];
+    } else {
+      bb = 0.0;
+      if (k == 0) bb += __ldg(&pk->lift) * v_bot;
+      if (k == nz - 1) bb += __ldg(&pk->lift) * v_top;
+    }
+    double rho = 0.0;
+    if (SC && __ldg(&pk->sc)) {
+      const PlaneTDGL pt = ldg_struct(pk);
+      if (SC == 2 && pt.fd) {
+        const double u = pc_d * pt.inv_vt;
+        double dn, dp;
+        const double n = pt.Nc * fd_half(pt.eta_e0 + u, dn);
+        const double p = pt.Nv * fd_half(pt.eta_p0 - u, dp);
+        rho = pt.kq * (p - n + pt.Nnet);
+        if (s_out) s_out[t] = (T)(pt.kq * fma(pt.Nc, dn, pt.Nv * dp) * pt.inv_vt);
+      } else {
+        double ep, em;
+        exp_pm(pc_d * pt.inv_vt, ep, em);
+        const double n = pt.n0 * ep;
+        const double p = pt.p0 * em;
+        rho = pt.kq * (p - n + pt.Nnet);
+        if (s_out) s_out[t] = (T)(pt.kq * (n + p) * pt.inv_vt);
+      }
+      acc_rho = fma(rho, rho, acc_rho);
+    }
+    const df b_df = df_from_double(SC ? bb + rho : bb);
+    // r = ((b + rho) - diag phi) + (z couplings) + (lateral couplings), as a tree
+    const df r0 = df_add_fast(b_df, df_neg(df_mul(df{c.diag_h, c.diag_l}, pc)));
+    const df rz = df_add_fast(df_mul(df{c.czhi_h, c.czhi_l}, pu), df_mul(df{c.czlo_h, c.czlo_l}, pd));
+    const df rl = df_add_fast(df_mul(df{c.cy_h, c.cy_l}, sy), df_mul(df{c.cx_h, c.cx_l}, sx));
+    const df r = df_add_fast(df_add_fast(r0, rz), rl);
+    if (sizeof(T) == sizeof(float))
+      r_out[t] = (T)r.h;
+    else
+      r_out[t] = (T)((double)r.h + (double)r.l);
+    acc_r = fmaf(r.h, r.h, acc_r);
+    if (a.first) {
+      const float bh = df_from_double(bb).h;
+      acc_b = fmaf(bh, bh, acc_b);
+    }
+    pd = pc;
+    pc = pu;
+    pc_d = pu_d;
   }
 }
 

@@ -512,7 +512,7 @@ __global__ void __launch_bounds__(kTailThreads) tail_kernel(MGArgs<T> g, TailArg
 }
 
 // grid (x chunk, row chunk, z chunk): block z owns planes [z kchunk, (z+1) kchunk)
-template <typename T, bool SC>
+template <typename T, int SC, bool DF = false>
 __global__ void __launch_bounds__(kResidBX* kResidBY) resid_kernel(ResidArgs a) {
   pdl_enter();
   const int i = blockIdx.x * kResidBX + threadIdx.x;
@@ -520,13 +520,25 @@ __global__ void __launch_bounds__(kResidBX* kResidBY) resid_kernel(ResidArgs a) 
   const int k0 = blockIdx.z * a.kchunk;
   const int k1 = min(a.nz, k0 + a.kchunk);
   double acc_r = 0.0, acc_b = 0.0, acc_rho = 0.0;
-  if (i < a.nx && j < a.ny) resid_column<T, SC>(a, i, j, k0, k1, acc_r, acc_b, acc_rho);
-  if (a.no_stats) return;
-  // ||b||^2 is summed on the first residual of a solve only, ||rho||^2 with carriers only
-  if (SC || a.first)
-    block_sum3(acc_r, acc_b, acc_rho);
-  else
-    block_sum1(acc_r);
+  if constexpr (DF) {
+    float fr = 0.0f, fb = 0.0f;
+    if (i < a.nx && j < a.ny) resid_column_df<T, SC>(a, i, j, k0, k1, fr, fb, acc_rho);
+    if (a.no_stats) return;
+    // the squared norms within the block in FP32 (no FP64 work per cell), across
+    // blocks in FP64 below; ||rho||^2 in FP64
+    block_sum2f(fr, fb);
+    if (SC) block_sum1(acc_rho);
+    acc_r = (double)fr;
+    acc_b = (double)fb;
+  } else {
+    if (i < a.nx && j < a.ny) resid_column<T, SC>(a, i, j, k0, k1, acc_r, acc_b, acc_rho);
+    if (a.no_stats) return;
+    // ||b||^2 is summed on the first residual of a solve only, ||rho||^2 with carriers only
+    if (SC || a.first)
+      block_sum3(acc_r, acc_b, acc_rho);
+    else
+      block_sum1(acc_r);
+  }
   __shared__ bool last;
   const int nblk = gridDim.x * gridDim.y * gridDim.z;
   const int bid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
@@ -809,14 +821,22 @@ void launch_tail(const MGArgs<T>& a, const TailArgs& t, size_t smem, cudaStream_
 }
 
 template <typename T>
-void launch_resid(const ResidArgs& a, cudaStream_t s) {
+void launch_resid(const ResidArgs& a_in, cudaStream_t s) {
+  ResidArgs a = a_in;
+  a.warp_rows = a.nx % 32 == 0;
   dim3 block(kResidBX, kResidBY);
   dim3 grid((a.nx + kResidBX - 1) / kResidBX, (a.ny + kResidBY - 1) / kResidBY,
             (a.nz + a.kchunk - 1) / a.kchunk);
-  if (a.carriers)
-    launch_k(resid_kernel<T, true>, grid, block, 0, s, a);
-  else
-    launch_k(resid_kernel<T, false>, grid, block, 0, s, a);
+  // carriers: 0 none, 1 Boltzmann statistics only, 2 with Fermi-Dirac planes
+  if (a.coef_df) {
+    if (a.carriers == 2) launch_k(resid_kernel<T, 2, true>, grid, block, 0, s, a);
+    else if (a.carriers == 1) launch_k(resid_kernel<T, 1, true>, grid, block, 0, s, a);
+    else launch_k(resid_kernel<T, 0, true>, grid, block, 0, s, a);
+  } else {
+    if (a.carriers == 2) launch_k(resid_kernel<T, 2>, grid, block, 0, s, a);
+    else if (a.carriers == 1) launch_k(resid_kernel<T, 1>, grid, block, 0, s, a);
+    else launch_k(resid_kernel<T, 0>, grid, block, 0, s, a);
+  }
 }
 
 template <typename T>

@@ -61,7 +61,7 @@ EXPORTS = ["ferrox_init_geometry", "ferrox_set_bias", "ferrox_solve_poisson", "f
            "ferrox_step", "ferrox_charge", "ferrox_sync_stats", "ferrox_clear_status",
            "ferrox_get_state", "ferrox_set_state", "ferrox_fe_planes", "ferrox_get_state_fe",
            "ferrox_set_state_fe", "ferrox_destroy", "ferrox_last_error",
-           "ferrox_level_shape", "ferrox_profile_step", "ferrox_profile_step_bytes", "ferrox_qv_sweep",
+           "ferrox_level_shape", "ferrox_profile_step", "ferrox_profile_step_bytes", "ferrox_qv_sweep", "ferrox_residual",
            "ferrox_tdgl_update_static",
            "ferrox_init_batch", "ferrox_batch_set_bias", "ferrox_batch_solve_poisson",
            "ferrox_batch_step", "ferrox_batch_charge", "ferrox_batch_stats", "ferrox_batch_tuning",
@@ -106,6 +106,7 @@ def load(path: str = LIB_PATH):
                                        C.POINTER(C.c_int), C.POINTER(C.c_int)]
     lib.ferrox_profile_step.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int)]
     lib.ferrox_qv_sweep.argtypes = [vp, C.POINTER(C.c_double), C.c_int, C.c_int, C.POINTER(Charge)]
+    lib.ferrox_residual.argtypes = [vp, C.c_int, vp]
     lib.ferrox_profile_step_bytes.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int),
                                               C.POINTER(C.c_double)]
     lib.ferrox_tdgl_update_static.argtypes = [C.POINTER(Geometry), C.c_double, C.c_double,
@@ -278,6 +279,16 @@ class Device:
         pp = C.c_void_p(P_fe_host.ctypes.data) if P_fe_host is not None else None
         fp = C.c_void_p(phi_host.ctypes.data) if phi_host is not None else None
         self._ck(self.lib.ferrox_set_state_fe(self.ctx, pp, fp))
+
+    def residual(self, double_float=False):
+        """r = b + rho(phi) - A phi of the current state (scaled by h^2/eps0), float64
+        [Nz][Ny][Nx], in FP64 or in the mixed form's double-float arithmetic."""
+        import numpy as np
+        nz = sum(int(l["ncells"]) for l in self.geom["layers"])
+        out = np.empty((nz, self.geom["ny"], self.geom["nx"]), dtype=np.float64)
+        self._ck(self.lib.ferrox_residual(self.ctx, 1 if double_float else 0,
+                                          C.c_void_p(out.ctypes.data)))
+        return out
 
     def qv_sweep(self, v_app, steps_per_point):
         """Triangular-wave (or any) Q-V protocol run natively: a list of charge
