@@ -3,7 +3,7 @@ with the library's own kernels, then run with and without the network.
 
 The network may only change how many V-cycles a solve needs: both runs stop on
 the same residual test, so their trajectories agree to the solver tolerance.
-The test reports the gain (cycles per step with / without) and bounds any loss.
+The tests assert the V-cycle gain and report the time per step.
 """
 import numpy as np
 import pytest
@@ -57,7 +57,63 @@ def test_learned_warm_start_gain_and_same_answer():
     assert rej < 40
     assert np.linalg.norm(Pa - Pb) <= 1e-9 * np.linalg.norm(Pa)
     assert np.linalg.norm(phia - phib) <= 1e-9 * np.linalg.norm(phia)
-    assert cb <= 1.5 * ca + 1.0
+    # the same answer either way; on this small stack the gain is small (measured
+    # 7.25 -> 7.17 V-cycles per step); the 256x256x32 test below asserts the gain
+    assert cb <= ca
+    net.close()
+
+
+def test_learned_warm_start_gain_on_the_256x256x32_sweep():
+    """The bench's learned form on the 256x256x32 MFIM sweep workload (fast mixed form:
+    extrapolated guess, up to 8 V-cycles per FP64 residual): a network trained on 300
+    snapshots of the workload itself cuts the V-cycles per step by more than 10% at the
+    same 1e-10 residual test and the same trajectory (measured on GB300: 7.62 -> 4.65
+    V-cycles per step over the first 40 steps at -2 V).  The time per step with and
+    without the network is reported (measured 1.009 -> 0.924 ms)."""
+    from paper_2210_15668_gb300 import ferrox
+    cfg = I.mfim_sweep()
+    geom = cfg["geom"]
+    P0 = I.random_polarization(geom, cfg["seed"])
+    num = ferrox.make_numerics(4e-13, tol=1e-10, precision=ferrox.MIXED, guess=1, inner=-8)
+    d = ferrox.Device(geom, P0, numerics=num)
+    lv = d.levels()[2]
+    net = ferrox.NN(lv[2], lv[1], lv[0], capacity=300, seed=7)
+    d.set_bias(0.0, cfg["sweep"][0])
+    d.solve_poisson()
+    d.attach_nn(net, 1)
+    for k in range(300):
+        if k % 25 == 0:
+            d.set_bias(0.0, cfg["sweep"][(k // 25) % len(cfg["sweep"])])
+        d.step(1)
+    d.close()
+    net.train(epochs=20, lr=3e-4, batch=8)
+    out = {}
+    for mode in (0, 2):
+        e = ferrox.Device(geom, P0, numerics=num)
+        e.set_bias(0.0, -2.0)
+        e.solve_poisson()
+        if mode == 2:
+            e.attach_nn(net, 2)
+        e.step(5)
+        torch.cuda.synchronize()
+        s0 = e.stats()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(e.stream)
+        e.step(40)
+        b.record(e.stream)
+        torch.cuda.synchronize()
+        s1 = e.stats()
+        assert s1["status"] == 0
+        out[mode] = (e.get_state(), (s1["vcycles"] - s0["vcycles"]) / 40, a.elapsed_time(b) / 40,
+                     s1["nn_rejected"] - s0["nn_rejected"])
+        e.close()
+    (Pa, phia), ca, ta, _ = out[0]
+    (Pb, phib), cb, tb, rej = out[2]
+    print(f"256x256x32: V-cycles per step {ca:.2f} without, {cb:.2f} with the network; "
+          f"ms per step {ta:.3f} / {tb:.3f}; rejected {rej} of 40")
+    assert cb < 0.9 * ca, (ca, cb)
+    assert np.linalg.norm(Pa - Pb) <= 2e-8 * np.linalg.norm(Pa)
+    assert np.linalg.norm(phia - phib) <= 2e-8 * np.linalg.norm(phia)
     net.close()
 
 
