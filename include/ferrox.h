@@ -272,7 +272,11 @@ enum {
 /* One time step run eagerly (no CUDA graph) with a CUDA event pair around every
  * launch, for a per-kernel time breakdown: on return ms[k] is the summed device
  * time and count[k] the number of launches of class k (arrays of FERROX_K_COUNT).
- * The result of the step is the same as ferrox_step(ctx, 1).  Synchronises. */
+ * The launches between two host synchronisations (one V-cycle, or the TDGL
+ * update) are queued behind a short untimed delay kernel, so the device runs
+ * them back to back and the events time the kernels, not the host's launch
+ * rate.  The result of the step is the same as ferrox_step(ctx, 1).
+ * Synchronises. */
 ferrox_status ferrox_profile_step(ferrox_ctx* ctx, double* ms, int* count);
 
 /* The same step, also reporting in bytes[k] (array of FERROX_K_COUNT, may be

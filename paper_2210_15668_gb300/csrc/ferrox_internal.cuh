@@ -273,6 +273,8 @@ struct TDGLArgs {
                           // 3: right-hand side of the current P only
 };
 void launch_tdgl(const TDGLArgs& a, cudaStream_t s);
+// a single-thread kernel that spins for `cycles` SM clock cycles (bounded)
+void launch_delay(long long cycles, cudaStream_t s);
 
 struct ChargeArgs {
   const double* phi;

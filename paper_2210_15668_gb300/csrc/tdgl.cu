@@ -159,6 +159,14 @@ __global__ void static_b_kernel(double* b, const PlaneTDGL* planes, const DevPar
     b[k * plane + t] = v;
 }
 
+// Holds the stream for a bounded number of SM clock cycles (the profiler queues a
+// batch of launches behind it so that they then run back to back).
+__global__ void delay_kernel(long long cycles) {
+  const long long t0 = clock64();
+  while (clock64() - t0 < cycles) {
+  }
+}
+
 __global__ void stats_step_kernel(DevStats* st, int n, int launches) {
   pdl_enter();
   st->steps += n;
@@ -199,6 +207,8 @@ void launch_static_b(double* b, const PlaneTDGL* planes, const DevParams* prm, i
   if (blocks > 152) blocks = 152;
   static_b_kernel<<<dim3((int)blocks, 2), 256, 0, s>>>(b, planes, prm, nx, ny, nz);
 }
+
+void launch_delay(long long cycles, cudaStream_t s) { delay_kernel<<<1, 1, 0, s>>>(cycles); }
 
 void launch_stats_step(DevStats* st, int nsteps, int launches, cudaStream_t s) {
   launch_k(stats_step_kernel, dim3(1), dim3(1), 0, s, st, nsteps, launches);
