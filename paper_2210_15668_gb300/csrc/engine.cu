@@ -428,6 +428,29 @@ double update_clamp(const ferrox_ctx* c) {
   return 10.0 * kKB * tmax / kQ;
 }
 
+// a plane's FP64 coefficients as double-float pairs: h = the nearest float, l = the
+// nearest float to the remainder
+PlaneCoefDF split_coef_df(const PlaneCoef<double>& q) {
+  auto split = [](double x, float& h, float& l) {
+    h = (float)x;
+    l = (float)(x - (double)h);
+  };
+  PlaneCoefDF d;
+  split(q.cx, d.cx_h, d.cx_l);
+  split(q.cy, d.cy_h, d.cy_l);
+  split(q.czlo, d.czlo_h, d.czlo_l);
+  split(q.czhi, d.czhi_h, d.czhi_l);
+  split(q.diag, d.diag_h, d.diag_l);
+  return d;
+}
+
+// the mixed form evaluates its outer residual in double-float arithmetic unless
+// FERROX_DF_RESID=0 is set in the environment (FP64 residual; for comparisons)
+bool df_resid_enabled() {
+  const char* v = std::getenv("FERROX_DF_RESID");
+  return !(v && v[0] == '0');
+}
+
 // residual instantiation for the stack's carriers: 0 none, 1 Boltzmann only, 2 with
 // Fermi-Dirac planes
 int carrier_kind(const ferrox_ctx* c) {
@@ -1288,24 +1311,11 @@ ferrox_status ferrox_init_geometry(ferrox_ctx** out, const ferrox_geometry* geom
     // the same coefficients as double-float pairs: h = the nearest float, l = the
     // nearest float to the remainder
     std::vector<PlaneCoefDF> cdf(ctx->nz);
-    auto split = [](double x, float& h, float& l) {
-      h = (float)x;
-      l = (float)(x - (double)h);
-    };
-    for (int k = 0; k < ctx->nz; ++k) {
-      const PlaneCoef<double>& q = c64[k];
-      split(q.cx, cdf[k].cx_h, cdf[k].cx_l);
-      split(q.cy, cdf[k].cy_h, cdf[k].cy_l);
-      split(q.czlo, cdf[k].czlo_h, cdf[k].czlo_l);
-      split(q.czhi, cdf[k].czhi_h, cdf[k].czhi_l);
-      split(q.diag, cdf[k].diag_h, cdf[k].diag_l);
-    }
+    for (int k = 0; k < ctx->nz; ++k) cdf[k] = split_coef_df(c64[k]);
     FX_INIT_CK(cudaMalloc(&ctx->coef_df, ctx->nz * sizeof(PlaneCoefDF)));
     FX_INIT_CK(cudaMemcpy(ctx->coef_df, cdf.data(), ctx->nz * sizeof(PlaneCoefDF),
                           cudaMemcpyHostToDevice));
-    // FERROX_DF_RESID=0 in the environment keeps the FP64 residual in the mixed form
-    const char* df_env = std::getenv("FERROX_DF_RESID");
-    ctx->df_resid = mixed && !(df_env && df_env[0] == '0');
+    ctx->df_resid = mixed && df_resid_enabled();
   }
   ctx->dense_lev = dense_level(ctx);
   if (mixed) {
@@ -2169,6 +2179,9 @@ ferrox_status ferrox_init_batch(ferrox_batch** out, int n, const ferrox_geometry
     ra.r_out = static_cast<char*>(B->r) + (size_t)p.arena_off * tsz;
     ra.s_out = has_sc && c.has_sc ? static_cast<char*>(B->s) + (size_t)p.arena_off * tsz : nullptr;
     ra.carriers = carrier_kind(&c);
+    // FP64 residual: measured, the double-float form is slower in this latency-bound
+    // kernel (64 instances: 1004 against 1091 Mcell-steps/s)
+    ra.coef_df = nullptr;
     ra.partials = nullptr;
     ra.stats = B->stats + i;
     ra.tol = num->tol; ra.max_cycles = num->max_cycles; ra.first = 1; ra.set_cond = 0;
