@@ -791,26 +791,37 @@ def run_reference(args, ws, rank):
 
 
 def run_nn_forward(args):
-    """Event-timed forwards of the warm-start network (random weights) on the
-    benchmark stack's level-2 grid, 64 x 64 x 8, from a seeded input."""
+    """Event-timed forwards of the warm-start network (random weights) on the level-2
+    grids of the 256x256x32 stack (64 x 64 x 8) and of the 512x512x128 stack
+    (128 x 128 x 32), from a seeded input, with the convolutions on the tcgen05
+    kernel and on the mma.sync kernel."""
     import torch
     from paper_2210_15668_gb300 import ferrox
-    D, H, W = 8, 64, 64
-    net = ferrox.NN(D, H, W, seed=3)
-    g = torch.Generator(device="cuda").manual_seed(0)
-    x = torch.randn(D * H * W, 16, device="cuda", dtype=torch.float32, generator=g)
-    for _ in range(args.warmup):
-        net.forward(x)
-    torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record()
-    for _ in range(args.steps):
-        net.forward(x)
-    b.record()
-    torch.cuda.synchronize()
-    print(json.dumps({"nn_forward_us": a.elapsed_time(b) / args.steps * 1e3, "grid": [D, H, W],
-                      "forwards": args.steps}))
-    net.close()
+    out = {}
+    for D, H, W in ((8, 64, 64), (32, 128, 128)):
+        net = ferrox.NN(D, H, W, seed=3)
+        g = torch.Generator(device="cuda").manual_seed(0)
+        x = torch.randn(D * H * W, 16, device="cuda", dtype=torch.float32, generator=g)
+        res = {}
+        for tc in (True, False):
+            net.use_tensor_memory(tc)
+            for _ in range(args.warmup):
+                net.forward(x)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(args.steps):
+                net.forward(x)
+            b.record()
+            torch.cuda.synchronize()
+            res["tcgen05" if tc else "mma_sync"] = a.elapsed_time(b) / args.steps * 1e3
+        info = net.kernel_info()
+        net.use_tensor_memory(True)
+        res["tc_convs"] = net.kernel_info()["tc_forward"]
+        res["fault"] = info["fault"]
+        out[f"{D}x{H}x{W}"] = res
+        net.close()
+    print(json.dumps({"nn_forward_us": out, "forwards": args.steps}))
 
 
 def main():

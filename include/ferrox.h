@@ -395,12 +395,27 @@ ferrox_status ferrox_nn_set_params(ferrox_nn* nn, const float* w, const float* b
  * which are then cleared. */
 ferrox_status ferrox_nn_adam_step(ferrox_nn* nn, double lr);
 ferrox_status ferrox_nn_snapshot_count(const ferrox_nn* nn, int* count);
-/* `epochs` passes over the stored snapshots, an Adam step every `batch` of them;
- * loss_per_epoch (host, may be NULL) receives the mean loss of each epoch. */
+/* `epochs` passes over the stored snapshots, each in a fresh pseudo-random order
+ * (fixed seed: repeated calls on the same store repeat), an Adam step every
+ * `batch` of them with a step size that decays from lr to lr / 10 (cosine) over
+ * the call; loss_per_epoch (host, may be NULL) receives the mean loss of each
+ * epoch. */
 ferrox_status ferrox_nn_train(ferrox_nn* nn, int epochs, double lr, int batch,
                               float* loss_per_epoch);
 ferrox_status ferrox_nn_destroy(ferrox_nn* nn);
 const char* ferrox_nn_last_error(const ferrox_nn* nn);
+/* Convolution kernels.  use_tensor_memory = 1 (the default) runs every
+ * convolution whose grid has an x extent that is a multiple of 8 and a y extent
+ * that is a multiple of 16 on the tcgen05 kernel (FP32 accumulators in tensor
+ * memory); 0 runs all of them on the mma.sync kernel.  Takes effect for later
+ * calls and for graphs captured afterwards.  Returns EINVAL for other values. */
+ferrox_status ferrox_nn_use_tensor_memory(ferrox_nn* nn, int use_tensor_memory);
+/* After synchronising the network's stream: tc_forward / tc_backward = how many
+ * of the 6 forward and 5 adjoint convolutions of one pass run on the tcgen05
+ * kernel; fault = 1 if a tcgen05 convolution gave up waiting for its MMAs (about
+ * a second; that launch then left its output incomplete), else 0.  Any output
+ * may be NULL. */
+ferrox_status ferrox_nn_kernel_info(ferrox_nn* nn, int* tc_forward, int* tc_backward, int* fault);
 /* Attach a network to a context: mode 0 detaches, 1 records one snapshot per
  * ferrox_step (order 1; the steps then run without a CUDA graph), 2 applies the
  * network before every predictor solve (captured in the step graph).  The

@@ -300,8 +300,15 @@ struct NNGrid {
 #include <algorithm>
 struct ferrox_nn;
 namespace fx {
-void nn_conv_fwd(const __nv_bfloat16* in, int cin, const __nv_bfloat16* wk, const float* bias,
-                 int cout, NNGrid g, int relu, __nv_bfloat16* out_bf, float* out_f, cudaStream_t s);
+// returns true when the tensor-memory (tcgen05) kernel ran, false for the mma.sync kernel
+// (f_ch0: out_f receives output channel 0 only, one float per voxel)
+bool nn_conv_fwd(const __nv_bfloat16* in, int cin, const __nv_bfloat16* wk, const __nv_bfloat16* wt,
+                 const float* bias, int cout, NNGrid g, int relu, __nv_bfloat16* out_bf, float* out_f,
+                 int f_ch0, int* fault, cudaStream_t s);
+bool nn_conv_upcat_tc(const __nv_bfloat16* a4, const __nv_bfloat16* s1, const __nv_bfloat16* wt,
+                      const float* bias, NNGrid g, int relu, __nv_bfloat16* out_bf, int* fault, cudaStream_t s);
+bool nn_conv_uses_tc(int cin, int cout, NNGrid g);
+cudaError_t nn_tc_setup();
 void nn_conv_wgrad(const __nv_bfloat16* in, int cin, const __nv_bfloat16* dout, int cout, NNGrid g,
                    float* gw, float* gb, cudaStream_t s);
 void nn_pool2(const __nv_bfloat16* in, NNGrid f, int C, __nv_bfloat16* out, cudaStream_t s);
@@ -312,7 +319,8 @@ void nn_skip_grad(const float* dcat, const float* dp, const __nv_bfloat16* s1, N
                   __nv_bfloat16* out, cudaStream_t s);
 void nn_mse(const float* y, const float* tgt, int M, __nv_bfloat16* dy, float* loss, cudaStream_t s);
 void nn_adam(float* p, float* g, float* m, float* v, int n, float lr, int step, cudaStream_t s);
-void nn_pack(const float* w, int cin, int cout, __nv_bfloat16* wk, __nv_bfloat16* wb, cudaStream_t s);
+void nn_pack(const float* w, int cin, int cout, __nv_bfloat16* wk, __nv_bfloat16* wb, __nv_bfloat16* wkt,
+             __nv_bfloat16* wbt, cudaStream_t s);
 __nv_bfloat16* nn_input(ferrox_nn* N);
 const float* nn_output(ferrox_nn* N);
 void nn_run_forward(ferrox_nn* N, cudaStream_t s);

@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -68,7 +69,7 @@ template <int COUT>
 __global__ void __launch_bounds__(32 * kConvTiles * 3) conv_fwd_kernel(
     const bf16* __restrict__ in, int cin, const bf16* __restrict__ wk,
     const float* __restrict__ bias, NNGrid g, int relu, bf16* __restrict__ out_bf,
-    float* __restrict__ out_f) {
+    float* __restrict__ out_f, int f_ch0) {
   __shared__ float part[2][kConvTiles][COUT / 8][4][32];
   const int lane = threadIdx.x, tile = threadIdx.y, slab = threadIdx.z;
   const int M = g.D * g.H * g.W;
@@ -137,11 +138,299 @@ __global__ void __launch_bounds__(32 * kConvTiles * 3) conv_fwd_kernel(
       if (relu) { v0 = fmaxf(v0, 0.f); v1 = fmaxf(v1, 0.f); }
       if (out_bf)
         *reinterpret_cast<__nv_bfloat162*>(out_bf + (size_t)m * COUT + co) = __floats2bfloat162_rn(v0, v1);
-      if (out_f) {
+      if (out_f && f_ch0) {
+        if (co == 0) out_f[m] = v0;
+      } else if (out_f) {
         out_f[(size_t)m * COUT + co] = v0;
         out_f[(size_t)m * COUT + co + 1] = v1;
       }
     }
+  }
+}
+
+// ---- 3x3x3 convolution on the fifth-generation tensor cores (tcgen05, TMEM) ----------
+//
+// A tile is 8 (x) x 16 (y) x zt (z) voxels.  Its input with a one-voxel halo
+// (10 x 18 x (zt + 2) voxels, periodic in x and y, zero outside z) is staged in
+// shared memory in the no-swizzle K-major layout of the tensor core's operands:
+// for each 8-channel chunk a plane of 16-byte entries [z][y][x].  Eight
+// consecutive x voxels are then one 8 x 16 B core matrix and the 16 y rows of a
+// tile are core matrices 160 B apart, so the A operand of every tap is the same
+// staged tile seen through a shifted descriptor: the 27 taps need no further
+// data movement.  The weights of all taps sit beside it as [tap][ci/8][co][ci%8].
+// One thread issues the 128 x COUT x 16 MMAs (27 taps x CIN/16 K-steps per
+// z-plane) into FP32 accumulators in tensor memory; the four warps read their
+// 32 rows back with tcgen05.ld for the bias, ReLU and BF16/FP32 store.
+//
+// CTAs are persistent: the weights are loaded once, and the halo buffers and
+// accumulators are double-buffered, so the loads of tile i + 1 and the epilogue
+// of tile i - 1 run while the tensor core works on tile i.
+constexpr int kTcX = 8, kTcY = 16, kTcHX = kTcX + 2, kTcHY = kTcY + 2;
+constexpr int kTcPlane = kTcHX * kTcHY;             // halo entries per z-plane
+constexpr int kTcThreads = 128;
+constexpr long long kTcWaitCycles = 2000000000LL;   // ~1 s at 2 GHz
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void tc_cp16(unsigned dst, const void* src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0)
+               : "memory");
+}
+
+// shared-memory matrix descriptor: start address, leading (K-direction) and
+// stride (8-row group) byte offsets, descriptor version 1, no swizzle.  The start
+// address is the low field (bits 0-13, in 16-byte units), so a descriptor of an
+// address 16 k bytes further is this one plus k.
+__device__ __forceinline__ unsigned long long tc_desc(unsigned addr, unsigned lbo, unsigned sbo) {
+  return (unsigned long long)((addr & 0x3FFFFu) >> 4) | ((unsigned long long)(lbo >> 4) << 16) |
+         ((unsigned long long)(sbo >> 4) << 32) | (1ull << 46);
+}
+
+// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, M = 128, N = n
+__host__ __device__ constexpr unsigned tc_idesc(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(n >> 3) << 17) | ((unsigned)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(unsigned d, unsigned long long a, unsigned long long b, unsigned idesc,
+                                       unsigned accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(unsigned mbar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(done)
+      : "r"(mbar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// bounded wait on an mbarrier phase; false when the limit ran out
+__device__ __forceinline__ bool mbar_wait(unsigned mbar, unsigned parity, long long limit) {
+  const long long t0 = clock64();
+  while (!mbar_try(mbar, parity))
+    if (clock64() - t0 > limit) return false;
+  return true;
+}
+
+// 16 consecutive FP32 accumulator columns of this warp's 32 rows
+__device__ __forceinline__ void tc_ld16(unsigned taddr, float (&v)[16]) {
+  unsigned r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+      "[%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__host__ __device__ constexpr int tc_cols(int n) {
+  return n <= 32 ? 32 : n <= 64 ? 64 : n <= 128 ? 128 : n <= 256 ? 256 : 512;
+}
+
+struct TcTile {
+  int x0, y0, z0;
+};
+
+__device__ __forceinline__ TcTile tc_tile(int t, const NNGrid& g, int zt) {
+  const int nbx = g.W / kTcX, nby = g.H / kTcY;
+  return TcTile{(t % nbx) * kTcX, ((t / nbx) % nby) * kTcY, (t / (nbx * nby)) * zt};
+}
+
+// Stage the halo of one tile: warp w takes halo rows (z, y) w, w + 4, ...; lane j
+// takes entries j and j + 32 of a row, entry q = x * NCH + chunk, so a warp reads
+// consecutive 16-byte chunks of consecutive voxels.  With UP the 48 input
+// channels are the concatenation [up(a4) (32), s1 (16)] read in place: chunks
+// 0-3 from the coarse field a4 (= in) at the parent voxel, chunks 4-5 from s1.
+template <int CIN, bool UP>
+__device__ __forceinline__ void tc_load_halo(const bf16* __restrict__ in, const bf16* __restrict__ s1,
+                                             const NNGrid& g, TcTile t, int zt, unsigned buf, int chunk_entries) {
+  constexpr int NCH = CIN / 8, PER_ROW = kTcHX * NCH;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int Hc = g.H / 2, Wc = g.W / 2;
+  int goff[2], soff[2];
+  bool have[2], fine[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int q = lane + 32 * h;
+    have[h] = q < PER_ROW;
+    const int xx = have[h] ? q / NCH : 0, k = q % NCH;
+    int gx = t.x0 + xx - 1;
+    gx = gx < 0 ? gx + g.W : (gx >= g.W ? gx - g.W : gx);
+    fine[h] = !UP || k >= 4;
+    goff[h] = UP ? (k < 4 ? (gx >> 1) * 32 + 8 * k : gx * 16 + 8 * (k - 4)) : gx * CIN + 8 * k;
+    soff[h] = 16 * (k * chunk_entries + xx);
+  }
+  const int rows = kTcHY * (zt + 2);
+  for (int r = warp; r < rows; r += kTcThreads / 32) {
+    const int zz = r / kTcHY, yy = r - zz * kTcHY;
+    int gy = t.y0 + yy - 1;
+    gy = gy < 0 ? gy + g.H : (gy >= g.H ? gy - g.H : gy);
+    int gz = t.z0 + zz - 1;
+    const bool okz = gz >= 0 && gz < g.D;
+    gz = okz ? gz : 0;
+    const bf16* row = UP ? s1 + (size_t)(gz * g.H + gy) * g.W * 16 : in + (size_t)(gz * g.H + gy) * g.W * CIN;
+    const bf16* crow = UP ? in + (size_t)((gz >> 1) * Hc + (gy >> 1)) * Wc * 32 : row;
+    const unsigned srow = buf + 16u * (unsigned)(r * kTcHX);
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+      if (have[h]) tc_cp16(srow + soff[h], (fine[h] ? row : crow) + goff[h], okz);
+  }
+}
+
+template <int CIN, int COUT>
+__device__ __forceinline__ void tc_epilogue(unsigned tmem_acc, const NNGrid& g, TcTile t, int zt,
+                                            const float* __restrict__ bias, int relu, bf16* __restrict__ out_bf,
+                                            float* __restrict__ out_f, int f_ch0) {
+  const int tid = threadIdx.x, warp = tid >> 5;
+  // thread tid holds accumulator row tid = voxel (y0 + tid / 8, x0 + tid % 8)
+  const int x = t.x0 + (tid & 7), y = t.y0 + (tid >> 3);
+  for (int p = 0; p < zt; ++p) {
+    const size_t m = ((size_t)(t.z0 + p) * g.H + y) * g.W + x;
+#pragma unroll
+    for (int j = 0; j < COUT / 16; ++j) {
+      float v[16];
+      tc_ld16(tmem_acc + ((unsigned)(32 * warp) << 16) + (unsigned)(p * COUT + 16 * j), v);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        if (bias) v[i] += __ldg(bias + 16 * j + i);
+        if (relu) v[i] = fmaxf(v[i], 0.f);
+      }
+      if (out_bf) {
+        uint4 q[2];
+        __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(q);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) h[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+        uint4* o = reinterpret_cast<uint4*>(out_bf + m * COUT + 16 * j);
+        o[0] = q[0];
+        o[1] = q[1];
+      }
+      if (out_f && f_ch0) {
+        if (j == 0) out_f[m] = v[0];
+      } else if (out_f) {
+        float4* o = reinterpret_cast<float4*>(out_f + m * COUT + 16 * j);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) o[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+      }
+    }
+  }
+}
+
+template <int CIN, int COUT, bool UP>
+__global__ void __launch_bounds__(kTcThreads) conv_tc_kernel(
+    const bf16* __restrict__ in, const bf16* __restrict__ s1, const bf16* __restrict__ wt,
+    const float* __restrict__ bias, NNGrid g, int zt, int relu, bf16* __restrict__ out_bf,
+    float* __restrict__ out_f, int f_ch0, int* __restrict__ fault) {
+  constexpr int NCH = CIN / 8;
+  constexpr int WBYTES = 27 * CIN * COUT * 2;
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned long long* mbar = reinterpret_cast<unsigned long long*>(smem);   // two barriers
+  unsigned* tslot = reinterpret_cast<unsigned*>(smem + 16);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int ncols = tc_cols(2 * zt * COUT);
+  const int chunk_entries = kTcPlane * (zt + 2);
+  const unsigned hbytes = 16u * NCH * chunk_entries;
+  const unsigned sw = smem_u32(smem + 128);
+  const unsigned hb0 = sw + WBYTES, mb0 = smem_u32(mbar);   // buffer / barrier b at + b hbytes / + 8 b
+  const int ntiles = (g.W / kTcX) * (g.H / kTcY) * (g.D / zt);
+  const int nmine = blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb0) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb0 + 8) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  // weights (a straight copy of the packed array) and the first tile, one group
+  for (int i = tid; i < WBYTES / 16; i += kTcThreads) tc_cp16(sw + 16u * i, wt + 8 * i, true);
+  if (nmine > 0) tc_load_halo<CIN, UP>(in, s1, g, tc_tile(blockIdx.x, g, zt), zt, hb0, chunk_entries);
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+
+  constexpr unsigned idesc = tc_idesc(COUT);
+  const unsigned a_lbo = 16u * chunk_entries, b_lbo = 16u * COUT;
+  const unsigned long long bdesc0 = tc_desc(sw, b_lbo, 128u);
+  unsigned tmem = 0;
+  bool ok = true;
+  int issued = 0;   // tiles whose MMAs were committed
+  for (int i = 0; i < nmine; ++i) {
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    ok = !__syncthreads_or(!ok);
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (!ok) break;
+    tmem = *tslot;
+    const int cur = i & 1;
+    if (tid == 0) {
+      const unsigned d0 = tmem + (unsigned)(cur * zt * COUT);
+      const unsigned long long adesc0 = tc_desc(hb0 + cur * hbytes, a_lbo, 16u * kTcHX);
+      const unsigned long long kstep = 2ull * (unsigned long long)chunk_entries;   // 16-byte units
+      for (int p = 0; p < zt; ++p) {
+        const unsigned long long ap = adesc0 + (unsigned long long)(p * kTcPlane);
+#pragma unroll 3
+        for (int tap = 0; tap < 27; ++tap) {
+          const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+          const unsigned long long at = ap + (unsigned long long)((dz * kTcHY + dy) * kTcHX + dx);
+#pragma unroll
+          for (int ks = 0; ks < CIN / 16; ++ks)
+            tc_mma(d0 + (unsigned)(p * COUT), at + ks * kstep,
+                   bdesc0 + (unsigned long long)((tap * NCH + 2 * ks) * COUT), idesc, (tap | ks) != 0);
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mb0 + 8 * cur)
+                   : "memory");
+    }
+    issued = i + 1;
+    __syncwarp();
+    if (i > 0) {   // tile i - 1: its MMAs done frees its halo buffer and accumulator
+      ok = __all_sync(0xffffffffu, mbar_wait(mb0 + 8 * (cur ^ 1), ((i - 1) >> 1) & 1, kTcWaitCycles));
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    }
+    if (ok && i + 1 < nmine)
+      tc_load_halo<CIN, UP>(in, s1, g, tc_tile(blockIdx.x + (i + 1) * gridDim.x, g, zt), zt,
+                            hb0 + (cur ^ 1) * hbytes, chunk_entries);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    if (ok && i > 0)
+      tc_epilogue<CIN, COUT>(tmem + (unsigned)((cur ^ 1) * zt * COUT), g, tc_tile(blockIdx.x + (i - 1) * gridDim.x, g, zt),
+                             zt, bias, relu, out_bf, out_f, f_ch0);
+  }
+  if (ok && nmine > 0) {
+    const int l = nmine - 1;
+    ok = __all_sync(0xffffffffu, mbar_wait(mb0 + 8 * (l & 1), (l >> 1) & 1, kTcWaitCycles));
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (ok)
+      tc_epilogue<CIN, COUT>(tmem + (unsigned)((l & 1) * zt * COUT), g, tc_tile(blockIdx.x + l * gridDim.x, g, zt), zt,
+                             bias, relu, out_bf, out_f, f_ch0);
+  }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  if (!ok && tid == 0) {
+    atomicExch(fault, 1);
+    // let the last committed MMAs drain before the columns are freed
+    if (issued > 0) mbar_wait(mb0 + 8 * ((issued - 1) & 1), ((issued - 1) >> 1) & 1, kTcWaitCycles);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const unsigned base = *tslot;
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(base), "r"(ncols) : "memory");
   }
 }
 
@@ -225,34 +514,48 @@ __global__ void bias_grad_kernel(const bf16* __restrict__ dout, int M, int C, in
   atomicAdd(gb + c, s);
 }
 
-// 2x2x2 mean of a fine channels-last field
+// 2x2x2 mean of a fine channels-last field: one thread per coarse voxel and
+// 8-channel chunk (16 bytes)
 __global__ void pool2_kernel(const bf16* __restrict__ in, NNGrid f, int C, bf16* __restrict__ out) {
-  const int Dc = f.D / 2, Hc = f.H / 2, Wc = f.W / 2;
-  const long long n = (long long)Dc * Hc * Wc * C;
+  const int Dc = f.D / 2, Hc = f.H / 2, Wc = f.W / 2, nch = C / 8;
+  const long long n = (long long)Dc * Hc * Wc * nch;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
-    const int c = (int)(t % C);
-    const long long v = t / C;
+    const int k = (int)(t % nch);
+    const long long v = t / nch;
     const int X = (int)(v % Wc), Y = (int)((v / Wc) % Hc), Z = (int)(v / ((long long)Wc * Hc));
-    float s = 0.f;
+    float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (int q = 0; q < 8; ++q) {
       const int z = 2 * Z + (q >> 2), y = 2 * Y + ((q >> 1) & 1), x = 2 * X + (q & 1);
-      s += __bfloat162float(in[((size_t)(z * f.H + y) * f.W + x) * C + c]);
+      const uint4 u = *reinterpret_cast<const uint4*>(in + ((size_t)(z * f.H + y) * f.W + x) * C + 8 * k);
+      const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float2 p = __bfloat1622float2(h[i]);
+        s[2 * i] += p.x;
+        s[2 * i + 1] += p.y;
+      }
     }
-    out[t] = __float2bfloat16(0.125f * s);
+    uint4 o;
+    __nv_bfloat162* oh = reinterpret_cast<__nv_bfloat162*>(&o);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) oh[i] = __floats2bfloat162_rn(0.125f * s[2 * i], 0.125f * s[2 * i + 1]);
+    *reinterpret_cast<uint4*>(out + (size_t)v * C + 8 * k) = o;
   }
 }
 
-// cat[v] = [a4(parent of v) (32 channels), s1(v) (16 channels)]
+// cat[v] = [a4(parent of v) (32 channels), s1(v) (16 channels)]: one thread per
+// voxel and 8-channel chunk (16 bytes)
 __global__ void upcat_kernel(const bf16* __restrict__ a4, const bf16* __restrict__ s1, NNGrid f,
                              bf16* __restrict__ cat) {
-  const long long n = (long long)f.D * f.H * f.W * 48;
+  const long long n = (long long)f.D * f.H * f.W * 6;
   const int Hc = f.H / 2, Wc = f.W / 2;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
-    const int c = (int)(t % 48);
-    const long long v = t / 48;
+    const int k = (int)(t % 6);
+    const long long v = t / 6;
     const int x = (int)(v % f.W), y = (int)((v / f.W) % f.H), z = (int)(v / ((long long)f.W * f.H));
-    if (c < 32) cat[t] = a4[((size_t)((z / 2) * Hc + y / 2) * Wc + x / 2) * 32 + c];
-    else cat[t] = s1[(size_t)v * 16 + (c - 32)];
+    const uint4 u = k < 4 ? *reinterpret_cast<const uint4*>(a4 + ((size_t)((z / 2) * Hc + y / 2) * Wc + x / 2) * 32 + 8 * k)
+                          : *reinterpret_cast<const uint4*>(s1 + (size_t)v * 16 + 8 * (k - 4));
+    *reinterpret_cast<uint4*>(cat + (size_t)v * 48 + 8 * k) = u;
   }
 }
 
@@ -301,7 +604,7 @@ __global__ void mse_kernel(const float* __restrict__ y, const float* __restrict_
                            bf16* __restrict__ dy, float* __restrict__ loss) {
   float s = 0.f;
   for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {
-    const float d = y[(size_t)m * 16] - tgt[m];
+    const float d = y[m] - tgt[m];
     s += d * d;
     dy[(size_t)m * 16] = __float2bfloat16(2.f * d / M);
     for (int c = 1; c < 16; ++c) dy[(size_t)m * 16 + c] = __float2bfloat16(0.f);
@@ -325,15 +628,19 @@ __global__ void adam_kernel(float* __restrict__ p, float* __restrict__ g, float*
 }
 
 // kernel layouts from the FP32 master [tap][ci][co]: forward wk[tap][co][ci];
-// adjoint wb[tap][ci][co] = w[26 - tap][ci][co] read as a conv with Cin' = co, Cout' = ci
+// adjoint wb[tap][ci][co] = w[26 - tap][ci][co] read as a conv with Cin' = co, Cout' = ci;
+// the same two in the tensor-memory kernel's operand layout [tap][cin/8][cout][cin%8]:
+// wkt for the forward, wbt (Cin' = co, Cout' = ci) for the adjoint
 __global__ void pack_kernel(const float* __restrict__ w, int cin, int cout, bf16* __restrict__ wk,
-                            bf16* __restrict__ wb) {
+                            bf16* __restrict__ wb, bf16* __restrict__ wkt, bf16* __restrict__ wbt) {
   const int n = 27 * cin * cout;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
     const int co = t % cout, ci = (t / cout) % cin, tap = t / (cin * cout);
     const bf16 val = __float2bfloat16(w[t]);
     wk[((size_t)tap * cout + co) * cin + ci] = val;
     wb[((size_t)(26 - tap) * cin + ci) * cout + co] = val;
+    wkt[(((size_t)tap * (cin / 8) + ci / 8) * cout + co) * 8 + ci % 8] = val;
+    wbt[(((size_t)(26 - tap) * (cout / 8) + co / 8) * cin + ci) * 8 + co % 8] = val;
   }
 }
 
@@ -343,17 +650,111 @@ int grid1(long long n, int threads) {
   return (int)(b < 1 ? 1 : b);
 }
 
+// dynamic shared memory of a tensor-memory CTA (barriers, weights, two halo
+// buffers), padded so that the CTAs that fit on one SM never ask for more than
+// its 512 tensor-memory columns together
+size_t tc_smem(int cin, int cout, int zt) {
+  const size_t b = 128 + (size_t)27 * cin * cout * 2 + 2 * (size_t)(cin / 8) * kTcPlane * (zt + 2) * 16;
+  const int per_sm = 512 / tc_cols(2 * zt * cout);
+  const size_t floor_b = 233472 / (per_sm + 1) - 1024 + 16;
+  return std::max(b, floor_b);
+}
+
+int tc_tiles(NNGrid g, int zt) { return (g.W / kTcX) * (g.H / kTcY) * (g.D / zt); }
+
+int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n < 1) n = 1;
+  }
+  return n;
+}
+
+// z-planes per tile: the most of {4, 2} that divides D, fits the shared memory
+// and still gives every SM a tile, else 1
+int tc_zt(int cin, int cout, NNGrid g) {
+  for (int zt : {4, 2})
+    if (g.D % zt == 0 && tc_smem(cin, cout, zt) <= 232448 && tc_tiles(g, zt) >= sm_count()) return zt;
+  return 1;
+}
+
+template <int CIN, int COUT, bool UP = false>
+void launch_conv_tc(const bf16* in, const bf16* s1, const bf16* wt, const float* bias, NNGrid g, int relu,
+                    bf16* out_bf, float* out_f, int f_ch0, int* fault, cudaStream_t s) {
+  const int zt = tc_zt(CIN, COUT, g);
+  const size_t smem = tc_smem(CIN, COUT, zt);
+  const int per_sm = std::max(1, std::min(16, (int)(233472 / (smem + 1024))));
+  const int blocks = std::min(tc_tiles(g, zt), sm_count() * per_sm);
+  conv_tc_kernel<CIN, COUT, UP><<<blocks, kTcThreads, smem, s>>>(in, s1, wt, bias, g, zt, relu, out_bf, out_f,
+                                                                    f_ch0, fault);
+}
+
 }  // namespace
 
-void nn_conv_fwd(const bf16* in, int cin, const bf16* wk, const float* bias, int cout, NNGrid g,
-                 int relu, bf16* out_bf, float* out_f, cudaStream_t s) {
+// Shared-memory limits of the tensor-memory kernels, set once per process when
+// a network is created, so that no launch (possibly inside a stream capture)
+// has to configure its function first.
+cudaError_t nn_tc_setup() {
+  static cudaError_t done = [] {
+    const int lim = 232448;
+    const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = cudaSuccess;
+    auto set = [&](const void* f) {
+      const cudaError_t r = cudaFuncSetAttribute(f, a, lim);
+      if (e == cudaSuccess) e = r;
+    };
+    set((const void*)conv_tc_kernel<16, 16, false>);
+    set((const void*)conv_tc_kernel<16, 32, false>);
+    set((const void*)conv_tc_kernel<16, 48, false>);
+    set((const void*)conv_tc_kernel<32, 16, false>);
+    set((const void*)conv_tc_kernel<32, 32, false>);
+    set((const void*)conv_tc_kernel<48, 16, false>);
+    set((const void*)conv_tc_kernel<48, 16, true>);
+    return e;
+  }();
+  return done;
+}
+
+// The tensor-memory kernel takes grids whose x extent is a multiple of 8 and y
+// extent a multiple of 16; other grids use the mma.sync kernel.
+bool nn_conv_uses_tc(int cin, int cout, NNGrid g) {
+  if (g.W % kTcX || g.H % kTcY || g.D < 1) return false;
+  return (cin == 16 && (cout == 16 || cout == 32 || cout == 48)) || (cin == 32 && (cout == 16 || cout == 32)) ||
+         (cin == 48 && cout == 16);
+}
+
+bool nn_conv_fwd(const bf16* in, int cin, const bf16* wk, const bf16* wt, const float* bias, int cout,
+                 NNGrid g, int relu, bf16* out_bf, float* out_f, int f_ch0, int* fault, cudaStream_t s) {
+  if (wt && fault && nn_conv_uses_tc(cin, cout, g)) {
+    auto go = [&](auto launch) { launch(in, nullptr, wt, bias, g, relu, out_bf, out_f, f_ch0, fault, s); };
+    if (cin == 16 && cout == 16) go(launch_conv_tc<16, 16>);
+    else if (cin == 16 && cout == 32) go(launch_conv_tc<16, 32>);
+    else if (cin == 16 && cout == 48) go(launch_conv_tc<16, 48>);
+    else if (cin == 32 && cout == 16) go(launch_conv_tc<32, 16>);
+    else if (cin == 32 && cout == 32) go(launch_conv_tc<32, 32>);
+    else go(launch_conv_tc<48, 16>);
+    return true;
+  }
   const int M = g.D * g.H * g.W;
   const int tiles = (M + 15) / 16;
   const int blocks = (tiles + kConvTiles - 1) / kConvTiles;
   const dim3 block(32, kConvTiles, 3);
-  if (cout == 16) conv_fwd_kernel<16><<<blocks, block, 0, s>>>(in, cin, wk, bias, g, relu, out_bf, out_f);
-  else if (cout == 32) conv_fwd_kernel<32><<<blocks, block, 0, s>>>(in, cin, wk, bias, g, relu, out_bf, out_f);
-  else if (cout == 48) conv_fwd_kernel<48><<<blocks, block, 0, s>>>(in, cin, wk, bias, g, relu, out_bf, out_f);
+  if (cout == 16) conv_fwd_kernel<16><<<blocks, block, 0, s>>>(in, cin, wk, bias, g, relu, out_bf, out_f, f_ch0);
+  else if (cout == 32) conv_fwd_kernel<32><<<blocks, block, 0, s>>>(in, cin, wk, bias, g, relu, out_bf, out_f, f_ch0);
+  else if (cout == 48) conv_fwd_kernel<48><<<blocks, block, 0, s>>>(in, cin, wk, bias, g, relu, out_bf, out_f, f_ch0);
+  return false;
+}
+
+// conv(48 -> 16) of [up(a4), s1] on the tensor-memory kernel without forming the
+// concatenation; false (nothing launched) where the grid does not allow it
+bool nn_conv_upcat_tc(const bf16* a4, const bf16* s1, const bf16* wt, const float* bias, NNGrid g, int relu,
+                      bf16* out_bf, int* fault, cudaStream_t s) {
+  if (!wt || !fault || !nn_conv_uses_tc(48, 16, g)) return false;
+  launch_conv_tc<48, 16, true>(a4, s1, wt, bias, g, relu, out_bf, nullptr, 0, fault, s);
+  return true;
 }
 
 void nn_conv_wgrad(const bf16* in, int cin, const bf16* dout, int cout, NNGrid g, float* gw,
@@ -373,10 +774,10 @@ void nn_conv_wgrad(const bf16* in, int cin, const bf16* dout, int cout, NNGrid g
 }
 
 void nn_pool2(const bf16* in, NNGrid f, int C, bf16* out, cudaStream_t s) {
-  pool2_kernel<<<grid1((long long)f.D * f.H * f.W * C / 8, 256), 256, 0, s>>>(in, f, C, out);
+  pool2_kernel<<<grid1((long long)f.D * f.H * f.W * C / 64, 256), 256, 0, s>>>(in, f, C, out);
 }
 void nn_upcat(const bf16* a4, const bf16* s1, NNGrid f, bf16* cat, cudaStream_t s) {
-  upcat_kernel<<<grid1((long long)f.D * f.H * f.W * 48, 256), 256, 0, s>>>(a4, s1, f, cat);
+  upcat_kernel<<<grid1((long long)f.D * f.H * f.W * 6, 256), 256, 0, s>>>(a4, s1, f, cat);
 }
 void nn_mask(const float* d, const bf16* act, long long n, bf16* out, cudaStream_t s) {
   mask_kernel<<<grid1(n, 256), 256, 0, s>>>(d, act, n, out);
@@ -395,8 +796,8 @@ void nn_adam(float* p, float* g, float* m, float* v, int n, float lr, int step, 
   const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
   adam_kernel<<<grid1(n, 256), 256, 0, s>>>(p, g, m, v, n, lr, b1, b2, c1, c2, 1e-8f);
 }
-void nn_pack(const float* w, int cin, int cout, bf16* wk, bf16* wb, cudaStream_t s) {
-  pack_kernel<<<grid1(27 * cin * cout, 256), 256, 0, s>>>(w, cin, cout, wk, wb);
+void nn_pack(const float* w, int cin, int cout, bf16* wk, bf16* wb, bf16* wkt, bf16* wbt, cudaStream_t s) {
+  pack_kernel<<<grid1(27 * cin * cout, 256), 256, 0, s>>>(w, cin, cout, wk, wb, wkt, wbt);
 }
 
 }  // namespace fx
@@ -418,9 +819,6 @@ __global__ void f32_to_bf16_kernel(const float* __restrict__ in, long long n, bf
     out[t] = __float2bfloat16(in[t]);
 }
 
-__global__ void channel0_kernel(const float* __restrict__ y, int M, float* __restrict__ out) {
-  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) out[m] = y[(size_t)m * 16];
-}
 
 }  // namespace
 }  // namespace fx
@@ -441,6 +839,10 @@ struct ferrox_nn {
   float* vb[fx::kLayers] = {};
   bf16* wk[fx::kLayers] = {};
   bf16* wb[fx::kLayers] = {};
+  bf16* wkt[fx::kLayers] = {};   // tensor-memory operand layouts of wk and wb
+  bf16* wbt[fx::kLayers] = {};
+  int* fault = nullptr;          // set by a tensor-memory convolution whose wait ran out
+  bool tc = true;                // tensor-memory convolutions where the grid allows
   bf16 *x = nullptr, *a1 = nullptr, *s1 = nullptr, *p = nullptr, *a3 = nullptr, *a4 = nullptr,
        *cat = nullptr, *a5 = nullptr, *dy = nullptr, *t16a = nullptr, *t16b = nullptr,
        *t32a = nullptr, *t32b = nullptr, *tcoarse16 = nullptr;
@@ -483,21 +885,35 @@ cudaError_t nalloc(ferrox_nn* N, P** ptr, size_t bytes) {
 }
 
 void repack(ferrox_nn* N) {
-  for (int l = 0; l < fx::kLayers; ++l) fx::nn_pack(N->w[l], fx::kCin[l], fx::kCout[l], N->wk[l], N->wb[l], N->stream);
+  for (int l = 0; l < fx::kLayers; ++l)
+    fx::nn_pack(N->w[l], fx::kCin[l], fx::kCout[l], N->wk[l], N->wb[l], N->wkt[l], N->wbt[l], N->stream);
 }
 
-// forward pass from N->x; output (16 channels, FP32) in N->y
-void forward(ferrox_nn* N) {
+// one convolution of layer l: forward weights, or the adjoint's when adjoint is set
+void conv(ferrox_nn* N, int l, bool adjoint, const bf16* in, fx::NNGrid g, int relu, bf16* out_bf, float* out_f,
+          cudaStream_t s, int f_ch0 = 0) {
+  const int cin = adjoint ? fx::kCout[l] : fx::kCin[l], cout = adjoint ? fx::kCin[l] : fx::kCout[l];
+  fx::nn_conv_fwd(in, cin, adjoint ? N->wb[l] : N->wk[l], !N->tc ? nullptr : adjoint ? N->wbt[l] : N->wkt[l],
+                  adjoint ? nullptr : N->b[l], cout, g, relu, out_bf, out_f, f_ch0, N->fault, s);
+}
+
+// forward pass from N->x; output channel 0 (FP32) in N->y.  The concatenation
+// [up(a4), s1] is formed in memory only for a backward pass (keep_cat) or where
+// the tensor-memory kernel cannot read it in place.
+void forward(ferrox_nn* N, bool keep_cat) {
   cudaStream_t s = N->stream;
   using namespace fx;
-  nn_conv_fwd(N->x, 16, N->wk[0], N->b[0], 16, N->g, 1, N->a1, nullptr, s);
-  nn_conv_fwd(N->a1, 16, N->wk[1], N->b[1], 16, N->g, 1, N->s1, nullptr, s);
+  conv(N, 0, false, N->x, N->g, 1, N->a1, nullptr, s);
+  conv(N, 1, false, N->a1, N->g, 1, N->s1, nullptr, s);
   nn_pool2(N->s1, N->g, 16, N->p, s);
-  nn_conv_fwd(N->p, 16, N->wk[2], N->b[2], 32, N->gc, 1, N->a3, nullptr, s);
-  nn_conv_fwd(N->a3, 32, N->wk[3], N->b[3], 32, N->gc, 1, N->a4, nullptr, s);
-  nn_upcat(N->a4, N->s1, N->g, N->cat, s);
-  nn_conv_fwd(N->cat, 48, N->wk[4], N->b[4], 16, N->g, 1, N->a5, nullptr, s);
-  nn_conv_fwd(N->a5, 16, N->wk[5], N->b[5], 16, N->g, 0, nullptr, N->y, s);
+  conv(N, 2, false, N->p, N->gc, 1, N->a3, nullptr, s);
+  conv(N, 3, false, N->a3, N->gc, 1, N->a4, nullptr, s);
+  if (keep_cat || !N->tc ||
+      !nn_conv_upcat_tc(N->a4, N->s1, N->wkt[4], N->b[4], N->g, 1, N->a5, N->fault, s)) {
+    nn_upcat(N->a4, N->s1, N->g, N->cat, s);
+    conv(N, 4, false, N->cat, N->g, 1, N->a5, nullptr, s);
+  }
+  conv(N, 5, false, N->a5, N->g, 0, nullptr, N->y, s, 1);   // output channel 0 only
 }
 
 // backward pass from N->dy (gradient of the loss w.r.t. the output); accumulates gw, gb
@@ -506,19 +922,19 @@ void backward(ferrox_nn* N) {
   using namespace fx;
   const long long M = N->M, Mc = N->Mc;
   nn_conv_wgrad(N->a5, 16, N->dy, 16, N->g, N->gw[5], N->gb[5], s);
-  nn_conv_fwd(N->dy, 16, N->wb[5], nullptr, 16, N->g, 0, nullptr, N->df, s);
+  conv(N, 5, true, N->dy, N->g, 0, nullptr, N->df, s);
   nn_mask(N->df, N->a5, M * 16, N->t16a, s);                                  // da5
   nn_conv_wgrad(N->cat, 48, N->t16a, 16, N->g, N->gw[4], N->gb[4], s);
-  nn_conv_fwd(N->t16a, 16, N->wb[4], nullptr, 48, N->g, 0, nullptr, N->dcat, s);
+  conv(N, 4, true, N->t16a, N->g, 0, nullptr, N->dcat, s);
   nn_up_grad(N->dcat, N->a4, N->g, N->t32a, s);                               // da4
   nn_conv_wgrad(N->a3, 32, N->t32a, 32, N->gc, N->gw[3], N->gb[3], s);
-  nn_conv_fwd(N->t32a, 32, N->wb[3], nullptr, 32, N->gc, 0, nullptr, N->df, s);
+  conv(N, 3, true, N->t32a, N->gc, 0, nullptr, N->df, s);
   nn_mask(N->df, N->a3, Mc * 32, N->t32b, s);                                 // da3
   nn_conv_wgrad(N->p, 16, N->t32b, 32, N->gc, N->gw[2], N->gb[2], s);
-  nn_conv_fwd(N->t32b, 32, N->wb[2], nullptr, 16, N->gc, 0, nullptr, N->dpc, s); // dp
+  conv(N, 2, true, N->t32b, N->gc, 0, nullptr, N->dpc, s);                   // dp
   nn_skip_grad(N->dcat, N->dpc, N->s1, N->g, N->t16b, s);                     // ds1
   nn_conv_wgrad(N->a1, 16, N->t16b, 16, N->g, N->gw[1], N->gb[1], s);
-  nn_conv_fwd(N->t16b, 16, N->wb[1], nullptr, 16, N->g, 0, nullptr, N->df, s);
+  conv(N, 1, true, N->t16b, N->g, 0, nullptr, N->df, s);
   nn_mask(N->df, N->a1, M * 16, N->t16a, s);                                  // da1
   nn_conv_wgrad(N->x, 16, N->t16a, 16, N->g, N->gw[0], N->gb[0], s);
 }
@@ -539,7 +955,7 @@ const float* nn_output(ferrox_nn* N) { return N->y; }
 void nn_run_forward(ferrox_nn* N, cudaStream_t s) {
   cudaStream_t keep = N->stream;
   N->stream = s;
-  forward(N);
+  forward(N, false);
   N->stream = keep;
 }
 NNGrid nn_grid(const ferrox_nn* N) { return N->g; }
@@ -569,6 +985,10 @@ ferrox_status ferrox_nn_create(ferrox_nn** out, int D, int H, int W, int capacit
   N->Mc = N->M / 8;
   N->cap = capacity;
   N->stream = static_cast<cudaStream_t>(cuda_stream);
+  if (const cudaError_t te = fx::nn_tc_setup(); te != cudaSuccess) {
+    delete N;
+    return nfail(nullptr, FERROX_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(te));
+  }
   const size_t M = N->M, Mc = N->Mc;
   auto fail_alloc = [&](cudaError_t e) {
     const std::string m = std::string("cudaMalloc: ") + cudaGetErrorString(e);
@@ -585,6 +1005,8 @@ ferrox_status ferrox_nn_create(ferrox_nn** out, int D, int H, int W, int capacit
       if ((e = nalloc(N, p, nb * sizeof(float))) != cudaSuccess) return fail_alloc(e);
     if ((e = nalloc(N, &N->wk[l], nw * sizeof(bf16))) != cudaSuccess) return fail_alloc(e);
     if ((e = nalloc(N, &N->wb[l], nw * sizeof(bf16))) != cudaSuccess) return fail_alloc(e);
+    if ((e = nalloc(N, &N->wkt[l], nw * sizeof(bf16))) != cudaSuccess) return fail_alloc(e);
+    if ((e = nalloc(N, &N->wbt[l], nw * sizeof(bf16))) != cudaSuccess) return fail_alloc(e);
     cudaMemcpy(N->w[l], weights + woff, nw * sizeof(float), cudaMemcpyHostToDevice);
     cudaMemcpy(N->b[l], biases + boff, nb * sizeof(float), cudaMemcpyHostToDevice);
     woff += nw;
@@ -597,10 +1019,11 @@ ferrox_status ferrox_nn_create(ferrox_nn** out, int D, int H, int W, int capacit
       {&N->tcoarse16, Mc * 16}};
   for (auto& bq : bufs)
     if ((e = nalloc(N, bq.p, bq.n * sizeof(bf16))) != cudaSuccess) return fail_alloc(e);
-  struct { float** p; size_t n; } fbufs[] = {{&N->y, M * 16}, {&N->df, M * 48}, {&N->dcat, M * 48},
+  struct { float** p; size_t n; } fbufs[] = {{&N->y, M}, {&N->df, M * 48}, {&N->dcat, M * 48},
                                               {&N->dpc, Mc * 16}, {&N->loss, 4}};
   for (auto& bq : fbufs)
     if ((e = nalloc(N, bq.p, bq.n * sizeof(float))) != cudaSuccess) return fail_alloc(e);
+  if ((e = nalloc(N, &N->fault, sizeof(int))) != cudaSuccess) return fail_alloc(e);
   if (capacity > 0) {
     if ((e = nalloc(N, &N->snap_x, (size_t)capacity * M * 16 * sizeof(bf16))) != cudaSuccess) return fail_alloc(e);
     if ((e = nalloc(N, &N->snap_t, (size_t)capacity * M * sizeof(float))) != cudaSuccess) return fail_alloc(e);
@@ -617,8 +1040,8 @@ ferrox_status ferrox_nn_create(ferrox_nn** out, int D, int H, int W, int capacit
 ferrox_status ferrox_nn_forward(ferrox_nn* N, const float* x_dev, float* y_dev) {
   if (!N || !x_dev || !y_dev) return nfail(N, FERROX_EINVAL, "null argument");
   fx::f32_to_bf16_kernel<<<fx::grid1((long long)N->M * 16, 256), 256, 0, N->stream>>>(x_dev, (long long)N->M * 16, N->x);
-  forward(N);
-  fx::channel0_kernel<<<fx::grid1(N->M, 256), 256, 0, N->stream>>>(N->y, N->M, y_dev);
+  forward(N, false);
+  FX_NCK(cudaMemcpyAsync(y_dev, N->y, (size_t)N->M * sizeof(float), cudaMemcpyDeviceToDevice, N->stream));
   FX_NCK(cudaGetLastError());
   return FERROX_OK;
 }
@@ -628,7 +1051,7 @@ ferrox_status ferrox_nn_loss_grad(ferrox_nn* N, const float* x_dev, const float*
   if (!N || !x_dev || !t_dev) return nfail(N, FERROX_EINVAL, "null argument");
   fx::f32_to_bf16_kernel<<<fx::grid1((long long)N->M * 16, 256), 256, 0, N->stream>>>(x_dev, (long long)N->M * 16, N->x);
   FX_NCK(cudaMemsetAsync(N->loss, 0, sizeof(float), N->stream));
-  forward(N);
+  forward(N, true);
   fx::nn_mse(N->y, t_dev, N->M, N->dy, N->loss, N->stream);
   backward(N);
   FX_NCK(cudaGetLastError());
@@ -695,20 +1118,38 @@ ferrox_status ferrox_nn_train(ferrox_nn* N, int epochs, double lr, int batch, fl
   if (!N || epochs < 0 || batch < 1 || !(lr > 0.0)) return nfail(N, FERROX_EINVAL, "bad argument");
   if (N->count < 1) return nfail(N, FERROX_ESTATE, "no snapshots collected");
   const size_t M = N->M;
+  // a fresh order of the snapshots every epoch (Fisher-Yates with a splitmix64
+  // stream of fixed seed, so runs repeat), and a cosine decay of the step size
+  // from lr to lr / 10 over all Adam steps of the call
+  std::vector<int> order(N->count);
+  for (int q = 0; q < N->count; ++q) order[q] = q;
+  unsigned long long state = 0x2545F4914F6CDD1Dull;
+  auto next = [&state]() {
+    unsigned long long z = (state += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  };
+  const long long per_epoch = (N->count + batch - 1) / batch, total = std::max(1LL, per_epoch * epochs);
+  long long k = 0;
   for (int ep = 0; ep < epochs; ++ep) {
+    for (int q = N->count - 1; q > 0; --q) std::swap(order[q], order[(int)(next() % (unsigned long long)(q + 1))]);
     FX_NCK(cudaMemsetAsync(N->loss, 0, sizeof(float), N->stream));
-    for (int q = 0; q < N->count; ++q) {
+    for (int j = 0; j < N->count; ++j) {
+      const int q = order[j];
       FX_NCK(cudaMemcpyAsync(N->x, N->snap_x + (size_t)q * M * 16, M * 16 * sizeof(bf16),
                              cudaMemcpyDeviceToDevice, N->stream));
-      forward(N);
+      forward(N, true);
       fx::nn_mse(N->y, N->snap_t + (size_t)q * M, N->M, N->dy, N->loss, N->stream);
       backward(N);
-      if ((q + 1) % batch == 0 || q + 1 == N->count) {
+      if ((j + 1) % batch == 0 || j + 1 == N->count) {
+        const double lr_k = lr * (0.1 + 0.45 * (1.0 + std::cos(3.141592653589793 * (double)k / (double)total)));
+        ++k;
         N->adam_step += 1;
         for (int l = 0; l < fx::kLayers; ++l) {
           const int nw = 27 * fx::kCin[l] * fx::kCout[l], nb = fx::kCout[l];
-          fx::nn_adam(N->w[l], N->gw[l], N->mw[l], N->vw[l], nw, (float)lr, N->adam_step, N->stream);
-          fx::nn_adam(N->b[l], N->gb[l], N->mb[l], N->vb[l], nb, (float)lr, N->adam_step, N->stream);
+          fx::nn_adam(N->w[l], N->gw[l], N->mw[l], N->vw[l], nw, (float)lr_k, N->adam_step, N->stream);
+          fx::nn_adam(N->b[l], N->gb[l], N->mb[l], N->vb[l], nb, (float)lr_k, N->adam_step, N->stream);
         }
         repack(N);
       }
@@ -728,6 +1169,31 @@ ferrox_status ferrox_nn_destroy(ferrox_nn* N) {
 }
 
 const char* ferrox_nn_last_error(const ferrox_nn* N) { return N ? N->err.c_str() : g_nn_error.c_str(); }
+
+ferrox_status ferrox_nn_use_tensor_memory(ferrox_nn* N, int on) {
+  if (!N || (on != 0 && on != 1)) return nfail(N, FERROX_EINVAL, "use_tensor_memory must be 0 or 1");
+  N->tc = on != 0;
+  return FERROX_OK;
+}
+
+ferrox_status ferrox_nn_kernel_info(ferrox_nn* N, int* tc_forward, int* tc_backward, int* fault) {
+  if (!N) return nfail(nullptr, FERROX_EINVAL, "null network");
+  int f = 0, b = 0;
+  if (N->tc) {
+    for (int l = 0; l < fx::kLayers; ++l) {
+      const fx::NNGrid g = (l == 2 || l == 3) ? N->gc : N->g;
+      f += fx::nn_conv_uses_tc(fx::kCin[l], fx::kCout[l], g);
+      if (l > 0) b += fx::nn_conv_uses_tc(fx::kCout[l], fx::kCin[l], g);
+    }
+  }
+  if (tc_forward) *tc_forward = f;
+  if (tc_backward) *tc_backward = b;
+  if (fault) {
+    FX_NCK(cudaStreamSynchronize(N->stream));
+    FX_NCK(cudaMemcpy(fault, N->fault, sizeof(int), cudaMemcpyDeviceToHost));
+  }
+  return FERROX_OK;
+}
 
 }  // extern "C"
 
@@ -798,7 +1264,7 @@ __global__ void apply_kernel(const float* __restrict__ y, LevelDesc L, const dou
                              T* __restrict__ e) {
   const double s = *scale;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < L.ncell; t += (long long)gridDim.x * blockDim.x)
-    e[L.off + t] = (T)(s * (double)y[t * 16]);
+    e[L.off + t] = (T)(s * (double)y[t]);
 }
 
 // e0 = phi - phi_guess (fine level), the error the initial guess had

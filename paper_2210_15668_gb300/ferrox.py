@@ -70,7 +70,8 @@ EXPORTS = ["ferrox_init_geometry", "ferrox_set_bias", "ferrox_solve_poisson", "f
            "ferrox_carrier_exp",
            "ferrox_nn_create", "ferrox_nn_forward", "ferrox_nn_loss_grad", "ferrox_nn_params",
            "ferrox_nn_set_params", "ferrox_nn_adam_step", "ferrox_nn_snapshot_count", "ferrox_nn_train",
-           "ferrox_nn_destroy", "ferrox_nn_last_error", "ferrox_attach_nn"]
+           "ferrox_nn_destroy", "ferrox_nn_last_error", "ferrox_nn_use_tensor_memory", "ferrox_nn_kernel_info",
+           "ferrox_attach_nn"]
 
 KERNEL_CLASSES = ["tdgl", "resid", "smooth_fine", "smooth_coarse", "restrict", "prolong", "tail",
                   "update", "copy"]
@@ -495,9 +496,13 @@ class NN:
             lib.ferrox_nn_destroy.argtypes = [vp]
             lib.ferrox_nn_last_error.argtypes = [vp]
             lib.ferrox_nn_last_error.restype = C.c_char_p
+            ip = C.POINTER(C.c_int)
+            lib.ferrox_nn_use_tensor_memory.argtypes = [vp, C.c_int]
+            lib.ferrox_nn_kernel_info.argtypes = [vp, ip, ip, ip]
             for n in ("ferrox_nn_create", "ferrox_nn_forward", "ferrox_nn_loss_grad", "ferrox_nn_params",
                       "ferrox_nn_set_params", "ferrox_nn_adam_step", "ferrox_nn_snapshot_count",
-                      "ferrox_nn_train", "ferrox_nn_destroy"):
+                      "ferrox_nn_train", "ferrox_nn_destroy", "ferrox_nn_use_tensor_memory",
+                      "ferrox_nn_kernel_info"):
                 getattr(lib, n).restype = C.c_int
             lib._nn_declared = True
         self.shape = (D, H, W)
@@ -544,6 +549,17 @@ class NN:
         wf = np.concatenate([np.asarray(w, np.float32).ravel() for w in ws])
         bf = np.concatenate([np.asarray(b, np.float32).ravel() for b in bs])
         self._ck(self.lib.ferrox_nn_set_params(self.ctx, wf.ctypes.data_as(fp), bf.ctypes.data_as(fp)))
+
+    def use_tensor_memory(self, on=True):
+        """Run the convolutions on the tcgen05 kernel where the grid allows (default), or
+        all of them on the mma.sync kernel."""
+        self._ck(self.lib.ferrox_nn_use_tensor_memory(self.ctx, 1 if on else 0))
+
+    def kernel_info(self):
+        """Number of forward / adjoint convolutions on the tcgen05 kernel, and its fault flag."""
+        f, b, flt = C.c_int(), C.c_int(), C.c_int()
+        self._ck(self.lib.ferrox_nn_kernel_info(self.ctx, C.byref(f), C.byref(b), C.byref(flt)))
+        return {"tc_forward": f.value, "tc_backward": b.value, "fault": flt.value}
 
     def adam_step(self, lr):
         self._ck(self.lib.ferrox_nn_adam_step(self.ctx, float(lr)))

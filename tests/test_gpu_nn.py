@@ -133,3 +133,78 @@ def test_adam_training_lowers_the_loss():
         net.adam_step(1e-3)
     assert last < 0.5 * first, (first, last)
     net.close()
+
+
+def forward_bf16_storage(params, x):
+    """The oracle's forward with BF16 rounding wherever the GPU stores BF16 activations."""
+    r = bf16_round
+    relu = lambda a: np.maximum(a, 0.0)  # noqa: E731
+    a1 = r(relu(onn.conv3d(x, *params[0])))
+    s1 = r(relu(onn.conv3d(a1, *params[1])))
+    p = r(onn.pool2(s1))
+    a3 = r(relu(onn.conv3d(p, *params[2])))
+    a4 = r(relu(onn.conv3d(a3, *params[3])))
+    cat = np.concatenate([onn.up2(a4), s1], axis=3)
+    a5 = r(relu(onn.conv3d(cat, *params[4])))
+    return onn.conv3d(a5, *params[5])[..., 0]
+
+
+# (grid, convolutions of the forward pass on the tcgen05 kernel): the fine grid
+# needs x % 8 == 0 and y % 16 == 0, the pooled grid the same; (16, 128, 128) runs
+# four z-planes per CTA on the fine grid, (6, 32, 16) an odd pooled depth
+TC_SHAPES = [((4, 32, 16), 6), ((6, 32, 16), 6), ((4, 16, 8), 4), ((16, 128, 128), 6)]
+
+
+@pytest.mark.parametrize("shape,n_tc", TC_SHAPES, ids=[f"{s[0]}x{s[1]}x{s[2]}" for s, _ in TC_SHAPES])
+def test_tensor_memory_forward_matches_oracle(shape, n_tc):
+    """tcgen05 convolutions (FP32 accumulators in tensor memory) against the oracle with
+    the GPU's BF16 storage emulated: the remaining differences are FP32 summation
+    order and the BF16 roundings it flips (bound 5e-3 normwise); against the plain FP64
+    oracle 2e-2 as for the mma.sync kernel.  The mma.sync kernel on the same network and
+    input agrees to 5e-3."""
+    net, x, params = make(1, *shape)
+    info = net.kernel_info()
+    assert info["tc_forward"] == n_tc and info["fault"] == 0, info
+    xt = torch.as_tensor(x.reshape(-1, 16), dtype=torch.float32, device="cuda")
+    y = net.forward(xt).cpu().numpy().reshape(shape)
+    assert net.kernel_info()["fault"] == 0
+    y_bf = forward_bf16_storage(params, x)
+    y_or, _ = onn.forward(params, x)
+    net.use_tensor_memory(False)
+    assert net.kernel_info()["tc_forward"] == 0
+    y_ms = net.forward(xt).cpu().numpy().reshape(shape)
+    print(f"{shape}: rel err vs BF16-storage oracle {rel(y, y_bf):.2e}, vs FP64 oracle {rel(y, y_or):.2e}, "
+          f"vs mma.sync {rel(y, y_ms):.2e}")
+    assert rel(y, y_bf) <= 5e-3
+    assert rel(y, y_or) <= 2e-2
+    assert rel(y, y_ms) <= 5e-3
+    net.close()
+
+
+def test_tensor_memory_gradients_match_oracle():
+    """Backward pass with the adjoint convolutions on the tcgen05 kernel (all five at
+    4x32x16) against the oracle with BF16 storage emulated, as for the mma.sync path."""
+    net, x, params = make(2, 4, 32, 16)
+    assert net.kernel_info()["tc_backward"] == 5
+    t = np.random.default_rng(3).standard_normal((4, 32, 16))
+    loss_or, g_or = forward_backward_bf16_storage(params, x, t)
+    xt = torch.as_tensor(x.reshape(-1, 16), dtype=torch.float32, device="cuda")
+    tt = torch.as_tensor(t.ravel(), dtype=torch.float32, device="cuda")
+    loss = net.loss_grad(xt, tt)
+    _, _, gw, gb = net.params()
+    assert net.kernel_info()["fault"] == 0
+    assert abs(loss - loss_or) <= 2e-2 * loss_or
+    for layer in range(6):
+        e_w = rel(gw[layer], g_or[layer][0].reshape(27, *g_or[layer][0].shape[3:]))
+        e_b = rel(gb[layer], g_or[layer][1])
+        print(f"layer {layer}: grad rel err w {e_w:.2e} b {e_b:.2e}")
+        assert e_w <= 2e-2 and e_b <= 2e-2, (layer, e_w, e_b)
+    net.close()
+
+
+def test_use_tensor_memory_rejects_other_values():
+    from paper_2210_15668_gb300 import ferrox
+    net, _, _ = make(1, 4, 16, 8)
+    with pytest.raises(ferrox.FerroxError, match="EINVAL"):
+        net._ck(net.lib.ferrox_nn_use_tensor_memory(net.ctx, 2))
+    net.close()
