@@ -87,6 +87,7 @@ struct ferrox_ctx {
   PlaneCoefDF* coef_df = nullptr;     // level 0 as double-float pairs (double-float residual)
   bool df_resid = false;              // the mixed form's outer residual in double-float
   PlaneTDGL* planes_d = nullptr;
+  PlaneF32* planes_f32_d = nullptr;   // FP32 TDGL arithmetic only
   LevelDesc* lv_d = nullptr;
   LevelDesc* lvt_d = nullptr;
   DevParams* params_d = nullptr;
@@ -729,6 +730,28 @@ void enqueue_update(ferrox_ctx* c, cudaStream_t s) {
                    adapt_max(c) > 0 ? e : nullptr);
 }
 
+// The FP32 TDGL coefficients of each plane (see PlaneF32): the force's
+// coefficients rounded to FP32, d2z rewritten on differences, and the right-hand
+// side b = -(Pf(k + 1/2) - Pf(k - 1/2)) h/eps0 folded into weights of P_{k-1},
+// P_k, P_{k+1} (the face value is P_k on an electrode face).
+std::vector<PlaneF32> planes_f32(const std::vector<PlaneTDGL>& pl, double b_scale) {
+  const int nz = (int)pl.size();
+  std::vector<PlaneF32> out(nz);
+  for (int k = 0; k < nz; ++k) {
+    const PlaneTDGL& p = pl[k];
+    PlaneF32& q = out[k];
+    q.fe = p.fe;
+    q.alpha = (float)p.alpha; q.beta = (float)p.beta; q.gamma = (float)p.gamma;
+    q.g11 = (float)p.g11; q.g44 = (float)p.g44; q.Gamma = (float)p.Gamma;
+    q.wz_dn = (float)p.wz_dn; q.wz_up = (float)p.wz_up; q.wz_sum = (float)(p.wz_dn + p.wz_c + p.wz_up);
+    q.fw_L = (float)p.fw_L; q.fw_R = (float)p.fw_R; q.fpc = (float)p.fpc;
+    q.c_dn = k == 0 ? 0.0 : b_scale * p.fw_R;
+    q.c_0 = b_scale * ((k == 0 ? 1.0 : p.fw_L) - (k == nz - 1 ? 1.0 : pl[k + 1].fw_R));
+    q.c_up = k == nz - 1 ? 0.0 : -b_scale * pl[k + 1].fw_L;
+  }
+  return out;
+}
+
 TDGLArgs tdgl_args(ferrox_ctx* c, int mode) {
   TDGLArgs a{};
   a.phi = c->phi; a.b = c->b; a.planes = c->planes_d; a.params = c->params_d;
@@ -740,6 +763,8 @@ TDGLArgs tdgl_args(ferrox_ctx* c, int mode) {
   a.F_store = c->Fbuf;
   if (mode == 0 || mode == 1 || mode == 3) { a.P_in = c->P; a.P_out = c->Pbuf; a.P_base = nullptr; }
   else { a.P_in = c->Pbuf; a.P_out = c->P; a.P_base = c->P; }
+  a.planes_f32 = c->planes_f32_d;
+  a.dtf = (float)a.dt; a.inv_hf = (float)a.inv_h; a.inv_h2f = (float)a.inv_h2;
   return a;
 }
 
@@ -1144,7 +1169,7 @@ void release(ferrox_ctx* c) {
   for (auto g : ge) if (g) cudaGraphExecDestroy(g);
   for (auto g : gr) if (g) cudaGraphDestroy(g);
   void* ptrs[] = {c->b, c->Pbuf, c->Fbuf, c->phi_prev, c->e_arena, c->e_alt, c->r_arena, c->s_arena, c->coef, c->coef0, c->coef_df,
-                  c->planes_d, c->lv_d, c->lvt_d, c->nn_scale, c->phi_guess, c->nn_pf, c->nn_stats, c->params_d, c->stats_d, c->partials_d, c->charge_d,
+                  c->planes_d, c->planes_f32_d, c->lv_d, c->lvt_d, c->nn_scale, c->phi_guess, c->nn_pf, c->nn_stats, c->params_d, c->stats_d, c->partials_d, c->charge_d,
                   c->charge_part_d, c->dense_d, c->dense_wide_d};
   for (void* p : ptrs) if (p) cudaFree(p);
   if (c->host_pinned) cudaFreeHost(c->host_pinned);
@@ -1199,6 +1224,10 @@ ferrox_status validate(const ferrox_geometry* g, const ferrox_numerics* n, const
   if (n->bottom_sweeps < 0) return bad("bottom_sweeps must be >= 0");
   if (n->inner < -16 || n->inner > 16) return bad("inner must be in -16..16");
   if (n->guess != 0 && n->guess != 1) return bad("guess must be 0 or 1");
+  if (n->tdgl_arith != FERROX_TDGL_FP64 && n->tdgl_arith != FERROX_TDGL_FP32)
+    return bad("tdgl_arith must be FERROX_TDGL_FP64 or FERROX_TDGL_FP32");
+  if (n->tdgl_arith == FERROX_TDGL_FP32 && (n->precision != FERROX_MIXED || g->ncomp != 1))
+    return bad("FP32 TDGL arithmetic needs the mixed precision and one polarization component");
   return FERROX_OK;
 }
 
@@ -1356,6 +1385,11 @@ ferrox_status ferrox_init_geometry(ferrox_ctx** out, const ferrox_geometry* geom
   }
   FX_INIT_CK(cudaMemcpy(ctx->planes_d, ctx->planes.data(), ctx->nz * sizeof(PlaneTDGL),
                         cudaMemcpyHostToDevice));
+  if (ctx->num.tdgl_arith == FERROX_TDGL_FP32) {
+    const std::vector<PlaneF32> pf = planes_f32(ctx->planes, ctx->h / kEps0);
+    FX_INIT_CK(cudaMalloc(&ctx->planes_f32_d, pf.size() * sizeof(PlaneF32)));
+    FX_INIT_CK(cudaMemcpy(ctx->planes_f32_d, pf.data(), pf.size() * sizeof(PlaneF32), cudaMemcpyHostToDevice));
+  }
   FX_INIT_CK(cudaMemcpy(ctx->lv_d, ctx->lv.data(), ctx->lv.size() * sizeof(LevelDesc),
                         cudaMemcpyHostToDevice));
   FX_INIT_CK(cudaMemset(ctx->b, 0, N * sizeof(double)));
@@ -2023,6 +2057,8 @@ ferrox_status ferrox_init_batch(ferrox_batch** out, int n, const ferrox_geometry
   if (num->order != 1) return bfail(nullptr, FERROX_EINVAL, "the batched engine runs order-1 steps");
   if (num->nonlinear != FERROX_NEWTON)
     return bfail(nullptr, FERROX_EINVAL, "the batched engine iterates the carrier charge by Newton");
+  if (num->tdgl_arith != FERROX_TDGL_FP64)
+    return bfail(nullptr, FERROX_EINVAL, "the batched engine evaluates the TDGL force in FP64");
   if (num->inner > 1 || num->inner < 0)
     return bfail(nullptr, FERROX_EINVAL, "the batched engine runs one V-cycle per outer iteration");
   ferrox_batch* B = new ferrox_batch();

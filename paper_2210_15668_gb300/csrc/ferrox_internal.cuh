@@ -257,6 +257,17 @@ void launch_update(double* phi, const T* e0, long long n, const DevStats* stats,
 void launch_inner_arm(const DevStats* st, unsigned long long handle, cudaStream_t s);
 void launch_inner_countdown(DevStats* st, unsigned long long handle, cudaStream_t s);
 
+// Per-plane coefficients of the FP32-arithmetic TDGL update (mixed form): the
+// force's coefficients as floats, and the right-hand side folded into three FP64
+// weights of the new P below, at and above the plane.
+struct PlaneF32 {
+  int fe, pad;
+  float alpha, beta, gamma, g11, g44, Gamma;
+  float wz_dn, wz_up, wz_sum;   // d2z = wz_dn (P_dn - P) + wz_up (P_up - P) + wz_sum P
+  float fw_L, fw_R, fpc;        // lower face (k - 1/2), as in PlaneTDGL
+  double c_dn, c_0, c_up;       // b = c_dn P_{k-1} + c_0 P_k + c_up P_{k+1} (+ electrode lift)
+};
+
 struct TDGLArgs {
   const double* P_in;     // [ncomp][nz][ny][nx]
   double* P_out;          // new P (FE planes written)
@@ -271,6 +282,8 @@ struct TDGLArgs {
   double dt, inv_h, inv_h2, b_scale;  // b_scale = h0/eps0
   int mode;               // 0: order-1 update, 1: order-2 predictor, 2: order-2 corrector,
                           // 3: right-hand side of the current P only
+  const PlaneF32* planes_f32;   // non-null: force in FP32 arithmetic (one component only)
+  float dtf, inv_hf, inv_h2f;
 };
 void launch_tdgl(const TDGLArgs& a, cudaStream_t s);
 // a single-thread kernel that spins for `cycles` SM clock cycles (bounded)

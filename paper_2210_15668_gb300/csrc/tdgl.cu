@@ -16,6 +16,7 @@
 // interpolation across material interfaces, electrode value on electrode faces).
 #include <cuda_runtime.h>
 
+#include "df_arith.cuh"
 #include "ferrox_internal.cuh"
 #include "tdgl_device.cuh"
 
@@ -32,6 +33,164 @@ __global__ void __launch_bounds__(kBX* kBY) tdgl_kernel(TDGLArgs a) {
   const int j = blockIdx.y * kBY + threadIdx.y;
   if (i >= a.nx || j >= a.ny) return;
   tdgl_column(a, i, j);
+}
+
+// ---- column-chunked update (one component) ---------------------------------------------
+//
+// Four threads share an (x, y) column, each marching its own chunk of the dynamic
+// planes, so the grid has four times the threads of the one-thread-per-column
+// kernel (whose registers and 256 CTAs capped occupancy).  The right-hand side of
+// a plane needs the new P of the planes below and above it: inside a chunk the
+// march has them in registers; for a chunk's first and last planes the neighbour
+// chunk's edge value comes through shared memory after one barrier, so no plane
+// is computed twice.
+//
+// F32: the force is evaluated in FP32 arithmetic (mixed form).  Every difference
+// of state values (Laplacian, d2/dz2, face potentials) is formed from the
+// double-float splits of the FP64 values before rounding to FP32, so it carries
+// FP32 relative accuracy of the difference itself rather than of the values; the
+// FP64 state is advanced by one FP64 addition, and the right-hand side by three
+// FP64 multiply-adds on per-plane weights.  Conversions between the two formats
+// use integer operations (the conversion instructions run on the FP64 pipe).
+constexpr int kCX = 32, kCY = 2, kCZ = 4;
+
+__device__ __forceinline__ float df_diff(df a, df b) { return (a.h - b.h) + (a.l - b.l); }
+
+// a float as an FP64 value (exact for normal floats; FP32 subnormals, below
+// 2^-126, become signed zero)
+__device__ __forceinline__ double f64_of_float(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned sign = u & 0x80000000u, e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+  unsigned hi;
+  if (e == 0u) hi = sign;
+  else if (e == 255u) hi = sign | 0x7ff00000u | (m >> 3);
+  else hi = sign | ((e + 896u) << 20) | (m >> 3);
+  const unsigned lo = e == 0u ? 0u : (m & 7u) << 29;
+  return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
+}
+
+// z-component force of plane k (FP32 arithmetic on double-float differences)
+__device__ __forceinline__ float force_z_f32(const TDGLArgs& a, const PlaneF32& q, const PlaneF32* qs,
+                                             const double* Pz, const double* phi, long long t, int k,
+                                             int i, int j, int im, int ip, int jm, int jp, df vb, df vt) {
+  const long long plane = (long long)a.nx * a.ny;
+  const df P = df_from_double(Pz[t]);
+  const float lat = (df_diff(df_from_double(Pz[t - i + im]), P) + df_diff(df_from_double(Pz[t - i + ip]), P)) +
+                    (df_diff(df_from_double(Pz[t + (long long)(jm - j) * a.nx]), P) +
+                     df_diff(df_from_double(Pz[t + (long long)(jp - j) * a.nx]), P));
+  const bool fe_dn = k > 0 && __ldg(&qs[k - 1].fe);
+  const bool fe_up = k < a.nz - 1 && __ldg(&qs[k + 1].fe);
+  const df Pdn = fe_dn ? df_from_double(Pz[t - plane]) : df{0.f, 0.f};
+  const df Pup = fe_up ? df_from_double(Pz[t + plane]) : df{0.f, 0.f};
+  const float dPdn = df_diff(P, Pdn), dPup = df_diff(Pup, P);
+  const df ph = df_from_double(phi[t]);
+  // Phi_f(k + 1/2) - Phi_f(k - 1/2) as (upper face - phi_k) + (phi_k - lower face);
+  // the face interpolation weights sum to one, so phi_k cancels exactly
+  float up, dn;
+  if (k == a.nz - 1) {
+    up = df_diff(vt, ph);
+  } else {
+    const float fwR = __ldg(&qs[k + 1].fw_R), fpc = __ldg(&qs[k + 1].fpc);
+    up = fwR * df_diff(df_from_double(phi[t + plane]), ph) - fpc * dPup;
+  }
+  if (k == 0) dn = df_diff(ph, vb);
+  else dn = q.fw_L * df_diff(ph, df_from_double(phi[t - plane])) + q.fpc * dPdn;
+  const float p = P.h, p2 = p * p;
+  float dF = p * fmaf(p2, fmaf(q.gamma, p2, q.beta), q.alpha);
+  dF = fmaf(-q.g44, lat * a.inv_h2f, dF);
+  dF = fmaf(-q.g11, fmaf(q.wz_dn, -dPdn, fmaf(q.wz_up, dPup, q.wz_sum * p)), dF);
+  dF = fmaf(up + dn, a.inv_hf, dF);
+  return -q.Gamma * dF;
+}
+
+__device__ __forceinline__ double advance_f32(const TDGLArgs& a, long long idx, float f) {
+  if (a.mode == 0) return a.P_in[idx] + f64_of_float(a.dtf * f);
+  if (a.mode == 1) {
+    a.F_store[idx] = f64_of_float(f);
+    return a.P_in[idx] + f64_of_float(a.dtf * f);
+  }
+  const float F0 = df_from_double(a.F_store[idx]).h;   // exact: stored from a float
+  return a.P_base[idx] + f64_of_float(0.5f * a.dtf * (F0 + f));
+}
+
+template <bool F32>
+__device__ __forceinline__ double rhs_of(const TDGLArgs& a, int k, double pdn, double pn, double pup,
+                                         double v_bot, double v_top) {
+  if constexpr (F32) {
+    const PlaneF32* q = a.planes_f32 + k;
+    double b = fma(__ldg(&q->c_dn), pdn, fma(__ldg(&q->c_0), pn, __ldg(&q->c_up) * pup));
+    if (k == 0) b = fma(__ldg(&a.planes[0].lift), v_bot, b);
+    if (k == a.nz - 1) b = fma(__ldg(&a.planes[a.nz - 1].lift), v_top, b);
+    return b;
+  } else {
+    return rhs_value(a, a.planes, k, pdn, pn, pup, v_bot, v_top);
+  }
+}
+
+template <bool F32>
+__global__ void __launch_bounds__(kCX* kCY* kCZ) tdgl_chunk_kernel(TDGLArgs a) {
+  pdl_enter();
+  __shared__ double first_s[kCZ][kCY][kCX], last_s[kCZ][kCY][kCX];
+  const int tx = threadIdx.x, ty = threadIdx.y, c = threadIdx.z;
+  const int i = blockIdx.x * kCX + tx, j = blockIdx.y * kCY + ty;
+  const bool col = i < a.nx && j < a.ny;
+  const int per = (a.kd_hi - a.kd_lo + 1 + kCZ - 1) / kCZ;
+  const int k0 = a.kd_lo + c * per, k1 = min(a.kd_hi, k0 + per - 1);   // empty when k0 > k1
+  const long long plane = (long long)a.nx * a.ny;
+  const long long cix = (long long)j * a.nx + i;
+  const double v_bot = a.params->v_bot, v_top = a.params->v_top;
+  // new P of planes k1 - 1 and k1 (after the march), and of k0 and k0 + 1
+  double pm2 = 0.0, pm1 = 0.0, p_first = 0.0, p_second = 0.0;
+  if (col && k0 <= k1) {
+    const int im = (i == 0) ? a.nx - 1 : i - 1, ip = (i == a.nx - 1) ? 0 : i + 1;
+    const int jm = (j == 0) ? a.ny - 1 : j - 1, jp = (j == a.ny - 1) ? 0 : j + 1;
+    const double* Pz = a.P_in;
+    df vb{0.f, 0.f}, vt{0.f, 0.f};
+    if constexpr (F32) {
+      vb = df_from_double(v_bot);
+      vt = df_from_double(v_top);
+    }
+    for (int k = k0; k <= k1; ++k) {
+      const long long t = k * plane + cix;
+      double pn = 0.0;
+      bool fe;
+      if constexpr (F32) fe = __ldg(&a.planes_f32[k].fe);
+      else fe = __ldg(&a.planes[k].fe);
+      if (fe) {
+        if (a.mode == 3) {
+          pn = Pz[t];
+        } else if constexpr (F32) {
+          const PlaneF32 q = ldg_struct(a.planes_f32 + k);
+          const float f = force_z_f32(a, q, a.planes_f32, Pz, a.phi, t, k, i, j, im, ip, jm, jp, vb, vt);
+          pn = advance_f32(a, t, f);
+          a.P_out[t] = pn;
+        } else {
+          const PlaneTDGL pt = ldg_struct(a.planes + k);
+          const double f = force_z(a, pt, a.planes, Pz, a.phi, t, k, i, j, im, ip, jm, jp, v_bot, v_top);
+          pn = advance(a, t, f);
+          a.P_out[t] = pn;
+        }
+      }
+      if (k == k0) p_first = pn;
+      if (k == k0 + 1) p_second = pn;
+      if (k >= k0 + 2) a.b[(k - 1) * plane + cix] = rhs_of<F32>(a, k - 1, pm2, pm1, pn, v_bot, v_top);
+      pm2 = pm1;
+      pm1 = pn;
+    }
+    first_s[c][ty][tx] = p_first;
+    last_s[c][ty][tx] = pm1;
+  }
+  __syncthreads();
+  if (!col || k0 > k1) return;
+  // the chunk's first and last planes, with the neighbour chunks' edge values
+  const double below = k0 - 1 >= a.kd_lo ? last_s[c - 1][ty][tx] : 0.0;
+  const double above = k1 + 1 <= a.kd_hi ? first_s[c + 1][ty][tx] : 0.0;
+  if (k1 == k0) {
+    a.b[k0 * plane + cix] = rhs_of<F32>(a, k0, below, p_first, above, v_bot, v_top);
+  } else {
+    a.b[k0 * plane + cix] = rhs_of<F32>(a, k0, below, p_first, p_second, v_bot, v_top);
+    a.b[k1 * plane + cix] = rhs_of<F32>(a, k1, pm2, pm1, above, v_bot, v_top);
+  }
 }
 
 // b on the dynamic planes from an updated 3-component P (needs new in-plane
@@ -182,8 +341,14 @@ void launch_tdgl(const TDGLArgs& a, cudaStream_t s) {
     rhs3_kernel<<<grid, block, 0, s>>>(a, a.P_in);
     return;
   }
+  if (a.ncomp == 1) {
+    const dim3 cb(kCX, kCY, kCZ), cg((a.nx + kCX - 1) / kCX, (a.ny + kCY - 1) / kCY);
+    if (a.planes_f32) launch_k(tdgl_chunk_kernel<true>, cg, cb, 0, s, a);
+    else launch_k(tdgl_chunk_kernel<false>, cg, cb, 0, s, a);
+    return;
+  }
   launch_k(tdgl_kernel, grid, block, 0, s, a);
-  if (a.ncomp == 3) rhs3_kernel<<<grid, block, 0, s>>>(a, a.P_out);
+  rhs3_kernel<<<grid, block, 0, s>>>(a, a.P_out);
 }
 
 void launch_charge(const ChargeArgs& a, cudaStream_t s) {

@@ -42,7 +42,7 @@ class Numerics(C.Structure):
     _fields_ = [("dt", C.c_double), ("order", C.c_int), ("tol", C.c_double), ("nu1", C.c_int),
                 ("nu2", C.c_int), ("max_cycles", C.c_int), ("precision", C.c_int),
                 ("bottom_sweeps", C.c_int), ("guess", C.c_int), ("inner", C.c_int),
-                ("nonlinear", C.c_int)]
+                ("nonlinear", C.c_int), ("tdgl_arith", C.c_int)]
 
 
 class Charge(C.Structure):
@@ -156,12 +156,14 @@ def make_layers(layers):
 
 
 NEWTON, FIXED_POINT = 0, 1
+TDGL_FP64, TDGL_FP32 = 0, 1
 
 
 def make_numerics(dt, order=1, tol=1e-10, nu1=2, nu2=2, max_cycles=200, precision=FP64,
-                  bottom_sweeps=0, guess=0, inner=1, nonlinear=NEWTON):
+                  bottom_sweeps=0, guess=0, inner=1, nonlinear=NEWTON, tdgl_arith=TDGL_FP64):
     return Numerics(float(dt), int(order), float(tol), int(nu1), int(nu2), int(max_cycles),
-                    int(precision), int(bottom_sweeps), int(guess), int(inner), int(nonlinear))
+                    int(precision), int(bottom_sweeps), int(guess), int(inner), int(nonlinear),
+                    int(tdgl_arith))
 
 
 def tdgl_update_static(geom, dt, v_bottom, v_top, P, phi, stream=None):
