@@ -105,12 +105,12 @@ def test_fp32_force_mixed_64x64x16_100_steps():
 
 def test_fp32_force_is_rejected_outside_the_mixed_uniaxial_form():
     from paper_2210_15668_gb300 import ferrox
-    geom = I.make_geometry(16, 16, I.mfim_stack(8))
+    geom = I.make_geometry(16, 16, I.mfim_stack(12, n_fe=8))
     P = I.random_polarization(geom, seed=1)
     for prec in (ferrox.FP64, ferrox.FP64_DEFECT):
         with pytest.raises(ferrox.FerroxError, match="EINVAL"):
             ferrox.Device(geom, P, numerics=ferrox.make_numerics(DT, precision=prec, tdgl_arith=ferrox.TDGL_FP32))
-    g3 = I.make_geometry(16, 16, I.mfim_stack(8), ncomp=3)
+    g3 = I.make_geometry(16, 16, I.mfim_stack(12, n_fe=8), ncomp=3)
     with pytest.raises(ferrox.FerroxError, match="EINVAL"):
         ferrox.Device(g3, I.random_polarization(g3, seed=1),
                       numerics=ferrox.make_numerics(DT, precision=ferrox.MIXED, tdgl_arith=ferrox.TDGL_FP32))
