@@ -84,6 +84,8 @@ struct ferrox_ctx {
   void* s_arena = nullptr;
   void* coef = nullptr;               // PlaneCoef<T> of all levels
   PlaneCoef<double>* coef0 = nullptr; // level 0 in FP64 (outer residual)
+  PlaneCoef<double>* coef0s = nullptr; // level 0 divided by the diagonal (direct form's sweeps)
+  double* bs = nullptr;                // b / diag (direct form's fine sweeps)
   PlaneCoefDF* coef_df = nullptr;     // level 0 as double-float pairs (double-float residual)
   bool df_resid = false;              // the mixed form's outer residual in double-float
   PlaneTDGL* planes_d = nullptr;
@@ -610,14 +612,18 @@ MGArgs<double> fine_args(ferrox_ctx* c) {
   return a;
 }
 
-// nu1 red/black sweep pairs on phi; zst: honour the solve's b = 0 flag (phi = 0)
+// nu1 red/black sweep pairs on phi; zst: honour the solve's b = 0 flag (phi = 0).
+// The sweeps read b / diag (written once per solve by the prologue) with the
+// level's coefficients divided by the diagonal.
 template <typename W>
 void enqueue_fine_sweeps(ferrox_ctx* c, cudaStream_t s, W wrap, int nu, const DevStats* zst) {
-  const MGArgs<double> fa = fine_args(c);
+  MGArgs<double> fa = fine_args(c);
+  fa.r = c->bs;
+  fa.coef = c->coef0s;
   for (int sw = 0; sw < nu; ++sw) {
     const double sb = sweep_bytes<double>(c, c->lv[0]);
-    wrap(FERROX_K_SMOOTH0, sb, [&] { launch_smooth<double>(fa, c->lv[0], 0, 0, nullptr, s, zst); });
-    wrap(FERROX_K_SMOOTH0, sb, [&] { launch_smooth<double>(fa, c->lv[0], 1, 0, nullptr, s, zst); });
+    wrap(FERROX_K_SMOOTH0, sb, [&] { launch_smooth_scaled(fa, c->lv[0], 0, s, zst); });
+    wrap(FERROX_K_SMOOTH0, sb, [&] { launch_smooth_scaled(fa, c->lv[0], 1, s, zst); });
   }
 }
 
@@ -636,7 +642,7 @@ void enqueue_check(ferrox_ctx* c, cudaStream_t s, W wrap, int first, int set_con
   ck.set_cond = set_cond;
   ck.launches_per_cycle = vcycle_launches(c);
   ck.cond_handle = handle;
-  ck.first_launches = 2 * c->num.nu1 + 1;
+  ck.first_launches = 2 * c->num.nu1 + 2;   // b / diag, pre-smoothing, the check
   const MGArgs<double> fa = fine_args(c);
   double* rc = static_cast<double*>(c->r_arena);
   // phi and b of the fine level read, the coarse residual written
@@ -648,6 +654,8 @@ void enqueue_check(ferrox_ctx* c, cudaStream_t s, W wrap, int first, int set_con
 template <typename W = NoWrap>
 void enqueue_direct_prologue(ferrox_ctx* c, cudaStream_t s, W wrap, int set_cond,
                              unsigned long long handle) {
+  const double nb = (double)c->lv[0].ncell * 16.0;
+  wrap(FERROX_K_COPY, nb, [&] { launch_scale_rhs(c->b, c->coef0, c->nx, c->ny, c->nz, c->bs, s); });
   enqueue_fine_sweeps(c, s, wrap, c->num.nu1, nullptr);
   enqueue_check(c, s, wrap, 1, set_cond, handle);
 }
@@ -1168,7 +1176,7 @@ void release(ferrox_ctx* c) {
   cudaGraph_t gr[4] = {c->gr_step, c->gr_solve, c->gr_tdgl, c->gr_step_nn};
   for (auto g : ge) if (g) cudaGraphExecDestroy(g);
   for (auto g : gr) if (g) cudaGraphDestroy(g);
-  void* ptrs[] = {c->b, c->Pbuf, c->Fbuf, c->phi_prev, c->e_arena, c->e_alt, c->r_arena, c->s_arena, c->coef, c->coef0, c->coef_df,
+  void* ptrs[] = {c->b, c->Pbuf, c->Fbuf, c->phi_prev, c->e_arena, c->e_alt, c->r_arena, c->s_arena, c->coef, c->coef0, c->coef0s, c->bs, c->coef_df,
                   c->planes_d, c->planes_f32_d, c->lv_d, c->lvt_d, c->nn_scale, c->phi_guess, c->nn_pf, c->nn_stats, c->params_d, c->stats_d, c->partials_d, c->charge_d,
                   c->charge_part_d, c->dense_d, c->dense_wide_d};
   for (void* p : ptrs) if (p) cudaFree(p);
@@ -1336,6 +1344,17 @@ ferrox_status ferrox_init_geometry(ferrox_ctx** out, const ferrox_geometry* geom
   FX_INIT_CK(cudaMalloc(&ctx->coef0, ctx->nz * sizeof(PlaneCoef<double>)));
   FX_INIT_CK(cudaMemcpy(ctx->coef0, c64.data(), ctx->nz * sizeof(PlaneCoef<double>),
                         cudaMemcpyHostToDevice));
+  if (ctx->direct) {
+    // the direct form's fine sweeps: couplings divided by the diagonal, b / diag
+    std::vector<PlaneCoef<double>> cs(c64.begin(), c64.begin() + ctx->nz);
+    for (auto& q : cs) {
+      q.cx *= q.invdiag; q.cy *= q.invdiag; q.czlo *= q.invdiag; q.czhi *= q.invdiag;
+      q.diag = 1.0; q.invdiag = 1.0;
+    }
+    FX_INIT_CK(cudaMalloc(&ctx->coef0s, ctx->nz * sizeof(PlaneCoef<double>)));
+    FX_INIT_CK(cudaMemcpy(ctx->coef0s, cs.data(), ctx->nz * sizeof(PlaneCoef<double>), cudaMemcpyHostToDevice));
+    FX_INIT_CK(cudaMalloc(&ctx->bs, N * sizeof(double)));
+  }
   {
     // the same coefficients as double-float pairs: h = the nearest float, l = the
     // nearest float to the remainder

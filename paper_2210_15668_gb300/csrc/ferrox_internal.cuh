@@ -226,6 +226,12 @@ template <typename T>
 int smooth_rb_tile(const LevelDesc& L, bool has_s);
 template <typename T>
 cudaError_t smooth_rb_prepare();
+// direct FP64 form, fine level: a colour sweep on bs = b / diag with coefficients
+// divided by the diagonal (six FP64 operations per cell), and bs from b
+void launch_smooth_scaled(const MGArgs<double>& a, const LevelDesc& L, int color, cudaStream_t s,
+                          const DevStats* zero_stats);
+void launch_scale_rhs(const double* b, const PlaneCoef<double>* coef, int nx, int ny, int nz, double* bs,
+                      cudaStream_t s);
 template <typename T>
 void launch_smooth_rb(const MGArgs<T>& a, const LevelDesc& L, const T* e_in, T* e_out,
                       int zero_init, const UpdateArgs* upd, cudaStream_t s);

@@ -57,7 +57,11 @@ __global__ void __launch_bounds__(256) smooth_kernel(MGArgs<T> a, LevelDesc L, i
 // thread: the loads of all KZ cells are issued before their arithmetic, so each
 // thread keeps KZ independent chains in flight.  Same operations in the same
 // order as smooth_pair.
-template <typename T, int KZ>
+//
+// SCALED (the direct FP64 form's fine level): r holds b / diag and the
+// coefficients are divided by the diagonal on the host, so a cell is six FP64
+// operations (two additions, four multiply-adds) instead of seven.
+template <typename T, int KZ, bool SCALED = false>
 __global__ void __launch_bounds__(256) smooth_kz_kernel(MGArgs<T> a, LevelDesc L, int color,
                                                         const DevStats* zst) {
   pdl_enter();
@@ -102,8 +106,20 @@ __global__ void __launch_bounds__(256) smooth_kz_kernel(MGArgs<T> a, LevelDesc L
     acc = fma(c[q].cy, v[q][3] + v[q][4], acc);
     acc = fma(c[q].czlo, v[q][5], acc);
     acc = fma(c[q].czhi, v[q][6], acc);
-    a.e[id] = c[q].has_s ? acc / (c[q].diag + a.s[id]) : acc * c[q].invdiag;
+    if constexpr (SCALED) a.e[id] = acc;
+    else a.e[id] = c[q].has_s ? acc / (c[q].diag + a.s[id]) : acc * c[q].invdiag;
   }
+}
+
+// bs = b / diag on every cell of the fine level (once per solve of the direct form)
+__global__ void __launch_bounds__(256) scale_rhs_kernel(const double* __restrict__ b,
+                                                        const PlaneCoef<double>* __restrict__ coef,
+                                                        long long plane, long long n,
+                                                        double* __restrict__ bs) {
+  pdl_enter();
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    bs[t] = b[t] * __ldg(&coef[t / plane].invdiag);
 }
 
 // ---- fused red-black sweep (one launch per full sweep, out of place) -------------------
@@ -718,6 +734,23 @@ int smooth_rb_tile(const LevelDesc& L, bool) {
   if (sizeof(T) != sizeof(float)) return 0;
   if ((L.nx & 3) || (L.ny & 1) || L.nx < 36 || L.ny < kRbTY || L.ncell < kRbMinCells) return 0;
   return 1;
+}
+
+// colour sweep of the direct FP64 form's fine level on b / diag with scaled coefficients
+void launch_smooth_scaled(const MGArgs<double>& a, const LevelDesc& L, int color, cudaStream_t s,
+                          const DevStats* zero_stats) {
+  dim3 block, grid;
+  block_shape((L.nx + 1) >> 1, L.ny, block, grid, L.nz,
+              spread_threads((long long)((L.nx + 1) >> 1) * L.ny * L.nz));
+  launch_k(smooth_kz_kernel<double, 1, true>, grid, block, 0, s, a, L, color, zero_stats);
+}
+
+void launch_scale_rhs(const double* b, const PlaneCoef<double>* coef, int nx, int ny, int nz, double* bs,
+                      cudaStream_t s) {
+  const long long plane = (long long)nx * ny, n = plane * nz;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152LL * 8) blocks = 152LL * 8;
+  launch_k(scale_rhs_kernel, dim3((unsigned)blocks), dim3(256), 0, s, b, coef, plane, n, bs);
 }
 
 template <typename T>
