@@ -86,6 +86,7 @@ struct ferrox_ctx {
   PlaneCoef<double>* coef0 = nullptr; // level 0 in FP64 (outer residual)
   PlaneCoef<double>* coef0s = nullptr; // level 0 divided by the diagonal (direct form's sweeps)
   double* bs = nullptr;                // b / diag (direct form's fine sweeps)
+  void* sinv0 = nullptr;               // 1 / (diag + s) on level 0 (T; with a Newton shift)
   PlaneCoefDF* coef_df = nullptr;     // level 0 as double-float pairs (double-float residual)
   bool df_resid = false;              // the mixed form's outer residual in double-float
   PlaneTDGL* planes_d = nullptr;
@@ -515,6 +516,10 @@ int smoothing_launches(const ferrox_ctx* c, int l, int nu) {
 template <typename T, typename W = NoWrap>
 void enqueue_levels(ferrox_ctx* c, cudaStream_t s, W wrap, int l0, bool first, bool last) {
   MGArgs<T> a = mg_args<T>(c);
+  // level 0's sweeps multiply by 1 / (diag + s), written with s by the residual
+  MGArgs<T> a0 = a;
+  a0.sinv = static_cast<const T*>(c->sinv0);
+  auto sw_args = [&](int l) -> const MGArgs<T>& { return l == 0 ? a0 : a; };
   const int nu1 = c->num.nu1, nu2 = c->num.nu2;
   const int constant = 0;
   const int lt = c->tail_first, L = (int)c->lv.size() - 1;
@@ -528,13 +533,13 @@ void enqueue_levels(ferrox_ctx* c, cudaStream_t s, W wrap, int l0, bool first, b
         const int zero = sw == 0 && (first || l > 0);
         T* src = sw % 2 ? alt : own;
         T* dst = sw % 2 ? own : alt;
-        wrap(ks, 2.0 * sb, [&] { launch_smooth_rb<T>(a, c->lv[l], src, dst, zero, nullptr, s); });
+        wrap(ks, 2.0 * sb, [&] { launch_smooth_rb<T>(sw_args(l), c->lv[l], src, dst, zero, nullptr, s); });
       }
     } else {
       for (int sw = 0; sw < nu1; ++sw) {
         const int zero = sw == 0 && (first || l > 0);
-        wrap(ks, sb, [&] { launch_smooth<T>(a, c->lv[l], 0, zero, nullptr, s); });
-        wrap(ks, sb, [&] { launch_smooth<T>(a, c->lv[l], 1, 0, nullptr, s); });
+        wrap(ks, sb, [&] { launch_smooth<T>(sw_args(l), c->lv[l], 0, zero, nullptr, s); });
+        wrap(ks, sb, [&] { launch_smooth<T>(sw_args(l), c->lv[l], 1, 0, nullptr, s); });
       }
     }
     wrap(FERROX_K_RESTRICT, restrict_bytes<T>(c->lv[l], c->lv[l + 1]),
@@ -574,11 +579,11 @@ void enqueue_levels(ferrox_ctx* c, cudaStream_t s, W wrap, int l0, bool first, b
         T* src = sw % 2 ? alt : own;
         T* dst = sw % 2 ? own : alt;
         wrap(ks, 2.0 * sb + ub,
-             [&] { launch_smooth_rb<T>(a, c->lv[l], src, dst, 0, fuse ? &upd : nullptr, s); });
+             [&] { launch_smooth_rb<T>(sw_args(l), c->lv[l], src, dst, 0, fuse ? &upd : nullptr, s); });
       } else {
         const double ub = fuse ? 0.5 * (double)c->lv[0].ncell * 16.0 : 0.0;
-        wrap(ks, sb, [&] { launch_smooth<T>(a, c->lv[l], 0, 0, nullptr, s); });
-        wrap(ks, sb + ub, [&] { launch_smooth<T>(a, c->lv[l], 1, 0, fuse ? &upd : nullptr, s); });
+        wrap(ks, sb, [&] { launch_smooth<T>(sw_args(l), c->lv[l], 0, 0, nullptr, s); });
+        wrap(ks, sb + ub, [&] { launch_smooth<T>(sw_args(l), c->lv[l], 1, 0, fuse ? &upd : nullptr, s); });
       }
     }
   }
@@ -713,6 +718,7 @@ void enqueue_resid(ferrox_ctx* c, cudaStream_t s, int first, int set_cond,
   a.nx = c->nx; a.ny = c->ny; a.nz = c->nz;
   a.r_out = c->r_arena;
   a.s_out = c->shift ? c->s_arena : nullptr;
+  a.sinv_out = c->shift ? c->sinv0 : nullptr;
   a.carriers = carrier_kind(c);
   a.coef_df = c->df_resid ? c->coef_df : nullptr;
   a.partials = c->partials_d;
@@ -932,6 +938,7 @@ void enqueue_nn_features(ferrox_ctx* c, cudaStream_t s, __nv_bfloat16* x) {
   a.nx = c->nx; a.ny = c->ny; a.nz = c->nz;
   a.r_out = c->r_arena;
   a.s_out = c->shift ? c->s_arena : nullptr;
+  a.sinv_out = c->shift ? c->sinv0 : nullptr;
   a.carriers = carrier_kind(c);
   a.coef_df = c->df_resid ? c->coef_df : nullptr;
   a.stats = c->stats_d;
@@ -1176,7 +1183,7 @@ void release(ferrox_ctx* c) {
   cudaGraph_t gr[4] = {c->gr_step, c->gr_solve, c->gr_tdgl, c->gr_step_nn};
   for (auto g : ge) if (g) cudaGraphExecDestroy(g);
   for (auto g : gr) if (g) cudaGraphDestroy(g);
-  void* ptrs[] = {c->b, c->Pbuf, c->Fbuf, c->phi_prev, c->e_arena, c->e_alt, c->r_arena, c->s_arena, c->coef, c->coef0, c->coef0s, c->bs, c->coef_df,
+  void* ptrs[] = {c->b, c->Pbuf, c->Fbuf, c->phi_prev, c->e_arena, c->e_alt, c->r_arena, c->s_arena, c->coef, c->coef0, c->coef0s, c->bs, c->sinv0, c->coef_df,
                   c->planes_d, c->planes_f32_d, c->lv_d, c->lvt_d, c->nn_scale, c->phi_guess, c->nn_pf, c->nn_stats, c->params_d, c->stats_d, c->partials_d, c->charge_d,
                   c->charge_part_d, c->dense_d, c->dense_wide_d};
   for (void* p : ptrs) if (p) cudaFree(p);
@@ -1326,6 +1333,7 @@ ferrox_status ferrox_init_geometry(ferrox_ctx** out, const ferrox_geometry* geom
   }
   FX_INIT_CK(cudaMalloc(&ctx->r_arena, ctx->arena * tsz));
   if (ctx->shift) FX_INIT_CK(cudaMalloc(&ctx->s_arena, ctx->arena * tsz));
+  if (ctx->shift) FX_INIT_CK(cudaMalloc(&ctx->sinv0, ctx->lv[0].ncell * tsz));
   FX_INIT_CK(cudaMalloc(&ctx->planes_d, ctx->nz * sizeof(PlaneTDGL)));
   FX_INIT_CK(cudaMalloc(&ctx->lv_d, ctx->lv.size() * sizeof(LevelDesc)));
   FX_INIT_CK(cudaMalloc(&ctx->params_d, sizeof(DevParams)));

@@ -170,6 +170,7 @@ struct ResidArgs {
   int carriers;                      // carrier charge: 0 none, 1 Boltzmann planes only, 2 with
                                      // Fermi-Dirac planes
   const PlaneCoefDF* coef_df;        // non-null: stencil in double-float arithmetic (FP32 pipe)
+  void* sinv_out;                    // with s_out: 1 / (diag + s) of level 0 (float or double)
   int warp_rows;                     // nx is a multiple of 32: each warp holds 32 cells of a row
 };
 
@@ -181,6 +182,9 @@ struct MGArgs {
   T* s;                     // level arena of Newton shifts (null when no SC)
   const PlaneCoef<T>* coef; // all levels
   const LevelDesc* lv;      // device copy of the level table
+  const T* sinv = nullptr;  // 1 / (diag + s) of the swept level, from the level's first cell
+                            // (index id - L.off): sweeps multiply by it instead of dividing
+                            // (null: divide)
 };
 
 // phi += e folded into the last fine-level black sweep

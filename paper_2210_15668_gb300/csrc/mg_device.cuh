@@ -66,11 +66,11 @@ __device__ __forceinline__ void smooth_pair(const MGArgs<T>& a, const LevelDesc&
   if (i < L.nx) {
     id = lidx(L, i, j, k);
     if (zero_init) {
-      const T d = c.has_s ? T(1) / (c.diag + a.s[id]) : c.invdiag;
+      const T d = c.has_s ? (a.sinv ? a.sinv[id - L.off] : T(1) / (c.diag + a.s[id])) : c.invdiag;
       ev = a.r[id] * d;
     } else {
       const T num = gs_numerator(a.e, a.r, c, L, i, j, k, id);
-      ev = c.has_s ? num / (c.diag + a.s[id]) : num * c.invdiag;
+      ev = c.has_s ? (a.sinv ? num * a.sinv[id - L.off] : num / (c.diag + a.s[id])) : num * c.invdiag;
     }
     a.e[id] = ev;
   }
@@ -453,6 +453,24 @@ __device__ __forceinline__ double fd_half(double eta, double& dF) {
 // register window; accumulates r^2, b^2 (first residual of a solve only) and
 // rho^2.  SC = 0 compiles out the carrier term (stacks without a semiconductor
 // layer), SC = 1 keeps Boltzmann statistics only, SC = 2 also Fermi-Dirac.
+// The Newton shift of a level-0 cell, and with sinv_out the reciprocal of the
+// shifted diagonal (in T, from the diagonal as the sweeps' T coefficients hold
+// it), which the level-0 sweeps multiply by instead of dividing in every sweep.
+template <typename T>
+__device__ __forceinline__ void put_shift(const ResidArgs& a, long long t, double sv, T diag_t) {
+  const T s = (T)sv;
+  static_cast<T*>(a.s_out)[t] = s;
+  if (a.sinv_out) static_cast<T*>(a.sinv_out)[t] = T(1) / (diag_t + s);
+}
+
+// the level-0 diagonal in T from its double-float pair (float: the high part is
+// the nearest float)
+template <typename T>
+__device__ __forceinline__ T diag_of_df(const PlaneCoefDF& c) {
+  if constexpr (sizeof(T) == sizeof(float)) return c.diag_h;
+  else return (double)c.diag_h + (double)c.diag_l;
+}
+
 template <typename T, int SC = 2>
 __device__ __forceinline__ void resid_column(const ResidArgs& a, int i, int j, int k0, int k1,
                                              double& acc_r, double& acc_b, double& acc_rho) {
@@ -493,14 +511,14 @@ __device__ __forceinline__ void resid_column(const ResidArgs& a, int i, int j, i
         const double n = pt.Nc * fd_half(pt.eta_e0 + u, dn);
         const double p = pt.Nv * fd_half(pt.eta_p0 - u, dp);
         rho = pt.kq * (p - n + pt.Nnet);
-        if (s_out) s_out[t] = (T)(pt.kq * fma(pt.Nc, dn, pt.Nv * dp) * pt.inv_vt);
+        if (s_out) put_shift<T>(a, t, pt.kq * fma(pt.Nc, dn, pt.Nv * dp) * pt.inv_vt, (T)c.diag);
       } else {
         double ep, em;
         exp_pm(pc * pt.inv_vt, ep, em);
         const double n = pt.n0 * ep;
         const double p = pt.p0 * em;
         rho = pt.kq * (p - n + pt.Nnet);
-        if (s_out) s_out[t] = (T)(pt.kq * (n + p) * pt.inv_vt);
+        if (s_out) put_shift<T>(a, t, pt.kq * (n + p) * pt.inv_vt, (T)c.diag);
       }
       acc_rho = fma(rho, rho, acc_rho);
     }
@@ -585,14 +603,14 @@ __device__ __forceinline__ void resid_column_df(const ResidArgs& a, int i, int j
         const double n = pt.Nc * fd_half(pt.eta_e0 + u, dn);
         const double p = pt.Nv * fd_half(pt.eta_p0 - u, dp);
         rho = pt.kq * (p - n + pt.Nnet);
-        if (s_out) s_out[t] = (T)(pt.kq * fma(pt.Nc, dn, pt.Nv * dp) * pt.inv_vt);
+        if (s_out) put_shift<T>(a, t, pt.kq * fma(pt.Nc, dn, pt.Nv * dp) * pt.inv_vt, diag_of_df<T>(c));
       } else {
         double ep, em;
         exp_pm(pc_d * pt.inv_vt, ep, em);
         const double n = pt.n0 * ep;
         const double p = pt.p0 * em;
         rho = pt.kq * (p - n + pt.Nnet);
-        if (s_out) s_out[t] = (T)(pt.kq * (n + p) * pt.inv_vt);
+        if (s_out) put_shift<T>(a, t, pt.kq * (n + p) * pt.inv_vt, diag_of_df<T>(c));
       }
       acc_rho = fma(rho, rho, acc_rho);
     }

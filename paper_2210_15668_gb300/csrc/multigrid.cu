@@ -107,7 +107,8 @@ __global__ void __launch_bounds__(256) smooth_kz_kernel(MGArgs<T> a, LevelDesc L
     acc = fma(c[q].czlo, v[q][5], acc);
     acc = fma(c[q].czhi, v[q][6], acc);
     if constexpr (SCALED) a.e[id] = acc;
-    else a.e[id] = c[q].has_s ? acc / (c[q].diag + a.s[id]) : acc * c[q].invdiag;
+    else if (!c[q].has_s) a.e[id] = acc * c[q].invdiag;
+    else a.e[id] = a.sinv ? acc * a.sinv[id - L.off] : acc / (c[q].diag + a.s[id]);
   }
 }
 
@@ -146,6 +147,7 @@ struct RBArgs {
   T* e_out;                 // level-relative
   const T* r;               // level-relative
   const T* s;               // level-relative Newton shift (null without SC)
+  const T* sinv;            // level-relative 1 / (diag + s): multiply instead of divide
   const PlaneCoef<T>* coef; // the level's planes
   int nx, ny, nz;
   int kz;                   // planes per block (z chunk)
@@ -215,7 +217,8 @@ __global__ void __launch_bounds__(256) smooth_rb_kernel(RBArgs<float> a) {
       if (has_e) cp_async16(Es + (j % kRbNE) * kRbEP + e_soff, a.e_in + zoff + e_goff, zin);
       if (has_r && z >= z0 - 1 && z <= z1) {
         cp_async16(Rs + (j % kRbNR) * kRbRP + r_soff, a.r + zoff + r_goff, zin);
-        if (a.s) cp_async16(Ss + (j % kRbNR) * kRbRP + r_soff, a.s + zoff + r_goff, zin);
+        if (a.sinv) cp_async16(Ss + (j % kRbNR) * kRbRP + r_soff, a.sinv + zoff + r_goff, zin);
+        else if (a.s) cp_async16(Ss + (j % kRbNR) * kRbRP + r_soff, a.s + zoff + r_goff, zin);
       }
     }
     cp_async_commit();   // one group per unit, empty past the end
@@ -264,7 +267,7 @@ __global__ void __launch_bounds__(256) smooth_rb_kernel(RBArgs<float> a) {
         const int q = ry * kRbW + lx;
         float ev;
         if (a.zero_init) {
-          const float d = c.has_s ? 1.0f / (c.diag + S[q]) : c.invdiag;
+          const float d = c.has_s ? (a.sinv ? S[q] : 1.0f / (c.diag + S[q])) : c.invdiag;
           ev = R[q] * d;
         } else {
           const int e = q + kRbW;             // the e planes start one row lower
@@ -273,7 +276,7 @@ __global__ void __launch_bounds__(256) smooth_rb_kernel(RBArgs<float> a) {
           acc = fmaf(c.cy, Ec[e - kRbW] + Ec[e + kRbW], acc);
           acc = fmaf(c.czlo, Ed[e], acc);
           acc = fmaf(c.czhi, Eu[e], acc);
-          ev = c.has_s ? acc / (c.diag + S[q]) : acc * c.invdiag;
+          ev = c.has_s ? (a.sinv ? acc * S[q] : acc / (c.diag + S[q])) : acc * c.invdiag;
         }
         R[q] = ev;
       }
@@ -295,7 +298,7 @@ __global__ void __launch_bounds__(256) smooth_rb_kernel(RBArgs<float> a) {
       acc = fmaf(c.cy, Rc[qb - kRbW] + Rc[qb + kRbW], acc);
       acc = fmaf(c.czlo, Rd[qb], acc);
       acc = fmaf(c.czhi, Ru[qb], acc);
-      const float eb = c.has_s ? acc / (c.diag + S[qb]) : acc * c.invdiag;
+      const float eb = c.has_s ? (a.sinv ? acc * S[qb] : acc / (c.diag + S[qb])) : acc * c.invdiag;
       const float er = Rc[q0 + 1 - second];
       const int id = pb * plane + gy_b * nx + x0 + 2 * bk;
       const float2 v = second ? make_float2(er, eb) : make_float2(eb, er);
@@ -762,6 +765,7 @@ void launch_smooth_rb(const MGArgs<T>& a, const LevelDesc& L, const T* e_in, T* 
     r.e_out = e_out;
     r.r = a.r + L.off;
     r.s = a.s ? a.s + L.off : nullptr;
+    r.sinv = a.sinv;
     r.coef = a.coef + L.coef_off;
     r.nx = L.nx; r.ny = L.ny; r.nz = L.nz;
     r.kz = rb_kz(L);
