@@ -173,10 +173,12 @@ def kernel_work(kind, cells, fe_cells, dyn_cells, tsz):
     return None, None
 
 
-def class_rooflines(prof, hbm_peak, fp64_classes=()):
+def class_rooflines(prof, hbm_peak, fp64_classes=(), df_classes=()):
     """Per kernel class of one eager, event-timed step: time, launches, algorithmic
     bytes (from the library's own per-launch count), effective GB/s and fraction of
-    the measured HBM peak; plus the whole step (sum over classes)."""
+    the measured HBM peak; plus the whole step (sum over classes).  fp64_classes are
+    labelled bound by the FP64 pipe, df_classes (the mixed form's double-float outer
+    residual) by instruction issue on the FP32 and integer pipes."""
     out = {}
     tb = tm = 0.0
     for k, (ms, n, by) in prof.items():
@@ -185,7 +187,9 @@ def class_rooflines(prof, hbm_peak, fp64_classes=()):
         gbs = by / (ms / 1e3) / 1e9 if ms > 0 else None
         out[k] = {"ms": round(ms, 4), "launches": n, "bytes": by,
                   "gbs": gbs, "hbm_frac": gbs / hbm_peak if gbs else None}
-        if k in fp64_classes:
+        if k in df_classes:
+            out[k]["bound"] = "issue (double-float on the FP32 and integer pipes)"
+        elif k in fp64_classes:
             out[k]["bound"] = "alu (FP64 pipe)"
         tb += by
         tm += ms
@@ -325,7 +329,8 @@ def run_ours(args, ws, rank, local):
     share = dom_ms / step_ms if step_ms else None
     fp64_classes = (("tdgl", "resid", "update") if prec_main == ferrox.MIXED else
                     ("tdgl", "resid", "update", "smooth_fine", "smooth_coarse", "restrict", "prolong", "tail"))
-    classes, whole = class_rooflines(prof, hbm_peak, fp64_classes)
+    classes, whole = class_rooflines(prof, hbm_peak, fp64_classes,
+                                     ("resid",) if prec_main == ferrox.MIXED else ())
     whole["graph_ms_per_step"] = t_max / K
     whole["vcycles_profiled_step"] = sp1["vcycles"] - sp0["vcycles"]
     whole["vcycles_per_timed_step"] = vcycles_per_step
@@ -364,7 +369,8 @@ def run_ours(args, ws, rank, local):
         t2 = reduce_max(t2, ws)
         v2 = ws * cells * K / (t2 / 1e3) / 1e6
         prof2 = d2.profile_step(with_bytes=True)
-        cl2, wh2 = class_rooflines(prof2, hbm_peak, ("tdgl", "resid", "update"))
+        cl2, wh2 = class_rooflines(prof2, hbm_peak, ("tdgl", "resid", "update"),
+                                   ("resid",) if prec_o == ferrox.MIXED else ())
         wh2["graph_ms_per_step"] = t2 / K
         other = {"precision": "fp64" if prec_o == ferrox.FP64 else "mixed", "value": v2,
                  "ms_per_step": t2 / K, "vcycles_per_step": (s21["vcycles"] - s20["vcycles"]) / K,
@@ -386,7 +392,7 @@ def run_ours(args, ws, rank, local):
         t4, s40, s41, _ = timed_run(d4, K, args.warmup)
         t4 = reduce_max(t4, ws)
         prof4 = d4.profile_step(with_bytes=True)
-        cl4, wh4 = class_rooflines(prof4, hbm_peak, ("tdgl", "resid", "update"))
+        cl4, wh4 = class_rooflines(prof4, hbm_peak, ("tdgl", "resid", "update"), ("resid",))
         wh4["graph_ms_per_step"] = t4 / K
         fast = {"precision": "mixed", "guess": "extrapolated", "inner": FAST_INNER,
                 "value": ws * cells * K / (t4 / 1e3) / 1e6, "ms_per_step": t4 / K,
@@ -611,7 +617,8 @@ def run_mfism(args, ws, hbm_peak):
                 fp64c = ("tdgl", "resid", "update") + (() if kw["precision"] == ferrox.MIXED else
                                                       ("smooth_fine", "smooth_coarse", "restrict",
                                                        "prolong", "tail"))
-                cl, wh = class_rooflines(prof, hbm_peak, fp64c)
+                cl, wh = class_rooflines(prof, hbm_peak, fp64c,
+                                         ("resid",) if kw["precision"] == ferrox.MIXED else ())
                 wh["graph_ms_per_step"] = t / K
                 r["roofline_classes"] = cl
                 r["whole_step"] = wh

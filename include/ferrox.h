@@ -371,6 +371,15 @@ ferrox_status ferrox_check_wait_timeout(double seconds, int* status_out, void* c
  * n < 0 or a null pointer with n > 0. */
 ferrox_status ferrox_carrier_exp(const double* u_dev, double* ep_dev, double* em_dev, long long n,
                                  void* cuda_stream);
+/* The same pair in double-float arithmetic on the FP32 pipe, as the mixed form's
+ * residual evaluates it for |u| <= 70: u_hl_dev holds n arguments as float pairs
+ * (u = h + l, 2n floats, 8-byte aligned); ep_dev[i] and em_dev[i] receive the
+ * result pairs of e^{+u} and e^{-u} summed in FP64.  About 2^-47 relative for
+ * |u| <= 70; outside that range the values are not specified (the residual then
+ * uses the FP64 routine).  Synchronises; FERROX_EINVAL for n < 0, a null
+ * pointer with n > 0 or a misaligned u_hl_dev. */
+ferrox_status ferrox_carrier_exp_df(const float* u_hl_dev, double* ep_dev, double* em_dev, long long n,
+                                    void* cuda_stream);
 const char* ferrox_batch_last_error(const ferrox_batch* b);
 
 /* ---- learned warm start ------------------------------------------------------------------

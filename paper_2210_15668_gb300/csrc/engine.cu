@@ -370,6 +370,7 @@ ferrox_status build_planes(ferrox_ctx* c) {
       p.n0 = n0; p.p0 = p0; p.Nnet = N;
       p.kq = kQ * h * h / kEps0;
       p.inv_vt = kQ / (kKB * L.T);
+      p.kqn0 = p.kq * n0; p.kqp0 = p.kq * p0; p.kqN = p.kq * N;
       p.fd = L.stats == FERROX_FERMI_DIRAC;
       if (p.fd) {
         p.Nc = effective_dos(L.m_e, L.T);
@@ -2441,6 +2442,17 @@ ferrox_status ferrox_carrier_exp(const double* u_dev, double* ep_dev, double* em
   if (n < 0 || (n > 0 && (!u_dev || !ep_dev || !em_dev))) return bfail(nullptr, FERROX_EINVAL, "bad argument");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   FX_BCK(launch_carrier_exp(u_dev, ep_dev, em_dev, n, s));
+  FX_BCK(cudaStreamSynchronize(s));
+  return FERROX_OK;
+}
+
+ferrox_status ferrox_carrier_exp_df(const float* u_hl_dev, double* ep_dev, double* em_dev, long long n,
+                                    void* cuda_stream) {
+  ferrox_batch* B = nullptr;
+  if (n < 0 || (n > 0 && (!u_hl_dev || !ep_dev || !em_dev))) return bfail(nullptr, FERROX_EINVAL, "bad argument");
+  if (reinterpret_cast<uintptr_t>(u_hl_dev) % 8) return bfail(nullptr, FERROX_EINVAL, "u_hl must be 8-byte aligned");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  FX_BCK(launch_carrier_exp_df(u_hl_dev, ep_dev, em_dev, n, s));
   FX_BCK(cudaStreamSynchronize(s));
   return FERROX_OK;
 }

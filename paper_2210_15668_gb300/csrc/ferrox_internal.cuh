@@ -87,6 +87,8 @@ struct PlaneTDGL {
   double kq, n0, p0, Nnet, inv_vt;
   // Fermi-Dirac: n = Nc F(eta_e0 + phi/VT), p = Nv F(eta_p0 - phi/VT)
   double Nc, Nv, eta_e0, eta_p0;
+  // kq n0, kq p0, kq Nnet (the double-float residual forms rho from these)
+  double kqn0, kqp0, kqN;
 };
 
 // ---- per-plane multigrid coefficients of one level ----------------------------------
@@ -418,6 +420,7 @@ struct BatchArgs {
 
 cudaError_t launch_barrier_timeout(GridBar* gb, int* status, long long limit, cudaStream_t s);
 cudaError_t launch_carrier_exp(const double* u, double* ep, double* em, long long n, cudaStream_t s);
+cudaError_t launch_carrier_exp_df(const float* u_hl, double* ep, double* em, long long n, cudaStream_t s);
 template <typename T>
 cudaError_t batch_prepare(size_t smem);
 template <typename T>

@@ -561,6 +561,7 @@ __device__ __forceinline__ void resid_column_df(const ResidArgs& a, int i, int j
   double pc_d = phi[(long long)k0 * plane + col];
   df pd = k0 > 0 ? df_from_double(phi[(long long)(k0 - 1) * plane + col]) : df{0.0f, 0.0f};
   df pc = df_from_double(pc_d);
+  float rho2f = 0.0f;   // rho^2 of the double-float carrier path (enters only the scale of the test)
   for (int k = k0; k < k1; ++k) {
     const long long t = k * plane + col;
     const double pu_d = (k < nz - 1) ? phi[t + plane] : 0.0;
@@ -594,27 +595,47 @@ __device__ __forceinline__ void resid_column_df(const ResidArgs& a, int i, int j
       if (k == 0) bb += __ldg(&pk->lift) * v_bot;
       if (k == nz - 1) bb += __ldg(&pk->lift) * v_top;
     }
-    double rho = 0.0;
+    df b_df = df_from_double(bb);
     if (SC && __ldg(&pk->sc)) {
       const PlaneTDGL pt = ldg_struct(pk);
-      if (SC == 2 && pt.fd) {
-        const double u = pc_d * pt.inv_vt;
-        double dn, dp;
-        const double n = pt.Nc * fd_half(pt.eta_e0 + u, dn);
-        const double p = pt.Nv * fd_half(pt.eta_p0 - u, dp);
-        rho = pt.kq * (p - n + pt.Nnet);
-        if (s_out) put_shift<T>(a, t, pt.kq * fma(pt.Nc, dn, pt.Nv * dp) * pt.inv_vt, diag_of_df<T>(c));
+      // Boltzmann densities in double-float on the FP32 pipe while |u| <= kExpDFMax:
+      // rho = kq p0 e^{-u} - kq n0 e^{u} + kq Nnet, u = phi / V_T
+      const df inv_vt = df_from_double(pt.inv_vt);
+      const df u = df_mul(pc, inv_vt);
+      if (!(SC == 2 && pt.fd) && fabsf(u.h) <= kExpDFMax) {
+        df ep, em;
+        exp_pm_df(u, ep, em);
+        const df kn = df_mul(df_from_double(pt.kqn0), ep);
+        const df kp = df_mul(df_from_double(pt.kqp0), em);
+        const df rho = df_add(df_add(kp, df_neg(kn)), df_from_double(pt.kqN));
+        b_df = df_add(b_df, rho);
+        rho2f = fmaf(rho.h, rho.h, rho2f);
+        if (s_out) {
+          const float sv = (kn.h + kp.h) * inv_vt.h;
+          s_out[t] = (T)sv;
+          if (a.sinv_out) static_cast<T*>(a.sinv_out)[t] = (T)(1.0f / (c.diag_h + sv));
+        }
       } else {
-        double ep, em;
-        exp_pm(pc_d * pt.inv_vt, ep, em);
-        const double n = pt.n0 * ep;
-        const double p = pt.p0 * em;
-        rho = pt.kq * (p - n + pt.Nnet);
-        if (s_out) put_shift<T>(a, t, pt.kq * (n + p) * pt.inv_vt, diag_of_df<T>(c));
+        double rho;
+        if (SC == 2 && pt.fd) {
+          const double uu = pc_d * pt.inv_vt;
+          double dn, dp;
+          const double n = pt.Nc * fd_half(pt.eta_e0 + uu, dn);
+          const double p = pt.Nv * fd_half(pt.eta_p0 - uu, dp);
+          rho = pt.kq * (p - n + pt.Nnet);
+          if (s_out) put_shift<T>(a, t, pt.kq * fma(pt.Nc, dn, pt.Nv * dp) * pt.inv_vt, diag_of_df<T>(c));
+        } else {
+          double ep, em;
+          exp_pm(pc_d * pt.inv_vt, ep, em);
+          const double n = pt.n0 * ep;
+          const double p = pt.p0 * em;
+          rho = pt.kq * (p - n + pt.Nnet);
+          if (s_out) put_shift<T>(a, t, pt.kq * (n + p) * pt.inv_vt, diag_of_df<T>(c));
+        }
+        b_df = df_from_double(bb + rho);
+        acc_rho = fma(rho, rho, acc_rho);
       }
-      acc_rho = fma(rho, rho, acc_rho);
     }
-    const df b_df = df_from_double(SC ? bb + rho : bb);
     // r = ((b + rho) - diag phi) + (z couplings) + (lateral couplings), as a tree
     const df r0 = df_add_fast(b_df, df_neg(df_mul(df{c.diag_h, c.diag_l}, pc)));
     const df rz = df_add_fast(df_mul(df{c.czhi_h, c.czhi_l}, pu), df_mul(df{c.czlo_h, c.czlo_l}, pd));
@@ -633,6 +654,7 @@ __device__ __forceinline__ void resid_column_df(const ResidArgs& a, int i, int j
     pc = pu;
     pc_d = pu_d;
   }
+  if (SC) acc_rho += (double)rho2f;
 }
 
 // Convergence decision of one solve from its summed norms (one thread).

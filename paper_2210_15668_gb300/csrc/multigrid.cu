@@ -914,6 +914,29 @@ cudaError_t launch_carrier_exp(const double* u, double* ep, double* em, long lon
   return cudaGetLastError();
 }
 
+// the double-float pair routine on arguments given as float pairs (h, l); each
+// result pair is returned as its FP64 sum
+__global__ void __launch_bounds__(256) carrier_exp_df_kernel(const float2* __restrict__ u,
+                                                             double* __restrict__ ep,
+                                                             double* __restrict__ em, long long n) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) {
+    const float2 v = u[i];
+    df a, b;
+    exp_pm_df(df{v.x, v.y}, a, b);
+    ep[i] = (double)a.h + (double)a.l;
+    em[i] = (double)b.h + (double)b.l;
+  }
+}
+
+cudaError_t launch_carrier_exp_df(const float* u_hl, double* ep, double* em, long long n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  long long b = (n + 255) / 256;
+  if (b > 152LL * 8) b = 152LL * 8;
+  carrier_exp_df_kernel<<<(int)b, 256, 0, s>>>(reinterpret_cast<const float2*>(u_hl), ep, em, n);
+  return cudaGetLastError();
+}
+
 #define FX_INST(T)                                                                              \
   template void launch_smooth<T>(const MGArgs<T>&, const LevelDesc&, int, int,                  \
                                  const UpdateArgs*, cudaStream_t, const DevStats*);             \

@@ -67,7 +67,7 @@ EXPORTS = ["ferrox_init_geometry", "ferrox_set_bias", "ferrox_solve_poisson", "f
            "ferrox_batch_step", "ferrox_batch_charge", "ferrox_batch_stats", "ferrox_batch_tuning",
            "ferrox_batch_groups", "ferrox_batch_set_shape",
            "ferrox_batch_destroy", "ferrox_batch_last_error", "ferrox_check_wait_timeout",
-           "ferrox_carrier_exp",
+           "ferrox_carrier_exp", "ferrox_carrier_exp_df",
            "ferrox_nn_create", "ferrox_nn_forward", "ferrox_nn_loss_grad", "ferrox_nn_params",
            "ferrox_nn_set_params", "ferrox_nn_adam_step", "ferrox_nn_snapshot_count", "ferrox_nn_train",
            "ferrox_nn_destroy", "ferrox_nn_last_error", "ferrox_nn_use_tensor_memory", "ferrox_nn_kernel_info",
@@ -127,6 +127,7 @@ def load(path: str = LIB_PATH):
     lib.ferrox_batch_last_error.restype = C.c_char_p
     lib.ferrox_check_wait_timeout.argtypes = [C.c_double, C.POINTER(C.c_int), vp]
     lib.ferrox_carrier_exp.argtypes = [vp, vp, vp, C.c_longlong, vp]
+    lib.ferrox_carrier_exp_df.argtypes = [vp, vp, vp, C.c_longlong, vp]
     lib.ferrox_attach_nn.argtypes = [vp, vp, C.c_int]
     for name in EXPORTS:
         if name not in ("ferrox_last_error", "ferrox_batch_last_error", "ferrox_nn_last_error"):
@@ -457,6 +458,25 @@ def carrier_exp(u, stream=None):
     em = torch.empty_like(u)
     rc = lib.ferrox_carrier_exp(C.c_void_p(u.data_ptr()), C.c_void_p(ep.data_ptr()),
                                 C.c_void_p(em.data_ptr()), u.numel(), C.c_void_p(st.cuda_stream))
+    if rc != FERROX_OK:
+        raise FerroxError(rc, lib.ferrox_batch_last_error(None).decode())
+    return ep, em
+
+
+def carrier_exp_df(u_hl, stream=None):
+    """(e^u, e^-u) in double-float arithmetic for arguments given as float pairs: u_hl
+    a CUDA float32 tensor [n, 2] (h, l); the result pairs are returned summed in FP64."""
+    import torch
+    lib = load()
+    if not (u_hl.is_cuda and u_hl.dtype == torch.float32 and u_hl.dim() == 2 and u_hl.shape[1] == 2):
+        raise TypeError("u_hl must be a CUDA float32 tensor of shape [n, 2]")
+    u_hl = u_hl.contiguous()
+    st = stream if stream is not None else torch.cuda.current_stream()
+    n = u_hl.shape[0]
+    ep = torch.empty(n, dtype=torch.float64, device=u_hl.device)
+    em = torch.empty(n, dtype=torch.float64, device=u_hl.device)
+    rc = lib.ferrox_carrier_exp_df(C.c_void_p(u_hl.data_ptr()), C.c_void_p(ep.data_ptr()),
+                                   C.c_void_p(em.data_ptr()), C.c_longlong(n), C.c_void_p(st.cuda_stream))
     if rc != FERROX_OK:
         raise FerroxError(rc, lib.ferrox_batch_last_error(None).decode())
     return ep, em

@@ -60,3 +60,31 @@ def test_empty_and_bad_arguments():
     lib = ferrox.load()
     assert lib.ferrox_carrier_exp(None, None, None, C.c_longlong(4), None) == ferrox.FERROX_EINVAL
     assert lib.ferrox_carrier_exp(None, None, None, C.c_longlong(-1), None) == ferrox.FERROX_EINVAL
+
+
+def test_double_float_pair_error_bound():
+    """The double-float pair (FP32 pipe) the mixed form's residual uses for |u| <= 70,
+    against e^{h + l} in extended precision for the exact argument pairs: relative
+    error <= 2^-45 (a few 2^-48 roundings of the pair arithmetic)."""
+    from paper_2210_15668_gb300 import ferrox
+    rng = np.random.default_rng(11)
+    x = np.concatenate([
+        rng.uniform(-70.0, 70.0, 1_000_000),
+        rng.uniform(-40.0, 40.0, 1_000_000),
+        rng.uniform(-1e-3, 1e-3, 100_000),
+        np.arange(-3000, 3001) * (np.log(2) / 64),
+        np.arange(-3000, 3001) * (np.log(2) / 64) + np.log(2) / 128,
+        [0.0, 70.0, -70.0],
+    ])
+    x = x[np.abs(x) <= 70.0]
+    h = x.astype(np.float32)
+    l = (x - h.astype(np.float64)).astype(np.float32)
+    u_hl = np.stack([h, l], axis=1)
+    ep, em = ferrox.carrier_exp_df(torch.from_numpy(u_hl).cuda())
+    ep, em = ep.cpu().numpy().astype(np.longdouble), em.cpu().numpy().astype(np.longdouble)
+    u = h.astype(np.longdouble) + l.astype(np.longdouble)
+    rp = np.abs(ep / np.exp(u) - 1).astype(np.float64)
+    rm = np.abs(em / np.exp(-u) - 1).astype(np.float64)
+    print(f"double-float pair: max rel error e^u {rp.max():.2e}, e^-u {rm.max():.2e} (2^-45 = {2.0**-45:.2e})")
+    assert rp.max() <= 2.0 ** -45 and rm.max() <= 2.0 ** -45
+    assert ep[x == 0.0][0] == 1.0 and em[x == 0.0][0] == 1.0
