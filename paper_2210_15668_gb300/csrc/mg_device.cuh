@@ -108,11 +108,16 @@ __host__ __device__ __forceinline__ int black_residual_zero(const LevelDesc& F, 
 // to sc).  NORM also accumulates the squared residuals of the children it
 // computes into rr and, with want_b, the squared right-hand sides of all
 // children into bb (the direct FP64 form's stopping test).
-template <typename T, bool NORM = false>
+//
+// With a float accumulator (the direct FP64 form's check) the squares are summed
+// in FP32 from FP32 approximations taken with integer operations (the FP64 ->
+// FP32 conversion instruction runs on the FP64 pipe): the norms only scale the
+// stopping test, where a relative error of ~1e-6 in ||r|| is immaterial.
+template <typename T, bool NORM = false, typename A = double>
 __device__ __forceinline__ void restrict_children(const MGArgs<T>& fa, T* rc, T* sc,
                                                   const LevelDesc& F, const LevelDesc& C, int I,
-                                                  int J, int K, int skip_black, double& rr,
-                                                  double& bb, int want_b) {
+                                                  int J, int K, int skip_black, A& rr,
+                                                  A& bb, int want_b) {
   const int nxc = F.crx ? 2 : 1, nyc = F.cry ? 2 : 1, nzc = F.crz ? 2 : 1;
   const int i0 = F.crx ? 2 * I : I, j0 = F.cry ? 2 * J : J, k0 = F.crz ? 2 * K : K;
   T sum = T(0), ssum = T(0);
@@ -123,11 +128,21 @@ __device__ __forceinline__ void restrict_children(const MGArgs<T>& fa, T* rc, T*
         if (!(skip_black && ((i + j + k) & 1))) {
           const T r = cell_residual(fa, F, i, j, k);
           sum += r;
-          if (NORM) rr = fma((double)r, (double)r, rr);
+          if constexpr (NORM && sizeof(A) == sizeof(float)) {
+            const float rf = dev::df_from_double((double)r).h;
+            rr = fmaf(rf, rf, rr);
+          } else if constexpr (NORM) {
+            rr = fma((double)r, (double)r, rr);
+          }
         }
         if (NORM && want_b) {
           const double b = fa.r[lidx(F, i, j, k)];
-          bb = fma(b, b, bb);
+          if constexpr (sizeof(A) == sizeof(float)) {
+            const float bf = dev::df_from_double(b).h;
+            bb = fmaf(bf, bf, bb);
+          } else {
+            bb = fma(b, b, bb);
+          }
         }
         if (sc) ssum += fa.s[lidx(F, i, j, k)];
       }

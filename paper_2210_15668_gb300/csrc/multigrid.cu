@@ -337,21 +337,19 @@ __global__ void __launch_bounds__(256) restrict_check_kernel(MGArgs<T> fa, T* rc
   pdl_enter();
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = blockIdx.y * blockDim.y + threadIdx.y;
-  double rr = 0.0, bb = 0.0, zz = 0.0;
+  float rr = 0.0f, bb = 0.0f;   // FP32 sums of the squares (see restrict_children)
   if (I < C.nx && J < C.ny)
-    restrict_children<T, true>(fa, rc, nullptr, F, C, I, J, (int)blockIdx.z, skip_black, rr, bb,
-                               ck.first);
-  if (ck.first)
-    block_sum3(rr, bb, zz);
-  else
-    block_sum1(rr);
+    restrict_children<T, true, float>(fa, rc, nullptr, F, C, I, J, (int)blockIdx.z, skip_black, rr,
+                                      bb, ck.first);
+  block_sum2f(rr, bb);
+  double zz = 0.0;
   __shared__ bool last;
   const int nblk = gridDim.x * gridDim.y * gridDim.z;
   const int bid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   if (tid == 0) {
-    ck.partials[bid] = rr;
-    ck.partials[nblk + bid] = ck.first ? bb : 0.0;
+    ck.partials[bid] = (double)rr;
+    ck.partials[nblk + bid] = ck.first ? (double)bb : 0.0;
     __threadfence();
     const unsigned int prev = atomicAdd(&ck.stats->done_ctr, 1u);
     last = (prev == (unsigned)nblk - 1);
