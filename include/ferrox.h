@@ -333,9 +333,10 @@ ferrox_status ferrox_init_batch(ferrox_batch** out, int n, const ferrox_geometry
                                 void* cuda_stream);
 /* Electrode potentials of every instance (arrays of n).  Asynchronous. */
 ferrox_status ferrox_batch_set_bias(ferrox_batch* b, const double* v_bottom, const double* v_top);
-/* Step 0 for every instance (one persistent launch). */
+/* Step 0 for every instance (one persistent launch, or the phase graph). */
 ferrox_status ferrox_batch_solve_poisson(ferrox_batch* b);
-/* nsteps time steps of every instance in one persistent launch. */
+/* nsteps time steps of every instance: one persistent launch, or nsteps launches
+ * of the phase graph (see ferrox_batch_engine).  The first call autotunes. */
 ferrox_status ferrox_batch_step(ferrox_batch* b, int nsteps);
 /* Q, V_fe and electrode charges of every instance (array of n).  Synchronises. */
 ferrox_status ferrox_batch_charge(ferrox_batch* b, ferrox_charge_t* out);
@@ -354,6 +355,17 @@ ferrox_status ferrox_batch_groups(const ferrox_batch* b, int* ngroups);
  * Every shape computes the same results; only the speed differs. */
 ferrox_status ferrox_batch_set_shape(ferrox_batch* b, int threads, int rows_per_unit,
                                      int ctas_per_sm, int grouped);
+/* The engine the autotuner chose (ESTATE before the first step): 0 = one
+ * persistent launch with grid barriers between its phases; 1 = a CUDA graph of
+ * per-phase launches (TDGL, residual, per-instance decision, each level's colour
+ * sweeps and transfers, the per-instance tails) whose solve loop is a WHILE node
+ * the decision kernel sets while any instance is above the tolerance.  Both run
+ * the same work units with the same operations and per-instance sums, so they
+ * give identical results; only the speed differs. */
+ferrox_status ferrox_batch_engine(const ferrox_batch* b, int* engine);
+/* Fix the engine instead of autotuning it (0 with the current shape at one CTA
+ * per SM, or 1).  EINVAL for other values.  Synchronises. */
+ferrox_status ferrox_batch_set_engine(ferrox_batch* b, int engine);
 ferrox_status ferrox_batch_destroy(ferrox_batch* b);
 
 /* Failure-detection check of the bounded device waits: a two-block launch in

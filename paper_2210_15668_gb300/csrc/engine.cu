@@ -1816,6 +1816,9 @@ struct ferrox_batch {
   int threads = 512, rows_per_unit = 1, blocks = 0;
   size_t smem = 0;
   bool tuned = false;
+  int engine = 0;                     // 0: one persistent launch; 1: a graph of per-phase launches
+  int unit_blocks = 0;                // CTAs of the per-phase launches (engine 1)
+  cudaStream_t cap2 = nullptr;        // captures the phase graph's WHILE body
   cudaGraphExec_t ge_step = nullptr, ge_solve = nullptr;
   cudaGraph_t gr_step = nullptr, gr_solve = nullptr;
   std::string err;
@@ -1824,7 +1827,7 @@ struct ferrox_batch {
 namespace {
 
 std::mutex g_tune_mu;
-struct TuneChoice { int threads, rows, bps, grouped; };
+struct TuneChoice { int threads, rows, bps, grouped, engine; };
 std::vector<std::pair<std::string, TuneChoice>> g_tune_cache;
 
 ferrox_status bfail(ferrox_batch* b, ferrox_status s, const std::string& m) {
@@ -1974,14 +1977,49 @@ std::string batch_key(const ferrox_batch* B) {
   return k;
 }
 
-// time each candidate launch shape on one step from a saved state, keep the fastest
+// the graph of per-phase launches of one step (mode 0) or one solve (mode 1)
+ferrox_status phase_graph(ferrox_batch* B, int mode, cudaGraph_t* g, cudaGraphExec_t* ge) {
+  *g = nullptr;
+  *ge = nullptr;
+  const BatchArgs a = batch_args(B, mode);
+  FX_BCK(cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeRelaxed));
+  const cudaError_t le = B->mixed ? capture_phases<float>(a, B->unit_blocks, B->smem, B->cap, B->cap2)
+                                  : capture_phases<double>(a, B->unit_blocks, B->smem, B->cap, B->cap2);
+  const cudaError_t ce = cudaStreamEndCapture(B->cap, g);
+  if (le != cudaSuccess || ce != cudaSuccess) {
+    if (*g) cudaGraphDestroy(*g);
+    *g = nullptr;
+    cudaGetLastError();
+    return bfail(B, FERROX_ECUDA, std::string("capturing the phase graph: ") +
+                                      cudaGetErrorString(le != cudaSuccess ? le : ce));
+  }
+  FX_BCK(cudaGraphInstantiate(ge, *g, 0));
+  return FERROX_OK;
+}
+
+// the per-phase launches: one-row units, eight CTAs of 256 threads per SM
+ferrox_status phase_configure(ferrox_batch* B) {
+  int dev = 0, sms = 0;
+  FX_BCK(cudaGetDevice(&dev));
+  FX_BCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const ferrox_status rc = batch_configure(B, 256, 1, 1, 0);
+  if (rc != FERROX_OK) return rc;
+  B->unit_blocks = 8 * sms;
+  return FERROX_OK;
+}
+
+// time each candidate launch shape on one step from a saved state, keep the fastest;
+// the candidates are the persistent kernel's shapes and the graph of per-phase launches
 ferrox_status batch_autotune(ferrox_batch* B) {
   const std::string key = batch_key(B);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     for (auto& kv : g_tune_cache)
-      if (kv.first == key)
+      if (kv.first == key) {
+        B->engine = kv.second.engine;
+        if (B->engine == 1) return phase_configure(B);
         return batch_configure(B, kv.second.threads, kv.second.rows, kv.second.bps, kv.second.grouped);
+      }
   }
   const size_t bytes = (size_t)B->cells * sizeof(double);
   cudaStream_t s = B->stream;
@@ -2023,16 +2061,59 @@ ferrox_status batch_autotune(ferrox_batch* B) {
       FX_BCK(cudaMemcpyAsync(B->stats, st0.data(), B->n * sizeof(DevStats), cudaMemcpyHostToDevice, s));
       FX_BCK(cudaStreamSynchronize(s));
     }
+  // the graph of per-phase launches: the better of two launches (the first uploads it)
+  int engine = 0;
+  {
+    ferrox_status rc = phase_configure(B);
+    if (rc != FERROX_OK) return rc;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    rc = phase_graph(B, 0, &g, &ge);
+    if (rc != FERROX_OK) return rc;
+    float pbest = 1e30f;
+    for (int rep = 0; rep < 2 && rc == FERROX_OK; ++rep) {
+      cudaError_t e = cudaEventRecord(e0, s);
+      if (e == cudaSuccess) e = cudaGraphLaunch(ge, s);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      int gst = 0;
+      if (e == cudaSuccess) e = cudaMemcpy(&gst, B->status, sizeof(int), cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) rc = bfail(B, FERROX_ECUDA, cudaGetErrorString(e));
+      else if (gst != 0) rc = bfail(B, (ferrox_status)gst, "phase graph failed while tuning");
+      pbest = std::min(pbest, ms);
+      if (rc == FERROX_OK) {
+        e = cudaMemcpyAsync(B->P, B->backup, bytes, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(B->phi, B->backup + B->cells, bytes, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(B->stats, st0.data(), B->n * sizeof(DevStats), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = bfail(B, FERROX_ECUDA, cudaGetErrorString(e));
+      }
+    }
+    cudaGraphExecDestroy(ge);
+    cudaGraphDestroy(g);
+    if (rc != FERROX_OK) return rc;
+    if (pbest < best) engine = 1;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune_cache.push_back({key, {bt, bR, bB, bG}});
+    g_tune_cache.push_back({key, {bt, bR, bB, bG, engine}});
   }
+  B->engine = engine;
+  if (engine == 1) return phase_configure(B);
   return batch_configure(B, bt, bR, bB, bG);
 }
 
 ferrox_status batch_build_graphs(ferrox_batch* B) {
+  if (B->engine == 1) {
+    ferrox_status rc = phase_graph(B, 0, &B->gr_step, &B->ge_step);
+    if (rc == FERROX_OK) rc = phase_graph(B, 1, &B->gr_solve, &B->ge_solve);
+    return rc;
+  }
   for (int mode = 0; mode < 2; ++mode) {
     cudaGraph_t g = nullptr;
     cudaGraphExec_t ge = nullptr;
@@ -2064,6 +2145,7 @@ void batch_release(ferrox_batch* B) {
   for (void* p : ptrs) if (p) cudaFree(p);
   if (B->host_pinned) cudaFreeHost(B->host_pinned);
   if (B->cap) cudaStreamDestroy(B->cap);
+  if (B->cap2) cudaStreamDestroy(B->cap2);
   delete B;
 }
 
@@ -2160,6 +2242,7 @@ ferrox_status ferrox_init_batch(ferrox_batch** out, int n, const ferrox_geometry
   const size_t tsz = B->tsz;
   const bool has_sc = std::any_of(B->plans.begin(), B->plans.end(), [](const BatchPlan& p) { return p.c.has_sc; });
   FX_BINIT(cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking));
+  FX_BINIT(cudaStreamCreateWithFlags(&B->cap2, cudaStreamNonBlocking));
   FX_BINIT(cudaMalloc(&B->b, cells * sizeof(double)));
   FX_BINIT(cudaMalloc(&B->Pbuf, cells * sizeof(double)));
   FX_BINIT(cudaMalloc(&B->backup, 2 * cells * sizeof(double)));
@@ -2271,6 +2354,7 @@ ferrox_status ferrox_init_batch(ferrox_batch** out, int n, const ferrox_geometry
   FX_BINIT(cudaMemset(B->stats, 0, n * sizeof(DevStats)));
   FX_BINIT(cudaMemset(B->params, 0, n * sizeof(DevParams)));
   FX_BINIT(B->mixed ? batch_prepare<float>(B->smem) : batch_prepare<double>(B->smem));
+  FX_BINIT(B->mixed ? phase_prepare<float>(B->smem) : phase_prepare<double>(B->smem));
   ferrox_status rc = batch_configure(B, 512, 1);
   if (rc != FERROX_OK) return cleanup(rc);
   FX_BINIT(cudaDeviceSynchronize());
@@ -2309,6 +2393,10 @@ ferrox_status ferrox_batch_step(ferrox_batch* B, int nsteps) {
     rc = batch_build_graphs(B);
     if (rc != FERROX_OK) return rc;
     B->tuned = true;
+  }
+  if (B->engine == 1) {   // the phase graph is one step
+    for (int k = 0; k < nsteps; ++k) FX_BCK(cudaGraphLaunch(B->ge_step, B->stream));
+    return FERROX_OK;
   }
   // pageable source: staged before the call returns, so the graph reads this count
   FX_BCK(cudaMemcpyAsync(B->nsteps_d, &nsteps, sizeof(int), cudaMemcpyHostToDevice, B->stream));
@@ -2384,8 +2472,32 @@ ferrox_status ferrox_batch_tuning(const ferrox_batch* B, int* threads, int* rows
   if (!B) return FERROX_EINVAL;
   if (threads) *threads = B->threads;
   if (rows_per_unit) *rows_per_unit = B->rows_per_unit;
-  if (blocks) *blocks = B->blocks;
+  if (blocks) *blocks = B->engine == 1 ? B->unit_blocks : B->blocks;
   return B->tuned ? FERROX_OK : FERROX_ESTATE;
+}
+
+ferrox_status ferrox_batch_engine(const ferrox_batch* B, int* engine) {
+  if (!B || !engine) return FERROX_EINVAL;
+  *engine = B->engine;
+  return B->tuned ? FERROX_OK : FERROX_ESTATE;
+}
+
+ferrox_status ferrox_batch_set_engine(ferrox_batch* B, int engine) {
+  if (!B) return bfail(nullptr, FERROX_EINVAL, "null batch");
+  if (engine != 0 && engine != 1) return bfail(B, FERROX_EINVAL, "engine must be 0 or 1");
+  FX_BCK(cudaStreamSynchronize(B->stream));
+  B->engine = engine;
+  const ferrox_status rc0 = engine == 1 ? phase_configure(B)
+                                        : batch_configure(B, B->threads, B->rows_per_unit, 1, B->grouped);
+  if (rc0 != FERROX_OK) return rc0;
+  if (B->ge_step) { cudaGraphExecDestroy(B->ge_step); B->ge_step = nullptr; }
+  if (B->ge_solve) { cudaGraphExecDestroy(B->ge_solve); B->ge_solve = nullptr; }
+  if (B->gr_step) { cudaGraphDestroy(B->gr_step); B->gr_step = nullptr; }
+  if (B->gr_solve) { cudaGraphDestroy(B->gr_solve); B->gr_solve = nullptr; }
+  const ferrox_status rc = batch_build_graphs(B);
+  if (rc != FERROX_OK) return rc;
+  B->tuned = true;
+  return FERROX_OK;
 }
 
 ferrox_status ferrox_batch_set_shape(ferrox_batch* B, int threads, int rows_per_unit,
@@ -2400,6 +2512,7 @@ ferrox_status ferrox_batch_set_shape(ferrox_batch* B, int threads, int rows_per_
                   : batch_occupancy<double>(threads, B->smem, &per_sm));
   if (ctas_per_sm > per_sm) return bfail(B, FERROX_EINVAL, "that many CTAs per SM do not fit");
   FX_BCK(cudaStreamSynchronize(B->stream));
+  B->engine = 0;
   ferrox_status rc = batch_configure(B, threads, rows_per_unit, ctas_per_sm, grouped);
   if (rc != FERROX_OK) return rc;
   if (B->ge_step) { cudaGraphExecDestroy(B->ge_step); B->ge_step = nullptr; }

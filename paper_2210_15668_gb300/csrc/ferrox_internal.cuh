@@ -8,6 +8,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <cstring>
 
 #include "../../include/ferrox.h"
 
@@ -57,15 +58,20 @@ constexpr int kTailMaxSmem = 200 * 1024; // shared memory available to the tail 
 constexpr int kResidBX = 32, kResidBY = 8; // residual: one thread per (x, y) column
 
 // Copy of a read-only table entry through the read-only data path (8-byte
-// loads); fields the caller never uses are removed by the compiler.
+// loads); fields the caller never uses are removed by the compiler.  The words
+// land in an integer buffer and reach the struct by memcpy: storing them through
+// an integer pointer into the struct and then reading its double or int fields
+// breaks the aliasing rules, and the optimiser may then read fields it considers
+// never written.
 template <typename S>
 __device__ __forceinline__ S ldg_struct(const S* p) {
   static_assert(sizeof(S) % 8 == 0, "table entries are padded to 8 bytes");
-  S out;
+  unsigned long long w[sizeof(S) / 8];
   const unsigned long long* src = reinterpret_cast<const unsigned long long*>(p);
-  unsigned long long* dst = reinterpret_cast<unsigned long long*>(&out);
 #pragma unroll
-  for (int q = 0; q < (int)(sizeof(S) / 8); ++q) dst[q] = __ldg(src + q);
+  for (int q = 0; q < (int)(sizeof(S) / 8); ++q) w[q] = __ldg(src + q);
+  S out;
+  memcpy(&out, w, sizeof(S));
   return out;
 }
 
@@ -427,6 +433,12 @@ template <typename T>
 cudaError_t batch_occupancy(int threads, size_t smem, int* blocks_per_sm);
 template <typename T>
 cudaError_t launch_batch(const BatchArgs& a, int blocks, int threads, size_t smem, cudaStream_t s);
+// the batched step as a graph of per-phase launches (same results as batch_kernel)
+template <typename T>
+cudaError_t phase_prepare(size_t tail_smem);
+template <typename T>
+cudaError_t capture_phases(const BatchArgs& a, int unit_blocks, size_t tail_smem, cudaStream_t s,
+                           cudaStream_t s2);
 void launch_set_params(DevParams* p, double v_bot, double v_top, cudaStream_t s);
 void launch_static_b(double* b, const PlaneTDGL* planes, const DevParams* prm, int nx, int ny,
                      int nz, cudaStream_t s);

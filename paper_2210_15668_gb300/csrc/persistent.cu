@@ -347,6 +347,98 @@ __global__ void __launch_bounds__(512, 1) batch_kernel(BatchArgs A) {
 #undef FX_BAR
 }
 
+// ---- the same phases as separate kernels of a CUDA graph -----------------------------
+// One launch per phase over the whole grid (a single CTA group spanning every
+// instance), so each phase keeps only its own registers, and kernel boundaries
+// take the place of the grid barriers.  The work units, the per-cell operations
+// and the per-instance sums are those of batch_kernel, so the two engines give
+// identical results.
+
+template <typename T>
+__device__ __forceinline__ MGArgs<T> batch_mg(const BatchArgs& A) {
+  MGArgs<T> mg;
+  mg.e = static_cast<T*>(A.e);
+  mg.r = static_cast<T*>(A.r);
+  mg.s = static_cast<T*>(A.s);
+  mg.coef = static_cast<const PlaneCoef<T>*>(A.coef);
+  mg.lv = A.lv;
+  return mg;
+}
+
+// warps of the whole grid share the units; CTAs are ranked for the per-instance tail
+template <typename T>
+__device__ __forceinline__ Ctx<T> grid_ctx(const BatchArgs& A) {
+  const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+  return Ctx<T>{A, batch_mg<T>(A), (int)(threadIdx.x & 31), gwarp, nwarps, 0, A.ninst, (int)blockIdx.x,
+                (int)gridDim.x};
+}
+
+__global__ void __launch_bounds__(256) ph_activate_kernel(BatchArgs A) {
+  pdl_enter();
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.ninst; i += gridDim.x * blockDim.x)
+    A.active[i] = 1;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) ph_tdgl_kernel(BatchArgs A, int mode) {
+  pdl_enter();
+  phase_tdgl(grid_ctx<T>(A), mode);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) ph_resid_kernel(BatchArgs A, int first, int copy_back) {
+  pdl_enter();
+  phase_resid(grid_ctx<T>(A), first, copy_back);
+}
+
+// the per-instance decisions in one CTA, then WHILE = any instance still active
+template <typename T>
+__global__ void __launch_bounds__(1024) ph_decide_kernel(BatchArgs A, int first, unsigned long long handle) {
+  pdl_enter();
+  const Ctx<T> c{A, batch_mg<T>(A), (int)(threadIdx.x & 31), (int)(threadIdx.x >> 5), (int)(blockDim.x >> 5),
+                 0, A.ninst, 0, 1};
+  phase_decide(c, first);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int any = 0;
+    for (int i = 0; i < A.ninst; ++i) any |= A.active[i];
+    cudaGraphSetConditional((cudaGraphConditionalHandle)handle, any ? 1u : 0u);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) ph_smooth_kernel(BatchArgs A, int l, int color, int zero_init,
+                                                        int fuse_update) {
+  pdl_enter();
+  phase_smooth(grid_ctx<T>(A), l, color, zero_init, fuse_update);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) ph_transfer_kernel(BatchArgs A, int l, int op) {
+  pdl_enter();
+  phase_transfer(grid_ctx<T>(A), l, op);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) ph_tail_kernel(BatchArgs A) {
+  extern __shared__ __align__(16) unsigned char psmem[];
+  pdl_enter();
+  phase_tail(grid_ctx<T>(A), psmem);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) ph_update_kernel(BatchArgs A) {
+  pdl_enter();
+  phase_update(grid_ctx<T>(A));
+}
+
+__global__ void ph_steps_kernel(BatchArgs A) {
+  pdl_enter();
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.ninst; i += gridDim.x * blockDim.x)
+    A.inst[i].resid.stats->steps += 1;
+}
+
 // Failure-detection check: block 1 never arrives, so block 0's bounded wait
 // must run out and record FERROX_ETIMEOUT.
 __global__ void barrier_timeout_kernel(GridBar* gb, int* status, long long limit) {
@@ -386,6 +478,76 @@ cudaError_t launch_batch(const BatchArgs& a, int blocks, int threads, size_t sme
   return cudaLaunchKernelEx(&cfg, batch_kernel<T>, a);
 }
 
+template <typename T>
+cudaError_t phase_prepare(size_t tail_smem) {
+  return cudaFuncSetAttribute(ph_tail_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tail_smem);
+}
+
+// One time step (mode 0) or one Poisson solve (mode 1) of every instance as a
+// sequence of phase launches on the capturing stream s, the solve loop in a
+// WHILE node whose body is captured on s2 (the conditional handle is created
+// on the graph s is capturing into).
+template <typename T>
+cudaError_t capture_phases(const BatchArgs& a, int unit_blocks, size_t tail_smem, cudaStream_t s,
+                           cudaStream_t s2) {
+  cudaError_t e;
+  const dim3 ub(unit_blocks), ut(256);
+  const int mode = a.mode;
+  if ((e = launch_k(ph_activate_kernel, dim3(1), dim3(256), 0, s, a)) != cudaSuccess) return e;
+  if ((e = launch_k(ph_tdgl_kernel<T>, ub, ut, 0, s, a, mode == 1 ? 3 : 0)) != cudaSuccess) return e;
+  if ((e = launch_k(ph_resid_kernel<T>, ub, ut, 0, s, a, 1, mode == 0 ? 1 : 0)) != cudaSuccess) return e;
+  cudaStreamCaptureStatus st;
+  cudaGraph_t g;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  if ((e = cudaStreamGetCaptureInfo(s, &st, nullptr, &g, nullptr, nullptr, nullptr)) != cudaSuccess) return e;
+  cudaGraphConditionalHandle h;
+  if ((e = cudaGraphConditionalHandleCreate(&h, g, 0, 0)) != cudaSuccess) return e;
+  if ((e = launch_k(ph_decide_kernel<T>, dim3(1), dim3(1024), 0, s, a, 1, (unsigned long long)h)) != cudaSuccess)
+    return e;
+  if ((e = cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, nullptr, &nd)) != cudaSuccess) return e;
+  cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cn;
+  if ((e = cudaGraphAddNode(&cn, g, deps, nullptr, nd, &cp)) != cudaSuccess) return e;
+  if ((e = cudaStreamBeginCaptureToGraph(s2, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                         cudaStreamCaptureModeRelaxed)) != cudaSuccess)
+    return e;
+  // one V-cycle on the active instances, then their residual and decisions
+  for (int l = 0; l < a.Ldown; ++l) {
+    for (int sw = 0; sw < a.nu1; ++sw) {
+      launch_k(ph_smooth_kernel<T>, ub, ut, 0, s2, a, l, 0, sw == 0 ? 1 : 0, 0);
+      launch_k(ph_smooth_kernel<T>, ub, ut, 0, s2, a, l, 1, 0, 0);
+    }
+    launch_k(ph_transfer_kernel<T>, ub, ut, 0, s2, a, l, 0);
+  }
+  launch_k(ph_tail_kernel<T>, dim3(a.ninst), dim3(512), tail_smem, s2, a);
+  for (int l = a.Ldown - 1; l >= 0; --l) {
+    launch_k(ph_transfer_kernel<T>, ub, ut, 0, s2, a, l, 1);
+    for (int sw = 0; sw < a.nu2; ++sw) {
+      launch_k(ph_smooth_kernel<T>, ub, ut, 0, s2, a, l, 0, 0, 0);
+      launch_k(ph_smooth_kernel<T>, ub, ut, 0, s2, a, l, 1, 0, (l == 0 && sw == a.nu2 - 1) ? 1 : 0);
+    }
+  }
+  if (a.any_full_tail || a.nu2 == 0) launch_k(ph_update_kernel<T>, ub, ut, 0, s2, a);
+  launch_k(ph_resid_kernel<T>, ub, ut, 0, s2, a, 0, 0);
+  launch_k(ph_decide_kernel<T>, dim3(1), dim3(1024), 0, s2, a, 0, (unsigned long long)h);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  cudaGraph_t body_out;
+  if ((e = cudaStreamEndCapture(s2, &body_out)) != cudaSuccess) return e;
+  if ((e = cudaStreamUpdateCaptureDependencies(s, &cn, nullptr, 1, cudaStreamSetCaptureDependencies)) !=
+      cudaSuccess)
+    return e;
+  if (mode == 0) launch_k(ph_steps_kernel, dim3(1), dim3(256), 0, s, a);
+  return cudaGetLastError();
+}
+
+template cudaError_t phase_prepare<double>(size_t);
+template cudaError_t phase_prepare<float>(size_t);
+template cudaError_t capture_phases<double>(const BatchArgs&, int, size_t, cudaStream_t, cudaStream_t);
+template cudaError_t capture_phases<float>(const BatchArgs&, int, size_t, cudaStream_t, cudaStream_t);
 template cudaError_t batch_prepare<double>(size_t);
 template cudaError_t batch_prepare<float>(size_t);
 template cudaError_t batch_occupancy<double>(int, size_t, int*);

@@ -65,7 +65,7 @@ EXPORTS = ["ferrox_init_geometry", "ferrox_set_bias", "ferrox_solve_poisson", "f
            "ferrox_tdgl_update_static",
            "ferrox_init_batch", "ferrox_batch_set_bias", "ferrox_batch_solve_poisson",
            "ferrox_batch_step", "ferrox_batch_charge", "ferrox_batch_stats", "ferrox_batch_tuning",
-           "ferrox_batch_groups", "ferrox_batch_set_shape",
+           "ferrox_batch_groups", "ferrox_batch_set_shape", "ferrox_batch_engine", "ferrox_batch_set_engine",
            "ferrox_batch_destroy", "ferrox_batch_last_error", "ferrox_check_wait_timeout",
            "ferrox_carrier_exp", "ferrox_carrier_exp_df",
            "ferrox_nn_create", "ferrox_nn_forward", "ferrox_nn_loss_grad", "ferrox_nn_params",
@@ -122,6 +122,8 @@ def load(path: str = LIB_PATH):
     lib.ferrox_batch_tuning.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
     lib.ferrox_batch_groups.argtypes = [vp, C.POINTER(C.c_int)]
     lib.ferrox_batch_set_shape.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int]
+    lib.ferrox_batch_engine.argtypes = [vp, C.POINTER(C.c_int)]
+    lib.ferrox_batch_set_engine.argtypes = [vp, C.c_int]
     lib.ferrox_batch_destroy.argtypes = [vp]
     lib.ferrox_batch_last_error.argtypes = [vp]
     lib.ferrox_batch_last_error.restype = C.c_char_p
@@ -406,8 +408,14 @@ class Batch:
         rc = self.lib.ferrox_batch_tuning(self.ctx, C.byref(t), C.byref(r), C.byref(b))
         g = C.c_int()
         self.lib.ferrox_batch_groups(self.ctx, C.byref(g))
+        e = C.c_int()
+        self.lib.ferrox_batch_engine(self.ctx, C.byref(e))
         return dict(threads=t.value, rows_per_unit=r.value, blocks=b.value, groups=g.value,
-                    tuned=rc == FERROX_OK)
+                    engine=e.value, tuned=rc == FERROX_OK)
+
+    def set_engine(self, engine):
+        """0: one persistent launch; 1: the graph of per-phase launches (same results)."""
+        self._ck(self.lib.ferrox_batch_set_engine(self.ctx, int(engine)))
 
     def set_shape(self, threads, rows_per_unit, ctas_per_sm, grouped):
         """Fix the launch shape instead of autotuning it (same results, other speed)."""

@@ -158,3 +158,51 @@ def test_launch_shapes_give_identical_results():
         assert cycles == outs[0][1]
         for (P, phi), (P0, phi0) in zip(states, outs[0][0]):
             assert np.array_equal(P, P0) and np.array_equal(phi, phi0)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_phase_graph_engine_matches_persistent(precision):
+    """The graph of per-phase launches runs the persistent kernel's work units with
+    the same operations and per-instance sums: bit-identical states and equal cycle
+    and V-cycle counts after Step 0 and five steps, instances of uneven sizes
+    (including the 96^2 and 128^2 ones of the sweep) and biases."""
+    from paper_2210_15668_gb300 import ferrox
+    rng = np.random.default_rng(21)
+    sizes = [32, 128, 48, 96, 64, 32]
+    geoms = [I.make_geometry(s, s, I.mfim_stack(16)) for s in sizes]
+    P0s = [I.random_polarization(g, seed=200 + i) for i, g in enumerate(geoms)]
+    biases = rng.uniform(-2.0, 2.0, size=len(geoms))
+    num = ferrox.make_numerics(4e-13, tol=1e-10, precision=precision)
+    outs = []
+    for engine in (0, 1):
+        B = ferrox.Batch(geoms, P0s, num)
+        if engine == 0:
+            B.set_shape(256, 1, 1, 0)
+        else:
+            B.set_engine(1)
+        assert B.tuning()["engine"] == engine
+        B.set_bias(np.zeros(len(geoms)), biases)
+        B.solve_poisson()
+        B.step(5)
+        st = B.stats()
+        assert all(x["status"] == 0 and x["steps"] == 5 for x in st)
+        outs.append(([B.state(i) for i in range(len(geoms))],
+                     [(x["cycles"], x["vcycles"], x["solves"]) for x in st]))
+        B.close()
+    (s0, c0), (s1, c1) = outs
+    assert c1 == c0
+    # both carry the full coarse-grid correction: the single-instance solver needs
+    # 6-8 V-cycles per solve on these stacks, a V-cycle whose coarse levels
+    # correct too little 18 or more
+    assert all(c / s <= 10 for c, _, s in c0), c0
+    for (P, phi), (Pr, phir) in zip(s1, s0):
+        assert np.array_equal(P, Pr) and np.array_equal(phi, phir)
+
+
+def test_set_engine_rejects_other_values():
+    from paper_2210_15668_gb300 import ferrox
+    geoms, P0s, _ = small_batch(n=2)
+    B = ferrox.Batch(geoms, P0s, ferrox.make_numerics(4e-13))
+    with pytest.raises(ferrox.FerroxError, match="EINVAL"):
+        B.set_engine(2)
+    B.close()
