@@ -274,14 +274,18 @@ __device__ __forceinline__ int div32(int t, unsigned long long m) {
   return (int)(((unsigned long long)(unsigned)t * m) >> 32);
 }
 
-// tail_smooth and tail_vcycle are kept out of line.  Inlined into their callers,
-// the FP64 instantiation lost the tail's smoothing (the first tail level kept
-// its old shared-memory contents; measured in the batched engines: 35 V-cycles
-// per solve instead of 8 on a 32x32x16 stack), depending only on the
-// surrounding code; out of line both batched engines and the single-instance
-// tail give the same, expected correction.
+// FX_TAIL_LINKAGE: how tail_smooth and tail_vcycle are compiled in this
+// translation unit.  The batched engines (persistent.cu) set __noinline__:
+// inlined there, the FP64 instantiation lost the tail's smoothing (the first
+// tail level kept its old shared-memory contents; 35 V-cycles per solve instead
+// of 8 on a 32x32x16 stack), depending only on the surrounding code.  The
+// single-instance tail kernel inlines them (same V-cycle counts either way,
+// checked by the solver tests' cycle bounds).
+#ifndef FX_TAIL_LINKAGE
+#define FX_TAIL_LINKAGE
+#endif
 template <typename T>
-__device__ __noinline__ void tail_smooth(const MGArgs<T>& a, const LevelDesc& L, int sweeps, int zero_first) {
+__device__ FX_TAIL_LINKAGE void tail_smooth(const MGArgs<T>& a, const LevelDesc& L, int sweeps, int zero_first) {
   const int hx = (L.nx + 1) >> 1;
   const int items = hx * L.ny * L.nz;
   const unsigned long long mx = magic32(hx), my = magic32(L.ny);
@@ -320,7 +324,7 @@ __device__ void tail_dense(const T* __restrict__ inv, int n, const T* r, T* e) {
 // levels below it are not visited; otherwise the coarsest level is relaxed
 // t.bottom_sweeps times.
 template <typename T>
-__device__ __noinline__ void tail_vcycle(const MGArgs<T>& g, const TailArgs& t, unsigned char* tail_smem) {
+__device__ FX_TAIL_LINKAGE void tail_vcycle(const MGArgs<T>& g, const TailArgs& t, unsigned char* tail_smem) {
   T* se = reinterpret_cast<T*>(tail_smem);
   T* sr = se + t.elems;
   T* ss = g.s ? sr + t.elems : nullptr;

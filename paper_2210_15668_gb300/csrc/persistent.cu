@@ -17,6 +17,9 @@
 #include <cuda_runtime.h>
 
 #include "ferrox_internal.cuh"
+#ifndef FX_TAIL_LINKAGE
+#define FX_TAIL_LINKAGE __noinline__   // see mg_device.cuh
+#endif
 #include "mg_device.cuh"
 #include "tdgl_device.cuh"
 
