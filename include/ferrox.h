@@ -478,9 +478,8 @@ ferrox_status ferrox_attach_nn(ferrox_ctx* ctx, ferrox_nn* nn, int mode);
  * calls.  All calls share the one array: calls whose GPU work overlaps (two
  * streams, or two host threads) race and must be serialised by the caller.
  * The first call on each device looks up the array's device address with
- * that device current; make that first call before any stream capture.  The
- * plane table is copied from pageable host memory, so the call waits for
- * work already queued on the stream before it returns. */
+ * that device current.  The plane table is copied from pageable host memory,
+ * so the call waits for work already queued on the stream before it returns. */
 ferrox_status ferrox_tdgl_update_static(const ferrox_geometry* geom, double dt, double v_bottom,
                                         double v_top, double* P_dev, const double* phi_dev,
                                         void* cuda_stream);

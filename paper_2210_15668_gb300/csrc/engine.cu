@@ -1998,11 +1998,11 @@ ferrox_status phase_graph(ferrox_batch* B, int mode, cudaGraph_t* g, cudaGraphEx
 }
 
 // the per-phase launches: one-row units, eight CTAs of 256 threads per SM
-ferrox_status phase_configure(ferrox_batch* B) {
+ferrox_status phase_configure(ferrox_batch* B, int R = 1) {
   int dev = 0, sms = 0;
   FX_BCK(cudaGetDevice(&dev));
   FX_BCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const ferrox_status rc = batch_configure(B, 256, 1, 1, 0);
+  const ferrox_status rc = batch_configure(B, 256, R, 1, 0);
   if (rc != FERROX_OK) return rc;
   B->unit_blocks = 8 * sms;
   return FERROX_OK;
@@ -2017,7 +2017,7 @@ ferrox_status batch_autotune(ferrox_batch* B) {
     for (auto& kv : g_tune_cache)
       if (kv.first == key) {
         B->engine = kv.second.engine;
-        if (B->engine == 1) return phase_configure(B);
+        if (B->engine == 1) return phase_configure(B, kv.second.rows);
         return batch_configure(B, kv.second.threads, kv.second.rows, kv.second.bps, kv.second.grouped);
       }
   }
@@ -2061,10 +2061,11 @@ ferrox_status batch_autotune(ferrox_batch* B) {
       FX_BCK(cudaMemcpyAsync(B->stats, st0.data(), B->n * sizeof(DevStats), cudaMemcpyHostToDevice, s));
       FX_BCK(cudaStreamSynchronize(s));
     }
-  // the graph of per-phase launches: the better of two launches (the first uploads it)
-  int engine = 0;
-  {
-    ferrox_status rc = phase_configure(B);
+  // the graph of per-phase launches with 1, 2 or 4 rows per work unit: the
+  // better of two launches each (the first uploads the graph)
+  int engine = 0, pR = 1;
+  for (int ri = 0; ri < 3; ++ri) {
+    ferrox_status rc = phase_configure(B, cand_R[ri]);
     if (rc != FERROX_OK) return rc;
     cudaGraph_t g = nullptr;
     cudaGraphExec_t ge = nullptr;
@@ -2095,16 +2096,16 @@ ferrox_status batch_autotune(ferrox_batch* B) {
     cudaGraphExecDestroy(ge);
     cudaGraphDestroy(g);
     if (rc != FERROX_OK) return rc;
-    if (pbest < best) engine = 1;
+    if (pbest < best) { best = pbest; engine = 1; pR = cand_R[ri]; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune_cache.push_back({key, {bt, bR, bB, bG, engine}});
+    g_tune_cache.push_back({key, {bt, engine == 1 ? pR : bR, bB, bG, engine}});
   }
   B->engine = engine;
-  if (engine == 1) return phase_configure(B);
+  if (engine == 1) return phase_configure(B, pR);
   return batch_configure(B, bt, bR, bB, bG);
 }
 
