@@ -1805,6 +1805,7 @@ struct ferrox_batch {
   int ngroups = 1;
   bool grouped = false;
   int* status = nullptr;
+  unsigned int* ticket = nullptr;     // decision kernel of the graph engine: blocks done
   int* nsteps_d = nullptr;
   int* dbg = nullptr;
   DevParams* params = nullptr;
@@ -1877,6 +1878,7 @@ BatchArgs batch_args(ferrox_batch* B, int mode) {
   a.nu1 = B->num.nu1; a.nu2 = B->num.nu2; a.rows_per_unit = B->rows_per_unit;
   a.any_full_tail = B->any_full_tail;
   a.dbg = B->dbg;
+  a.ticket = B->ticket;
   return a;
 }
 
@@ -2141,7 +2143,7 @@ void batch_release(ferrox_batch* B) {
   if (B->gr_step) cudaGraphDestroy(B->gr_step);
   if (B->gr_solve) cudaGraphDestroy(B->gr_solve);
   void* ptrs[] = {B->b, B->Pbuf, B->backup, B->e, B->r, B->s, B->coef, B->dense, B->coef0, B->planes, B->lv,
-                  B->lvt, B->pre, B->partials, B->active, B->bar, B->grp_d, B->status, B->nsteps_d, B->dbg, B->params,
+                  B->lvt, B->pre, B->partials, B->active, B->bar, B->grp_d, B->status, B->ticket, B->nsteps_d, B->dbg, B->params,
                   B->stats, B->inst, B->charge_part, B->charge_out};
   for (void* p : ptrs) if (p) cudaFree(p);
   if (B->host_pinned) cudaFreeHost(B->host_pinned);
@@ -2261,6 +2263,8 @@ ferrox_status ferrox_init_batch(ferrox_batch** out, int n, const ferrox_geometry
   FX_BINIT(cudaMalloc(&B->bar, (size_t)n * sizeof(GridBar)));
   FX_BINIT(cudaMalloc(&B->grp_d, 2 * (size_t)(n + 1) * sizeof(int)));
   FX_BINIT(cudaMalloc(&B->status, sizeof(int)));
+  FX_BINIT(cudaMalloc(&B->ticket, sizeof(unsigned int)));
+  FX_BINIT(cudaMemset(B->ticket, 0, sizeof(unsigned int)));
   FX_BINIT(cudaMalloc(&B->nsteps_d, sizeof(int)));
   FX_BINIT(cudaMalloc(&B->dbg, (8 + 1024) * sizeof(int)));
   FX_BINIT(cudaMemset(B->dbg, 0, (8 + 1024) * sizeof(int)));

@@ -422,6 +422,7 @@ struct BatchArgs {
   double tol;
   int max_cycles, nu1, nu2, rows_per_unit, any_full_tail, pad;
   int* dbg;             // optional self-check record (null: off)
+  unsigned int* ticket; // graph engine: blocks of the decision kernel done (0 between launches)
 };
 
 cudaError_t launch_barrier_timeout(GridBar* gb, int* status, long long limit, cudaStream_t s);

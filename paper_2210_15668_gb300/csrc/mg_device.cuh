@@ -41,14 +41,25 @@ __device__ __forceinline__ T gs_numerator(const T* e, const T* r, const PlaneCoe
 
 struct Upd {
   double* phi;      // fine-level potential (null: no fused update)
-  double clamp;
+  double clamp;     // |e| limit of one update (infinite without carriers)
   int zero;         // set phi = 0 (degenerate zero right-hand side)
+  float clampf;     // the limit rounded to FP32 (FP32 corrections)
 };
 
+// phi += e, e clamped to [-clamp, clamp].  An FP32 correction is clamped in FP32
+// against the limit rounded to float and converted once: one FP64-pipe
+// conversion and one FP64 add per cell instead of a conversion, two FP64
+// min/max and the add (GB300 runs FP64 at 1/58 of the FP32 rate).  With an
+// infinite limit (no carriers) the result is the same bit for bit.
 template <typename T>
 __device__ __forceinline__ void apply_update(const Upd& u, int idx, T e) {
-  if (u.zero) u.phi[idx] = 0.0;
-  else u.phi[idx] += fmin(fmax((double)e, -u.clamp), u.clamp);
+  if (u.zero) {
+    u.phi[idx] = 0.0;
+  } else if constexpr (sizeof(T) == sizeof(float)) {
+    u.phi[idx] += (double)fminf(fmaxf(e, -u.clampf), u.clampf);
+  } else {
+    u.phi[idx] += fmin(fmax(e, -u.clamp), u.clamp);
+  }
 }
 
 // One red/black pair position (ip) of a row: update the cell of `color`; on a
@@ -289,7 +300,7 @@ __device__ FX_TAIL_LINKAGE void tail_smooth(const MGArgs<T>& a, const LevelDesc&
   const int hx = (L.nx + 1) >> 1;
   const int items = hx * L.ny * L.nz;
   const unsigned long long mx = magic32(hx), my = magic32(L.ny);
-  const Upd none{nullptr, 0.0, 0};
+  const Upd none{nullptr, 0.0, 0, 0.0f};
   for (int sw = 0; sw < sweeps; ++sw)
     for (int color = 0; color < 2; ++color) {
       const int zi = (zero_first && sw == 0 && color == 0);

@@ -631,7 +631,7 @@ __global__ void __launch_bounds__(256) update_kernel(double* __restrict__ phi, c
                                                      long long n, const DevStats* stats,
                                                      double clamp, T* zero_e) {
   pdl_enter();
-  const Upd u{phi, clamp, stats->zero_phi};
+  const Upd u{phi, clamp, stats->zero_phi, (float)clamp};
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
        t += (long long)gridDim.x * blockDim.x) {
     apply_update(u, t, e0[t]);
@@ -691,9 +691,9 @@ void launch_smooth(const MGArgs<T>& a, const LevelDesc& L, int color, int zero_i
   dim3 block, grid;
   block_shape((L.nx + 1) >> 1, L.ny, block, grid, L.nz,
               spread_threads((long long)((L.nx + 1) >> 1) * L.ny * L.nz));
-  Upd u{nullptr, 0.0, 0};
+  Upd u{nullptr, 0.0, 0, 0.0f};
   const DevStats* st = nullptr;
-  if (upd) { u.phi = upd->phi; u.clamp = upd->clamp; st = upd->stats; }
+  if (upd) { u.phi = upd->phi; u.clamp = upd->clamp; u.clampf = (float)upd->clamp; st = upd->stats; }
   launch_k(smooth_kernel<T>, grid, block, 0, s, a, L, color, zero_init, u, st, zero_stats);
 }
 
@@ -768,8 +768,8 @@ void launch_smooth_rb(const MGArgs<T>& a, const LevelDesc& L, const T* e_in, T* 
     r.nx = L.nx; r.ny = L.ny; r.nz = L.nz;
     r.kz = rb_kz(L);
     r.zero_init = zero_init;
-    r.u = Upd{nullptr, 0.0, 0};
-    if (upd) { r.u.phi = upd->phi; r.u.clamp = upd->clamp; r.st = upd->stats; }
+    r.u = Upd{nullptr, 0.0, 0, 0.0f};
+    if (upd) { r.u.phi = upd->phi; r.u.clamp = upd->clamp; r.u.clampf = (float)upd->clamp; r.st = upd->stats; }
     const dim3 grid((L.nx + kRbTX - 1) / kRbTX, (L.ny + kRbTY - 1) / kRbTY,
                     (L.nz + r.kz - 1) / r.kz);
     launch_k(smooth_rb_kernel, grid, dim3(256), rb_smem_bytes(zero_init, r.s != nullptr), s, r);
