@@ -1806,6 +1806,8 @@ struct ferrox_batch {
   bool grouped = false;
   int* status = nullptr;
   unsigned int* ticket = nullptr;     // decision kernel of the graph engine: blocks done
+  int* tile_pre = nullptr;            // graph engine's TDGL: prefix of column tiles per instance
+  int ntiles = 0;
   int* nsteps_d = nullptr;
   int* dbg = nullptr;
   DevParams* params = nullptr;
@@ -1879,6 +1881,8 @@ BatchArgs batch_args(ferrox_batch* B, int mode) {
   a.any_full_tail = B->any_full_tail;
   a.dbg = B->dbg;
   a.ticket = B->ticket;
+  a.tile_pre = B->tile_pre;
+  a.ntiles = B->ntiles;
   return a;
 }
 
@@ -2143,7 +2147,7 @@ void batch_release(ferrox_batch* B) {
   if (B->gr_step) cudaGraphDestroy(B->gr_step);
   if (B->gr_solve) cudaGraphDestroy(B->gr_solve);
   void* ptrs[] = {B->b, B->Pbuf, B->backup, B->e, B->r, B->s, B->coef, B->dense, B->coef0, B->planes, B->lv,
-                  B->lvt, B->pre, B->partials, B->active, B->bar, B->grp_d, B->status, B->ticket, B->nsteps_d, B->dbg, B->params,
+                  B->lvt, B->pre, B->partials, B->active, B->bar, B->grp_d, B->status, B->ticket, B->tile_pre, B->nsteps_d, B->dbg, B->params,
                   B->stats, B->inst, B->charge_part, B->charge_out};
   for (void* p : ptrs) if (p) cudaFree(p);
   if (B->host_pinned) cudaFreeHost(B->host_pinned);
@@ -2265,6 +2269,16 @@ ferrox_status ferrox_init_batch(ferrox_batch** out, int n, const ferrox_geometry
   FX_BINIT(cudaMalloc(&B->status, sizeof(int)));
   FX_BINIT(cudaMalloc(&B->ticket, sizeof(unsigned int)));
   FX_BINIT(cudaMemset(B->ticket, 0, sizeof(unsigned int)));
+  {
+    std::vector<int> tp(n + 1, 0);
+    for (int i = 0; i < n; ++i) {
+      const ferrox_ctx& c = B->plans[i].c;
+      tp[i + 1] = tp[i] + ((c.nx + kTdglTileX - 1) / kTdglTileX) * ((c.ny + kTdglTileY - 1) / kTdglTileY);
+    }
+    B->ntiles = tp[n];
+    FX_BINIT(cudaMalloc(&B->tile_pre, (n + 1) * sizeof(int)));
+    FX_BINIT(cudaMemcpy(B->tile_pre, tp.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice));
+  }
   FX_BINIT(cudaMalloc(&B->nsteps_d, sizeof(int)));
   FX_BINIT(cudaMalloc(&B->dbg, (8 + 1024) * sizeof(int)));
   FX_BINIT(cudaMemset(B->dbg, 0, (8 + 1024) * sizeof(int)));

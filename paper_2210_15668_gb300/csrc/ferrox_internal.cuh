@@ -56,6 +56,7 @@ constexpr int kDenseWide = 512;         // a first tail level up to this size (s
                                         // instead of the tail V-cycle
 constexpr int kTailMaxSmem = 200 * 1024; // shared memory available to the tail CTA
 constexpr int kResidBX = 32, kResidBY = 8; // residual: one thread per (x, y) column
+constexpr int kTdglTileX = 32, kTdglTileY = 2, kTdglChunks = 4;  // batched TDGL: column tile, z chunks
 
 // Copy of a read-only table entry through the read-only data path (8-byte
 // loads); fields the caller never uses are removed by the compiler.  The words
@@ -410,6 +411,8 @@ struct BatchArgs {
   const LevelDesc* lvt; // tail levels of all instances (shared-memory offsets)
   const void* dense;    // T: inverses of the instances' dense tail levels
   const int* pre;       // unit prefix tables: rows, smoothing rows per level, coarse rows per level
+  const int* tile_pre;  // graph engine's TDGL: prefix of 32 x 2 column tiles per instance
+  int ntiles;           // ... and their total
   int Ldown;            // deepest multi-block level count over instances
   double* partials;     // 3 per row unit
   int* active;          // per instance

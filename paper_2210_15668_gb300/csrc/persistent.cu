@@ -446,10 +446,66 @@ __global__ void __launch_bounds__(256) ph_activate_kernel(BatchArgs A) {
     A.active[i] = 1;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) ph_tdgl_kernel(BatchArgs A, int mode) {
+// TDGL update (or right-hand side only, mode 3) of the graph engine: one block per
+// 32 x 2 column tile of one instance, each column's dynamic planes split into
+// kTdglChunks chunks marched by one thread each.  A chunk's first and last right-
+// hand sides need the neighbouring chunks' new P, exchanged through shared memory.
+// The operations per cell are tdgl_column's (force_z, advance, rhs_value on the
+// same new-P values), so both engines give identical results; the persistent
+// kernel keeps one thread per column (its blocks are one-dimensional).
+__global__ void __launch_bounds__(kTdglTileX* kTdglTileY* kTdglChunks) ph_tdgl_chunk_kernel(BatchArgs A, int mode) {
   pdl_enter();
-  phase_tdgl(grid_ctx<T>(A), mode);
+  __shared__ double first_s[kTdglChunks][kTdglTileY][kTdglTileX], last_s[kTdglChunks][kTdglTileY][kTdglTileX];
+  const int inst = find_inst(A.tile_pre, A.ninst, (int)blockIdx.x);
+  TDGLArgs a = ldg_struct(A.inst + inst).tdgl;
+  a.mode = mode;
+  const int tile = (int)blockIdx.x - A.tile_pre[inst];
+  const int tiles_x = (a.nx + kTdglTileX - 1) / kTdglTileX;
+  const int ty_tile = tile / tiles_x, tx_tile = tile - ty_tile * tiles_x;
+  const int tx = threadIdx.x, ty = threadIdx.y, c = threadIdx.z;
+  const int i = tx_tile * kTdglTileX + tx, j = ty_tile * kTdglTileY + ty;
+  const bool col = i < a.nx && j < a.ny;
+  const int per = (a.kd_hi - a.kd_lo + 1 + kTdglChunks - 1) / kTdglChunks;
+  const int k0 = a.kd_lo + c * per, k1 = min(a.kd_hi, k0 + per - 1);   // empty when k0 > k1
+  const long long plane = (long long)a.nx * a.ny;
+  const long long cix = (long long)j * a.nx + i;
+  const double v_bot = a.params->v_bot, v_top = a.params->v_top;
+  double pm2 = 0.0, pm1 = 0.0, p_first = 0.0, p_second = 0.0;
+  if (col && k0 <= k1) {
+    const int im = (i == 0) ? a.nx - 1 : i - 1, ip = (i == a.nx - 1) ? 0 : i + 1;
+    const int jm = (j == 0) ? a.ny - 1 : j - 1, jp = (j == a.ny - 1) ? 0 : j + 1;
+    for (int k = k0; k <= k1; ++k) {
+      const long long t = k * plane + cix;
+      double pn = 0.0;
+      if (__ldg(&a.planes[k].fe)) {
+        if (mode == 3) {
+          pn = a.P_in[t];
+        } else {
+          const PlaneTDGL pt = ldg_struct(a.planes + k);
+          const double f = force_z(a, pt, a.planes, a.P_in, a.phi, t, k, i, j, im, ip, jm, jp, v_bot, v_top);
+          pn = advance(a, t, f);
+          a.P_out[t] = pn;
+        }
+      }
+      if (k == k0) p_first = pn;
+      if (k == k0 + 1) p_second = pn;
+      if (k >= k0 + 2) a.b[(k - 1) * plane + cix] = rhs_value(a, a.planes, k - 1, pm2, pm1, pn, v_bot, v_top);
+      pm2 = pm1;
+      pm1 = pn;
+    }
+    first_s[c][ty][tx] = p_first;
+    last_s[c][ty][tx] = pm1;
+  }
+  __syncthreads();
+  if (!col || k0 > k1) return;
+  const double below = k0 - 1 >= a.kd_lo ? last_s[c - 1][ty][tx] : 0.0;
+  const double above = k1 + 1 <= a.kd_hi ? first_s[c + 1][ty][tx] : 0.0;
+  if (k1 == k0) {
+    a.b[k0 * plane + cix] = rhs_value(a, a.planes, k0, below, p_first, above, v_bot, v_top);
+  } else {
+    a.b[k0 * plane + cix] = rhs_value(a, a.planes, k0, below, p_first, p_second, v_bot, v_top);
+    a.b[k1 * plane + cix] = rhs_value(a, a.planes, k1, pm2, pm1, above, v_bot, v_top);
+  }
 }
 
 template <typename T>
@@ -572,7 +628,9 @@ cudaError_t capture_phases(const BatchArgs& a, int unit_blocks, size_t tail_smem
   // the decision kernels' ticket starts every graph launch at 0
   if ((e = cudaMemsetAsync(a.ticket, 0, sizeof(unsigned int), s)) != cudaSuccess) return e;
   if ((e = launch_k(ph_activate_kernel, dim3(1), dim3(256), 0, s, a)) != cudaSuccess) return e;
-  if ((e = launch_k(ph_tdgl_kernel<T>, ub, ut, 0, s, a, mode == 1 ? 3 : 0)) != cudaSuccess) return e;
+  if ((e = launch_k(ph_tdgl_chunk_kernel, dim3(a.ntiles), dim3(kTdglTileX, kTdglTileY, kTdglChunks), 0, s, a,
+                    mode == 1 ? 3 : 0)) != cudaSuccess)
+    return e;
   if ((e = launch_k(ph_resid_kernel<T>, ub, ut, 0, s, a, 1, mode == 0 ? 1 : 0)) != cudaSuccess) return e;
   cudaStreamCaptureStatus st;
   cudaGraph_t g;
