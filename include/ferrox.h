@@ -312,17 +312,18 @@ const char* ferrox_last_error(const ferrox_ctx* ctx);
 ferrox_status ferrox_level_shape(const ferrox_ctx* ctx, int l, int* nx, int* ny, int* nz,
                                  int* nlevels);
 
-/* ---- batched persistent Q-V sweeps ----------------------------------------------------
+/* ---- batched Q-V sweeps -----------------------------------------------------------------
  * n independent device stacks (instances) of possibly different lateral size,
- * stack and bias, advanced together by ONE cooperative persistent kernel
- * launch per call: every phase of the time step runs over all instances at
- * once, separated by grid barriers whose waits are bounded in time (on expiry
- * the launch records FERROX_ETIMEOUT instead of hanging); each instance checks
- * its own convergence and drops out when done.  The launch is captured in a
- * CUDA graph.  Its shape (threads per block, rows per work unit) is chosen by
- * timing the candidates on the first ferrox_batch_step, on a saved copy of
- * the state that is restored afterwards, and cached per problem shape.
- * This serves the Q-V sweeps of the Results section (many biases and sizes). */
+ * stack and bias, advanced together: every phase of the time step runs over all
+ * instances at once, and each instance checks its own convergence and drops out
+ * when done.  Two engines (ferrox_batch_engine): ONE cooperative persistent
+ * kernel per call with grid barriers between the phases, whose waits are
+ * bounded in time (on expiry the launch records FERROX_ETIMEOUT instead of
+ * hanging), or a CUDA graph of per-phase launches.  The engine and its shape
+ * (threads per block, rows per work unit) are chosen by timing the candidates
+ * on the first ferrox_batch_step, on a saved copy of the state that is
+ * restored afterwards, and cached per problem shape.  This serves the Q-V
+ * sweeps of the Results section (many biases and sizes). */
 typedef struct ferrox_batch ferrox_batch; /* opaque */
 
 /* Instances are uniaxial (ncomp = 1) and use order-1 steps.  P_dev and phi_dev
@@ -342,29 +343,32 @@ ferrox_status ferrox_batch_step(ferrox_batch* b, int nsteps);
 ferrox_status ferrox_batch_charge(ferrox_batch* b, ferrox_charge_t* out);
 /* Counters and status of every instance (array of n).  Synchronises. */
 ferrox_status ferrox_batch_stats(ferrox_batch* b, ferrox_stats* out);
-/* The launch shape the autotuner chose (ESTATE before the first step). */
+/* The launch shape the autotuner chose (ESTATE before the first step); with the
+ * phase graph, threads and blocks are those of its per-phase launches. */
 ferrox_status ferrox_batch_tuning(const ferrox_batch* b, int* threads, int* rows_per_unit,
                                   int* blocks);
 /* CTA groups of the tuned launch: 1 when every CTA works on every instance
  * behind one grid barrier; more when contiguous instance ranges run on their
  * own CTAs behind their own barriers. */
 ferrox_status ferrox_batch_groups(const ferrox_batch* b, int* ngroups);
-/* Fix the launch shape instead of autotuning it: threads per CTA (256 or 512),
- * rows per work unit (1, 2 or 4), CTAs per SM (1 .. what fits) and grouped (0:
- * one grid barrier over every instance; 1: CTA groups with their own barriers).
- * Every shape computes the same results; only the speed differs. */
+/* Fix the persistent engine and its launch shape instead of autotuning them:
+ * threads per CTA (256 or 512), rows per work unit (1, 2 or 4), CTAs per SM
+ * (1 .. what fits) and grouped (0: one grid barrier over every instance; 1: CTA
+ * groups with their own barriers).  Every shape computes the same results; only
+ * the speed differs. */
 ferrox_status ferrox_batch_set_shape(ferrox_batch* b, int threads, int rows_per_unit,
                                      int ctas_per_sm, int grouped);
 /* The engine the autotuner chose (ESTATE before the first step): 0 = one
  * persistent launch with grid barriers between its phases; 1 = a CUDA graph of
  * per-phase launches (TDGL, residual, per-instance decision, each level's colour
  * sweeps and transfers, the per-instance tails) whose solve loop is a WHILE node
- * the decision kernel sets while any instance is above the tolerance.  Both run
- * the same work units with the same operations and per-instance sums, so they
- * give identical results; only the speed differs. */
+ * the decision kernel sets while any instance is above the tolerance.  Both do
+ * the same operations per cell in the same order and form the same per-instance
+ * sums, so they give identical results; only the speed differs. */
 ferrox_status ferrox_batch_engine(const ferrox_batch* b, int* engine);
 /* Fix the engine instead of autotuning it (0 with the current shape at one CTA
- * per SM, or 1).  EINVAL for other values.  Synchronises. */
+ * per SM, or 1 with one row per work unit).  EINVAL for other values.
+ * Synchronises. */
 ferrox_status ferrox_batch_set_engine(ferrox_batch* b, int engine);
 ferrox_status ferrox_batch_destroy(ferrox_batch* b);
 

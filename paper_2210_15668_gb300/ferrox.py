@@ -343,7 +343,8 @@ class Device:
 
 
 class Batch:
-    """n independent device stacks advanced by one persistent launch per call.
+    """n independent device stacks advanced together (one persistent launch per call, or a
+    CUDA graph of per-phase launches: the autotuner picks).
 
     geoms: list of geometry dicts (ncomp = 1); P0s: list of (1, Nz, Ny, Nx) arrays.
     The state lives in two packed torch tensors (instances back to back)."""
