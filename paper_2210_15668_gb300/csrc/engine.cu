@@ -2345,8 +2345,10 @@ ferrox_status ferrox_init_batch(ferrox_batch** out, int n, const ferrox_geometry
     ra.r_out = static_cast<char*>(B->r) + (size_t)p.arena_off * tsz;
     ra.s_out = has_sc && c.has_sc ? static_cast<char*>(B->s) + (size_t)p.arena_off * tsz : nullptr;
     ra.carriers = carrier_kind(&c);
-    // FP64 residual: measured, the double-float form is slower in this latency-bound
-    // kernel (64 instances: 1004 against 1091 Mcell-steps/s)
+    // FP64 residual: measured, the double-float form is slower in the batched
+    // residual, whose columns give too few threads to hide its longer chains (64
+    // instances: 1004 against 1091 Mcell-steps/s in the persistent launch, 1048
+    // against 1111 in the graph of phases)
     ra.coef_df = nullptr;
     ra.partials = nullptr;
     ra.stats = B->stats + i;

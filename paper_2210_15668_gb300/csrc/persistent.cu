@@ -154,7 +154,8 @@ __device__ void phase_resid(const Ctx<T>& c, int first, int copy_back) {
           I.P[t] = I.Pbuf[t];
         }
       }
-      resid_column<T>(ra, x, j, 0, ra.nz, ar, ab, aq);
+      if (ra.carriers) resid_column<T>(ra, x, j, 0, ra.nz, ar, ab, aq);
+      else resid_column<T, 0>(ra, x, j, 0, ra.nz, ar, ab, aq);   // no b + rho add
     }
     ar = wsum(ar); ab = wsum(ab); aq = wsum(aq);
     if (c.lane == 0) {
@@ -416,8 +417,9 @@ __global__ void __launch_bounds__(512, 1) batch_kernel(BatchArgs A) {
 // ---- the same phases as separate kernels of a CUDA graph -----------------------------
 // One launch per phase over the whole grid (a single CTA group spanning every
 // instance), so each phase keeps only its own registers, and kernel boundaries
-// take the place of the grid barriers.  The work units, the per-cell operations
-// and the per-instance sums are those of batch_kernel, so the two engines give
+// take the place of the grid barriers.  The per-cell operations and the
+// per-instance sums are those of batch_kernel (the TDGL update and the
+// decisions are mapped onto threads differently), so the two engines give
 // identical results.
 
 template <typename T>
