@@ -669,11 +669,16 @@ def run_batch_qv(args, ws, precision=None):
     tuning = B.tuning()
     engine = ("one persistent cooperative launch per call" if tuning["engine"] == 0
               else "a CUDA graph per step: one launch per phase, the solve loop in a WHILE node")
+    # one more step with the same kernels launched one by one, CUDA-event timed per
+    # phase class (profilers cannot see the kernel nodes of the step's graph)
+    phases = B.profile_phases() if tuning["engine"] == 1 else None
     out = {"workload": "64 MFIM instances {32..128}^2 x 16, V ~ U[-2,2], seed 3", "cells": cells,
            "steps": K, "value": ws * cells * K / (t / 1e3) / 1e6, "unit": UNIT, "ms_per_step": t / K,
            "precision": "mixed" if precision == ferrox.MIXED else "fp64", "engine": engine,
            "vcycles_per_step_mean": float(np.mean([s1[i]["cycles"] - s0[i]["cycles"] for i in range(len(inst))])) / K,
-           "tuning": tuning, "l2": "working set ~270 MB > L2 (no flush)"}
+           "tuning": tuning, "l2": "working set ~270 MB > L2 (no flush)",
+           "phase_breakdown_one_step": None if phases is None else
+           {k: {"ms": round(v[0], 4), "launches": v[1]} for k, v in phases.items()}}
     B.close()
     return out
 

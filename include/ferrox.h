@@ -370,6 +370,20 @@ ferrox_status ferrox_batch_engine(const ferrox_batch* b, int* engine);
  * per SM, or 1 with one row per work unit).  EINVAL for other values.
  * Synchronises. */
 ferrox_status ferrox_batch_set_engine(ferrox_batch* b, int engine);
+/* Classes of ferrox_batch_profile_phases, in this order: TDGL update, outer
+ * residual, per-instance decisions, fine-level sweeps, coarser-level sweeps,
+ * transfers (restriction and prolongation), tails, other (flags, counters). */
+#define FERROX_PHASE_CLASSES 8
+/* One time step of every instance with the graph engine's kernels launched one
+ * by one (no graph), the solve loop driven from the host by the decision
+ * kernel's "any instance active" flag: the same kernels in the same order as a
+ * step of the graph, so the state advances exactly as ferrox_batch_step(b, 1)
+ * would.  Each launch is timed by CUDA events; ms_out and launches_out (arrays of
+ * FERROX_PHASE_CLASSES, caller-owned host memory) receive the time and the
+ * number of launches per class.  Kernel nodes of graphs with conditional nodes
+ * are invisible to profilers, so this is the step profilers can see.  ESTATE
+ * unless the batch is tuned to (or set to) the graph engine.  Synchronises. */
+ferrox_status ferrox_batch_profile_phases(ferrox_batch* b, double* ms_out, int* launches_out);
 ferrox_status ferrox_batch_destroy(ferrox_batch* b);
 
 /* Failure-detection check of the bounded device waits: a two-block launch in

@@ -1807,6 +1807,8 @@ struct ferrox_batch {
   int* status = nullptr;
   unsigned int* ticket = nullptr;     // decision kernel of the graph engine: blocks done
   int* tile_pre = nullptr;            // graph engine's TDGL: prefix of column tiles per instance
+  int* any_d = nullptr;               // phase profile: "any instance active" (device / pinned host)
+  int* any_h = nullptr;
   int ntiles = 0;
   int* nsteps_d = nullptr;
   int* dbg = nullptr;
@@ -2147,10 +2149,11 @@ void batch_release(ferrox_batch* B) {
   if (B->gr_step) cudaGraphDestroy(B->gr_step);
   if (B->gr_solve) cudaGraphDestroy(B->gr_solve);
   void* ptrs[] = {B->b, B->Pbuf, B->backup, B->e, B->r, B->s, B->coef, B->dense, B->coef0, B->planes, B->lv,
-                  B->lvt, B->pre, B->partials, B->active, B->bar, B->grp_d, B->status, B->ticket, B->tile_pre, B->nsteps_d, B->dbg, B->params,
+                  B->lvt, B->pre, B->partials, B->active, B->bar, B->grp_d, B->status, B->ticket, B->tile_pre, B->any_d, B->nsteps_d, B->dbg, B->params,
                   B->stats, B->inst, B->charge_part, B->charge_out};
   for (void* p : ptrs) if (p) cudaFree(p);
   if (B->host_pinned) cudaFreeHost(B->host_pinned);
+  if (B->any_h) cudaFreeHost(B->any_h);
   if (B->cap) cudaStreamDestroy(B->cap);
   if (B->cap2) cudaStreamDestroy(B->cap2);
   delete B;
@@ -2268,6 +2271,8 @@ ferrox_status ferrox_init_batch(ferrox_batch** out, int n, const ferrox_geometry
   FX_BINIT(cudaMalloc(&B->grp_d, 2 * (size_t)(n + 1) * sizeof(int)));
   FX_BINIT(cudaMalloc(&B->status, sizeof(int)));
   FX_BINIT(cudaMalloc(&B->ticket, sizeof(unsigned int)));
+  FX_BINIT(cudaMalloc(&B->any_d, sizeof(int)));
+  FX_BINIT(cudaMallocHost(&B->any_h, sizeof(int)));
   FX_BINIT(cudaMemset(B->ticket, 0, sizeof(unsigned int)));
   {
     std::vector<int> tp(n + 1, 0);
@@ -2543,6 +2548,26 @@ ferrox_status ferrox_batch_set_shape(ferrox_batch* B, int threads, int rows_per_
   rc = batch_build_graphs(B);
   if (rc != FERROX_OK) return rc;
   B->tuned = true;
+  return FERROX_OK;
+}
+
+static_assert(kPhaseClasses == FERROX_PHASE_CLASSES, "phase classes of the header and the engine");
+
+ferrox_status ferrox_batch_profile_phases(ferrox_batch* B, double* ms_out, int* launches_out) {
+  if (!B || !ms_out || !launches_out) return bfail(B, FERROX_EINVAL, "null argument");
+  if (!B->tuned || B->engine != 1)
+    return bfail(B, FERROX_ESTATE,
+                 "the phase profile runs the graph engine's kernels: tune it first or set engine 1");
+  for (int q = 0; q < kPhaseClasses; ++q) {
+    ms_out[q] = 0.0;
+    launches_out[q] = 0;
+  }
+  FX_BCK(cudaStreamSynchronize(B->stream));
+  const BatchArgs a = batch_args(B, 0);
+  FX_BCK(B->mixed ? profile_phases<float>(a, B->unit_blocks, B->smem, B->stream, B->any_d, B->any_h,
+                                          B->num.max_cycles, ms_out, launches_out)
+                  : profile_phases<double>(a, B->unit_blocks, B->smem, B->stream, B->any_d, B->any_h,
+                                           B->num.max_cycles, ms_out, launches_out));
   return FERROX_OK;
 }
 

@@ -426,6 +426,7 @@ struct BatchArgs {
   int max_cycles, nu1, nu2, rows_per_unit, any_full_tail, pad;
   int* dbg;             // optional self-check record (null: off)
   unsigned int* ticket; // graph engine: blocks of the decision kernel done (0 between launches)
+  int* any_out;         // eager phase replay: "any instance active" after each decision (else null)
 };
 
 cudaError_t launch_barrier_timeout(GridBar* gb, int* status, long long limit, cudaStream_t s);
@@ -443,6 +444,12 @@ cudaError_t phase_prepare(size_t tail_smem);
 template <typename T>
 cudaError_t capture_phases(const BatchArgs& a, int unit_blocks, size_t tail_smem, cudaStream_t s,
                            cudaStream_t s2);
+// the same phases launched one by one, the solve loop driven from the host, each
+// launch timed by CUDA events into ms[kPhaseClasses] / launches[kPhaseClasses]
+constexpr int kPhaseClasses = 8;   // tdgl, resid, decide, fine sweeps, coarse sweeps, transfers, tail, other
+template <typename T>
+cudaError_t profile_phases(const BatchArgs& a, int unit_blocks, size_t tail_smem, cudaStream_t s, int* any_dev,
+                           int* any_host, int max_cycles, double* ms, int* launches);
 void launch_set_params(DevParams* p, double v_bot, double v_top, cudaStream_t s);
 void launch_static_b(double* b, const PlaneTDGL* planes, const DevParams* prm, int nx, int ny,
                      int nz, cudaStream_t s);

@@ -16,6 +16,8 @@
 // most one more bounded wait, so a fault elsewhere can never hang the GPU.
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "ferrox_internal.cuh"
 #ifndef FX_TAIL_LINKAGE
 #define FX_TAIL_LINKAGE __noinline__   // see mg_device.cuh
@@ -538,7 +540,10 @@ __global__ void __launch_bounds__(32) ph_decide_kernel(BatchArgs A, int first, u
   int mine = 0;
   for (int i = threadIdx.x; i < A.ninst; i += blockDim.x) mine |= ld_flag(A.active + i);
   const int any = __syncthreads_or(mine);
-  if (threadIdx.x == 0) cudaGraphSetConditional((cudaGraphConditionalHandle)handle, any ? 1u : 0u);
+  if (threadIdx.x == 0) {
+    if (A.any_out) *A.any_out = any;   // eager replay: the host drives the loop
+    if (handle) cudaGraphSetConditional((cudaGraphConditionalHandle)handle, any ? 1u : 0u);
+  }
 }
 
 template <typename T>
@@ -682,6 +687,97 @@ cudaError_t capture_phases(const BatchArgs& a, int unit_blocks, size_t tail_smem
   return cudaGetLastError();
 }
 
+// One time step (mode 0) of every instance with the graph engine's kernels
+// launched one by one on s (no graph), the solve loop driven from the host by the
+// decision kernel's "any instance active" flag: the same kernels in the same
+// order, so the state advances exactly as a step of the graph.  Each launch is
+// bracketed by CUDA events; ms and launches accumulate per class.
+template <typename T>
+cudaError_t profile_phases(const BatchArgs& a0, int unit_blocks, size_t tail_smem, cudaStream_t s, int* any_dev,
+                           int* any_host, int max_cycles, double* ms, int* launches) {
+  enum { WAIT = -1, TDGL, RESID, DECIDE, SMOOTH_FINE, SMOOTH_COARSE, TRANSFER, TAIL, OTHER };
+  BatchArgs a = a0;
+  a.mode = 0;
+  a.any_out = any_dev;
+  const dim3 ub(unit_blocks), ut(256);
+  // (class, start event); the next mark ends the interval.  WAIT intervals hold
+  // the host's read of the flag (no launch): neither timed nor counted.
+  std::vector<std::pair<int, cudaEvent_t>> marks;
+  cudaError_t err = cudaSuccess;
+  auto mark = [&](int cls) {
+    cudaEvent_t e;
+    if (err == cudaSuccess) err = cudaEventCreate(&e);
+    if (err == cudaSuccess) err = cudaEventRecord(e, s);
+    if (err == cudaSuccess) marks.push_back({cls, e});
+  };
+  auto note = [&](cudaError_t e) { if (err == cudaSuccess) err = e; };
+  auto read_any = [&]() -> int {
+    if (err == cudaSuccess) err = cudaMemcpyAsync(any_host, any_dev, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+    return err == cudaSuccess ? *any_host : 0;
+  };
+  note(cudaMemsetAsync(a.ticket, 0, sizeof(unsigned int), s));
+  mark(OTHER);
+  note(launch_k(ph_activate_kernel, dim3(1), dim3(256), 0, s, a));
+  mark(TDGL);
+  note(launch_k(ph_tdgl_chunk_kernel, dim3(a.ntiles), dim3(kTdglTileX, kTdglTileY, kTdglChunks), 0, s, a, 0));
+  mark(RESID);
+  note(launch_k(ph_resid_kernel<T>, ub, ut, 0, s, a, 1, 1));
+  mark(DECIDE);
+  note(launch_k(ph_decide_kernel<T>, dim3(a.ninst), dim3(32), 0, s, a, 1, 0ULL));
+  mark(WAIT);
+  int any = read_any();
+  for (int cyc = 0; any && cyc <= max_cycles; ++cyc) {
+    for (int l = 0; l < a.Ldown; ++l) {
+      for (int sw = 0; sw < a.nu1; ++sw) {
+        mark(l == 0 ? SMOOTH_FINE : SMOOTH_COARSE);
+        note(launch_k(ph_smooth_kernel<T>, ub, ut, 0, s, a, l, 0, sw == 0 ? 1 : 0, 0));
+        mark(l == 0 ? SMOOTH_FINE : SMOOTH_COARSE);
+        note(launch_k(ph_smooth_kernel<T>, ub, ut, 0, s, a, l, 1, 0, 0));
+      }
+      mark(TRANSFER);
+      note(launch_k(ph_transfer_kernel<T>, ub, ut, 0, s, a, l, 0));
+    }
+    mark(TAIL);
+    note(launch_k(ph_tail_kernel<T>, dim3(a.ninst), dim3(512), tail_smem, s, a));
+    for (int l = a.Ldown - 1; l >= 0; --l) {
+      mark(TRANSFER);
+      note(launch_k(ph_transfer_kernel<T>, ub, ut, 0, s, a, l, 1));
+      for (int sw = 0; sw < a.nu2; ++sw) {
+        mark(l == 0 ? SMOOTH_FINE : SMOOTH_COARSE);
+        note(launch_k(ph_smooth_kernel<T>, ub, ut, 0, s, a, l, 0, 0, 0));
+        mark(l == 0 ? SMOOTH_FINE : SMOOTH_COARSE);
+        note(launch_k(ph_smooth_kernel<T>, ub, ut, 0, s, a, l, 1, 0, (l == 0 && sw == a.nu2 - 1) ? 1 : 0));
+      }
+    }
+    if (a.any_full_tail || a.nu2 == 0) {
+      mark(OTHER);
+      note(launch_k(ph_update_kernel<T>, ub, ut, 0, s, a));
+    }
+    mark(RESID);
+    note(launch_k(ph_resid_kernel<T>, ub, ut, 0, s, a, 0, 0));
+    mark(DECIDE);
+    note(launch_k(ph_decide_kernel<T>, dim3(a.ninst), dim3(32), 0, s, a, 0, 0ULL));
+    mark(WAIT);
+    any = read_any();
+  }
+  mark(OTHER);
+  note(launch_k(ph_steps_kernel, dim3(1), dim3(256), 0, s, a));
+  mark(WAIT);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+  for (size_t q = 0; q + 1 < marks.size(); ++q) {
+    if (marks[q].first == WAIT) continue;
+    float t = 0.f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&t, marks[q].second, marks[q + 1].second);
+    ms[marks[q].first] += t;
+    ++launches[marks[q].first];
+  }
+  for (auto& m : marks) cudaEventDestroy(m.second);
+  return err;
+}
+
+template cudaError_t profile_phases<double>(const BatchArgs&, int, size_t, cudaStream_t, int*, int*, int, double*, int*);
+template cudaError_t profile_phases<float>(const BatchArgs&, int, size_t, cudaStream_t, int*, int*, int, double*, int*);
 template cudaError_t phase_prepare<double>(size_t);
 template cudaError_t phase_prepare<float>(size_t);
 template cudaError_t capture_phases<double>(const BatchArgs&, int, size_t, cudaStream_t, cudaStream_t);

@@ -66,12 +66,16 @@ EXPORTS = ["ferrox_init_geometry", "ferrox_set_bias", "ferrox_solve_poisson", "f
            "ferrox_init_batch", "ferrox_batch_set_bias", "ferrox_batch_solve_poisson",
            "ferrox_batch_step", "ferrox_batch_charge", "ferrox_batch_stats", "ferrox_batch_tuning",
            "ferrox_batch_groups", "ferrox_batch_set_shape", "ferrox_batch_engine", "ferrox_batch_set_engine",
+           "ferrox_batch_profile_phases",
            "ferrox_batch_destroy", "ferrox_batch_last_error", "ferrox_check_wait_timeout",
            "ferrox_carrier_exp", "ferrox_carrier_exp_df",
            "ferrox_nn_create", "ferrox_nn_forward", "ferrox_nn_loss_grad", "ferrox_nn_params",
            "ferrox_nn_set_params", "ferrox_nn_adam_step", "ferrox_nn_snapshot_count", "ferrox_nn_train",
            "ferrox_nn_destroy", "ferrox_nn_last_error", "ferrox_nn_use_tensor_memory", "ferrox_nn_kernel_info",
            "ferrox_attach_nn"]
+
+# classes of ferrox_batch_profile_phases, in the header's order
+PHASE_CLASSES = ["tdgl", "resid", "decide", "smooth_fine", "smooth_coarse", "transfer", "tail", "other"]
 
 KERNEL_CLASSES = ["tdgl", "resid", "smooth_fine", "smooth_coarse", "restrict", "prolong", "tail",
                   "update", "copy"]
@@ -124,6 +128,7 @@ def load(path: str = LIB_PATH):
     lib.ferrox_batch_set_shape.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int]
     lib.ferrox_batch_engine.argtypes = [vp, C.POINTER(C.c_int)]
     lib.ferrox_batch_set_engine.argtypes = [vp, C.c_int]
+    lib.ferrox_batch_profile_phases.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int)]
     lib.ferrox_batch_destroy.argtypes = [vp]
     lib.ferrox_batch_last_error.argtypes = [vp]
     lib.ferrox_batch_last_error.restype = C.c_char_p
@@ -417,6 +422,15 @@ class Batch:
     def set_engine(self, engine):
         """0: one persistent launch; 1: the graph of per-phase launches (same results)."""
         self._ck(self.lib.ferrox_batch_set_engine(self.ctx, int(engine)))
+
+    def profile_phases(self):
+        """One time step with the graph engine's kernels launched one by one (the state
+        advances as step(1) would); {class: (ms, launches)} from CUDA events."""
+        n = len(PHASE_CLASSES)
+        ms = (C.c_double * n)()
+        nl = (C.c_int * n)()
+        self._ck(self.lib.ferrox_batch_profile_phases(self.ctx, ms, nl))
+        return {k: (ms[q], nl[q]) for q, k in enumerate(PHASE_CLASSES)}
 
     def set_shape(self, threads, rows_per_unit, ctas_per_sm, grouped):
         """Fix the launch shape instead of autotuning it (same results, other speed)."""

@@ -206,3 +206,50 @@ def test_set_engine_rejects_other_values():
     with pytest.raises(ferrox.FerroxError, match="EINVAL"):
         B.set_engine(2)
     B.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_phase_profile_advances_like_a_graph_step(precision):
+    """ferrox_batch_profile_phases launches the graph engine's kernels one by one
+    with the solve loop on the host: after it the state equals the state after one
+    step of the graph, bit for bit, with equal counters, and every phase class the
+    step runs has launches and time."""
+    from paper_2210_15668_gb300 import ferrox
+    sizes = [32, 96, 48]
+    geoms = [I.make_geometry(s, s, I.mfim_stack(16)) for s in sizes]
+    P0s = [I.random_polarization(g, seed=500 + i) for i, g in enumerate(geoms)]
+    num = ferrox.make_numerics(4e-13, tol=1e-10, precision=precision)
+    outs, prof = [], None
+    for use_profile in (False, True):
+        B = ferrox.Batch(geoms, P0s, num)
+        B.set_engine(1)
+        B.set_bias(np.zeros(len(sizes)), [-1.2, 0.4, 1.9])
+        B.solve_poisson()
+        if use_profile:
+            prof = B.profile_phases()
+        else:
+            B.step(1)
+        st = B.stats()
+        outs.append(([B.state(i) for i in range(len(sizes))],
+                     [(x["cycles"], x["vcycles"], x["solves"], x["steps"]) for x in st]))
+        B.close()
+    (s0, c0), (s1, c1) = outs
+    assert c1 == c0 and all(c[3] == 1 for c in c0)
+    for (P, phi), (Pr, phir) in zip(s1, s0):
+        assert np.array_equal(P, Pr) and np.array_equal(phi, phir)
+    assert prof["tdgl"][1] == 1
+    assert prof["decide"][1] == prof["resid"][1] >= 2
+    for k in ("tdgl", "resid", "decide", "smooth_fine", "transfer", "tail"):
+        assert prof[k][1] > 0 and prof[k][0] > 0.0, (k, prof)
+
+
+def test_phase_profile_needs_the_graph_engine():
+    from paper_2210_15668_gb300 import ferrox
+    geoms, P0s, _ = small_batch(n=2)
+    B = ferrox.Batch(geoms, P0s, ferrox.make_numerics(4e-13))
+    with pytest.raises(ferrox.FerroxError, match="ESTATE"):
+        B.profile_phases()          # not tuned yet
+    B.set_shape(256, 1, 1, 0)       # the persistent engine
+    with pytest.raises(ferrox.FerroxError, match="ESTATE"):
+        B.profile_phases()
+    B.close()
